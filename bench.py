@@ -1,0 +1,475 @@
+#!/usr/bin/env python
+"""Benchmark of the 6D MCL sensor-update hot path on GB300.
+
+One step = one pass of the whole path over one synthetic batch: scan packing,
+pose matrices, transform + TSDF look-up + score + per-chunk sums (the sensor
+kernel), log-weights, normalisation, systematic resampling with the particle
+gather. Default workload: OS0-64-shaped scan (64 rings x 1,024 azimuths =
+65,536 points) against a brick-sparse int16 TSDF of a 160 x 160 x 20 m
+four-storey building at 5 cm, 1,000,000 particles uniform over free space.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on a bounded particle sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle×point evals/s (1M×65,536, int16 TSDF)"
+UNIT = "evals/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=1_000_000)
+    ap.add_argument("--azimuths", type=int, default=1024)
+    ap.add_argument("--dtype", default="i16", choices=["f32", "f16", "i16"])
+    ap.add_argument("--building", type=float, default=160.0, help="building edge (m)")
+    ap.add_argument("--floors", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-gather", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target oracle CPU time for the cpu_baseline sample")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--ppi", type=int, default=0)
+    ap.add_argument("--unroll", type=int, default=0)
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Largest value over all ranks (control plane only: one scalar)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(args, rank: int):
+    import scenes
+    dt = {"f32": scenes.F32, "f16": scenes.F16, "i16": scenes.I16}[args.dtype]
+    return scenes.os064_building(P=args.particles, dtype=dt, seed=3, azimuths=args.azimuths,
+                                 size=args.building, floors=args.floors)
+
+
+def rank_particles(wl, rank: int):
+    """Each rank localises its own robot session: same map, own particle cloud."""
+    if rank == 0:
+        return wl.particles
+    import scenes
+    return scenes.particles_free(wl.scene, len(wl.particles), 0.1, 10.0, 1000 + rank)
+
+
+def algorithmic_bytes(P: int, N: int, elem: int, brick: bool) -> int:
+    """Bytes the sensor kernel must move per launch: one map element per
+    (particle, point) evaluation plus one 8-byte brick-index entry for a
+    brick map; each pose record (48 B), scan point (16 B) and weight (4 B) once."""
+    return P * N * (elem + (8 if brick else 0)) + P * 48 + N * 16 + P * 4
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("k_sensor.cu", "mcl_internal.h"):
+        with open(os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(P: int, N: int):
+    """DRAM bytes per sensor launch from the committed ncu summary, scaled by
+    evaluations, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "sensor_dram_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_digest") != kernel_source_digest():
+        return None
+    return rec["dram_bytes_per_eval"] * P * N
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def time_oracle(wl, target_s: float, max_particles: int | None = None):
+    """Oracle sensor update + normalise + resample on a particle sample sized
+    to about target_s seconds of CPU work. Returns (evals/s, particles, seconds)."""
+    import numpy as np
+    import oracle
+    om = oracle.Map.from_scene_map(wl.map)
+    N = len(wl.scan)
+    probe = 64
+    t0 = time.perf_counter()
+    L = oracle.sensor_update(om, wl.particles[:probe], wl.scan, wl.sigma_hit)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(len(wl.particles), max(probe, probe * target_s / dt)))
+    if max_particles:
+        n = min(n, max_particles)
+    t0 = time.perf_counter()
+    L = oracle.sensor_update(om, wl.particles[:n], wl.scan, wl.sigma_hit)
+    w, *_ = oracle.normalise(L)
+    oracle.resample(w.astype(np.float32), 0.5)
+    dt = time.perf_counter() - t0
+    return n * N / dt, n, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    wl = make_workload(args, 0)
+    N = len(wl.scan)
+    om = oracle.Map.from_scene_map(wl.map)
+    total_budget = 150.0
+    per_step = total_budget / max(1, args.steps + args.warmup)
+    rate, _, _ = time_oracle(wl, min(per_step, 5.0))
+    n = int(max(16, min(len(wl.particles), rate * per_step / N)))
+    parts = wl.particles[:n]
+
+    def step():
+        L = oracle.sensor_update(om, parts, wl.scan, wl.sigma_hit)
+        w, *_ = oracle.normalise(L)
+        oracle.resample(w.astype(np.float32), 0.5)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n * N * args.steps / dt
+    cores = oracle.num_threads()
+    sample = f"{n} of {len(wl.particles)} particles x {N} points per step (FP64 oracle, OpenMP)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args, wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, wl):
+    m = wl.map
+    return {
+        "workload": wl.name, "particles": int(len(wl.particles)), "points": int(len(wl.scan)),
+        "scan": f"64 rings (+-45 deg) x {args.azimuths} azimuths, sigma 0.02 m",
+        "map": {"kind": "brick16", "index": "hash", "dtype": args.dtype,
+                "extent_m": [args.building, args.building, 5.0 * args.floors], "voxel_m": 0.05,
+                "dims": list(m.dims), "bricks": int(len(m.coords)), "bytes": int(m.values.nbytes),
+                "truncation_m": 0.3},
+        "sigma_hit": wl.sigma_hit, "mode": "logprod",
+        "l2": "inputs larger than L2 (map %.2f GB, L2 129 MB)" % (m.values.nbytes / 1e9),
+    }
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2310_04172_gb300 import mcl
+    mcl.lib()
+
+    wl = make_workload(args, rank)
+    parts_np = rank_particles(wl, rank)
+    P, N = len(parts_np), len(wl.scan)
+    m = mcl.map_from_scene(wl.map)
+    elem = 4 if args.dtype == "f32" else 2
+    stream = torch.cuda.Stream(device=dev)
+    parts = torch.from_numpy(parts_np).to(dev)
+    parts_next = torch.empty_like(parts)
+    scan = torch.from_numpy(np.ascontiguousarray(wl.scan)).to(dev)
+    logw = torch.empty(P, device=dev)
+    w = torch.empty(P, device=dev)
+    idx = torch.empty(P, dtype=torch.int32, device=dev)
+    import scenes
+    offsets = scenes.uniform(11 + rank, 200, args.steps + args.warmup + 64)
+    prm = mcl.sensor_params(sigma_hit=wl.sigma_hit, points_per_chunk=args.chunk,
+                            lanes_per_particle=args.lanes, particles_per_item=args.ppi,
+                            unroll=args.unroll)
+    plan = mcl.mcl_sensor_plan_get(m, P, N, prm)
+
+    def step(k, s):
+        mcl.mcl_sensor_update(m, parts, scan, prm, logw, w, s)
+        mcl.mcl_resample(w, float(offsets[k % len(offsets)]), idx, parts, parts_next, s)
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            step(k, stream)
+    mcl.mcl_sync(stream)
+
+    gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+    gpu_id = gpu_id if gpu_id.startswith("GPU-") else f"GPU-{gpu_id}"
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    with ClockSampler(gpu_id) as clocks:
+        start.record(stream)
+        mcl.mcl_profile_begin()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                step(args.warmup + k, stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        prof = mcl.mcl_profile_end()
+    if dist is not None:
+        dist.barrier()
+    mcl.mcl_sync(stream)
+    ms = start.elapsed_time(end)
+    ms_max = max_over_ranks(dist, ms, dev)
+    evals = float(P) * N * args.steps
+    total_evals = sum_over_ranks(dist, evals, dev)
+    value = total_evals / (ms_max / 1e3)
+    launches = sum(v["launches"] for v in prof.values())
+
+    # roofline of the dominant kernel, timed live in the region above
+    sensor_ms = prof["sensor"]["ms"] / max(1, prof["sensor"]["launches"])
+    abytes = algorithmic_bytes(P, N, elem, True)
+    achieved = abytes / (sensor_ms / 1e3) / 1e9
+    peak, peak_src = peaks()
+    traffic = measured_traffic(P, N)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+            "kernel": "k_sensor", "kernel_ms": sensor_ms,
+            "algorithmic_bytes_per_launch": abytes,
+            "bytes_per_eval": elem + 8}
+
+    # gather roofline: uniform-random element reads over a buffer of the map's size
+    gather = None
+    if not args.no_gather:
+        gather = gather_roofline(torch, mcl, dev, stream, int(wl.map.values.nbytes), elem, value)
+
+    # end to end through the C ABI with host buffers (pinned), copies in the region
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, mcl, m, parts_np, wl.scan, prm, offsets, args, dev, dist)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        rate, n, dt = time_oracle(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{n} of {P} particles x {N} points, sensor update + normalise + "
+                         f"resample, {dt:.1f} s (FP64, OpenMP over particles)"}
+
+    if rank == 0:
+        cfg = config_dict(args, wl)
+        cfg["launch"] = plan
+        cfg["parallelism"] = f"replicas{world}" if world > 1 else "single"
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg, "roofline": roof, "gather_roofline": gather, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
+            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["launches"]},
+        }
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def gather_roofline(torch, mcl, dev, stream, nbytes, elem, evals_per_s):
+    """Uniform-random gathers/s at the map footprint (HBM) and in L2 (64 MB)."""
+    out = {}
+    for label, size in (("map_footprint", nbytes), ("l2_resident_64MB", 64 << 20)):
+        dt = torch.int16 if elem == 2 else torch.float32
+        buf = torch.ones(max(1, size // elem), dtype=dt, device=dev)
+        blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+        iters = 64
+        with torch.cuda.stream(stream):
+            mcl.mcl_gather_bench(buf, blocks, iters, 1, stream)
+        best = None
+        for rep in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                n = mcl.mcl_gather_bench(buf, blocks, iters, 2 + rep, stream)
+            b.record(stream)
+            b.synchronize()
+            rate = n / (a.elapsed_time(b) / 1e3)
+            best = rate if best is None else max(best, rate)
+        out[label] = {"bytes": int(buf.numel() * elem), "gathers_per_s": best}
+        del buf
+    out["frac_evals"] = evals_per_s / out["map_footprint"]["gathers_per_s"]
+    out["elem_bytes"] = elem
+    return out
+
+
+def end_to_end(torch, mcl, m, parts_np, scan_np, prm, offsets, args, dev, dist):
+    import numpy as np
+    P, N = len(parts_np), len(scan_np)
+    s = torch.cuda.Stream(device=dev)
+    h_parts = torch.from_numpy(parts_np).pin_memory()
+    h_scan = torch.from_numpy(np.ascontiguousarray(scan_np)).pin_memory()
+    h_w = torch.empty(P, dtype=torch.float32).pin_memory()
+    h_idx = torch.empty(P, dtype=torch.int32).pin_memory()
+    d_parts = torch.empty((P, 6), device=dev)
+    d_next = torch.empty_like(d_parts)
+    d_scan = torch.empty((N, 3), device=dev)
+    d_logw = torch.empty(P, device=dev)
+    d_w = torch.empty(P, device=dev)
+    d_idx = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def step(k):
+        with torch.cuda.stream(s):
+            d_parts.copy_(h_parts, non_blocking=True)
+            d_scan.copy_(h_scan, non_blocking=True)
+            mcl.mcl_sensor_update(m, d_parts, d_scan, prm, d_logw, d_w, s)
+            mcl.mcl_resample(d_w, float(offsets[k % len(offsets)]), d_idx, d_parts, d_next, s)
+            h_w.copy_(d_w, non_blocking=True)
+            h_idx.copy_(d_idx, non_blocking=True)
+        s.synchronize()
+
+    step(0)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(k + 1)
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(dist, dt, dev)
+    world = dist.get_world_size() if dist is not None else 1
+    return {"value": world * float(P) * N * args.steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(h_parts.numel() * 4 + h_scan.numel() * 4),
+            "d2h_bytes_per_step": int(h_w.numel() * 4 + h_idx.numel() * 4),
+            "ms_per_step": 1e3 * dt / args.steps}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

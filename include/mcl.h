@@ -1,0 +1,270 @@
+/*
+ * mcl.h - C ABI of the GB300 library for the 6D Monte Carlo Localization
+ * sensor update in TSDF maps (Eisoldt, Mock, Porrmann, Wiemann, "Towards 6D
+ * MCL for LiDARs in 3D TSDF Maps on Embedded Systems with GPUs").
+ *
+ * Conventions for every call:
+ *  - The return value is an mcl_status; MCL_OK is 0. On failure,
+ *    mcl_last_error() returns a message for the calling thread. Nothing
+ *    throws across this boundary.
+ *  - Array arguments marked (device) are caller-owned CUDA device pointers
+ *    on the current device; (host) are caller-owned host pointers. The
+ *    library never frees caller memory and keeps no reference to it after
+ *    the call returns (device arrays are read or written by work enqueued on
+ *    `stream`, so they must stay valid until that work completes).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    asynchronous with respect to the host unless stated otherwise; errors of
+ *    the device work itself are reported by mcl_sync() or by a later call.
+ *  - Poses are FP32 rows (x, y, z, roll, pitch, yaw): the state
+ *    s = (x, y, z, phi, psi, theta) of Sec. III, Eq. 2, with
+ *    R = Rz(yaw) Ry(pitch) Rx(roll) mapping the sensor frame to the map frame.
+ *  - Scan points are FP32 rows (x, y, z) in the sensor frame.
+ *  - Scratch memory: the compute calls keep a library-owned device workspace
+ *    per (device, stream); it grows with cudaMalloc on first use at a larger
+ *    size, so call once with the largest sizes before capturing a stream
+ *    into a CUDA graph.
+ */
+#ifndef MCL_H_
+#define MCL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mcl_status;
+#define MCL_OK 0
+#define MCL_EINVAL 1      /* bad argument: size, pointer, alignment, value */
+#define MCL_ENOMEM 2      /* device or host allocation failed / over budget */
+#define MCL_EBUSY 3       /* no free slot (serving) */
+#define MCL_ETIMEDOUT 4   /* wait ran out of time */
+#define MCL_ECUDA 5       /* a CUDA runtime call failed */
+#define MCL_EINTERNAL 6   /* a kernel reported an internal error (status word) */
+
+typedef void* mcl_stream_t; /* cudaStream_t */
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* mcl_last_error(void);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t mcl_version(void);
+
+/* Waits for `stream`, then reports any CUDA error and any internal error a
+ * kernel of this library recorded in its device status word (a bounded wait
+ * that ran out, an index check that failed); the status word is cleared. */
+mcl_status mcl_sync(mcl_stream_t stream);
+
+/* ------------------------------------------------------------------ maps */
+
+enum { MCL_MAP_DENSE = 0, MCL_MAP_BRICK = 1 };
+enum { MCL_F32 = 0, MCL_F16 = 1, MCL_I16 = 2 };
+
+/* TSDF map description (Sec. III: a TSDF volume; the sparse form keeps fine
+ * blocks only where values lie within the truncation distance, every other
+ * cell reads the truncation value).
+ *
+ * Voxel (ix, iy, iz) covers [o + i r, o + (i + 1) r) on each axis. A point x
+ * falls in voxel i_k = floor(u_k) with u_k = (x_k - o_k) * inv_voxel in two
+ * FP32 roundings; it is inside iff 0 <= u_k < dims_k on every axis.
+ * Values are the signed distance at the voxel centre, clamped to
+ * [-truncation, truncation], stored as FP32, FP16 or scaled int16
+ * (q stands for q * truncation / 32767).
+ *
+ * DENSE: values[(iz * dims[1] + iy) * dims[0] + ix], at most 2^31 voxels.
+ * BRICK: 16^3 bricks; dims multiples of 16; brick b (coordinates
+ *        brick_coords[3b..3b+2] = (bx, by, bz) in brick units) holds
+ *        values[b * 4096 + (lz * 16 + ly) * 16 + lx]; a voxel in no listed
+ *        brick reads +truncation. At most 2^31 - 1 bricks and 2^32 - 2
+ *        brick cells; duplicated or out-of-range coordinates are EINVAL.
+ * inv_voxel = 0 lets the library use (float)(1.0 / voxel). */
+typedef struct mcl_map_desc {
+  uint32_t struct_size; /* sizeof(mcl_map_desc) */
+  int32_t kind;         /* MCL_MAP_DENSE or MCL_MAP_BRICK */
+  int32_t dtype;        /* MCL_F32, MCL_F16 or MCL_I16 */
+  float origin[3];      /* map-frame coordinates of the grid corner (m) */
+  float voxel;          /* voxel edge r (m), > 0 */
+  float inv_voxel;      /* 1 / r as used by the index rule, or 0 */
+  float truncation;     /* tau (m), > 0 */
+  int64_t dims[3];      /* grid size in voxels (x, y, z) */
+  int64_t n_bricks;     /* BRICK: number of bricks */
+  const int32_t* brick_coords; /* BRICK: (host) n_bricks x 3 int32 */
+} mcl_map_desc;
+
+typedef struct mcl_map_s* mcl_map_t;
+
+/* Uploads a map to the current device. `host_values` (host) holds the values
+ * in the layout above and the dtype given. The map owns its device memory.
+ * EINVAL for a bad description, ENOMEM if the device is out of memory. */
+mcl_status mcl_map_create(const mcl_map_desc* desc, const void* host_values, mcl_map_t* out);
+
+/* Frees the map's device memory (synchronises the device first). NULL is a no-op. */
+mcl_status mcl_map_destroy(mcl_map_t map);
+
+typedef struct mcl_map_info {
+  uint32_t struct_size;
+  int64_t device_bytes;   /* values + index bytes held on the device */
+  int64_t n_bricks;       /* BRICK: bricks stored; DENSE: 0 */
+  int64_t hash_capacity;  /* BRICK: hash table entries (power of two) */
+  int32_t hash_max_probe; /* BRICK: longest probe sequence of a stored brick */
+  int32_t device;         /* CUDA device that holds the map */
+} mcl_map_info;
+
+mcl_status mcl_map_get_info(mcl_map_t map, mcl_map_info* out);
+
+/* Map query at N world points (device, N x 3 FP32): out_index (device, N
+ * int64) gets the linear voxel index (iz * dims[1] + iy) * dims[0] + ix or -1
+ * outside the grid; out_value (device, N FP32) the value read there,
+ * dequantised, +truncation outside the grid or in a voxel of no brick. Either
+ * output may be NULL. Uses the index rule of the sensor update (Sec. III look-up). */
+mcl_status mcl_map_lookup(mcl_map_t map, const float* points, int64_t N, int64_t* out_index,
+                          float* out_value, mcl_stream_t stream);
+
+/* ------------------------------------------------------------------ sensor update */
+
+enum { MCL_LOGPROD = 0, MCL_SUM = 1 };
+#define MCL_NEGLECT_OUTSIDE 1u /* points without a stored value are left out */
+
+/* Sensor-model parameters (Sec. III, Eq. 3).
+ * mode LOGPROD: per-point score -d^2 / (2 sigma^2) (log of Eq. 3 without its
+ *   constant), particle log-weight L = sum of scores (product of p_hit).
+ * mode SUM: per-point score p_hit of Eq. 3, L = log(sum of p_hit).
+ * A point outside the grid or in a voxel of no brick reads d = +truncation
+ * (Sec. III clamping), or with MCL_NEGLECT_OUTSIDE contributes nothing.
+ * points_per_chunk and lanes_per_particle fix the FP32 summation order
+ * (points of one particle are split in chunks of points_per_chunk, each
+ * summed by lanes_per_particle lanes and a shuffle tree, chunks added in
+ * order); 0 selects the defaults 2048 and 32. Results are bit-reproducible
+ * for equal (points_per_chunk, lanes_per_particle). */
+typedef struct mcl_sensor_params {
+  uint32_t struct_size;       /* sizeof(mcl_sensor_params) */
+  float sigma_hit;            /* sigma of Eq. 3 (m), > 0 */
+  int32_t mode;               /* MCL_LOGPROD or MCL_SUM */
+  uint32_t flags;             /* MCL_NEGLECT_OUTSIDE or 0 */
+  int32_t points_per_chunk;   /* 0 or a multiple of 32 in [32, 8192] */
+  int32_t lanes_per_particle; /* 0, 8, 16 or 32 */
+  int32_t particles_per_item; /* launch shape hint, 0 = auto (no effect on results) */
+  int32_t unroll;             /* launch shape hint, 0 = auto (no effect on results) */
+} mcl_sensor_params;
+
+/* Sensor update of P particles (device, P x 6 FP32) against one scan
+ * (device, N x 3 FP32): every scan point is moved into the map frame by
+ * each particle's pose, the TSDF is read at the voxel that contains it, the
+ * score is summed per particle (Sec. III, Eq. 3; Sec. V-B). Writes the
+ * log-weights to logw (device, P FP32) and, if w is not NULL, the normalised
+ * weights w_p = exp(L_p - M) / sum_q exp(L_q - M), M = max L (device, P FP32).
+ * logw may be NULL if w is not. Pointers need 4-byte alignment.
+ * EINVAL: P or N outside [1, 2^31 - 1], sigma not finite and > 0, bad
+ * params, both outputs NULL. Non-finite pose values are not checked: their
+ * points fall outside the grid. */
+mcl_status mcl_sensor_update(mcl_map_t map, const float* particles, int64_t P, const float* scan,
+                             int64_t N, const mcl_sensor_params* params, float* logw, float* w,
+                             mcl_stream_t stream);
+
+/* Normalisation alone (Sec. V-A: weights summed for normalisation): w_p =
+ * exp(L_p - M) / S with M = max L, S = sum exp(L - M) in FP32, reduced in a
+ * fixed order. If M is not finite (no particle scored) every w_p = 1 / P.
+ * out_stats (device, 2 FP32, may be NULL) gets (M, S); S = 0 flags that
+ * degenerate case. */
+mcl_status mcl_normalise(const float* logw, int64_t P, float* w, float* out_stats,
+                         mcl_stream_t stream);
+
+/* Pose rows -> [R | t] (device, P x 12 FP32, rows [R_i0 R_i1 R_i2 t_i]):
+ * R = Rz(yaw) Ry(pitch) Rx(roll) evaluated in FP64 in the fixed order
+ * a = cy*sp, b = sy*sp, R = [[cy*cp, a*sr - sy*cr, a*cr + sy*sr],
+ * [sy*cp, b*sr + cy*cr, b*cr - cy*sr], [-sp, cp*sr, cp*cr]], each entry
+ * rounded to FP32. The sensor update uses exactly these matrices. */
+mcl_status mcl_pose_to_matrix(const float* particles, int64_t P, float* out_mat,
+                              mcl_stream_t stream);
+
+/* Launch plan the sensor update would use for these sizes on the current
+ * device (no work is enqueued). workspace_bytes is the scratch the call
+ * needs; points_per_chunk * lanes_per_particle fix the summation order. */
+typedef struct mcl_sensor_plan {
+  uint32_t struct_size;
+  int32_t points_per_chunk, lanes_per_particle, particles_per_item, unroll;
+  int32_t threads, grid, blocks_per_sm, num_sms;
+  int64_t n_items;          /* (chunk, particle block) work items */
+  int64_t workspace_bytes;  /* library scratch for one call */
+} mcl_sensor_plan;
+
+mcl_status mcl_sensor_plan_get(mcl_map_t map, int64_t P, int64_t N,
+                               const mcl_sensor_params* params, mcl_sensor_plan* out);
+
+/* ------------------------------------------------------------------ resampling */
+
+/* Systematic resampling (Sec. III: a new set drawn from the old one in
+ * proportion to the weights) with offset r in [0, 1):
+ *   q_p = rint(w_p * 2^52) * 2^-52, C_p = q_0 + ... + q_p (FP64, exact while
+ *   the total stays below 2, i.e. for normalised weights), S = C_{P-1},
+ *   t_j = ((j + r) / P) * S, idx_j = min{p : C_p > t_j}, else the last p
+ *   with q_p > 0. All-zero weights give idx_j = j.
+ * w (device, P FP32, >= 0), idx (device, P int32). If particles_in is not
+ * NULL, particles_out[j] = particles_in[idx_j] (device, P x 6 FP32; must not
+ * alias). EINVAL: P outside [1, 2^31 - 1], r outside [0, 1), idx NULL. */
+mcl_status mcl_resample(const float* w, int64_t P, double r, int32_t* idx,
+                        const float* particles_in, float* particles_out, mcl_stream_t stream);
+
+/* ------------------------------------------------------------------ motion update */
+
+/* Motion update (Sec. III: the motion model is applied to every particle).
+ * Increment u = delta + sigma * n per particle, n six standard normals from
+ * Philox4x32-10 (key = seed, counter = (b, particle, step_lo, step_hi),
+ * b = 0, 1, 2) and Box-Muller in FP64; then t' = t + R(s) u_t,
+ * R' = R(s) R(u_r), read back as roll = atan2(R'21, R'22),
+ * pitch = asin(-R'20), yaw = atan2(R'10, R'00) in [-pi, pi).
+ * particles (device, P x 6 FP32) are updated in place; delta and sigma are
+ * host arrays of 6. EINVAL: P outside [1, 2^31 - 1], a sigma < 0 or not finite. */
+mcl_status mcl_motion_update(float* particles, int64_t P, const float delta[6],
+                             const float sigma[6], uint64_t seed, uint64_t step,
+                             mcl_stream_t stream);
+
+/* ------------------------------------------------------------------ gather roofline */
+
+/* Microbenchmark of the map look-up pattern (Sec. VI-C: random TSDF reads
+ * bound the sensor update): blocks x 256 threads each read iters x 8
+ * elements of `buf` (device, n_elems elements of elem_bytes = 2 or 4 bytes)
+ * at uniform random positions. Gathers issued = blocks * 256 * iters * 8;
+ * time the call with events on `stream` to get gathers/s for that footprint.
+ * EINVAL: n_elems < 1, elem_bytes not 2 or 4, blocks or iters < 1. */
+mcl_status mcl_gather_bench(const void* buf, int64_t n_elems, int32_t elem_bytes, int32_t blocks,
+                            int32_t iters, uint64_t seed, mcl_stream_t stream);
+
+/* ------------------------------------------------------------------ runtime */
+
+/* Frees the library workspace kept for (current device, stream), after
+ * waiting for the stream. Call before destroying a stream the library used. */
+mcl_status mcl_workspace_release(mcl_stream_t stream);
+
+/* Per-phase device timing. Between mcl_profile_begin() and mcl_profile_end()
+ * every phase this library enqueues is bracketed by CUDA events recorded on
+ * its own stream; mcl_profile_end() waits for them and returns, per phase,
+ * the number of kernel launches and the summed elapsed milliseconds. Not for
+ * use while a stream is being captured into a graph. */
+enum {
+  MCL_PHASE_POSE = 0,     /* pose -> [R | t] */
+  MCL_PHASE_PACK = 1,     /* scan packing */
+  MCL_PHASE_SENSOR = 2,   /* transform, look-up, score, per-chunk sums */
+  MCL_PHASE_REDUCE = 3,   /* chunk sums -> log-weights, block statistics */
+  MCL_PHASE_NORMALISE = 4,
+  MCL_PHASE_RESAMPLE = 5, /* quantise, exact prefix sum, search, gather */
+  MCL_PHASE_MOTION = 6,
+  MCL_PHASE_OTHER = 7,
+  MCL_NUM_PHASES = 8
+};
+
+typedef struct mcl_profile {
+  uint32_t struct_size;
+  int64_t launches[MCL_NUM_PHASES];
+  double ms[MCL_NUM_PHASES];
+} mcl_profile;
+
+mcl_status mcl_profile_begin(void);
+mcl_status mcl_profile_end(mcl_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCL_H_ */

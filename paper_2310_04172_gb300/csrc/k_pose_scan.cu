@@ -1,0 +1,91 @@
+// Per-particle pose matrices, scan packing and the map query kernel.
+#include "mcl_internal.h"
+
+namespace mcl {
+namespace {
+
+// [R | t] rows from (x, y, z, roll, pitch, yaw) (Sec. III, Eq. 2). The
+// rotation R = Rz(yaw) Ry(pitch) Rx(roll) is evaluated in FP64 in a fixed
+// order with every product and sum rounded on its own (no contraction), and
+// each entry is rounded to FP32 once:
+//   a = cy*sp, b = sy*sp
+//   [ cy*cp   a*sr - sy*cr   a*cr + sy*sr ]
+//   [ sy*cp   b*sr + cy*cr   b*cr - cy*sr ]
+//   [ -sp     cp*sr          cp*cr        ]
+__global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4* __restrict__ mats) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float* s = poses + 6 * (size_t)p;
+  const float x = s[0], y = s[1], z = s[2];
+  const double roll = (double)s[3], pitch = (double)s[4], yaw = (double)s[5];
+  const double cr = cos(roll), sr = sin(roll);
+  const double cp = cos(pitch), sp = sin(pitch);
+  const double cy = cos(yaw), sy = sin(yaw);
+  const double a = __dmul_rn(cy, sp), b = __dmul_rn(sy, sp);
+  const double r00 = __dmul_rn(cy, cp);
+  const double r01 = __dsub_rn(__dmul_rn(a, sr), __dmul_rn(sy, cr));
+  const double r02 = __dadd_rn(__dmul_rn(a, cr), __dmul_rn(sy, sr));
+  const double r10 = __dmul_rn(sy, cp);
+  const double r11 = __dadd_rn(__dmul_rn(b, sr), __dmul_rn(cy, cr));
+  const double r12 = __dsub_rn(__dmul_rn(b, cr), __dmul_rn(cy, sr));
+  const double r20 = -sp;
+  const double r21 = __dmul_rn(cp, sr);
+  const double r22 = __dmul_rn(cp, cr);
+  float4* o = mats + 3 * (size_t)p;
+  o[0] = make_float4(__double2float_rn(r00), __double2float_rn(r01), __double2float_rn(r02), x);
+  o[1] = make_float4(__double2float_rn(r10), __double2float_rn(r11), __double2float_rn(r12), y);
+  o[2] = make_float4(__double2float_rn(r20), __double2float_rn(r21), __double2float_rn(r22), z);
+}
+
+// N x 3 scan rows -> N float4 (x, y, z, 0): 16-byte records that a bulk copy
+// can move and a lane can read with one 128-bit shared-memory load.
+__global__ void k_scan_pack(const float* __restrict__ scan, int N, float4* __restrict__ packed) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const float* q = scan + 3 * (size_t)j;
+  packed[j] = make_float4(q[0], q[1], q[2], 0.f);
+}
+
+template <int KIND, int DTYPE>
+__global__ void k_map_lookup(const MapView m, const float* __restrict__ pts, int N,
+                             long long* __restrict__ out_index, float* __restrict__ out_value) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const float* q = pts + 3 * (size_t)j;
+  float d;
+  long long linear;
+  lookup<KIND, DTYPE>(m, q[0], q[1], q[2], d, linear);
+  if (out_index) out_index[j] = linear;
+  if (out_value) out_value[j] = d;
+}
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, cudaStream_t s) {
+  k_pose_to_matrix<<<blocks_for(P, 256), 256, 0, s>>>(poses, P, mats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_pack(const float* scan, int N, float4* packed, cudaStream_t s) {
+  k_scan_pack<<<blocks_for(N, 256), 256, 0, s>>>(scan, N, packed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float* pts, int N,
+                              long long* out_index, float* out_value, cudaStream_t s) {
+  const int g = blocks_for(N, 256);
+#define MCL_LOOKUP_CASE(K, D) \
+  if (kind == K && dtype == D) { k_map_lookup<K, D><<<g, 256, 0, s>>>(m, pts, N, out_index, out_value); return cudaGetLastError(); }
+  MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_F32)
+  MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_F16)
+  MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_I16)
+  MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F32)
+  MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F16)
+  MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_I16)
+#undef MCL_LOOKUP_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mcl

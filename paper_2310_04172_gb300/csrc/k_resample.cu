@@ -1,0 +1,183 @@
+// Systematic resampling (Sec. III: a new particle set drawn from the current
+// one in proportion to the weights), exact and order-independent.
+//
+// Weights are quantised to integer multiples of 2^-52 (q = rint(w 2^52) 2^-52,
+// exact in FP64 for any FP32 w). For normalised weights every partial sum of
+// q stays below 2 and is therefore exact in FP64, so the prefix sum C is the
+// same bit for bit whatever the summation order: tiles of 4096 scan locally,
+// one block scans the tile totals, and each output j finds
+// min{p : C_p > t_j}, t_j = ((j + r) / P) S, by a binary search over tile ends
+// and then inside the tile.
+#include "mcl_internal.h"
+
+namespace mcl {
+namespace {
+
+constexpr int kRT = 1024, kRI = 4, kTile = kRT * kRI;
+
+__device__ __forceinline__ double warp_incl_scan(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double o = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v = __dadd_rn(v, o);
+  }
+  return v;
+}
+
+// Inclusive block scan of one double per thread (values exact, so the
+// association order does not change the result). Returns the inclusive value;
+// *total gets the block total.
+__device__ __forceinline__ double block_incl_scan(double v, double* sh, double* total) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double incl = warp_incl_scan(v);
+  __syncthreads();
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? sh[lane] : 0.0;
+    t = warp_incl_scan(t);
+    sh[lane] = t;
+  }
+  __syncthreads();
+  if (warp > 0) incl = __dadd_rn(incl, sh[warp - 1]);
+  *total = sh[nw - 1];
+  return incl;
+}
+
+__device__ __forceinline__ long long block_max_ll(long long v, long long* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  v = lane < nw ? sh[lane] : -1;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kRT) k_tile_scan(const float* __restrict__ w, int P,
+                                                   double* __restrict__ cum,
+                                                   double* __restrict__ tile_total,
+                                                   long long* __restrict__ tile_last) {
+  __shared__ double sh[32];
+  __shared__ long long shl[32];
+  const long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kRI;
+  double run = 0.0, q[kRI];
+  long long last = -1;
+#pragma unroll
+  for (int i = 0; i < kRI; ++i) {
+    const long long p = base + i;
+    double v = 0.0;
+    if (p < P) {
+      v = __dmul_rn(rint(__dmul_rn((double)w[p], 0x1.0p52)), 0x1.0p-52);
+      if (v > 0.0) last = p;
+    }
+    run = __dadd_rn(run, v);
+    q[i] = run;
+  }
+  double total;
+  const double incl = block_incl_scan(run, sh, &total);
+  const double excl = __dsub_rn(incl, run);
+#pragma unroll
+  for (int i = 0; i < kRI; ++i)
+    if (base + i < P) cum[base + i] = __dadd_rn(excl, q[i]);
+  last = block_max_ll(last, shl);
+  if (threadIdx.x == 0) {
+    tile_total[blockIdx.x] = total;
+    tile_last[blockIdx.x] = last;
+  }
+}
+
+// One block: tile totals -> exclusive tile offsets (in place); entry ntiles
+// receives the grand total S and the last index with a positive weight.
+__global__ void __launch_bounds__(kRT) k_tile_offsets(double* __restrict__ tile_total,
+                                                      long long* __restrict__ tile_last,
+                                                      int ntiles) {
+  __shared__ double sh[32];
+  __shared__ long long shl[32];
+  double carry = 0.0;
+  long long last = -1;
+  for (int b = 0; b < ntiles; b += kRT) {
+    const int i = b + threadIdx.x;
+    const double v = i < ntiles ? tile_total[i] : 0.0;
+    const long long l = i < ntiles ? tile_last[i] : -1;
+    double total;
+    const double incl = block_incl_scan(v, sh, &total);
+    if (i < ntiles) tile_total[i] = __dadd_rn(carry, __dsub_rn(incl, v));
+    carry = __dadd_rn(carry, total);
+    const long long lm = block_max_ll(l, shl);
+    last = lm > last ? lm : last;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    tile_total[ntiles] = carry;
+    tile_last[ntiles] = last;
+  }
+}
+
+__global__ void k_systematic(const double* __restrict__ cum, const double* __restrict__ tile_off,
+                             const long long* __restrict__ tile_last, int P, int ntiles, double r,
+                             int32_t* __restrict__ idx, const float* __restrict__ pin,
+                             float* __restrict__ pout) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  const double S = tile_off[ntiles];
+  int res;
+  if (!(S > 0.0)) {
+    res = j;  // all weights zero: identity
+  } else {
+    const double t = __dmul_rn(__ddiv_rn(__dadd_rn((double)j, r), (double)P), S);
+    int lo = 0, hi = ntiles;  // first tile whose end C exceeds t
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (tile_off[mid + 1] > t) hi = mid; else lo = mid + 1;
+    }
+    if (lo == ntiles) {
+      res = (int)tile_last[ntiles];
+    } else {
+      const double off = tile_off[lo];
+      int a = lo * kTile, b = min(P, a + kTile);
+      while (a < b) {
+        const int mid = (a + b) >> 1;
+        if (__dadd_rn(off, cum[mid]) > t) b = mid; else a = mid + 1;
+      }
+      res = a;
+    }
+  }
+  idx[j] = res;
+  if (pin) {
+    const float* src = pin + 6 * (size_t)res;
+    float* dst = pout + 6 * (size_t)j;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dst[k] = src[k];
+  }
+}
+
+}  // namespace
+
+int resample_tiles(int P) { return (P + kTile - 1) / kTile; }
+
+cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
+                            const float* particles_in, float* particles_out, double* cum,
+                            double* tile_total, long long* tile_last, cudaStream_t s) {
+  const int ntiles = resample_tiles(P);
+  k_tile_scan<<<ntiles, kRT, 0, s>>>(w, P, cum, tile_total, tile_last);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_tile_offsets<<<1, kRT, 0, s>>>(tile_total, tile_last, ntiles);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_systematic<<<(P + 255) / 256, 256, 0, s>>>(cum, tile_total, tile_last, P, ntiles, r, idx,
+                                               particles_in, particles_out);
+  return cudaGetLastError();
+}
+
+}  // namespace mcl

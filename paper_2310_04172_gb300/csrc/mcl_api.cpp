@@ -1,0 +1,620 @@
+// Host runtime behind the C ABI of include/mcl.h: argument checks, map upload
+// (dense grid or 16^3 bricks with an open-addressing hash of brick cells),
+// per-(device, stream) workspace, launch planning, per-phase event timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mcl_internal.h"
+
+using namespace mcl;
+
+namespace {
+
+thread_local std::string g_err;
+
+mcl_status fail(mcl_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+mcl_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free error so the next call starts clean
+  if (e == cudaErrorMemoryAllocation) return fail(MCL_ENOMEM, "%s: out of device memory", what);
+  return fail(MCL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MCL_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int64_t kMaxCount = 2147483647LL;
+
+struct DeviceState {
+  unsigned* status = nullptr;
+  int sms = 0;
+};
+
+std::mutex g_mu;
+std::map<int, DeviceState> g_dev;
+std::map<std::pair<int, uintptr_t>, std::pair<void*, size_t>> g_ws;
+
+mcl_status device_state(int* dev_out, DeviceState* out) {
+  int dev = 0;
+  MCL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& st = g_dev[dev];
+  if (!st.status) {
+    unsigned* p = nullptr;
+    MCL_CUDA(cudaMalloc(&p, sizeof(unsigned)));
+    MCL_CUDA(cudaMemset(p, 0, sizeof(unsigned)));
+    MCL_CUDA(cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev));
+    st.status = p;
+  }
+  *out = st;
+  if (dev_out) *dev_out = dev;
+  return MCL_OK;
+}
+
+// Scratch of at least `bytes` for (current device, stream). Grows by freeing
+// the old buffer after the stream drained and allocating a larger one.
+mcl_status workspace(cudaStream_t s, size_t bytes, void** out) {
+  int dev = 0;
+  MCL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto& slot = g_ws[{dev, (uintptr_t)s}];
+  if (slot.second < bytes) {
+    if (slot.first) {
+      MCL_CUDA(cudaStreamSynchronize(s));
+      MCL_CUDA(cudaFree(slot.first));
+      slot = {nullptr, 0};
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    void* p = nullptr;
+    MCL_CUDA(cudaMalloc(&p, want));
+    slot = {p, want};
+  }
+  *out = slot.first;
+  return MCL_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// ---------------------------------------------------------------- profiling
+struct PhaseEvents {
+  int phase, kernels;
+  cudaEvent_t a, b;
+};
+bool g_prof_on = false;
+std::vector<PhaseEvents> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct PhaseScope {
+  int phase, kernels;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseScope(int ph, cudaStream_t st, int nk = 1) : phase(ph), kernels(nk), s(st) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_prof_on) return;
+    a = take_event();
+    b = take_event();
+    cudaEventRecord(a, s);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prof.push_back({phase, kernels, a, b});
+  }
+};
+
+// ---------------------------------------------------------------- helpers
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+}  // namespace
+
+struct mcl_map_s {
+  int device = 0;
+  int kind = 0, dtype = 0;
+  MapView view{};
+  void* d_values = nullptr;
+  uint2* d_table = nullptr;
+  int64_t bytes = 0, n_bricks = 0, capacity = 0;
+  int max_probe = 0;
+};
+
+extern "C" {
+
+const char* mcl_last_error(void) { return g_err.c_str(); }
+
+int32_t mcl_version(void) { return 100; }
+
+mcl_status mcl_sync(mcl_stream_t stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  MCL_CUDA(cudaStreamSynchronize(s));
+  DeviceState st;
+  mcl_status rc = device_state(nullptr, &st);
+  if (rc) return rc;
+  unsigned v = 0;
+  MCL_CUDA(cudaMemcpy(&v, st.status, sizeof v, cudaMemcpyDeviceToHost));
+  if (v) {
+    MCL_CUDA(cudaMemset(st.status, 0, sizeof v));
+    return fail(MCL_EINTERNAL, "device status word 0x%x (%s%s)", v,
+                (v & kDevErrTimeout) ? "bounded wait ran out " : "",
+                (v & kDevErrIndex) ? "index check failed" : "");
+  }
+  return MCL_OK;
+}
+
+// ---------------------------------------------------------------- maps
+mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_map_t* out) {
+  if (!d || !out) return fail(MCL_EINVAL, "map_create: NULL desc or out");
+  *out = nullptr;
+  if (d->struct_size < sizeof(mcl_map_desc))
+    return fail(MCL_EINVAL, "map_create: struct_size %u < %zu", d->struct_size, sizeof(mcl_map_desc));
+  if (d->kind != MCL_MAP_DENSE && d->kind != MCL_MAP_BRICK)
+    return fail(MCL_EINVAL, "map_create: kind %d", d->kind);
+  if (d->dtype < MCL_F32 || d->dtype > MCL_I16) return fail(MCL_EINVAL, "map_create: dtype %d", d->dtype);
+  if (!finite_pos(d->voxel) || !finite_pos(d->truncation))
+    return fail(MCL_EINVAL, "map_create: voxel and truncation must be finite and > 0");
+  for (int k = 0; k < 3; ++k) {
+    if (!std::isfinite(d->origin[k])) return fail(MCL_EINVAL, "map_create: origin not finite");
+    if (d->dims[k] <= 0 || d->dims[k] > (1 << 24))
+      return fail(MCL_EINVAL, "map_create: dims[%d] = %lld outside [1, 2^24]", k, (long long)d->dims[k]);
+  }
+  float inv = d->inv_voxel == 0.f ? (float)(1.0 / (double)d->voxel) : d->inv_voxel;
+  if (!finite_pos(inv)) return fail(MCL_EINVAL, "map_create: inv_voxel must be finite and > 0");
+  const size_t es = d->dtype == MCL_F32 ? 4 : 2;
+
+  int dev = 0;
+  MCL_CUDA(cudaGetDevice(&dev));
+  mcl_map_s* m = new mcl_map_s();
+  m->device = dev;
+  m->kind = d->kind;
+  m->dtype = d->dtype;
+  MapView& v = m->view;
+  v.ox = d->origin[0];
+  v.oy = d->origin[1];
+  v.oz = d->origin[2];
+  v.inv = inv;
+  v.nx = (int)d->dims[0];
+  v.ny = (int)d->dims[1];
+  v.nz = (int)d->dims[2];
+  v.fnx = (float)v.nx;
+  v.fny = (float)v.ny;
+  v.fnz = (float)v.nz;
+  v.tau = d->truncation;
+  v.scale = (float)((double)d->truncation / 32767.0);
+
+  auto cleanup = [&](mcl_status s) {
+    if (m->d_values) cudaFree(m->d_values);
+    if (m->d_table) cudaFree(m->d_table);
+    delete m;
+    return s;
+  };
+
+  if (d->kind == MCL_MAP_DENSE) {
+    const int64_t total = d->dims[0] * d->dims[1] * d->dims[2];
+    if (total > kMaxCount) return cleanup(fail(MCL_EINVAL, "map_create: dense grid above 2^31 - 1 voxels"));
+    if (!host_values) return cleanup(fail(MCL_EINVAL, "map_create: NULL values"));
+    cudaError_t e = cudaMalloc(&m->d_values, (size_t)total * es);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
+    e = cudaMemcpy(m->d_values, host_values, (size_t)total * es, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
+    m->bytes = total * (int64_t)es;
+  } else {
+    for (int k = 0; k < 3; ++k)
+      if (d->dims[k] % kBrick) return cleanup(fail(MCL_EINVAL, "map_create: dims must be multiples of 16"));
+    const uint64_t nbx = (uint64_t)d->dims[0] / kBrick, nby = (uint64_t)d->dims[1] / kBrick,
+                   nbz = (uint64_t)d->dims[2] / kBrick;
+    if (nbx * nby * nbz > 0xFFFFFFFEull) return cleanup(fail(MCL_EINVAL, "map_create: too many brick cells"));
+    const int64_t nb = d->n_bricks;
+    if (nb < 0 || nb > (1LL << 29)) return cleanup(fail(MCL_EINVAL, "map_create: n_bricks %lld", (long long)nb));
+    if (nb > 0 && (!host_values || !d->brick_coords))
+      return cleanup(fail(MCL_EINVAL, "map_create: NULL brick values or coordinates"));
+    int bits = 1;
+    while ((1LL << bits) < std::max<int64_t>(2, 4 * nb)) ++bits;
+    const int64_t cap = 1LL << bits;
+    std::vector<uint2> table((size_t)cap, make_uint2(kEmptyKey, 0u));
+    const int shift = 32 - bits;
+    int max_probe = 1;
+    for (int64_t b = 0; b < nb; ++b) {
+      const int32_t* c = d->brick_coords + 3 * b;
+      if (c[0] < 0 || c[1] < 0 || c[2] < 0 || (uint64_t)c[0] >= nbx || (uint64_t)c[1] >= nby ||
+          (uint64_t)c[2] >= nbz)
+        return cleanup(fail(MCL_EINVAL, "map_create: brick %lld coordinates out of range", (long long)b));
+      const uint32_t key = (uint32_t)(((uint64_t)c[2] * nby + (uint64_t)c[1]) * nbx + (uint64_t)c[0]);
+      uint32_t h = brick_hash(key, shift);
+      int probe = 1;
+      while (table[h].x != kEmptyKey) {
+        if (table[h].x == key)
+          return cleanup(fail(MCL_EINVAL, "map_create: brick %lld duplicated", (long long)b));
+        h = (h + 1) & (uint32_t)(cap - 1);
+        ++probe;
+      }
+      table[h] = make_uint2(key, (uint32_t)b);
+      max_probe = std::max(max_probe, probe);
+    }
+    const size_t vbytes = (size_t)nb * kBrickVoxels * es;
+    cudaError_t e = cudaMalloc(&m->d_values, std::max(vbytes, (size_t)256));
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
+    if (vbytes) {
+      e = cudaMemcpy(m->d_values, host_values, vbytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
+    }
+    e = cudaMalloc(&m->d_table, (size_t)cap * sizeof(uint2));
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table"));
+    e = cudaMemcpy(m->d_table, table.data(), (size_t)cap * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table upload"));
+    v.table = m->d_table;
+    v.nbx = (uint32_t)nbx;
+    v.nby = (uint32_t)nby;
+    v.hash_mask = (uint32_t)(cap - 1);
+    v.hash_shift = shift;
+    v.max_probe = max_probe;
+    m->n_bricks = nb;
+    m->capacity = cap;
+    m->max_probe = max_probe;
+    m->bytes = (int64_t)vbytes + cap * (int64_t)sizeof(uint2);
+  }
+  v.values = m->d_values;
+  *out = m;
+  return MCL_OK;
+}
+
+mcl_status mcl_map_destroy(mcl_map_t m) {
+  if (!m) return MCL_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  if (m->d_values) cudaFree(m->d_values);
+  if (m->d_table) cudaFree(m->d_table);
+  cudaSetDevice(cur);
+  delete m;
+  return MCL_OK;
+}
+
+mcl_status mcl_map_get_info(mcl_map_t m, mcl_map_info* out) {
+  if (!m || !out) return fail(MCL_EINVAL, "map_get_info: NULL argument");
+  if (out->struct_size < sizeof(mcl_map_info)) return fail(MCL_EINVAL, "map_get_info: struct_size");
+  out->device_bytes = m->bytes;
+  out->n_bricks = m->n_bricks;
+  out->hash_capacity = m->capacity;
+  out->hash_max_probe = m->max_probe;
+  out->device = m->device;
+  return MCL_OK;
+}
+
+static mcl_status check_device(mcl_map_t m) {
+  int dev = 0;
+  MCL_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(MCL_EINVAL, "map lives on device %d, current device is %d", m->device, dev);
+  return MCL_OK;
+}
+
+mcl_status mcl_map_lookup(mcl_map_t m, const float* pts, int64_t N, int64_t* out_index,
+                          float* out_value, mcl_stream_t stream) {
+  if (!m || !pts) return fail(MCL_EINVAL, "map_lookup: NULL map or points");
+  if (N < 1 || N > kMaxCount) return fail(MCL_EINVAL, "map_lookup: N = %lld", (long long)N);
+  if (!aligned(pts, 4) || !aligned(out_index, 8) || !aligned(out_value, 4))
+    return fail(MCL_EINVAL, "map_lookup: misaligned pointer");
+  if (mcl_status rc = check_device(m)) return rc;
+  PhaseScope ps(MCL_PHASE_OTHER, (cudaStream_t)stream);
+  MCL_CUDA(launch_map_lookup(m->kind, m->dtype, m->view, pts, (int)N, (long long*)out_index,
+                             out_value, (cudaStream_t)stream));
+  return MCL_OK;
+}
+
+// ---------------------------------------------------------------- sensor update
+static mcl_status check_params(const mcl_sensor_params* p) {
+  if (!p) return fail(MCL_EINVAL, "sensor params: NULL");
+  if (p->struct_size < sizeof(mcl_sensor_params)) return fail(MCL_EINVAL, "sensor params: struct_size");
+  if (!finite_pos(p->sigma_hit)) return fail(MCL_EINVAL, "sensor params: sigma_hit must be finite and > 0");
+  if (p->mode != MCL_LOGPROD && p->mode != MCL_SUM) return fail(MCL_EINVAL, "sensor params: mode %d", p->mode);
+  if (p->flags & ~MCL_NEGLECT_OUTSIDE) return fail(MCL_EINVAL, "sensor params: unknown flags 0x%x", p->flags);
+  const int c = p->points_per_chunk;
+  if (c != 0 && (c < 32 || c > 8192 || c % 32))
+    return fail(MCL_EINVAL, "sensor params: points_per_chunk %d", c);
+  const int g = p->lanes_per_particle;
+  if (g != 0 && g != 8 && g != 16 && g != 32) return fail(MCL_EINVAL, "sensor params: lanes_per_particle %d", g);
+  if (p->particles_per_item < 0 || p->particles_per_item > 4096)
+    return fail(MCL_EINVAL, "sensor params: particles_per_item %d", p->particles_per_item);
+  if (p->unroll != 0 && p->unroll != 2 && p->unroll != 4)
+    return fail(MCL_EINVAL, "sensor params: unroll %d", p->unroll);
+  return MCL_OK;
+}
+
+struct Plan {
+  SensorShape sh;
+  int K, nblk, blocks_per_sm, sms;
+  long long n_items;
+  size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, total;
+};
+
+static mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p, Plan* pl) {
+  DeviceState st;
+  if (mcl_status rc = device_state(nullptr, &st)) return rc;
+  SensorShape& sh = pl->sh;
+  sh.chunk = p->points_per_chunk ? p->points_per_chunk : 2048;
+  sh.lanes = p->lanes_per_particle ? p->lanes_per_particle : 32;
+  sh.ppi = p->particles_per_item ? p->particles_per_item : 64;
+  sh.unroll = p->unroll ? p->unroll : 4;
+  sh.threads = 256;
+  int bps = 0;
+  MCL_CUDA(sensor_occupancy(m->kind, m->dtype, sh, &bps));
+  if (bps < 1) return fail(MCL_EINVAL, "sensor plan: launch shape does not fit on an SM");
+  pl->K = (int)((N + sh.chunk - 1) / sh.chunk);
+  pl->nblk = (int)((P + sh.ppi - 1) / sh.ppi);
+  pl->n_items = (long long)pl->K * pl->nblk;
+  pl->blocks_per_sm = bps;
+  pl->sms = st.sms;
+  sh.grid = (int)std::min<long long>(pl->n_items, (long long)st.sms * bps);
+  size_t o = 0;
+  pl->off_mats = o;
+  o = align256(o + (size_t)P * 3 * sizeof(float4));
+  pl->off_scan = o;
+  o = align256(o + (size_t)N * sizeof(float4));
+  pl->off_partial = o;
+  o = align256(o + (size_t)pl->K * (size_t)P * sizeof(float));
+  pl->off_logw = o;
+  o = align256(o + (size_t)P * sizeof(float));
+  pl->off_stats = o;
+  o = align256(o + (size_t)normalise_blocks((int)P) * sizeof(float2));
+  pl->off_ostats = o;
+  o = align256(o + 2 * sizeof(float));
+  pl->total = o;
+  return MCL_OK;
+}
+
+mcl_status mcl_sensor_plan_get(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p,
+                               mcl_sensor_plan* out) {
+  if (!m || !out) return fail(MCL_EINVAL, "sensor_plan: NULL argument");
+  if (out->struct_size < sizeof(mcl_sensor_plan)) return fail(MCL_EINVAL, "sensor_plan: struct_size");
+  if (P < 1 || P > kMaxCount || N < 1 || N > kMaxCount) return fail(MCL_EINVAL, "sensor_plan: sizes");
+  if (mcl_status rc = check_params(p)) return rc;
+  if (mcl_status rc = check_device(m)) return rc;
+  Plan pl;
+  if (mcl_status rc = make_plan(m, P, N, p, &pl)) return rc;
+  out->points_per_chunk = pl.sh.chunk;
+  out->lanes_per_particle = pl.sh.lanes;
+  out->particles_per_item = pl.sh.ppi;
+  out->unroll = pl.sh.unroll;
+  out->threads = pl.sh.threads;
+  out->grid = pl.sh.grid;
+  out->blocks_per_sm = pl.blocks_per_sm;
+  out->num_sms = pl.sms;
+  out->n_items = pl.n_items;
+  out->workspace_bytes = (int64_t)pl.total;
+  return MCL_OK;
+}
+
+mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, const float* scan,
+                             int64_t N, const mcl_sensor_params* p, float* logw, float* w,
+                             mcl_stream_t stream) {
+  if (!m || !particles || !scan) return fail(MCL_EINVAL, "sensor_update: NULL map, particles or scan");
+  if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "sensor_update: P = %lld", (long long)P);
+  if (N < 1 || N > kMaxCount) return fail(MCL_EINVAL, "sensor_update: N = %lld", (long long)N);
+  if (!logw && !w) return fail(MCL_EINVAL, "sensor_update: both outputs NULL");
+  if (!aligned(particles, 4) || !aligned(scan, 4) || !aligned(logw, 4) || !aligned(w, 4))
+    return fail(MCL_EINVAL, "sensor_update: pointers need 4-byte alignment");
+  if (mcl_status rc = check_params(p)) return rc;
+  if (mcl_status rc = check_device(m)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceState st;
+  if (mcl_status rc = device_state(nullptr, &st)) return rc;
+  Plan pl;
+  if (mcl_status rc = make_plan(m, P, N, p, &pl)) return rc;
+  char* ws = nullptr;
+  if (mcl_status rc = workspace(s, pl.total, (void**)&ws)) return rc;
+  float4* mats = (float4*)(ws + pl.off_mats);
+  float4* packed = (float4*)(ws + pl.off_scan);
+  float* partial = (float*)(ws + pl.off_partial);
+  float* L = logw ? logw : (float*)(ws + pl.off_logw);
+  float2* bstats = (float2*)(ws + pl.off_stats);
+  float* ostats = (float*)(ws + pl.off_ostats);
+  {
+    PhaseScope ps(MCL_PHASE_POSE, s);
+    MCL_CUDA(launch_pose_to_matrix(particles, (int)P, mats, s));
+  }
+  {
+    PhaseScope ps(MCL_PHASE_PACK, s);
+    MCL_CUDA(launch_scan_pack(scan, (int)N, packed, s));
+  }
+  const double sig = (double)p->sigma_hit;
+  SensorArgs a;
+  a.map = m->view;
+  a.mats = mats;
+  a.scan = packed;
+  a.partial = partial;
+  a.status = st.status;
+  a.P = (int)P;
+  a.N = (int)N;
+  a.chunk = pl.sh.chunk;
+  a.K = pl.K;
+  a.ppi = pl.sh.ppi;
+  a.nblk = pl.nblk;
+  a.n_items = pl.n_items;
+  a.mode = p->mode;
+  a.neglect = (p->flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
+  a.c = (float)(-0.5 / (sig * sig));
+  {
+    PhaseScope ps(MCL_PHASE_SENSOR, s);
+    MCL_CUDA(launch_sensor(m->kind, m->dtype, a, pl.sh, s));
+  }
+  const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
+  const int nb = normalise_blocks((int)P);
+  {
+    PhaseScope ps(MCL_PHASE_REDUCE, s);
+    MCL_CUDA(launch_finish_and_normalise(partial, (int)P, pl.K, p->mode, a.c, k, L, nullptr, bstats,
+                                         nb, nullptr, s));
+  }
+  if (w) {
+    PhaseScope ps(MCL_PHASE_NORMALISE, s);
+    MCL_CUDA(launch_normalise(L, (int)P, w, bstats, nb, ostats, s));
+  }
+  return MCL_OK;
+}
+
+mcl_status mcl_normalise(const float* logw, int64_t P, float* w, float* out_stats, mcl_stream_t stream) {
+  if (!logw || !w) return fail(MCL_EINVAL, "normalise: NULL logw or w");
+  if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "normalise: P = %lld", (long long)P);
+  if (!aligned(logw, 4) || !aligned(w, 4) || !aligned(out_stats, 4))
+    return fail(MCL_EINVAL, "normalise: misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = normalise_blocks((int)P);
+  void* ws = nullptr;
+  if (mcl_status rc = workspace(s, (size_t)nb * sizeof(float2), &ws)) return rc;
+  PhaseScope ps(MCL_PHASE_NORMALISE, s);
+  MCL_CUDA(launch_normalise(logw, (int)P, w, (float2*)ws, nb, out_stats, s));
+  return MCL_OK;
+}
+
+mcl_status mcl_pose_to_matrix(const float* particles, int64_t P, float* out_mat, mcl_stream_t stream) {
+  if (!particles || !out_mat) return fail(MCL_EINVAL, "pose_to_matrix: NULL pointer");
+  if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "pose_to_matrix: P = %lld", (long long)P);
+  if (!aligned(particles, 4) || !aligned(out_mat, 16))
+    return fail(MCL_EINVAL, "pose_to_matrix: particles need 4-byte, out_mat 16-byte alignment");
+  PhaseScope ps(MCL_PHASE_POSE, (cudaStream_t)stream);
+  MCL_CUDA(launch_pose_to_matrix(particles, (int)P, (float4*)out_mat, (cudaStream_t)stream));
+  return MCL_OK;
+}
+
+// ---------------------------------------------------------------- resampling
+mcl_status mcl_resample(const float* w, int64_t P, double r, int32_t* idx, const float* pin,
+                        float* pout, mcl_stream_t stream) {
+  if (!w || !idx) return fail(MCL_EINVAL, "resample: NULL w or idx");
+  if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "resample: P = %lld", (long long)P);
+  if (!(r >= 0.0 && r < 1.0)) return fail(MCL_EINVAL, "resample: r must lie in [0, 1)");
+  if (pin && !pout) return fail(MCL_EINVAL, "resample: particles_out NULL");
+  if (pin && pin == pout) return fail(MCL_EINVAL, "resample: particles_in and particles_out alias");
+  if (!aligned(w, 4) || !aligned(idx, 4) || !aligned(pin, 4) || !aligned(pout, 4))
+    return fail(MCL_EINVAL, "resample: misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nt = resample_tiles((int)P);
+  const size_t o_cum = 0, o_tot = align256((size_t)P * 8), o_last = align256(o_tot + (size_t)(nt + 1) * 8),
+               total = align256(o_last + (size_t)(nt + 1) * 8);
+  char* ws = nullptr;
+  if (mcl_status rc = workspace(s, total, (void**)&ws)) return rc;
+  PhaseScope ps(MCL_PHASE_RESAMPLE, s, 3);
+  MCL_CUDA(launch_resample(w, (int)P, r, idx, pin, pout, (double*)(ws + o_cum), (double*)(ws + o_tot),
+                           (long long*)(ws + o_last), s));
+  return MCL_OK;
+}
+
+// ---------------------------------------------------------------- motion
+mcl_status mcl_motion_update(float* particles, int64_t P, const float delta[6], const float sigma[6],
+                             uint64_t seed, uint64_t step, mcl_stream_t stream) {
+  if (!particles || !delta || !sigma) return fail(MCL_EINVAL, "motion_update: NULL pointer");
+  if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "motion_update: P = %lld", (long long)P);
+  if (!aligned(particles, 4)) return fail(MCL_EINVAL, "motion_update: misaligned particles");
+  for (int k = 0; k < 6; ++k) {
+    if (!std::isfinite(delta[k])) return fail(MCL_EINVAL, "motion_update: delta not finite");
+    if (!std::isfinite(sigma[k]) || sigma[k] < 0.f) return fail(MCL_EINVAL, "motion_update: sigma");
+  }
+  PhaseScope ps(MCL_PHASE_MOTION, (cudaStream_t)stream);
+  MCL_CUDA(launch_motion(particles, (int)P, delta, sigma, seed, step, (cudaStream_t)stream));
+  return MCL_OK;
+}
+
+// ---------------------------------------------------------------- gather roofline
+mcl_status mcl_gather_bench(const void* buf, int64_t n_elems, int32_t elem_bytes, int32_t blocks,
+                            int32_t iters, uint64_t seed, mcl_stream_t stream) {
+  if (!buf || n_elems < 1) return fail(MCL_EINVAL, "gather_bench: empty buffer");
+  if (elem_bytes != 2 && elem_bytes != 4) return fail(MCL_EINVAL, "gather_bench: elem_bytes %d", elem_bytes);
+  if (blocks < 1 || iters < 1) return fail(MCL_EINVAL, "gather_bench: blocks and iters must be >= 1");
+  if (!aligned(buf, (size_t)elem_bytes)) return fail(MCL_EINVAL, "gather_bench: misaligned buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  if (mcl_status rc = workspace(s, (size_t)blocks * sizeof(float), &ws)) return rc;
+  PhaseScope ps(MCL_PHASE_OTHER, s);
+  MCL_CUDA(launch_gather_bench(buf, n_elems, elem_bytes, blocks, iters, seed, (float*)ws, s));
+  return MCL_OK;
+}
+
+// ---------------------------------------------------------------- runtime
+mcl_status mcl_workspace_release(mcl_stream_t stream) {
+  int dev = 0;
+  MCL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ws.find({dev, (uintptr_t)stream});
+  if (it == g_ws.end()) return MCL_OK;
+  MCL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (it->second.first) MCL_CUDA(cudaFree(it->second.first));
+  g_ws.erase(it);
+  return MCL_OK;
+}
+
+mcl_status mcl_profile_begin(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& pe : g_prof) {
+    g_event_pool.push_back(pe.a);
+    g_event_pool.push_back(pe.b);
+  }
+  g_prof.clear();
+  g_prof_on = true;
+  return MCL_OK;
+}
+
+mcl_status mcl_profile_end(mcl_profile* out) {
+  std::vector<PhaseEvents> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prof_on = false;
+    recs.swap(g_prof);
+  }
+  if (out && out->struct_size < sizeof(mcl_profile)) return fail(MCL_EINVAL, "profile_end: struct_size");
+  if (out) {
+    for (int k = 0; k < MCL_NUM_PHASES; ++k) {
+      out->launches[k] = 0;
+      out->ms[k] = 0.0;
+    }
+  }
+  mcl_status rc = MCL_OK;
+  for (auto& pe : recs) {
+    cudaError_t e = cudaEventSynchronize(pe.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pe.a, pe.b);
+    if (e != cudaSuccess && rc == MCL_OK) rc = cuda_fail(e, "profile_end");
+    if (out && pe.phase >= 0 && pe.phase < MCL_NUM_PHASES) {
+      out->launches[pe.phase] += pe.kernels;
+      out->ms[pe.phase] += ms;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& pe : recs) {
+    g_event_pool.push_back(pe.a);
+    g_event_pool.push_back(pe.b);
+  }
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Internal declarations of the GB300 MCL library: the device view of a map,
+// the index and look-up rule, kernel launchers and the host runtime pieces.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mcl.h"
+
+namespace mcl {
+
+constexpr int kBrick = 16;
+constexpr int kBrickVoxels = kBrick * kBrick * kBrick;
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+// Bits of the per-device status word that kernels set instead of faulting.
+enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
+
+// Device view of a TSDF map (Sec. III). Passed by value to the kernels.
+struct MapView {
+  const void* values;   // dense grid or brick-major values
+  const uint2* table;   // BRICK: open-addressing hash (key, slot), capacity 2^bits
+  float ox, oy, oz;     // grid corner
+  float inv;            // 1 / voxel as used by the index rule
+  float fnx, fny, fnz;  // dims as FP32 for the inside test
+  int nx, ny, nz;
+  uint32_t nbx, nby;    // BRICK: brick grid size (x, y)
+  uint32_t hash_mask;   // capacity - 1
+  int hash_shift;       // 32 - bits
+  int max_probe;        // longest probe sequence of a stored key (>= 1)
+  float tau;            // truncation: value read where nothing is stored
+  float scale;          // I16: tau / 32767 in FP32
+};
+
+// Fibonacci hashing of a brick-cell key (Knuth, TAOCP vol. 3, 6.4).
+__host__ __device__ inline uint32_t brick_hash(uint32_t key, int shift) {
+  return (key * 0x9E3779B1u) >> shift;
+}
+
+#ifdef __CUDACC__
+
+// Scan point z seen from pose rows [R | t]: x_i = fma(R_i0, z0, fma(R_i1, z1,
+// fma(R_i2, z2, t_i))), exactly this order (Sec. III: the point as seen from
+// the particle).
+__device__ __forceinline__ void transform_point(const float4& r0, const float4& r1,
+                                                const float4& r2, const float4& z, float& x,
+                                                float& y, float& w) {
+  x = fmaf(r0.x, z.x, fmaf(r0.y, z.y, fmaf(r0.z, z.z, r0.w)));
+  y = fmaf(r1.x, z.x, fmaf(r1.y, z.y, fmaf(r1.z, z.z, r1.w)));
+  w = fmaf(r2.x, z.x, fmaf(r2.y, z.y, fmaf(r2.z, z.z, r2.w)));
+}
+
+// Voxel containing a map-frame point: u = (x - o) * inv in two FP32
+// roundings per axis, inside iff 0 <= u < n on all axes (NaN is outside),
+// i = floor(u). Returns false outside the grid.
+__device__ __forceinline__ bool voxel_of(const MapView& m, float x, float y, float z, int& ix,
+                                         int& iy, int& iz) {
+  float ux = __fmul_rn(__fsub_rn(x, m.ox), m.inv);
+  float uy = __fmul_rn(__fsub_rn(y, m.oy), m.inv);
+  float uz = __fmul_rn(__fsub_rn(z, m.oz), m.inv);
+  bool in = (ux >= 0.f) & (ux < m.fnx) & (uy >= 0.f) & (uy < m.fny) & (uz >= 0.f) & (uz < m.fnz);
+  ix = (int)ux;
+  iy = (int)uy;
+  iz = (int)uz;
+  return in;
+}
+
+template <int DTYPE>
+__device__ __forceinline__ float load_value(const MapView& m, size_t i) {
+  if constexpr (DTYPE == MCL_F32) {
+    return __ldg(static_cast<const float*>(m.values) + i);
+  } else if constexpr (DTYPE == MCL_F16) {
+    return __half2float(__ldg(static_cast<const __half*>(m.values) + i));
+  } else {
+    return (float)__ldg(static_cast<const short*>(m.values) + i) * m.scale;
+  }
+}
+
+// Brick-cell key and in-brick offset of a voxel.
+__device__ __forceinline__ void brick_key(const MapView& m, int ix, int iy, int iz, uint32_t& key,
+                                          uint32_t& local) {
+  key = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
+  local = ((uint32_t)(iz & 15) * kBrick + (uint32_t)(iy & 15)) * kBrick + (uint32_t)(ix & 15);
+}
+
+// Continue a probe sequence after a first entry that did not match. Bounded by
+// the longest stored probe sequence, so an absent key ends without an EMPTY.
+__device__ __forceinline__ uint32_t probe_rest(const MapView& m, uint32_t key, uint32_t h) {
+  for (int it = 1; it < m.max_probe; ++it) {
+    h = (h + 1) & m.hash_mask;
+    uint2 e = __ldg(m.table + h);
+    if (e.x == key) return e.y;
+    if (e.x == kEmptyKey) return kNoSlot;
+  }
+  return kNoSlot;
+}
+
+// Full single-point look-up (used by the map query kernel).
+template <int KIND, int DTYPE>
+__device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float z, float& d,
+                                       long long& linear) {
+  int ix, iy, iz;
+  linear = -1;
+  d = m.tau;
+  if (!voxel_of(m, x, y, z, ix, iy, iz)) return false;
+  linear = ((long long)iz * m.ny + iy) * m.nx + ix;
+  if constexpr (KIND == MCL_MAP_DENSE) {
+    d = load_value<DTYPE>(m, (size_t)linear);
+    return true;
+  } else {
+    uint32_t key, local;
+    brick_key(m, ix, iy, iz, key, local);
+    uint32_t h = brick_hash(key, m.hash_shift);
+    uint2 e = __ldg(m.table + h);
+    uint32_t slot = e.x == key ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key, h));
+    if (slot == kNoSlot) return false;
+    d = load_value<DTYPE>(m, (size_t)slot * kBrickVoxels + local);
+    return true;
+  }
+}
+
+#endif  // __CUDACC__
+
+// ---------------------------------------------------------------- launchers
+struct SensorShape {
+  int chunk;      // points per chunk (fixes the summation order)
+  int lanes;      // lanes per particle (fixes the summation order)
+  int ppi;        // particles per work item
+  int unroll;     // points per lane per loop step
+  int threads;    // threads per CTA
+  int grid;       // CTAs (persistent)
+};
+
+struct SensorArgs {
+  MapView map;
+  const float4* mats;  // P x 3 rows [R_i0 R_i1 R_i2 t_i]
+  const float4* scan;  // N packed (x, y, z, 0)
+  float* partial;      // K x P chunk partial sums (chunk-major)
+  unsigned* status;
+  int P, N, chunk, K, ppi, nblk;
+  long long n_items;
+  int mode, neglect;
+  float c;             // -1 / (2 sigma^2)
+};
+
+cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, cudaStream_t s);
+cudaError_t launch_scan_pack(const float* scan, int N, float4* packed, cudaStream_t s);
+cudaError_t launch_sensor(int kind, int dtype, const SensorArgs& a, const SensorShape& sh,
+                          cudaStream_t s);
+int sensor_smem_bytes(const SensorShape& sh);
+cudaError_t sensor_occupancy(int kind, int dtype, const SensorShape& sh, int* blocks_per_sm);
+
+// Finishing pass: L_p from the chunk partials, then block max / sum-exp.
+cudaError_t launch_finish_and_normalise(const float* partial, int P, int K, int mode, float c,
+                                        float k, float* logw, float* w, float2* block_stats,
+                                        int nblocks, float* out_stats, cudaStream_t s);
+cudaError_t launch_normalise(const float* logw, int P, float* w, float2* block_stats, int nblocks,
+                             float* out_stats, cudaStream_t s);
+int normalise_blocks(int P);
+
+cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float* pts, int N,
+                              long long* out_index, float* out_value, cudaStream_t s);
+
+// Resampling scratch: C (P doubles), per-tile totals and last positive index.
+int resample_tiles(int P);
+cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
+                            const float* particles_in, float* particles_out, double* cum,
+                            double* tile_total, long long* tile_last, cudaStream_t s);
+
+cudaError_t launch_motion(float* particles, int P, const float delta[6], const float sigma[6],
+                          uint64_t seed, uint64_t step, cudaStream_t s);
+
+cudaError_t launch_gather_bench(const void* buf, long long n_elems, int elem_bytes, int blocks,
+                                int iters, unsigned long long seed, float* sink, cudaStream_t s);
+
+}  // namespace mcl

@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in include/mcl.h (ctypes).
+
+Functions carry the C names and only marshal arguments: torch tensors (CUDA,
+contiguous, the dtype the C call expects) become device pointers, the current
+torch stream becomes the cudaStream_t. Every step of the computation runs in
+the CUDA kernels of libmcl.so; there is no CPU fallback. If the library is
+missing, loading raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmcl.so")
+
+MCL_OK, MCL_EINVAL, MCL_ENOMEM, MCL_EBUSY, MCL_ETIMEDOUT, MCL_ECUDA, MCL_EINTERNAL = range(7)
+MCL_MAP_DENSE, MCL_MAP_BRICK = 0, 1
+MCL_F32, MCL_F16, MCL_I16 = 0, 1, 2
+MCL_LOGPROD, MCL_SUM = 0, 1
+MCL_NEGLECT_OUTSIDE = 1
+PHASES = ("pose", "pack", "sensor", "reduce", "normalise", "resample", "motion", "other")
+
+_c_void_p, _i64, _i32, _u32, _u64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_uint32, ctypes.c_uint64)
+
+
+class mcl_map_desc(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("kind", _i32), ("dtype", _i32),
+                ("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float),
+                ("inv_voxel", ctypes.c_float), ("truncation", ctypes.c_float),
+                ("dims", _i64 * 3), ("n_bricks", _i64), ("brick_coords", _c_void_p)]
+
+
+class mcl_map_info(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("device_bytes", _i64), ("n_bricks", _i64),
+                ("hash_capacity", _i64), ("hash_max_probe", _i32), ("device", _i32)]
+
+
+class mcl_sensor_params(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("sigma_hit", ctypes.c_float), ("mode", _i32),
+                ("flags", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
+                ("particles_per_item", _i32), ("unroll", _i32)]
+
+
+class mcl_sensor_plan(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
+                ("particles_per_item", _i32), ("unroll", _i32), ("threads", _i32), ("grid", _i32),
+                ("blocks_per_sm", _i32), ("num_sms", _i32), ("n_items", _i64),
+                ("workspace_bytes", _i64)]
+
+
+class mcl_profile(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("launches", _i64 * 8), ("ms", ctypes.c_double * 8)]
+
+
+class MclError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mcl status {status}: {message}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = {
+    "mcl_last_error": (ctypes.c_char_p, []),
+    "mcl_version": (_i32, []),
+    "mcl_sync": (_i32, [_c_void_p]),
+    "mcl_map_create": (_i32, [ctypes.POINTER(mcl_map_desc), _c_void_p, ctypes.POINTER(_c_void_p)]),
+    "mcl_map_destroy": (_i32, [_c_void_p]),
+    "mcl_map_get_info": (_i32, [_c_void_p, ctypes.POINTER(mcl_map_info)]),
+    "mcl_map_lookup": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p]),
+    "mcl_sensor_update": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _i64,
+                                 ctypes.POINTER(mcl_sensor_params), _c_void_p, _c_void_p, _c_void_p]),
+    "mcl_normalise": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p]),
+    "mcl_pose_to_matrix": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p]),
+    "mcl_sensor_plan_get": (_i32, [_c_void_p, _i64, _i64, ctypes.POINTER(mcl_sensor_params),
+                                   ctypes.POINTER(mcl_sensor_plan)]),
+    "mcl_resample": (_i32, [_c_void_p, _i64, ctypes.c_double, _c_void_p, _c_void_p, _c_void_p,
+                            _c_void_p]),
+    "mcl_motion_update": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p, _u64, _u64, _c_void_p]),
+    "mcl_gather_bench": (_i32, [_c_void_p, _i64, _i32, _i32, _i32, _u64, _c_void_p]),
+    "mcl_workspace_release": (_i32, [_c_void_p]),
+    "mcl_profile_begin": (_i32, []),
+    "mcl_profile_end": (_i32, [ctypes.POINTER(mcl_profile)]),
+}
+
+
+def lib():
+    """The loaded libmcl.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                   "(or python -m paper_2310_04172_gb300._build); there is no fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != MCL_OK:
+        raise MclError(status, lib().mcl_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None, shape_last=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"{name} must have shape (n, {shape_last})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ API (C names)
+def mcl_version() -> int:
+    return int(lib().mcl_version())
+
+
+def mcl_sync(stream=None):
+    _check(lib().mcl_sync(_stream(stream)))
+
+
+class Map:
+    """Owning handle of a device-resident TSDF map (mcl_map_t)."""
+
+    def __init__(self, handle, desc):
+        self.handle = handle
+        self.desc = desc
+
+    def info(self) -> dict:
+        inf = mcl_map_info(struct_size=ctypes.sizeof(mcl_map_info))
+        _check(lib().mcl_map_get_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in mcl_map_info._fields_ if k != "struct_size"}
+
+    def close(self):
+        if self.handle:
+            _check(lib().mcl_map_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mcl_map_create(kind: int, dtype: int, origin, voxel: float, truncation: float, dims,
+                   values: np.ndarray, brick_coords: np.ndarray | None = None,
+                   inv_voxel: float = 0.0) -> Map:
+    """Upload a dense or brick TSDF (host arrays) to the current device."""
+    values = np.ascontiguousarray(values)
+    d = mcl_map_desc(struct_size=ctypes.sizeof(mcl_map_desc), kind=kind, dtype=dtype)
+    d.origin[:] = [float(x) for x in origin]
+    d.voxel, d.inv_voxel, d.truncation = float(voxel), float(inv_voxel), float(truncation)
+    d.dims[:] = [int(x) for x in dims]
+    keep = [values]
+    if kind == MCL_MAP_BRICK:
+        bc = np.ascontiguousarray(brick_coords, np.int32).reshape(-1, 3)
+        keep.append(bc)
+        d.n_bricks = len(bc)
+        d.brick_coords = bc.ctypes.data_as(ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    _check(lib().mcl_map_create(ctypes.byref(d), values.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+    return Map(h, d)
+
+
+def map_from_scene(m) -> Map:
+    """Upload a ``scenes.DenseMap`` / ``scenes.BrickMap`` (input generator objects)."""
+    if m.kind == "dense":
+        return mcl_map_create(MCL_MAP_DENSE, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
+                              m.dims, m.values, inv_voxel=m.inv_voxel)
+    return mcl_map_create(MCL_MAP_BRICK, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
+                          m.dims, m.values, m.coords, inv_voxel=m.inv_voxel)
+
+
+def mcl_map_destroy(m: Map):
+    m.close()
+
+
+def mcl_map_lookup(m: Map, points, out_index=None, out_value=None, stream=None):
+    import torch
+    n = points.shape[0]
+    if out_index is None:
+        out_index = torch.empty(n, dtype=torch.int64, device=points.device)
+    if out_value is None:
+        out_value = torch.empty(n, dtype=torch.float32, device=points.device)
+    _check(lib().mcl_map_lookup(m.handle, _dev_ptr(points, torch.float32, 3, "points"), n,
+                                _dev_ptr(out_index, torch.int64, None, "out_index"),
+                                _dev_ptr(out_value, torch.float32, None, "out_value"), _stream(stream)))
+    return out_index, out_value
+
+
+def sensor_params(sigma_hit: float = 0.1, mode: int = MCL_LOGPROD, flags: int = 0,
+                  points_per_chunk: int = 0, lanes_per_particle: int = 0,
+                  particles_per_item: int = 0, unroll: int = 0) -> mcl_sensor_params:
+    return mcl_sensor_params(struct_size=ctypes.sizeof(mcl_sensor_params), sigma_hit=sigma_hit,
+                             mode=mode, flags=flags, points_per_chunk=points_per_chunk,
+                             lanes_per_particle=lanes_per_particle,
+                             particles_per_item=particles_per_item, unroll=unroll)
+
+
+def mcl_sensor_update(m: Map, particles, scan, params: mcl_sensor_params, logw=None, w=None,
+                      stream=None):
+    import torch
+    P, N = particles.shape[0], scan.shape[0]
+    _check(lib().mcl_sensor_update(m.handle, _dev_ptr(particles, torch.float32, 6, "particles"), P,
+                                   _dev_ptr(scan, torch.float32, 3, "scan"), N, ctypes.byref(params),
+                                   _dev_ptr(logw, torch.float32, None, "logw"),
+                                   _dev_ptr(w, torch.float32, None, "w"), _stream(stream)))
+    return logw, w
+
+
+def mcl_sensor_plan_get(m: Map, P: int, N: int, params: mcl_sensor_params) -> dict:
+    pl = mcl_sensor_plan(struct_size=ctypes.sizeof(mcl_sensor_plan))
+    _check(lib().mcl_sensor_plan_get(m.handle, P, N, ctypes.byref(params), ctypes.byref(pl)))
+    return {k: getattr(pl, k) for k, _ in mcl_sensor_plan._fields_ if k != "struct_size"}
+
+
+def mcl_normalise(logw, w, out_stats=None, stream=None):
+    import torch
+    _check(lib().mcl_normalise(_dev_ptr(logw, torch.float32, None, "logw"), logw.shape[0],
+                               _dev_ptr(w, torch.float32, None, "w"),
+                               _dev_ptr(out_stats, torch.float32, None, "out_stats"), _stream(stream)))
+    return w
+
+
+def mcl_pose_to_matrix(particles, out_mat, stream=None):
+    import torch
+    _check(lib().mcl_pose_to_matrix(_dev_ptr(particles, torch.float32, 6, "particles"),
+                                    particles.shape[0], _dev_ptr(out_mat, torch.float32, 12, "out_mat"),
+                                    _stream(stream)))
+    return out_mat
+
+
+def mcl_resample(w, r: float, idx, particles_in=None, particles_out=None, stream=None):
+    import torch
+    _check(lib().mcl_resample(_dev_ptr(w, torch.float32, None, "w"), w.shape[0], float(r),
+                              _dev_ptr(idx, torch.int32, None, "idx"),
+                              _dev_ptr(particles_in, torch.float32, 6, "particles_in"),
+                              _dev_ptr(particles_out, torch.float32, 6, "particles_out"),
+                              _stream(stream)))
+    return idx
+
+
+def mcl_motion_update(particles, delta, sigma, seed: int, step: int, stream=None):
+    import torch
+    d = (ctypes.c_float * 6)(*[float(x) for x in delta])
+    s = (ctypes.c_float * 6)(*[float(x) for x in sigma])
+    _check(lib().mcl_motion_update(_dev_ptr(particles, torch.float32, 6, "particles"),
+                                   particles.shape[0], d, s, int(seed) & (2**64 - 1),
+                                   int(step) & (2**64 - 1), _stream(stream)))
+    return particles
+
+
+def mcl_gather_bench(buf, blocks: int, iters: int, seed: int = 1, stream=None) -> int:
+    """Launch the gather microbenchmark over a CUDA tensor (int16/float16 or float32
+    elements); returns the number of gathers issued."""
+    es = buf.element_size()
+    _check(lib().mcl_gather_bench(_dev_ptr(buf, None, None, "buf"), buf.numel(), es, int(blocks),
+                                  int(iters), int(seed), _stream(stream)))
+    return int(blocks) * 256 * int(iters) * 8
+
+
+def mcl_workspace_release(stream=None):
+    _check(lib().mcl_workspace_release(_stream(stream)))
+
+
+def mcl_profile_begin():
+    _check(lib().mcl_profile_begin())
+
+
+def mcl_profile_end() -> dict:
+    p = mcl_profile(struct_size=ctypes.sizeof(mcl_profile))
+    _check(lib().mcl_profile_end(ctypes.byref(p)))
+    return {name: {"launches": int(p.launches[i]), "ms": float(p.ms[i])}
+            for i, name in enumerate(PHASES)}

@@ -58,6 +58,8 @@ def _L():
             for name in ("scn_layout_room", "scn_layout_multiroom", "scn_layout_building"):
                 getattr(lib, name).argtypes = [u64, i64, P]
                 getattr(lib, name).restype = i64
+            lib.scn_layout_building_sized.argtypes = [u64, i64, dbl, dbl, ctypes.c_int, P]
+            lib.scn_layout_building_sized.restype = i64
             lib.scn_sdf.argtypes = [P, i64, P, i64, P]
             lib.scn_voxelize_dense.argtypes = [P, i64, P, dbl, P, dbl, ctypes.c_int, P]
             lib.scn_voxelize_dense.restype = ctypes.c_int
@@ -108,9 +110,15 @@ def multiroom(seed: int = 2, n_objects: int = 40) -> Scene:
                  (25.6, 25.6, 6.4), (0.2,))
 
 
-def building(seed: int = 3, n_objects_per_floor: int = 150) -> Scene:
-    return Scene("building", _layout("scn_layout_building", seed, n_objects_per_floor), (0, 0, 0),
-                 (160.0, 160.0, 20.0), (0.3, 5.3, 10.3, 15.3))
+def building(seed: int = 3, n_objects_per_floor: int = 150, size: float = 160.0,
+             floors: int = 4) -> Scene:
+    """size x size m building with `floors` storeys of 5 m (default 160 x 160 x 20 m)."""
+    lib = _L()
+    cnt = lib.scn_layout_building_sized(seed, n_objects_per_floor, size, size, floors, None)
+    boxes = np.zeros((cnt, 6), np.float64)
+    lib.scn_layout_building_sized(seed, n_objects_per_floor, size, size, floors, _ptr(boxes))
+    return Scene("building", boxes, (0, 0, 0), (size, size, 5.0 * floors),
+                 tuple(5.0 * f + 0.3 for f in range(floors)))
 
 
 def sdf(scene: Scene, pts) -> np.ndarray:
@@ -316,17 +324,25 @@ def vlp16_multiroom(P: int = 50_000, dtype: int = F32, seed: int = 2) -> Workloa
     return Workload("vlp16_multiroom_512x512x128_28800pts", sc, m, scan, parts, pose, 0.1)
 
 
-@functools.lru_cache(maxsize=4)
-def _building_map(seed: int, dtype: int):
-    sc = building(seed)
-    return sc, voxelize_bricks(sc, (0.0, 0.0, 0.0), 0.05, (3200, 3200, 400), 0.3, dtype)
+@functools.lru_cache(maxsize=2)
+def _building_maps(seed: int, dtypes: tuple, size: float, floors: int):
+    sc = building(seed, size=size, floors=floors)
+    up16 = lambda v: -(-int(round(v / 0.05)) // 16) * 16  # grid rounded up to whole bricks
+    dims = (up16(size), up16(size), up16(5.0 * floors))
+    return sc, voxelize_bricks_multi(sc, (0.0, 0.0, 0.0), 0.05, dims, 0.3, dtypes)
 
 
-def os064_building(P: int = 1_000_000, dtype: int = I16, seed: int = 3, azimuths: int = 1024) -> Workload:
-    """Brick-sparse 160x160x20 m building at 5 cm, 64x1024 OS0-64 scan, uniform free-space cloud."""
-    sc, m = _building_map(seed, dtype)
+def os064_building(P: int = 1_000_000, dtype: int = I16, seed: int = 3, azimuths: int = 1024,
+                   size: float = 160.0, floors: int = 4, dtypes: tuple | None = None) -> Workload:
+    """Brick-sparse building (default 160x160x20 m) at 5 cm in 16^3 bricks, OS0-64 scan of
+    64 rings x `azimuths`, uniform free-space cloud (roll/pitch within 10 deg, yaw uniform).
+    `dtypes` voxelises several storage types in one pass (Workload.info['maps'])."""
+    dts = tuple(dtypes) if dtypes else (dtype,)
+    sc, maps = _building_maps(seed, dts, size, floors)
+    m = maps[dtype]
     kw = dict(OS064, azimuths=azimuths)
     pose, scan = true_pose(sc, seed, kw)
     parts = particles_free(sc, P, 0.1, 10.0, seed + 7)
-    return Workload(f"os064_building_bricks_{len(m.coords)}_{64 * azimuths}pts", sc, m, scan,
-                    parts, pose, 0.1, {"bricks": int(len(m.coords)), "map_bytes": m.nbytes})
+    name = f"os064_building_{int(size)}m_{floors}fl_bricks{len(m.coords)}_{P}x{64 * azimuths}"
+    return Workload(name, sc, m, scan, parts, pose, 0.1,
+                    {"bricks": int(len(m.coords)), "map_bytes": m.nbytes, "maps": maps})

@@ -283,18 +283,21 @@ int64_t scn_layout_multiroom(uint64_t seed, int64_t n_objects, double* out) {
   return (int64_t)v.size();
 }
 
-// Multi-storey building 160 x 160 x 20 m: four storeys of 5 m (0.3 m slabs, 0.3 m
-// roof), 0.3 m outer walls, interior walls on a 10 m grid (each 10 m segment
-// present with probability 0.6, with a door with probability 0.7), pillars at
-// grid crossings with probability 0.3 and `n_objects_per_floor` boxes per storey.
-int64_t scn_layout_building(uint64_t seed, int64_t n_objects_per_floor, double* out) {
+// Multi-storey building X x Y m with `floors` storeys of 5 m (0.3 m slabs,
+// 0.3 m roof), 0.3 m outer walls, interior walls on a 10 m grid (each 10 m
+// segment present with probability 0.6, with a door with probability 0.7),
+// pillars at grid crossings with probability 0.3 and `n_objects_per_floor`
+// boxes per storey. The default workload is 160 x 160 m with four storeys.
+int64_t scn_layout_building_sized(uint64_t seed, int64_t n_objects_per_floor, double X, double Y,
+                                  int floors, double* out) {
   std::vector<Box> v;
   auto add = [&](double a, double b, double c, double d, double e, double f) {
     v.push_back(Box{{a, b, c}, {d, e, f}});
   };
-  const double X = 160.0, Y = 160.0, Z = 20.0, slab = 0.3, ow = 0.3, w = 0.1;
-  const int floors = 4;
+  const double slab = 0.3, ow = 0.3, w = 0.1;
   const double storey = 5.0, grid = 10.0, door_w = 1.2, door_h = 2.4;
+  const double Z = storey * floors;
+  const int gx = (int)(X / grid), gy = (int)(Y / grid);
   for (int f = 0; f < floors; ++f) add(0, 0, f * storey, X, Y, f * storey + slab);
   add(0, 0, Z - slab, X, Y, Z);
   add(0, 0, 0, ow, Y, Z);
@@ -305,13 +308,15 @@ int64_t scn_layout_building(uint64_t seed, int64_t n_objects_per_floor, double* 
   for (int f = 0; f < floors; ++f) {
     double z0 = f * storey + slab, z1 = (f + 1 < floors) ? (f + 1) * storey : Z - slab;
     for (int axis = 0; axis < 2; ++axis) {
-      for (int i = 1; i < 16; ++i) {
+      const int nl = axis == 0 ? gx : gy, ns = axis == 0 ? gy : gx;
+      const double span = axis == 0 ? Y : X;
+      for (int i = 1; i < nl; ++i) {
         double c = i * grid;
-        for (int s = 0; s < 16; ++s) {
+        for (int s = 0; s < ns; ++s) {
           double p_present = unif(seed, 7, k++), p_door = unif(seed, 7, k++);
           double u_door = unif(seed, 7, k++);
           if (p_present >= 0.6) continue;
-          double a0 = std::max(ow, s * grid), a1 = std::min(Y - ow, (s + 1) * grid);
+          double a0 = std::max(ow, s * grid), a1 = std::min(span - ow, (s + 1) * grid);
           if (p_door < 0.7) {
             double d0 = a0 + 0.5 + (a1 - a0 - 1.0 - door_w) * u_door, d1 = d0 + door_w;
             double segs[3][4] = {{a0, d0, z0, z1}, {d1, a1, z0, z1}, {d0, d1, z0 + door_h, z1}};
@@ -326,8 +331,8 @@ int64_t scn_layout_building(uint64_t seed, int64_t n_objects_per_floor, double* 
         }
       }
     }
-    for (int i = 1; i < 16; ++i)
-      for (int j = 1; j < 16; ++j) {
+    for (int i = 1; i < gx; ++i)
+      for (int j = 1; j < gy; ++j) {
         if (unif(seed, 8, (uint64_t)((f * 16 + i) * 16 + j)) >= 0.3) continue;
         double cx = i * grid + 1.5, cy = j * grid + 1.5;
         add(cx - 0.3, cy - 0.3, z0, cx + 0.3, cy + 0.3, z1);
@@ -345,6 +350,10 @@ int64_t scn_layout_building(uint64_t seed, int64_t n_objects_per_floor, double* 
     for (size_t i = 0; i < v.size(); ++i)
       for (int k2 = 0; k2 < 3; ++k2) { out[6 * i + k2] = v[i].lo[k2]; out[6 * i + 3 + k2] = v[i].hi[k2]; }
   return (int64_t)v.size();
+}
+
+int64_t scn_layout_building(uint64_t seed, int64_t n_objects_per_floor, double* out) {
+  return scn_layout_building_sized(seed, n_objects_per_floor, 160.0, 160.0, 4, out);
 }
 
 // ---------------------------------------------------------------- analytic SDF

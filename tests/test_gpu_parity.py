@@ -1,0 +1,390 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (float path against FP64):
+- voxel indices and resampled indices: bit-exact;
+- pose matrices: bit-exact (both sides round the same FP64 expressions);
+- log-weights: |L_gpu - L_ora| <= 1e-5 * max(1, |L_ora|);
+- normalised weights, LOGPROD: |log w_gpu - log w_ora| <= 1e-5 (max(1, |L_p|) +
+  max(1, |M|)) wherever w_ora >= 1e-30, and |sum w - 1| <= 1e-5;
+- normalised weights, SUM: |w_gpu - w_ora| <= 1e-5 w_ora (+1e-30);
+- motion update: 2e-6 relative on positions, 2e-6 rad on angles (libm ulps).
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2310_04172_gb300 import _build, mcl
+    _build.build()
+    mcl.lib()
+    torch.cuda.set_device(0)
+    return torch
+
+
+@pytest.fixture(scope="module")
+def mcl():
+    from paper_2310_04172_gb300 import mcl as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def room():
+    return scenes.room_plain(P=1000)
+
+
+def dev(torch, a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def check_logw(Lg, Lo, tol=TOL):
+    Lg = np.asarray(Lg, np.float64)
+    err = np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo))
+    assert np.all(np.isfinite(Lg) == np.isfinite(Lo))
+    fin = np.isfinite(Lo)
+    assert err[fin].max(initial=0) <= tol, f"max rel log-weight error {err[fin].max():.3g}"
+    return err[fin].max(initial=0)
+
+
+def check_w(wg, Lo, mode, tol=TOL):
+    wo, M, S, deg = oracle.normalise(Lo)
+    wg = np.asarray(wg, np.float64)
+    assert abs(wg.sum() - 1.0) <= tol
+    sel = wo >= 1e-30
+    if mode == oracle.LOGPROD:
+        bound = tol * (np.maximum(1.0, np.abs(Lo[sel])) + max(1.0, abs(M)))
+        assert np.all(np.abs(np.log(wg[sel]) - np.log(wo[sel])) <= bound)
+    else:
+        assert np.all(np.abs(wg[sel] - wo[sel]) <= tol * wo[sel] + 1e-30)
+
+
+def run_sensor(torch, mcl, m, parts, scan, sigma, mode=0, flags=0, **shape):
+    P = parts.shape[0]
+    logw = torch.empty(P, device="cuda")
+    w = torch.empty(P, device="cuda")
+    prm = mcl.sensor_params(sigma_hit=sigma, mode=mode, flags=flags, **shape)
+    mcl.mcl_sensor_update(m, dev(torch, parts), dev(torch, scan), prm, logw, w)
+    mcl.mcl_sync()
+    return logw.cpu().numpy(), w.cpu().numpy()
+
+
+# ----------------------------------------------------------------- a2: pose -> [R | t]
+def test_pose_matrix_bit_exact(torch_cuda, mcl):
+    torch = torch_cuda
+    rng = np.random.default_rng(1)
+    P = 200_000
+    poses = np.concatenate([rng.normal(0, 50, (P, 3)), rng.uniform(-4, 4, (P, 3))], 1).astype(np.float32)
+    poses[:8, 3:] = np.float32([[0, 0, 0], [math.pi, -math.pi, math.pi / 2], [-0.0, 0.0, -math.pi / 2],
+                                [1e-30, -1e-30, 3e-8], [100, -200, 1e4], [6.2831855, -6.2831855, 3.1415927],
+                                [0.5, 0.5, 0.5], [-1.5707964, 1.5707964, 0.0]])
+    out = torch.empty((P, 12), device="cuda")
+    mcl.mcl_pose_to_matrix(dev(torch, poses), out)
+    mcl.mcl_sync()
+    got = out.cpu().numpy().reshape(P, 3, 4)
+    ref = oracle.pose_to_matrix(poses, parity=True).astype(np.float32)
+    bad = np.argwhere(got != ref)
+    assert len(bad) == 0, f"{len(bad)} entries differ, first {bad[:3].tolist()}"
+
+
+# ----------------------------------------------------------------- a4/a5: index and look-up
+def lookup_points(rng, m, n=200_000):
+    lo = np.asarray(m.origin) - 0.6
+    hi = np.asarray(m.origin) + np.asarray(m.dims) * m.voxel + 0.6
+    pts = rng.uniform(lo, hi, (n, 3)).astype(np.float32)
+    # exactly on voxel faces (FP32 multiples of the voxel): belong to the upper voxel
+    k = rng.integers(0, np.asarray(m.dims), (5000, 3))
+    pts[:5000] = (np.float32(m.origin) + np.float32(m.voxel) * k.astype(np.float32)).astype(np.float32)
+    special = np.float32([np.nan, np.inf, -np.inf, 0.0, -0.0, 1e30, -1e30, 1e-40])
+    pts[5000:5000 + 512] = rng.choice(special, (512, 3))
+    return pts
+
+
+@pytest.mark.parametrize("kind", ["dense", "brick"])
+@pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16, scenes.I16])
+def test_map_lookup_bit_exact(torch_cuda, mcl, kind, dtype):
+    torch = torch_cuda
+    sc = scenes.room(1)
+    if kind == "dense":
+        sm = scenes.voxelize_dense(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
+    else:
+        sm = scenes.voxelize_bricks(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
+    m = mcl.map_from_scene(sm)
+    pts = lookup_points(np.random.default_rng(2), sm)
+    idx, val = mcl.mcl_map_lookup(m, dev(torch, pts))
+    mcl.mcl_sync()
+    oi, ov = oracle.map_lookup(oracle.Map.from_scene_map(sm), pts)
+    assert np.array_equal(idx.cpu().numpy(), oi)
+    v = val.cpu().numpy().astype(np.float64)
+    if dtype == scenes.I16:
+        assert np.max(np.abs(v - ov)) <= 2 * 0.3 * 2.0 ** -24
+    else:
+        assert np.array_equal(v, ov)
+    m.close()
+
+
+# ----------------------------------------------------------------- a1-a8: sensor update + normalise
+@pytest.mark.parametrize("kind", ["dense", "brick"])
+@pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16, scenes.I16])
+@pytest.mark.parametrize("mode", [oracle.LOGPROD, oracle.SUM])
+@pytest.mark.parametrize("neglect", [False, True])
+def test_sensor_update_room(torch_cuda, mcl, room, kind, dtype, mode, neglect):
+    torch = torch_cuda
+    sc = room.scene
+    if kind == "dense":
+        sm = scenes.voxelize_dense(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
+    else:
+        sm = scenes.voxelize_bricks(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
+    m = mcl.map_from_scene(sm)
+    parts = room.particles.copy()
+    parts[:50, :3] += np.float32(4.0)  # some particles see much of the scan outside the map
+    Lg, wg = run_sensor(torch, mcl, m, parts, room.scan, room.sigma_hit, mode,
+                        mcl.MCL_NEGLECT_OUTSIDE if neglect else 0)
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(sm), parts, room.scan, room.sigma_hit,
+                              mode, neglect, parity=True)
+    check_logw(Lg, Lo)
+    check_w(wg, Lo, mode)
+    m.close()
+
+
+@pytest.mark.parametrize("chunk,lanes,unroll,ppi", [
+    (32, 32, 2, 1), (64, 8, 4, 7), (256, 16, 2, 64), (1024, 32, 4, 500), (2048, 8, 2, 33),
+    (8192, 32, 4, 64), (4096, 16, 4, 128)])
+def test_sensor_update_launch_shapes_and_ragged_tails(torch_cuda, mcl, room, chunk, lanes, unroll, ppi):
+    torch = torch_cuda
+    m = mcl.map_from_scene(room.map)
+    parts = np.concatenate([room.particles, room.particles[:1]])  # P = 1001
+    scan = room.scan[:1000]  # N = 1000: ragged against every chunk size
+    Lg, wg = run_sensor(torch, mcl, m, parts, scan, room.sigma_hit, points_per_chunk=chunk,
+                        lanes_per_particle=lanes, unroll=unroll, particles_per_item=ppi)
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(room.map), parts, scan, room.sigma_hit)
+    check_logw(Lg, Lo)
+    check_w(wg, Lo, oracle.LOGPROD)
+    # the launch hints (particles per item, unroll) never change the summation order
+    other = dict(points_per_chunk=chunk, lanes_per_particle=lanes,
+                 unroll=6 - unroll, particles_per_item=max(1, ppi // 3))
+    Lg2, wg2 = run_sensor(torch, mcl, m, parts, scan, room.sigma_hit, **other)
+    assert np.array_equal(Lg, Lg2) and np.array_equal(wg, wg2)
+    m.close()
+
+
+def test_sensor_update_edge_cases(torch_cuda, mcl, room):
+    torch = torch_cuda
+    m = mcl.map_from_scene(room.map)
+    om = oracle.Map.from_scene_map(room.map)
+    # P = 1, N = 1
+    Lg, wg = run_sensor(torch, mcl, m, room.particles[:1], room.scan[:1], 0.1)
+    check_logw(Lg, oracle.sensor_update(om, room.particles[:1], room.scan[:1], 0.1))
+    assert wg[0] == 1.0
+    # every point outside the map, and NaN poses (their points fall outside)
+    far = np.tile(np.float32([[500, 500, 500, 0, 0, 0]]), (5, 1))
+    far[3, 0] = np.nan
+    far[4, 5] = np.inf
+    Lg, wg = run_sensor(torch, mcl, m, far, room.scan, 0.1)
+    Lo = oracle.sensor_update(om, far, room.scan, 0.1)
+    check_logw(Lg, Lo)
+    assert np.allclose(wg, 0.2, rtol=1e-6)
+    # SUM with neglect and nothing stored: degenerate, uniform weights, S = 0
+    Lg, wg = run_sensor(torch, mcl, m, far, room.scan, 0.1, mcl.MCL_SUM, mcl.MCL_NEGLECT_OUTSIDE)
+    assert np.all(np.isneginf(Lg)) and np.allclose(wg, 0.2)
+    stats = torch.empty(2, device="cuda")
+    w = torch.empty(5, device="cuda")
+    mcl.mcl_normalise(dev(torch, Lg), w, stats)
+    mcl.mcl_sync()
+    assert stats[1].item() == 0.0 and np.allclose(w.cpu().numpy(), 0.2)
+    m.close()
+
+
+def test_multiroom_vlp16_parity(torch_cuda, mcl):
+    torch = torch_cuda
+    for dtype in (scenes.F32, scenes.F16):
+        wl = scenes.vlp16_multiroom(P=2000, dtype=dtype)
+        m = mcl.map_from_scene(wl.map)
+        Lg, wg = run_sensor(torch, mcl, m, wl.particles, wl.scan, wl.sigma_hit)
+        Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), wl.particles, wl.scan,
+                                  wl.sigma_hit)
+        check_logw(Lg, Lo)
+        check_w(wg, Lo, oracle.LOGPROD)
+        m.close()
+
+
+@pytest.fixture(scope="module")
+def building_i16():
+    return scenes.os064_building(P=1_000_000, dtype=scenes.I16)
+
+
+def test_building_os064_parity_subset(torch_cuda, mcl, building_i16):
+    torch = torch_cuda
+    wl = building_i16
+    m = mcl.map_from_scene(wl.map)
+    parts = wl.particles[:3000]
+    Lg, wg = run_sensor(torch, mcl, m, parts, wl.scan, wl.sigma_hit)
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), parts, wl.scan, wl.sigma_hit)
+    check_logw(Lg, Lo)
+    check_w(wg, Lo, oracle.LOGPROD)
+    m.close()
+
+
+def test_building_full_size_sampled(torch_cuda, mcl, building_i16):
+    """1M particles x 65,536 points in the benchmark's launch configuration;
+    the oracle recomputes a seeded sample of particles one by one."""
+    torch = torch_cuda
+    wl = building_i16
+    m = mcl.map_from_scene(wl.map)
+    Lg, wg = run_sensor(torch, mcl, m, wl.particles, wl.scan, wl.sigma_hit)
+    rng = np.random.default_rng(7)
+    sample = np.concatenate([rng.choice(len(Lg), 300, replace=False), [int(np.argmax(Lg))]])
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), wl.particles[sample], wl.scan,
+                              wl.sigma_hit)
+    check_logw(Lg[sample], Lo)
+    w64 = wg.astype(np.float64)
+    assert abs(w64.sum() - 1.0) <= TOL
+    M = Lg.max()
+    ok = Lg[sample] - M > -60
+    np.testing.assert_allclose(w64[sample][ok] / w64.max(), np.exp((Lg[sample] - M).astype(np.float64))[ok],
+                               rtol=1e-4)
+    m.close()
+
+
+# ----------------------------------------------------------------- a9: systematic resampling
+@pytest.mark.parametrize("P", [1, 2, 3, 4095, 4096, 4097, 65537, 1_000_000])
+def test_resample_bit_exact(torch_cuda, mcl, P):
+    torch = torch_cuda
+    rng = np.random.default_rng(P)
+    w = rng.exponential(1.0, P) ** 4
+    w[rng.random(P) < 0.2] = 0.0
+    if w.sum() == 0:
+        w[0] = 1.0
+    w32 = (w / w.sum()).astype(np.float32)
+    wd = dev(torch, w32)
+    parts = rng.normal(0, 1, (P, 6)).astype(np.float32)
+    for r in (0.0, 0.5, 1.0 - 2.0 ** -53):
+        idx = torch.empty(P, dtype=torch.int32, device="cuda")
+        out = torch.empty((P, 6), device="cuda")
+        mcl.mcl_resample(wd, r, idx, dev(torch, parts), out)
+        mcl.mcl_sync()
+        ref, _ = oracle.resample(w32, r)
+        got = idx.cpu().numpy()
+        assert np.array_equal(got, ref)
+        assert np.array_equal(out.cpu().numpy(), parts[ref])
+
+
+def test_resample_degenerate_and_one_hot(torch_cuda, mcl):
+    torch = torch_cuda
+    idx = torch.empty(10, dtype=torch.int32, device="cuda")
+    mcl.mcl_resample(torch.zeros(10, device="cuda"), 0.3, idx)
+    mcl.mcl_sync()
+    assert list(idx.cpu().numpy()) == list(range(10))
+    w = torch.zeros(10, device="cuda")
+    w[7] = 1.0
+    mcl.mcl_resample(w, 0.99, idx)
+    mcl.mcl_sync()
+    assert np.all(idx.cpu().numpy() == 7)
+
+
+def test_resample_after_sensor_update(torch_cuda, mcl, room):
+    torch = torch_cuda
+    m = mcl.map_from_scene(room.map)
+    _, wg = run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit)
+    idx = torch.empty(len(wg), dtype=torch.int32, device="cuda")
+    mcl.mcl_resample(dev(torch, wg), 0.25, idx)
+    mcl.mcl_sync()
+    assert np.array_equal(idx.cpu().numpy(), oracle.resample(wg, 0.25)[0])
+    m.close()
+
+
+# ----------------------------------------------------------------- a13: motion update
+def test_motion_update_parity(torch_cuda, mcl):
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    P = 50_000
+    poses = np.concatenate([rng.normal(0, 30, (P, 3)), rng.uniform(-1.4, 1.4, (P, 3))], 1).astype(np.float32)
+    delta = np.float32([0.3, -0.1, 0.05, 0.01, -0.02, 0.2])
+    sigma = np.float32([0.1, 0.1, 0.05, 0.01, 0.01, 0.1])
+    t = dev(torch, poses)
+    mcl.mcl_motion_update(t, delta, sigma, seed=0x1234_5678_9ABC, step=42)
+    mcl.mcl_sync()
+    got = t.cpu().numpy().astype(np.float64)
+    ref = oracle.motion_update(poses, delta, sigma, 0x1234_5678_9ABC, 42).astype(np.float64)
+    pos_err = np.abs(got[:, :3] - ref[:, :3]) / np.maximum(1.0, np.abs(ref[:, :3]))
+    assert pos_err.max() <= 2e-6
+    ang = np.abs(np.angle(np.exp(1j * (got[:, 3:] - ref[:, 3:]))))
+    assert ang.max() <= 2e-6
+
+
+# ----------------------------------------------------------------- determinism, errors, profiling
+def test_repeat_calls_bit_identical(torch_cuda, mcl, room):
+    torch = torch_cuda
+    m = mcl.map_from_scene(room.map)
+    a = run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit)
+    b = run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    m.close()
+
+
+def test_invalid_arguments_are_refused(torch_cuda, mcl, room):
+    torch = torch_cuda
+    m = mcl.map_from_scene(room.map)
+    parts, scan = dev(torch, room.particles), dev(torch, room.scan)
+    logw = torch.empty(len(parts), device="cuda")
+    L = mcl.lib()
+    for bad in [dict(sigma_hit=0.0), dict(sigma_hit=float("nan")), dict(mode=7), dict(flags=8),
+                dict(points_per_chunk=48), dict(lanes_per_particle=12), dict(unroll=3)]:
+        kw = dict(sigma_hit=0.1)
+        kw.update(bad)
+        with pytest.raises(mcl.MclError) as e:
+            mcl.mcl_sensor_update(m, parts, scan, mcl.sensor_params(**kw), logw)
+        assert e.value.status == mcl.MCL_EINVAL
+    prm = mcl.sensor_params(0.1)
+    s = mcl._stream(None)
+    assert L.mcl_sensor_update(m.handle, parts.data_ptr(), 0, scan.data_ptr(), 10, ctypes.byref(prm),
+                               logw.data_ptr(), None, s) == mcl.MCL_EINVAL
+    assert L.mcl_sensor_update(m.handle, parts.data_ptr(), 10, scan.data_ptr(), 0, ctypes.byref(prm),
+                               logw.data_ptr(), None, s) == mcl.MCL_EINVAL
+    assert L.mcl_sensor_update(m.handle, parts.data_ptr() + 2, 10, scan.data_ptr(), 10,
+                               ctypes.byref(prm), logw.data_ptr(), None, s) == mcl.MCL_EINVAL
+    assert L.mcl_sensor_update(m.handle, parts.data_ptr(), 10, scan.data_ptr(), 10, ctypes.byref(prm),
+                               None, None, s) == mcl.MCL_EINVAL
+    idx = torch.empty(10, dtype=torch.int32, device="cuda")
+    for r in (-0.1, 1.0, float("nan")):
+        with pytest.raises(mcl.MclError):
+            mcl.mcl_resample(torch.ones(10, device="cuda"), r, idx)
+    with pytest.raises(mcl.MclError):
+        mcl.mcl_motion_update(parts, [0] * 6, [0, 0, -1, 0, 0, 0], 1, 1)
+    # brick maps: duplicated or out-of-range brick coordinates
+    with pytest.raises(mcl.MclError):
+        mcl.mcl_map_create(mcl.MCL_MAP_BRICK, mcl.MCL_I16, (0, 0, 0), 0.05, 0.3, (32, 32, 32),
+                           np.zeros((2, 16, 16, 16), np.int16), np.int32([[0, 0, 0], [0, 0, 0]]))
+    with pytest.raises(mcl.MclError):
+        mcl.mcl_map_create(mcl.MCL_MAP_BRICK, mcl.MCL_I16, (0, 0, 0), 0.05, 0.3, (32, 32, 32),
+                           np.zeros((1, 16, 16, 16), np.int16), np.int32([[2, 0, 0]]))
+    with pytest.raises(mcl.MclError):
+        mcl.mcl_map_create(mcl.MCL_MAP_BRICK, mcl.MCL_I16, (0, 0, 0), 0.05, 0.3, (30, 32, 32),
+                           np.zeros((1, 16, 16, 16), np.int16), np.int32([[0, 0, 0]]))
+    mcl.mcl_sync()  # nothing above reached the device: status stays clean
+    m.close()
+
+
+def test_profile_counts_phases(torch_cuda, mcl, room):
+    torch = torch_cuda
+    m = mcl.map_from_scene(room.map)
+    mcl.mcl_profile_begin()
+    run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit)
+    prof = mcl.mcl_profile_end()
+    assert prof["sensor"]["launches"] == 1 and prof["sensor"]["ms"] > 0
+    assert prof["pose"]["launches"] == 1 and prof["normalise"]["launches"] == 1
+    m.close()
