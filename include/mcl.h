@@ -206,6 +206,24 @@ mcl_status mcl_sensor_plan_get(mcl_map_t map, int64_t P, int64_t N,
 mcl_status mcl_resample(const float* w, int64_t P, double r, int32_t* idx,
                         const float* particles_in, float* particles_out, mcl_stream_t stream);
 
+/* Allocation-free variant of mcl_resample (the paper has no counterpart; it
+ * exists for callers that may not allocate device memory: real-time control
+ * loops that forbid allocation after start-up, since cudaMalloc and cudaFree
+ * can block and cudaFree synchronises the device, and plug-ins whose host
+ * application owns every device allocation). Same arguments, results and
+ * errors as mcl_resample (indices identical bit for bit), but its scratch is
+ * a fixed static device array inside the library, so P is limited to
+ * [1, 1048576] (2^20; larger P is EINVAL) and every GPU that loads the
+ * library holds that array (about 8.4 MB) until the process exits. Calls
+ * allocate nothing. The first call on each device looks up the array's
+ * device address with that device current; make that first call before
+ * capturing a stream into a graph. All calls on a device share the one
+ * array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and give wrong indices; serialise them. */
+mcl_status mcl_resample_noalloc(const float* w, int64_t P, double r, int32_t* idx,
+                                const float* particles_in, float* particles_out,
+                                mcl_stream_t stream);
+
 /* ------------------------------------------------------------------ motion update */
 
 /* Motion update (Sec. III: the motion model is applied to every particle).

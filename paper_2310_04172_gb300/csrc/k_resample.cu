@@ -8,6 +8,8 @@
 // one block scans the tile totals, and each output j finds
 // min{p : C_p > t_j}, t_j = ((j + r) / P) S, by a binary search over tile ends
 // and then inside the tile.
+#include <mutex>
+
 #include "mcl_internal.h"
 
 namespace mcl {
@@ -165,6 +167,51 @@ __global__ void k_systematic(const double* __restrict__ cum, const double* __res
 }  // namespace
 
 int resample_tiles(int P) { return (P + kTile - 1) / kTile; }
+
+// ---------------------------------------------------------------- static scratch
+// Scratch for the allocation-free entry point (mcl_resample_noalloc), for
+// callers that may not allocate device memory: the FP64 prefix C (one double
+// per particle) and the tile totals and last-positive indices (one entry per
+// tile plus the grand total), for at most kStaticMaxParticles particles. It is
+// a file-scope device array, so every GPU that loads the library holds it
+// (about 8.4 MB) until the process exits. Every call overwrites all of it that
+// it reads (k_tile_scan writes C and the tile entries, k_tile_offsets the
+// offsets and totals), so nothing has to start at zero; but all calls on a
+// device share it, and calls whose work overlaps on the GPU race.
+constexpr int kStaticTiles = (kStaticMaxParticles + kTile - 1) / kTile;
+constexpr size_t kStaticBytes =
+    (size_t)kStaticMaxParticles * sizeof(double) + 2 * (size_t)(kStaticTiles + 1) * sizeof(double);
+static __device__ __align__(256) unsigned char g_resample_scratch[kStaticBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};  // device address of the array, per device
+}  // namespace
+
+cudaError_t launch_resample_static(const float* w, int P, double r, int32_t* idx,
+                                   const float* particles_in, float* particles_out, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  void* base = nullptr;
+  {
+    // Once per device, with that device current: the host-side name of the
+    // array is only a stand-in, its device address comes from the runtime.
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_resample_scratch);
+      if (e != cudaSuccess) return e;
+      g_static_ptr[dev] = p;
+    }
+    base = g_static_ptr[dev];
+  }
+  double* cum = static_cast<double*>(base);
+  double* tile_total = cum + kStaticMaxParticles;
+  long long* tile_last = reinterpret_cast<long long*>(tile_total + (kStaticTiles + 1));
+  return launch_resample(w, P, r, idx, particles_in, particles_out, cum, tile_total, tile_last, s);
+}
 
 cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             const float* particles_in, float* particles_out, double* cum,

@@ -530,6 +530,21 @@ mcl_status mcl_resample(const float* w, int64_t P, double r, int32_t* idx, const
   return MCL_OK;
 }
 
+mcl_status mcl_resample_noalloc(const float* w, int64_t P, double r, int32_t* idx, const float* pin,
+                                float* pout, mcl_stream_t stream) {
+  if (!w || !idx) return fail(MCL_EINVAL, "resample_noalloc: NULL w or idx");
+  if (P < 1 || P > kStaticMaxParticles)
+    return fail(MCL_EINVAL, "resample_noalloc: P = %lld outside [1, %d] (static scratch limit)",
+                (long long)P, kStaticMaxParticles);
+  if (!(r >= 0.0 && r < 1.0)) return fail(MCL_EINVAL, "resample_noalloc: r must lie in [0, 1)");
+  if (pin && !pout) return fail(MCL_EINVAL, "resample_noalloc: particles_out NULL");
+  if (pin && pin == pout) return fail(MCL_EINVAL, "resample_noalloc: particles_in and particles_out alias");
+  if (!aligned(w, 4) || !aligned(idx, 4) || !aligned(pin, 4) || !aligned(pout, 4))
+    return fail(MCL_EINVAL, "resample_noalloc: misaligned pointer");
+  MCL_CUDA(launch_resample_static(w, (int)P, r, idx, pin, pout, (cudaStream_t)stream));
+  return MCL_OK;
+}
+
 // ---------------------------------------------------------------- motion
 mcl_status mcl_motion_update(float* particles, int64_t P, const float delta[6], const float sigma[6],
                              uint64_t seed, uint64_t step, mcl_stream_t stream) {

@@ -170,6 +170,13 @@ cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             const float* particles_in, float* particles_out, double* cum,
                             double* tile_total, long long* tile_last, cudaStream_t s);
 
+// Resampling with scratch in a static device array (no allocation), for at
+// most kStaticMaxParticles particles.
+constexpr int kStaticMaxParticles = 1 << 20;
+constexpr int kMaxDevices = 64;
+cudaError_t launch_resample_static(const float* w, int P, double r, int32_t* idx,
+                                   const float* particles_in, float* particles_out, cudaStream_t s);
+
 cudaError_t launch_motion(float* particles, int P, const float delta[6], const float sigma[6],
                           uint64_t seed, uint64_t step, cudaStream_t s);
 

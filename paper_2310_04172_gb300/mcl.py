@@ -83,6 +83,8 @@ SIGNATURES = {
                                    ctypes.POINTER(mcl_sensor_plan)]),
     "mcl_resample": (_i32, [_c_void_p, _i64, ctypes.c_double, _c_void_p, _c_void_p, _c_void_p,
                             _c_void_p]),
+    "mcl_resample_noalloc": (_i32, [_c_void_p, _i64, ctypes.c_double, _c_void_p, _c_void_p,
+                                    _c_void_p, _c_void_p]),
     "mcl_motion_update": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p, _u64, _u64, _c_void_p]),
     "mcl_gather_bench": (_i32, [_c_void_p, _i64, _i32, _i32, _i32, _u64, _c_void_p]),
     "mcl_workspace_release": (_i32, [_c_void_p]),
@@ -265,6 +267,17 @@ def mcl_resample(w, r: float, idx, particles_in=None, particles_out=None, stream
                               _dev_ptr(particles_in, torch.float32, 6, "particles_in"),
                               _dev_ptr(particles_out, torch.float32, 6, "particles_out"),
                               _stream(stream)))
+    return idx
+
+
+def mcl_resample_noalloc(w, r: float, idx, particles_in=None, particles_out=None, stream=None):
+    """mcl_resample without any device allocation (static scratch, P <= 2^20)."""
+    import torch
+    _check(lib().mcl_resample_noalloc(_dev_ptr(w, torch.float32, None, "w"), w.shape[0], float(r),
+                                      _dev_ptr(idx, torch.int32, None, "idx"),
+                                      _dev_ptr(particles_in, torch.float32, 6, "particles_in"),
+                                      _dev_ptr(particles_out, torch.float32, 6, "particles_out"),
+                                      _stream(stream)))
     return idx
 
 
