@@ -51,6 +51,9 @@ def parse_args(argv=None):
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--ppi", type=int, default=0)
     ap.add_argument("--unroll", type=int, default=0)
+    ap.add_argument("--pipeline", type=int, default=0, help="0 auto, 1 off, 2 on")
+    ap.add_argument("--order", type=int, default=0, help="particle order: 0 auto, 1 given, 2 spatial")
+    ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
     return ap.parse_args(argv)
 
 
@@ -171,7 +174,7 @@ def algorithmic_bytes(P: int, N: int, elem: int, brick: bool) -> int:
 
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("k_sensor.cu", "mcl_internal.h"):
+    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16.cu", "mcl_internal.h"):
         with open(os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -268,6 +271,7 @@ def config_dict(args, wl):
         "workload": wl.name, "particles": int(len(wl.particles)), "points": int(len(wl.scan)),
         "scan": f"64 rings (+-45 deg) x {args.azimuths} azimuths, sigma 0.02 m",
         "map": {"kind": "brick16", "index": "hash", "dtype": args.dtype,
+                "layout": ["linear", "block4"][args.layout],
                 "extent_m": [args.building, args.building, 5.0 * args.floors], "voxel_m": 0.05,
                 "dims": list(m.dims), "bricks": int(len(m.coords)), "bytes": int(m.values.nbytes),
                 "truncation_m": 0.3},
@@ -296,7 +300,7 @@ def run_ours(args):
     wl = make_workload(args, rank)
     parts_np = rank_particles(wl, rank)
     P, N = len(parts_np), len(wl.scan)
-    m = mcl.map_from_scene(wl.map)
+    m = mcl.map_from_scene(wl.map, args.layout)
     elem = 4 if args.dtype == "f32" else 2
     stream = torch.cuda.Stream(device=dev)
     parts = torch.from_numpy(parts_np).to(dev)
@@ -309,7 +313,7 @@ def run_ours(args):
     offsets = scenes.uniform(11 + rank, 200, args.steps + args.warmup + 64)
     prm = mcl.sensor_params(sigma_hit=wl.sigma_hit, points_per_chunk=args.chunk,
                             lanes_per_particle=args.lanes, particles_per_item=args.ppi,
-                            unroll=args.unroll)
+                            unroll=args.unroll, pipeline=args.pipeline, particle_order=args.order)
     plan = mcl.mcl_sensor_plan_get(m, P, N, prm)
 
     def step(k, s):

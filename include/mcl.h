@@ -60,6 +60,7 @@ mcl_status mcl_sync(mcl_stream_t stream);
 
 enum { MCL_MAP_DENSE = 0, MCL_MAP_BRICK = 1 };
 enum { MCL_F32 = 0, MCL_F16 = 1, MCL_I16 = 2 };
+enum { MCL_LAYOUT_LINEAR = 0, MCL_LAYOUT_BLOCK4 = 1 };
 
 /* TSDF map description (Sec. III: a TSDF volume; the sparse form keeps fine
  * blocks only where values lie within the truncation distance, every other
@@ -78,7 +79,12 @@ enum { MCL_F32 = 0, MCL_F16 = 1, MCL_I16 = 2 };
  *        values[b * 4096 + (lz * 16 + ly) * 16 + lx]; a voxel in no listed
  *        brick reads +truncation. At most 2^31 - 1 bricks and 2^32 - 2
  *        brick cells; duplicated or out-of-range coordinates are EINVAL.
- * inv_voxel = 0 lets the library use (float)(1.0 / voxel). */
+ * inv_voxel = 0 lets the library use (float)(1.0 / voxel).
+ * device_layout (BRICK) chooses how the library stores each brick on the
+ * device: MCL_LAYOUT_LINEAR keeps the x-fastest order, MCL_LAYOUT_BLOCK4
+ * stores 4x4x4 blocks (block-major, each block z-major) so that neighbouring
+ * voxels in x and y share memory sectors. host_values are always x-fastest;
+ * results do not depend on the layout. */
 typedef struct mcl_map_desc {
   uint32_t struct_size; /* sizeof(mcl_map_desc) */
   int32_t kind;         /* MCL_MAP_DENSE or MCL_MAP_BRICK */
@@ -90,6 +96,8 @@ typedef struct mcl_map_desc {
   int64_t dims[3];      /* grid size in voxels (x, y, z) */
   int64_t n_bricks;     /* BRICK: number of bricks */
   const int32_t* brick_coords; /* BRICK: (host) n_bricks x 3 int32 */
+  int32_t device_layout;       /* BRICK: MCL_LAYOUT_LINEAR or MCL_LAYOUT_BLOCK4 */
+  int32_t reserved;            /* 0 */
 } mcl_map_desc;
 
 typedef struct mcl_map_s* mcl_map_t;
@@ -145,7 +153,14 @@ typedef struct mcl_sensor_params {
   int32_t points_per_chunk;   /* 0 or a multiple of 32 in [32, 8192] */
   int32_t lanes_per_particle; /* 0, 8, 16 or 32 */
   int32_t particles_per_item; /* launch shape hint, 0 = auto (no effect on results) */
-  int32_t unroll;             /* launch shape hint, 0 = auto (no effect on results) */
+  int32_t unroll;             /* 0 (auto), 2, 4 or 8: look-ups in flight per lane (hint; lane
+                                 groups narrower than 32 always use 4; no effect on results) */
+  int32_t pipeline;           /* 0 (auto), 1 off, 2 on: overlap the next step's index look-ups
+                                 with this step's gathers (hint; only for unroll 2 or 4 with
+                                 32 lanes; no effect on results) */
+  int32_t particle_order;     /* 0 (auto), 1 as given, 2 spatial (Morton-ordered buckets over
+                                 the map extent): the order particles are evaluated in;
+                                 no effect on results */
 } mcl_sensor_params;
 
 /* Sensor update of P particles (device, P x 6 FP32) against one scan
@@ -183,7 +198,8 @@ mcl_status mcl_pose_to_matrix(const float* particles, int64_t P, float* out_mat,
  * needs; points_per_chunk * lanes_per_particle fix the summation order. */
 typedef struct mcl_sensor_plan {
   uint32_t struct_size;
-  int32_t points_per_chunk, lanes_per_particle, particles_per_item, unroll;
+  int32_t points_per_chunk, lanes_per_particle, particles_per_item, unroll, pipeline;
+  int32_t particle_order;   /* 1 as given, 2 spatial */
   int32_t threads, grid, blocks_per_sm, num_sms;
   int64_t n_items;          /* (chunk, particle block) work items */
   int64_t workspace_bytes;  /* library scratch for one call */

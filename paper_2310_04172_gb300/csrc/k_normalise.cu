@@ -46,7 +46,8 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
 // One block per contiguous particle range. With `partial`, L_p is first
 // assembled from the K chunk sums in chunk order: LOGPROD L = c * sum(d^2),
 // SUM L = log(k * sum exp(c d^2)).
-__global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ partial, int P, int K,
+__global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ partial,
+                                                    const int* __restrict__ rank, int P, int K,
                                                     int mode, float c, float k,
                                                     float* __restrict__ logw,
                                                     float2* __restrict__ stats, int range) {
@@ -57,7 +58,8 @@ __global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ pa
     float L;
     if (partial) {
       float s = 0.f;
-      for (int q = 0; q < K; ++q) s = __fadd_rn(s, partial[(size_t)q * P + p]);
+      const size_t slot = rank ? (size_t)rank[p] : (size_t)p;
+      for (int q = 0; q < K; ++q) s = __fadd_rn(s, partial[(size_t)q * P + slot]);
       L = mode == MCL_LOGPROD ? __fmul_rn(c, s) : logf(__fmul_rn(k, s));
       logw[p] = L;
     } else {
@@ -108,11 +110,12 @@ int normalise_blocks(int P) {
   return b < 1024 ? b : 1024;
 }
 
-cudaError_t launch_finish_and_normalise(const float* partial, int P, int K, int mode, float c,
-                                        float k, float* logw, float* w, float2* block_stats,
-                                        int nblocks, float* out_stats, cudaStream_t s) {
+cudaError_t launch_finish_and_normalise(const float* partial, const int* rank, int P, int K,
+                                        int mode, float c, float k, float* logw, float* w,
+                                        float2* block_stats, int nblocks, float* out_stats,
+                                        cudaStream_t s) {
   const int range = range_of(P, nblocks);
-  k_block_stats<<<nblocks, kT, 0, s>>>(partial, P, K, mode, c, k, logw, block_stats, range);
+  k_block_stats<<<nblocks, kT, 0, s>>>(partial, rank, P, K, mode, c, k, logw, block_stats, range);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !w) return e;
   k_normalise<<<nblocks, kT, 0, s>>>(logw, P, w, block_stats, nblocks, range, out_stats);
@@ -121,7 +124,7 @@ cudaError_t launch_finish_and_normalise(const float* partial, int P, int K, int 
 
 cudaError_t launch_normalise(const float* logw, int P, float* w, float2* block_stats, int nblocks,
                              float* out_stats, cudaStream_t s) {
-  return launch_finish_and_normalise(nullptr, P, 0, MCL_LOGPROD, 0.f, 0.f,
+  return launch_finish_and_normalise(nullptr, nullptr, P, 0, MCL_LOGPROD, 0.f, 0.f,
                                      const_cast<float*>(logw), w, block_stats, nblocks, out_stats, s);
 }
 

@@ -12,7 +12,8 @@ namespace {
 //   [ cy*cp   a*sr - sy*cr   a*cr + sy*sr ]
 //   [ sy*cp   b*sr + cy*cr   b*cr - cy*sr ]
 //   [ -sp     cp*sr          cp*cr        ]
-__global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4* __restrict__ mats) {
+__global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4* __restrict__ mats,
+                                 const int* __restrict__ rank) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const float* s = poses + 6 * (size_t)p;
@@ -31,7 +32,7 @@ __global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4*
   const double r20 = -sp;
   const double r21 = __dmul_rn(cp, sr);
   const double r22 = __dmul_rn(cp, cr);
-  float4* o = mats + 3 * (size_t)p;
+  float4* o = mats + 3 * (size_t)(rank ? rank[p] : p);
   o[0] = make_float4(__double2float_rn(r00), __double2float_rn(r01), __double2float_rn(r02), x);
   o[1] = make_float4(__double2float_rn(r10), __double2float_rn(r11), __double2float_rn(r12), y);
   o[2] = make_float4(__double2float_rn(r20), __double2float_rn(r21), __double2float_rn(r22), z);
@@ -59,17 +60,38 @@ __global__ void k_map_lookup(const MapView m, const float* __restrict__ pts, int
   if (out_value) out_value[j] = d;
 }
 
+template <typename T>
+__global__ void k_brick_to_block4(const T* __restrict__ src, T* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long b = i >> 12;
+  const uint32_t l = (uint32_t)i & 4095u;
+  dst[(b << 12) + block4_local(l & 15u, (l >> 4) & 15u, l >> 8)] = src[i];
+}
+
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, cudaStream_t s) {
-  k_pose_to_matrix<<<blocks_for(P, 256), 256, 0, s>>>(poses, P, mats);
+cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
+                                  cudaStream_t s) {
+  k_pose_to_matrix<<<blocks_for(P, 256), 256, 0, s>>>(poses, P, mats, rank);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scan_pack(const float* scan, int N, float4* packed, cudaStream_t s) {
   k_scan_pack<<<blocks_for(N, 256), 256, 0, s>>>(scan, N, packed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_bricks, int elem_bytes,
+                                   cudaStream_t s) {
+  const long long n = n_bricks * kBrickVoxels;
+  if (n <= 0) return cudaSuccess;
+  if (elem_bytes == 2)
+    k_brick_to_block4<<<blocks_for(n, 256), 256, 0, s>>>((const short*)src, (short*)dst, n);
+  else
+    k_brick_to_block4<<<blocks_for(n, 256), 256, 0, s>>>((const float*)src, (float*)dst, n);
   return cudaGetLastError();
 }
 

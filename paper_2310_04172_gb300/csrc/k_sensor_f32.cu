@@ -1,0 +1,11 @@
+// Sensor kernel instances for f32 maps (compiled as their own unit so the
+// storage types build in parallel).
+#include "k_sensor_impl.cuh"
+
+namespace mcl {
+
+void* sensor_kernel_f32(int kind, int layout, int mode, const SensorShape& sh) {
+  return sensor::pick_dtype<MCL_F32>(kind, layout, mode, sh);
+}
+
+}  // namespace mcl

@@ -1,0 +1,369 @@
+// Sensor update kernel (Sec. III, Eq. 3; Sec. V-B), GB300 design.
+//
+// The paper evaluates one particle per thread and loops over all scan points.
+// Here a persistent grid walks work items (point chunk c, block of `ppi`
+// particles) strided by the grid size. The CTA holds the chunk's scan points in
+// shared memory, staged with one bulk asynchronous copy (cp.async.bulk,
+// completion on an mbarrier) and re-staged only when the item's chunk changes;
+// that is the only CTA-wide barrier. A group of G lanes owns one particle: lane
+// l of the group takes points l, l + G, l + 2G, ... of the chunk, so
+// neighbouring lanes read neighbouring scan points (neighbouring azimuths of
+// one ring) and their map gathers fall in the same or adjacent sectors. Each
+// lane keeps U look-ups in flight per step (brick-hash entries first, then the
+// values). Per-point terms are summed in FP32 per lane in point order, then
+// over the group with a fixed xor-shuffle tree; lane 0 of the group writes the
+// particle's chunk sum to partial[c * P + p]. The summation order depends only
+// on (chunk, G).
+//
+// LOGPROD accumulates d^2 (the score -d^2 / (2 sigma^2) is applied once per
+// particle when the chunks are added); SUM accumulates exp(-d^2 / (2 sigma^2))
+// (Eq. 3 without its constant, applied at the end). For int16 maps the terms
+// use the stored integer q (d = q * scale): LOGPROD accumulates q^2 and the
+// chunk sum is multiplied by scale^2 once; SUM folds scale^2 into the exponent
+// constant. A point without a stored value reads +tau (q = 32767 for int16).
+#pragma once
+
+#include "mcl_internal.h"
+
+namespace mcl {
+namespace sensor {
+
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after about a second.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i >= 32) __nanosleep(256);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// What the accumulation works on: FP32 / FP16 values as floats; int16 as
+// the stored integer q converted to float (LOGPROD sums q^2 and the chunk sum
+// is scaled by scale^2 once; SUM folds scale^2 into the exponent constant).
+// Sums are FP32. (An exact int64 sum of q^2 was measured slower: its extra
+// registers cost a resident CTA per SM.)
+template <int DTYPE, int MODE>
+struct Raw {
+  using value = float;
+  using acc = float;
+};
+
+template <int DTYPE, int MODE>
+__device__ __forceinline__ typename Raw<DTYPE, MODE>::value load_raw(const void* values, size_t i) {
+  if constexpr (DTYPE == MCL_F32) {
+    return __ldg(static_cast<const float*>(values) + i);
+  } else if constexpr (DTYPE == MCL_F16) {
+    return __half2float(__ldg(static_cast<const __half*>(values) + i));
+  } else {
+    return (float)__ldg(static_cast<const short*>(values) + i);
+  }
+}
+
+// Value read where nothing is stored, in the same units.
+template <int DTYPE, int MODE>
+__device__ __forceinline__ typename Raw<DTYPE, MODE>::value outside_value(const SensorArgs& a) {
+  return a.vout;
+}
+
+// In-brick offset: linear x-fastest, or 4x4x4 blocks (block-major, each block
+// z-major) so that a 32-byte sector of int16 values is a 4 x 4 patch in x, y.
+template <int KIND>
+__device__ __forceinline__ uint32_t brick_local(int ix, int iy, int iz) {
+  const uint32_t lx = (uint32_t)ix & 15u, ly = (uint32_t)iy & 15u, lz = (uint32_t)iz & 15u;
+  if constexpr (KIND == kKindBrickBlock4) {
+    return ((lz >> 2) << 10) | ((ly >> 2) << 8) | ((lx >> 2) << 6) | ((lz & 3u) << 4) |
+           ((ly & 3u) << 2) | (lx & 3u);
+  } else {
+    return (lz << 8) | (ly << 4) | lx;
+  }
+}
+
+// Stage A of one step of U points per lane: load the points, transform them,
+// find their voxels and issue the first index look-up (brick maps: the hash
+// entry; dense maps: the value itself). FULL: every point index is inside the
+// chunk and the group is valid (no bounds predicates).
+template <int KIND, int DTYPE, int MODE, int U>
+struct Pending {
+  uint32_t key[U], loc[U];  // BRICK: brick-cell key, in-brick offset; DENSE: key = linear index
+  uint2 e[U];               // BRICK: first hash entry (EMPTY where not in[u])
+  typename Raw<DTYPE, MODE>::value dv[U];  // DENSE: value
+  bool in[U], v[U];
+};
+
+template <int KIND, int DTYPE, int MODE, int G, int U, bool FULL>
+__device__ __forceinline__ void stage_a(const SensorArgs& a, const float4* __restrict__ sscan,
+                                        int base, int glane, int cnt, bool gvalid,
+                                        const float4& r0, const float4& r1, const float4& r2,
+                                        Pending<KIND, DTYPE, MODE, U>& s) {
+  const MapView& m = a.map;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int j = base + u * G + glane;
+    s.v[u] = FULL || (gvalid && j < cnt);
+    const float4 z = sscan[FULL ? j : (s.v[u] ? j : 0)];
+    float x, y, w;
+    transform_point(r0, r1, r2, z, x, y, w);
+    int ix, iy, iz;
+    s.in[u] = s.v[u] && voxel_of(m, x, y, w, ix, iy, iz);
+    if constexpr (KIND == MCL_MAP_DENSE) {
+      s.key[u] = ((uint32_t)iz * (uint32_t)m.ny + (uint32_t)iy) * (uint32_t)m.nx + (uint32_t)ix;
+    } else {
+      s.key[u] = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
+      s.loc[u] = brick_local<KIND>(ix, iy, iz);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if constexpr (KIND == MCL_MAP_DENSE) {
+      s.dv[u] = s.in[u] ? load_raw<DTYPE, MODE>(m.values, s.key[u]) : outside_value<DTYPE, MODE>(a);
+    } else {
+      s.e[u] = s.in[u] ? __ldg(m.table + brick_hash(s.key[u], m.hash_shift))
+                       : make_uint2(kEmptyKey, 0u);
+    }
+  }
+}
+
+// Stage B: resolve the brick slot (further probes if the first entry was
+// another key) and issue the value gathers; outputs the values and which
+// points count.
+template <int KIND, int DTYPE, int MODE, int U>
+__device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND, DTYPE, MODE, U>& s,
+                                        typename Raw<DTYPE, MODE>::value* dv, bool* use) {
+  const MapView& m = a.map;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if constexpr (KIND == MCL_MAP_DENSE) {
+      dv[u] = s.dv[u];
+      use[u] = s.v[u] && (s.in[u] || !a.neglect);
+    } else {
+      uint32_t slot = kNoSlot;
+      if (s.in[u]) {
+        if (s.e[u].x == s.key[u]) slot = s.e[u].y;
+        else if (s.e[u].x != kEmptyKey)
+          slot = probe_rest(m, s.key[u], brick_hash(s.key[u], m.hash_shift));
+      }
+      const bool st = slot != kNoSlot;
+      dv[u] = st ? load_raw<DTYPE, MODE>(m.values, (size_t)slot * kBrickVoxels + s.loc[u])
+                 : outside_value<DTYPE, MODE>(a);
+      use[u] = s.v[u] && (st || !a.neglect);
+    }
+  }
+}
+
+template <int DTYPE, int MODE, int U>
+__device__ __forceinline__ void accumulate(const SensorArgs& a,
+                                           const typename Raw<DTYPE, MODE>::value* dv,
+                                           const bool* use, typename Raw<DTYPE, MODE>::acc& acc) {
+  if constexpr (MODE == MCL_LOGPROD) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (use[u]) acc = fmaf(dv[u], dv[u], acc);
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (use[u]) acc = __fadd_rn(acc, expf(__fmul_rn(__fmul_rn(dv[u], dv[u]), a.cs)));
+  }
+}
+
+// All points [0, end) of one particle's chunk, end a multiple of G*U, without
+// bounds checks. PIPE: stage A of step i+1 is issued before the gathers of
+// step i are consumed, so the index look-ups of the next step overlap the
+// value gathers of this one (the per-point order of the sum is unchanged).
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+__device__ __forceinline__ void eval_full(const SensorArgs& a, const float4* __restrict__ sscan,
+                                          int end, int glane, const float4& r0, const float4& r1,
+                                          const float4& r2, typename Raw<DTYPE, MODE>::acc& acc) {
+  constexpr int STEP = G * U;
+  using V = typename Raw<DTYPE, MODE>::value;
+  if (end <= 0) return;
+  Pending<KIND, DTYPE, MODE, U> s;
+  if constexpr (PIPE) {
+    stage_a<KIND, DTYPE, MODE, G, U, true>(a, sscan, 0, glane, end, true, r0, r1, r2, s);
+    for (int base = 0; base < end; base += STEP) {
+      V dv[U];
+      bool use[U];
+      stage_b<KIND, DTYPE, MODE, U>(a, s, dv, use);
+      if (base + STEP < end)
+        stage_a<KIND, DTYPE, MODE, G, U, true>(a, sscan, base + STEP, glane, end, true, r0, r1, r2, s);
+      accumulate<DTYPE, MODE, U>(a, dv, use, acc);
+    }
+  } else {
+    for (int base = 0; base < end; base += STEP) {
+      V dv[U];
+      bool use[U];
+      stage_a<KIND, DTYPE, MODE, G, U, true>(a, sscan, base, glane, end, true, r0, r1, r2, s);
+      stage_b<KIND, DTYPE, MODE, U>(a, s, dv, use);
+      accumulate<DTYPE, MODE, U>(a, dv, use, acc);
+    }
+  }
+}
+
+// One bounds-checked step (chunk tails, partly valid groups).
+template <int KIND, int DTYPE, int MODE, int G, int U>
+__device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* __restrict__ sscan,
+                                             int base, int glane, int cnt, bool gvalid,
+                                             const float4& r0, const float4& r1, const float4& r2,
+                                             typename Raw<DTYPE, MODE>::acc& acc) {
+  Pending<KIND, DTYPE, MODE, U> s;
+  typename Raw<DTYPE, MODE>::value dv[U];
+  bool use[U];
+  stage_a<KIND, DTYPE, MODE, G, U, false>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, s);
+  stage_b<KIND, DTYPE, MODE, U>(a, s, dv, use);
+  accumulate<DTYPE, MODE, U>(a, dv, use, acc);
+}
+
+// Resident CTAs per SM the register allocation is held to: only the 8-deep
+// loop is capped (3 CTAs measured faster than the 2 its free allocation gives).
+template <int U>
+struct MinBlocks {
+  static constexpr int value = U == 8 ? 3 : 5;
+};
+
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+__global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const SensorArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float4* sscan = reinterpret_cast<float4*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)a.chunk * sizeof(float4));
+  const uint32_t bar_s = smem_addr(bar);
+
+  constexpr int GPW = 32 / G;  // groups per warp
+  constexpr int STEP = G * U;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gid = lane / G, glane = lane % G;
+  const int ngroups = (blockDim.x >> 5) * GPW;
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar_s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  int loaded = -1;
+  uint32_t parity = 0;
+  for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int c = (int)(item / a.nblk);
+    const int p0 = (int)(item % a.nblk) * a.ppi;
+    const int pn = min(a.ppi, a.P - p0);
+    const int j0 = c * a.chunk;
+    const int cnt = min(a.chunk, a.N - j0);
+
+    if (c != loaded) {  // uniform over the CTA: every thread walks the same items
+      __syncthreads();  // every group is done with the staged chunk
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(float4);
+        mbar_expect_tx(bar_s, bytes);
+        bulk_copy_g2s(smem_addr(sscan), a.scan + j0, bytes, bar_s);
+      }
+      const bool ok = mbar_wait_bounded(bar_s, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicOr(a.status, kDevErrTimeout);
+          mbar_wait_bounded(bar_s, parity ^ 1u);  // let an in-flight copy land
+        }
+        return;
+      }
+      loaded = c;
+    }
+
+    const int full_end = (cnt / STEP) * STEP;
+    for (int i0 = warp * GPW; i0 < pn; i0 += ngroups) {
+      const int i = i0 + gid;
+      const bool gvalid = i < pn;
+      if (G == 32 && !gvalid) continue;  // warp-uniform for whole-warp groups
+      const size_t p = (size_t)p0 + (gvalid ? i : 0);
+      const float4 r0 = __ldg(a.mats + 3 * p), r1 = __ldg(a.mats + 3 * p + 1),
+                   r2 = __ldg(a.mats + 3 * p + 2);
+      typename Raw<DTYPE, MODE>::acc acc = 0;
+      int base = 0;
+      if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
+        eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, full_end, glane, r0, r1, r2, acc);
+        base = full_end;
+      }
+      for (; base < cnt; base += STEP)
+        eval_checked<KIND, DTYPE, MODE, G, U>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, acc);
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1)
+        acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+      if (glane == 0 && gvalid) a.partial[(size_t)c * a.P + p] = __fmul_rn(acc, a.store_scale);
+    }
+  }
+}
+
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&k_sensor<KIND, DTYPE, MODE, G, U, PIPE>);
+}
+
+// Kernel for one storage type, or NULL for an unsupported shape. Shapes:
+// G = 32 with U = 2 or 4 (plain or pipelined) or U = 8 (plain); G = 16 or 8
+// with U = 4 (plain).
+template <int KIND, int DTYPE, int MODE>
+void* pick_shape(const SensorShape& sh) {
+  const bool pipe = sh.pipeline != 0;
+  if (sh.lanes == 32) {
+    if (sh.unroll == 2) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 2, true>()
+                                    : kernel_ptr<KIND, DTYPE, MODE, 32, 2, false>();
+    if (sh.unroll == 4) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 4, true>()
+                                    : kernel_ptr<KIND, DTYPE, MODE, 32, 4, false>();
+    if (sh.unroll == 8 && !pipe) return kernel_ptr<KIND, DTYPE, MODE, 32, 8, false>();
+    return nullptr;
+  }
+  if (pipe || sh.unroll != 4) return nullptr;
+  if (sh.lanes == 16) return kernel_ptr<KIND, DTYPE, MODE, 16, 4, false>();
+  if (sh.lanes == 8) return kernel_ptr<KIND, DTYPE, MODE, 8, 4, false>();
+  return nullptr;
+}
+
+template <int DTYPE>
+void* pick_dtype(int kind, int layout, int mode, const SensorShape& sh) {
+  if (kind == MCL_MAP_DENSE)
+    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_DENSE, DTYPE, MCL_LOGPROD>(sh)
+                               : pick_shape<MCL_MAP_DENSE, DTYPE, MCL_SUM>(sh);
+  if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_LINEAR)
+    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_BRICK, DTYPE, MCL_LOGPROD>(sh)
+                               : pick_shape<MCL_MAP_BRICK, DTYPE, MCL_SUM>(sh);
+  if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)
+    return mode == MCL_LOGPROD ? pick_shape<kKindBrickBlock4, DTYPE, MCL_LOGPROD>(sh)
+                               : pick_shape<kKindBrickBlock4, DTYPE, MCL_SUM>(sh);
+  return nullptr;
+}
+
+}  // namespace sensor
+}  // namespace mcl

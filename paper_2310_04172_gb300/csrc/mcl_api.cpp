@@ -190,6 +190,11 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     if (d->dims[k] <= 0 || d->dims[k] > (1 << 24))
       return fail(MCL_EINVAL, "map_create: dims[%d] = %lld outside [1, 2^24]", k, (long long)d->dims[k]);
   }
+  if (d->kind == MCL_MAP_BRICK && d->device_layout != MCL_LAYOUT_LINEAR &&
+      d->device_layout != MCL_LAYOUT_BLOCK4)
+    return fail(MCL_EINVAL, "map_create: device_layout %d", d->device_layout);
+  if (d->kind == MCL_MAP_DENSE && d->device_layout != MCL_LAYOUT_LINEAR)
+    return fail(MCL_EINVAL, "map_create: dense maps are stored linearly");
   float inv = d->inv_voxel == 0.f ? (float)(1.0 / (double)d->voxel) : d->inv_voxel;
   if (!finite_pos(inv)) return fail(MCL_EINVAL, "map_create: inv_voxel must be finite and > 0");
   const size_t es = d->dtype == MCL_F32 ? 4 : 2;
@@ -213,6 +218,7 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
   v.fnz = (float)v.nz;
   v.tau = d->truncation;
   v.scale = (float)((double)d->truncation / 32767.0);
+  v.layout = d->kind == MCL_MAP_BRICK ? d->device_layout : MCL_LAYOUT_LINEAR;
 
   auto cleanup = [&](mcl_status s) {
     if (m->d_values) cudaFree(m->d_values);
@@ -266,9 +272,27 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     const size_t vbytes = (size_t)nb * kBrickVoxels * es;
     cudaError_t e = cudaMalloc(&m->d_values, std::max(vbytes, (size_t)256));
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
-    if (vbytes) {
+    if (vbytes && v.layout == MCL_LAYOUT_LINEAR) {
       e = cudaMemcpy(m->d_values, host_values, vbytes, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
+    } else if (vbytes) {
+      // upload through a staging buffer and reorder each brick on the device
+      const int64_t per = std::min<int64_t>(nb, 1 << 16);
+      const size_t brick_bytes = (size_t)kBrickVoxels * es;
+      void* stage = nullptr;
+      e = cudaMalloc(&stage, (size_t)per * brick_bytes);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create staging"));
+      for (int64_t b0 = 0; b0 < nb && e == cudaSuccess; b0 += per) {
+        const int64_t cnt = std::min(per, nb - b0);
+        e = cudaMemcpy(stage, (const char*)host_values + (size_t)b0 * brick_bytes,
+                       (size_t)cnt * brick_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = launch_brick_to_block4(stage, (char*)m->d_values + (size_t)b0 * brick_bytes, cnt,
+                                     (int)es, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      }
+      cudaFree(stage);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create block layout"));
     }
     e = cudaMalloc(&m->d_table, (size_t)cap * sizeof(uint2));
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table"));
@@ -348,17 +372,26 @@ static mcl_status check_params(const mcl_sensor_params* p) {
   if (g != 0 && g != 8 && g != 16 && g != 32) return fail(MCL_EINVAL, "sensor params: lanes_per_particle %d", g);
   if (p->particles_per_item < 0 || p->particles_per_item > 4096)
     return fail(MCL_EINVAL, "sensor params: particles_per_item %d", p->particles_per_item);
-  if (p->unroll != 0 && p->unroll != 2 && p->unroll != 4)
+  if (p->unroll != 0 && p->unroll != 2 && p->unroll != 4 && p->unroll != 8)
     return fail(MCL_EINVAL, "sensor params: unroll %d", p->unroll);
+  if (p->pipeline < 0 || p->pipeline > 2) return fail(MCL_EINVAL, "sensor params: pipeline %d", p->pipeline);
+  if (p->particle_order < 0 || p->particle_order > 2)
+    return fail(MCL_EINVAL, "sensor params: particle_order %d", p->particle_order);
   return MCL_OK;
 }
 
 struct Plan {
   SensorShape sh;
   int K, nblk, blocks_per_sm, sms;
+  bool spatial;
   long long n_items;
-  size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, total;
+  size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, off_key, off_rank,
+      off_hist, total;
 };
+
+// Particles are evaluated in spatial order unless told otherwise (or too few
+// to matter).
+constexpr int64_t kSpatialOrderMinParticles = 4096;
 
 static mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p, Plan* pl) {
   DeviceState st;
@@ -366,12 +399,22 @@ static mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_
   SensorShape& sh = pl->sh;
   sh.chunk = p->points_per_chunk ? p->points_per_chunk : 2048;
   sh.lanes = p->lanes_per_particle ? p->lanes_per_particle : 32;
-  sh.ppi = p->particles_per_item ? p->particles_per_item : 64;
+  sh.ppi = p->particles_per_item ? p->particles_per_item : 128;
   sh.unroll = p->unroll ? p->unroll : 4;
+  sh.pipeline = p->pipeline == 2 ? 1 : 0;
+  // unroll and pipeline are hints: lane groups narrower than a warp run the
+  // plain 4-deep loop, and the pipelined loop exists for 2 or 4 look-ups.
+  if (sh.lanes < 32) {
+    sh.unroll = 4;
+    sh.pipeline = 0;
+  } else if (sh.unroll == 8) {
+    sh.pipeline = 0;
+  }
   sh.threads = 256;
   int bps = 0;
-  MCL_CUDA(sensor_occupancy(m->kind, m->dtype, sh, &bps));
+  MCL_CUDA(sensor_occupancy(m->kind, m->view.layout, m->dtype, p->mode, sh, &bps));
   if (bps < 1) return fail(MCL_EINVAL, "sensor plan: launch shape does not fit on an SM");
+  pl->spatial = p->particle_order == 2 || (p->particle_order == 0 && P >= kSpatialOrderMinParticles);
   pl->K = (int)((N + sh.chunk - 1) / sh.chunk);
   pl->nblk = (int)((P + sh.ppi - 1) / sh.ppi);
   pl->n_items = (long long)pl->K * pl->nblk;
@@ -391,6 +434,12 @@ static mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_
   o = align256(o + (size_t)normalise_blocks((int)P) * sizeof(float2));
   pl->off_ostats = o;
   o = align256(o + 2 * sizeof(float));
+  pl->off_key = o;
+  o = align256(o + (pl->spatial ? (size_t)P * sizeof(uint32_t) : 0));
+  pl->off_rank = o;
+  o = align256(o + (pl->spatial ? (size_t)P * sizeof(int) : 0));
+  pl->off_hist = o;
+  o = align256(o + (pl->spatial ? order_hist_bytes() : 0));
   pl->total = o;
   return MCL_OK;
 }
@@ -408,6 +457,8 @@ mcl_status mcl_sensor_plan_get(mcl_map_t m, int64_t P, int64_t N, const mcl_sens
   out->lanes_per_particle = pl.sh.lanes;
   out->particles_per_item = pl.sh.ppi;
   out->unroll = pl.sh.unroll;
+  out->pipeline = pl.sh.pipeline ? 2 : 1;
+  out->particle_order = pl.spatial ? 2 : 1;
   out->threads = pl.sh.threads;
   out->grid = pl.sh.grid;
   out->blocks_per_sm = pl.blocks_per_sm;
@@ -441,9 +492,13 @@ mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, con
   float* L = logw ? logw : (float*)(ws + pl.off_logw);
   float2* bstats = (float2*)(ws + pl.off_stats);
   float* ostats = (float*)(ws + pl.off_ostats);
+  int* rank = pl.spatial ? (int*)(ws + pl.off_rank) : nullptr;
   {
-    PhaseScope ps(MCL_PHASE_POSE, s);
-    MCL_CUDA(launch_pose_to_matrix(particles, (int)P, mats, s));
+    PhaseScope ps(MCL_PHASE_POSE, s, pl.spatial ? 4 : 1);
+    if (pl.spatial)
+      MCL_CUDA(launch_particle_order(particles, (int)P, m->view, (uint32_t*)(ws + pl.off_key),
+                                     (uint32_t*)(ws + pl.off_hist), rank, s));
+    MCL_CUDA(launch_pose_to_matrix(particles, (int)P, mats, rank, s));
   }
   {
     PhaseScope ps(MCL_PHASE_PACK, s);
@@ -465,17 +520,22 @@ mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, con
   a.n_items = pl.n_items;
   a.mode = p->mode;
   a.neglect = (p->flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
-  a.c = (float)(-0.5 / (sig * sig));
+  const float c = (float)(-0.5 / (sig * sig));
+  const bool q16 = m->dtype == MCL_I16;
+  const double scale = (double)m->view.scale;
+  a.vout = q16 ? 32767.0f : m->view.tau;
+  a.cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : c;
+  a.store_scale = (q16 && p->mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
   {
     PhaseScope ps(MCL_PHASE_SENSOR, s);
-    MCL_CUDA(launch_sensor(m->kind, m->dtype, a, pl.sh, s));
+    MCL_CUDA(launch_sensor(m->kind, m->view.layout, m->dtype, a, pl.sh, s));
   }
   const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
   const int nb = normalise_blocks((int)P);
   {
     PhaseScope ps(MCL_PHASE_REDUCE, s);
-    MCL_CUDA(launch_finish_and_normalise(partial, (int)P, pl.K, p->mode, a.c, k, L, nullptr, bstats,
-                                         nb, nullptr, s));
+    MCL_CUDA(launch_finish_and_normalise(partial, rank, (int)P, pl.K, p->mode, c, k, L, nullptr,
+                                         bstats, nb, nullptr, s));
   }
   if (w) {
     PhaseScope ps(MCL_PHASE_NORMALISE, s);
@@ -504,7 +564,7 @@ mcl_status mcl_pose_to_matrix(const float* particles, int64_t P, float* out_mat,
   if (!aligned(particles, 4) || !aligned(out_mat, 16))
     return fail(MCL_EINVAL, "pose_to_matrix: particles need 4-byte, out_mat 16-byte alignment");
   PhaseScope ps(MCL_PHASE_POSE, (cudaStream_t)stream);
-  MCL_CUDA(launch_pose_to_matrix(particles, (int)P, (float4*)out_mat, (cudaStream_t)stream));
+  MCL_CUDA(launch_pose_to_matrix(particles, (int)P, (float4*)out_mat, nullptr, (cudaStream_t)stream));
   return MCL_OK;
 }
 

@@ -15,6 +15,7 @@ constexpr int kBrick = 16;
 constexpr int kBrickVoxels = kBrick * kBrick * kBrick;
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+constexpr int kKindBrickBlock4 = 2;  // internal kind: brick map stored in 4x4x4 blocks
 
 // Bits of the per-device status word that kernels set instead of faulting.
 enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
@@ -33,6 +34,7 @@ struct MapView {
   int max_probe;        // longest probe sequence of a stored key (>= 1)
   float tau;            // truncation: value read where nothing is stored
   float scale;          // I16: tau / 32767 in FP32
+  int layout;           // BRICK: MCL_LAYOUT_LINEAR or MCL_LAYOUT_BLOCK4
 };
 
 // Fibonacci hashing of a brick-cell key (Knuth, TAOCP vol. 3, 6.4).
@@ -79,11 +81,19 @@ __device__ __forceinline__ float load_value(const MapView& m, size_t i) {
   }
 }
 
+// In-brick offset of local voxel (lx, ly, lz) in the 4x4x4-block layout:
+// block-major (block index z, y, x), each block z-major.
+__host__ __device__ inline uint32_t block4_local(uint32_t lx, uint32_t ly, uint32_t lz) {
+  return ((lz >> 2) << 10) | ((ly >> 2) << 8) | ((lx >> 2) << 6) | ((lz & 3u) << 4) |
+         ((ly & 3u) << 2) | (lx & 3u);
+}
+
 // Brick-cell key and in-brick offset of a voxel.
 __device__ __forceinline__ void brick_key(const MapView& m, int ix, int iy, int iz, uint32_t& key,
                                           uint32_t& local) {
   key = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
-  local = ((uint32_t)(iz & 15) * kBrick + (uint32_t)(iy & 15)) * kBrick + (uint32_t)(ix & 15);
+  const uint32_t lx = (uint32_t)ix & 15u, ly = (uint32_t)iy & 15u, lz = (uint32_t)iz & 15u;
+  local = m.layout == MCL_LAYOUT_BLOCK4 ? block4_local(lx, ly, lz) : ((lz * kBrick + ly) * kBrick + lx);
 }
 
 // Continue a probe sequence after a first entry that did not match. Bounded by
@@ -130,6 +140,7 @@ struct SensorShape {
   int lanes;      // lanes per particle (fixes the summation order)
   int ppi;        // particles per work item
   int unroll;     // points per lane per loop step
+  int pipeline;   // 1: next step's index look-ups overlap this step's gathers
   int threads;    // threads per CTA
   int grid;       // CTAs (persistent)
 };
@@ -143,20 +154,36 @@ struct SensorArgs {
   int P, N, chunk, K, ppi, nblk;
   long long n_items;
   int mode, neglect;
-  float c;             // -1 / (2 sigma^2)
+  float vout;          // value read where nothing is stored, in storage units (tau, or 32767 for I16)
+  float cs;            // SUM exponent constant in storage units: -1/(2 sigma^2) (* scale^2 for I16)
+  float store_scale;   // chunk sum -> real units: scale^2 for I16 in LOGPROD (sum of q^2), else 1
 };
 
-cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, cudaStream_t s);
+// Pose rows -> [R | t]; with rank, particle p's matrix goes to slot rank[p].
+cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
+                                  cudaStream_t s);
+
+// Spatial processing order (slot rank[p] of particle p), see k_order.cu.
+size_t order_hist_bytes();
+cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, uint32_t* key,
+                                  uint32_t* hist, int* rank, cudaStream_t s);
 cudaError_t launch_scan_pack(const float* scan, int N, float4* packed, cudaStream_t s);
-cudaError_t launch_sensor(int kind, int dtype, const SensorArgs& a, const SensorShape& sh,
-                          cudaStream_t s);
+cudaError_t launch_sensor(int kind, int layout, int dtype, const SensorArgs& a,
+                          const SensorShape& sh, cudaStream_t s);
 int sensor_smem_bytes(const SensorShape& sh);
-cudaError_t sensor_occupancy(int kind, int dtype, const SensorShape& sh, int* blocks_per_sm);
+cudaError_t sensor_occupancy(int kind, int layout, int dtype, int mode, const SensorShape& sh,
+                             int* blocks_per_sm);
+
+// Map upload helper: x-fastest bricks (src) -> 4x4x4-block layout (dst).
+cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_bricks, int elem_bytes,
+                                   cudaStream_t s);
 
 // Finishing pass: L_p from the chunk partials, then block max / sum-exp.
-cudaError_t launch_finish_and_normalise(const float* partial, int P, int K, int mode, float c,
-                                        float k, float* logw, float* w, float2* block_stats,
-                                        int nblocks, float* out_stats, cudaStream_t s);
+// With rank, particle p's chunk sums sit in slot rank[p] of partial.
+cudaError_t launch_finish_and_normalise(const float* partial, const int* rank, int P, int K,
+                                        int mode, float c, float k, float* logw, float* w,
+                                        float2* block_stats, int nblocks, float* out_stats,
+                                        cudaStream_t s);
 cudaError_t launch_normalise(const float* logw, int P, float* w, float2* block_stats, int nblocks,
                              float* out_stats, cudaStream_t s);
 int normalise_blocks(int P);

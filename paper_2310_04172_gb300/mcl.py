@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libmcl.so")
 MCL_OK, MCL_EINVAL, MCL_ENOMEM, MCL_EBUSY, MCL_ETIMEDOUT, MCL_ECUDA, MCL_EINTERNAL = range(7)
 MCL_MAP_DENSE, MCL_MAP_BRICK = 0, 1
 MCL_F32, MCL_F16, MCL_I16 = 0, 1, 2
+MCL_LAYOUT_LINEAR, MCL_LAYOUT_BLOCK4 = 0, 1
 MCL_LOGPROD, MCL_SUM = 0, 1
 MCL_NEGLECT_OUTSIDE = 1
 PHASES = ("pose", "pack", "sensor", "reduce", "normalise", "resample", "motion", "other")
@@ -32,7 +33,8 @@ class mcl_map_desc(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("kind", _i32), ("dtype", _i32),
                 ("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float),
                 ("inv_voxel", ctypes.c_float), ("truncation", ctypes.c_float),
-                ("dims", _i64 * 3), ("n_bricks", _i64), ("brick_coords", _c_void_p)]
+                ("dims", _i64 * 3), ("n_bricks", _i64), ("brick_coords", _c_void_p),
+                ("device_layout", _i32), ("reserved", _i32)]
 
 
 class mcl_map_info(ctypes.Structure):
@@ -43,12 +45,14 @@ class mcl_map_info(ctypes.Structure):
 class mcl_sensor_params(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("sigma_hit", ctypes.c_float), ("mode", _i32),
                 ("flags", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
-                ("particles_per_item", _i32), ("unroll", _i32)]
+                ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
+                ("particle_order", _i32)]
 
 
 class mcl_sensor_plan(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
-                ("particles_per_item", _i32), ("unroll", _i32), ("threads", _i32), ("grid", _i32),
+                ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
+                ("particle_order", _i32), ("threads", _i32), ("grid", _i32),
                 ("blocks_per_sm", _i32), ("num_sms", _i32), ("n_items", _i64),
                 ("workspace_bytes", _i64)]
 
@@ -174,7 +178,7 @@ class Map:
 
 def mcl_map_create(kind: int, dtype: int, origin, voxel: float, truncation: float, dims,
                    values: np.ndarray, brick_coords: np.ndarray | None = None,
-                   inv_voxel: float = 0.0) -> Map:
+                   inv_voxel: float = 0.0, device_layout: int = MCL_LAYOUT_LINEAR) -> Map:
     """Upload a dense or brick TSDF (host arrays) to the current device."""
     values = np.ascontiguousarray(values)
     d = mcl_map_desc(struct_size=ctypes.sizeof(mcl_map_desc), kind=kind, dtype=dtype)
@@ -187,18 +191,20 @@ def mcl_map_create(kind: int, dtype: int, origin, voxel: float, truncation: floa
         keep.append(bc)
         d.n_bricks = len(bc)
         d.brick_coords = bc.ctypes.data_as(ctypes.c_void_p)
+        d.device_layout = device_layout
     h = ctypes.c_void_p()
     _check(lib().mcl_map_create(ctypes.byref(d), values.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
     return Map(h, d)
 
 
-def map_from_scene(m) -> Map:
+def map_from_scene(m, device_layout: int = MCL_LAYOUT_LINEAR) -> Map:
     """Upload a ``scenes.DenseMap`` / ``scenes.BrickMap`` (input generator objects)."""
     if m.kind == "dense":
         return mcl_map_create(MCL_MAP_DENSE, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
                               m.dims, m.values, inv_voxel=m.inv_voxel)
     return mcl_map_create(MCL_MAP_BRICK, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
-                          m.dims, m.values, m.coords, inv_voxel=m.inv_voxel)
+                          m.dims, m.values, m.coords, inv_voxel=m.inv_voxel,
+                          device_layout=device_layout)
 
 
 def mcl_map_destroy(m: Map):
@@ -220,11 +226,13 @@ def mcl_map_lookup(m: Map, points, out_index=None, out_value=None, stream=None):
 
 def sensor_params(sigma_hit: float = 0.1, mode: int = MCL_LOGPROD, flags: int = 0,
                   points_per_chunk: int = 0, lanes_per_particle: int = 0,
-                  particles_per_item: int = 0, unroll: int = 0) -> mcl_sensor_params:
+                  particles_per_item: int = 0, unroll: int = 0,
+                  pipeline: int = 0, particle_order: int = 0) -> mcl_sensor_params:
     return mcl_sensor_params(struct_size=ctypes.sizeof(mcl_sensor_params), sigma_hit=sigma_hit,
                              mode=mode, flags=flags, points_per_chunk=points_per_chunk,
                              lanes_per_particle=lanes_per_particle,
-                             particles_per_item=particles_per_item, unroll=unroll)
+                             particles_per_item=particles_per_item, unroll=unroll,
+                             pipeline=pipeline, particle_order=particle_order)
 
 
 def mcl_sensor_update(m: Map, particles, scan, params: mcl_sensor_params, logw=None, w=None,

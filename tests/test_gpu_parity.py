@@ -114,16 +114,25 @@ def lookup_points(rng, m, n=200_000):
     return pts
 
 
-@pytest.mark.parametrize("kind", ["dense", "brick"])
+KINDS = ["dense", "brick", "brick_block4"]
+
+
+def upload(mcl, sm, kind):
+    return mcl.map_from_scene(sm, mcl.MCL_LAYOUT_BLOCK4 if kind == "brick_block4" else 0)
+
+
+def room_map(sc, kind, dtype):
+    if kind == "dense":
+        return scenes.voxelize_dense(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
+    return scenes.voxelize_bricks(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
+
+
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16, scenes.I16])
 def test_map_lookup_bit_exact(torch_cuda, mcl, kind, dtype):
     torch = torch_cuda
-    sc = scenes.room(1)
-    if kind == "dense":
-        sm = scenes.voxelize_dense(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
-    else:
-        sm = scenes.voxelize_bricks(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
-    m = mcl.map_from_scene(sm)
+    sm = room_map(scenes.room(1), kind, dtype)
+    m = upload(mcl, sm, kind)
     pts = lookup_points(np.random.default_rng(2), sm)
     idx, val = mcl.mcl_map_lookup(m, dev(torch, pts))
     mcl.mcl_sync()
@@ -138,18 +147,14 @@ def test_map_lookup_bit_exact(torch_cuda, mcl, kind, dtype):
 
 
 # ----------------------------------------------------------------- a1-a8: sensor update + normalise
-@pytest.mark.parametrize("kind", ["dense", "brick"])
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16, scenes.I16])
 @pytest.mark.parametrize("mode", [oracle.LOGPROD, oracle.SUM])
 @pytest.mark.parametrize("neglect", [False, True])
 def test_sensor_update_room(torch_cuda, mcl, room, kind, dtype, mode, neglect):
     torch = torch_cuda
-    sc = room.scene
-    if kind == "dense":
-        sm = scenes.voxelize_dense(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
-    else:
-        sm = scenes.voxelize_bricks(sc, (0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, dtype)
-    m = mcl.map_from_scene(sm)
+    sm = room_map(room.scene, kind, dtype)
+    m = upload(mcl, sm, kind)
     parts = room.particles.copy()
     parts[:50, :3] += np.float32(4.0)  # some particles see much of the scan outside the map
     Lg, wg = run_sensor(torch, mcl, m, parts, room.scan, room.sigma_hit, mode,
@@ -163,7 +168,7 @@ def test_sensor_update_room(torch_cuda, mcl, room, kind, dtype, mode, neglect):
 
 @pytest.mark.parametrize("chunk,lanes,unroll,ppi", [
     (32, 32, 2, 1), (64, 8, 4, 7), (256, 16, 2, 64), (1024, 32, 4, 500), (2048, 8, 2, 33),
-    (8192, 32, 4, 64), (4096, 16, 4, 128)])
+    (8192, 32, 4, 64), (4096, 16, 4, 128), (2048, 32, 8, 64), (512, 16, 8, 9)])
 def test_sensor_update_launch_shapes_and_ragged_tails(torch_cuda, mcl, room, chunk, lanes, unroll, ppi):
     torch = torch_cuda
     m = mcl.map_from_scene(room.map)
@@ -176,7 +181,7 @@ def test_sensor_update_launch_shapes_and_ragged_tails(torch_cuda, mcl, room, chu
     check_w(wg, Lo, oracle.LOGPROD)
     # the launch hints (particles per item, unroll) never change the summation order
     other = dict(points_per_chunk=chunk, lanes_per_particle=lanes,
-                 unroll=6 - unroll, particles_per_item=max(1, ppi // 3))
+                 unroll={2: 4, 4: 8, 8: 2}[unroll], particles_per_item=max(1, ppi // 3))
     Lg2, wg2 = run_sensor(torch, mcl, m, parts, scan, room.sigma_hit, **other)
     assert np.array_equal(Lg, Lg2) and np.array_equal(wg, wg2)
     m.close()
@@ -227,16 +232,44 @@ def building_i16():
     return scenes.os064_building(P=1_000_000, dtype=scenes.I16)
 
 
-def test_building_os064_parity_subset(torch_cuda, mcl, building_i16):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_building_os064_parity_subset(torch_cuda, mcl, building_i16, layout):
     torch = torch_cuda
     wl = building_i16
-    m = mcl.map_from_scene(wl.map)
+    m = mcl.map_from_scene(wl.map, layout)
     parts = wl.particles[:3000]
     Lg, wg = run_sensor(torch, mcl, m, parts, wl.scan, wl.sigma_hit)
     Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), parts, wl.scan, wl.sigma_hit)
     check_logw(Lg, Lo)
     check_w(wg, Lo, oracle.LOGPROD)
     m.close()
+
+
+def test_particle_order_gives_identical_bits(torch_cuda, mcl, room, building_i16):
+    """Spatial processing order moves particles between slots, never changes a result."""
+    torch = torch_cuda
+    for sm, parts, scan in ((room.map, room.particles, room.scan),
+                            (building_i16.map, building_i16.particles[:20000], building_i16.scan)):
+        m = mcl.map_from_scene(sm)
+        a = run_sensor(torch, mcl, m, parts, scan, 0.1, particle_order=1)
+        b = run_sensor(torch, mcl, m, parts, scan, 0.1, particle_order=2)
+        c = run_sensor(torch, mcl, m, parts, scan, 0.1, particle_order=2, pipeline=2)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
+        m.close()
+
+
+def test_brick_layouts_give_identical_bits(torch_cuda, mcl, room):
+    """The device layout only moves values: same reads, same sums, same bits."""
+    torch = torch_cuda
+    for dtype in (scenes.F32, scenes.F16, scenes.I16):
+        sm = room_map(room.scene, "brick", dtype)
+        res = []
+        for layout in (0, 1):
+            m = mcl.map_from_scene(sm, layout)
+            res.append(run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit))
+            m.close()
+        assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
 def test_building_full_size_sampled(torch_cuda, mcl, building_i16):
@@ -343,7 +376,8 @@ def test_invalid_arguments_are_refused(torch_cuda, mcl, room):
     logw = torch.empty(len(parts), device="cuda")
     L = mcl.lib()
     for bad in [dict(sigma_hit=0.0), dict(sigma_hit=float("nan")), dict(mode=7), dict(flags=8),
-                dict(points_per_chunk=48), dict(lanes_per_particle=12), dict(unroll=3)]:
+                dict(points_per_chunk=48), dict(lanes_per_particle=12), dict(unroll=3),
+                dict(unroll=16), dict(pipeline=3), dict(particle_order=5)]:
         kw = dict(sigma_hit=0.1)
         kw.update(bad)
         with pytest.raises(mcl.MclError) as e:
