@@ -193,6 +193,22 @@ def measured_traffic(P: int, N: int):
     return rec["dram_bytes_per_eval"] * P * N
 
 
+def gather_source_digest() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", "k_gather_bench.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def gather_dram_bytes():
+    """DRAM bytes one uniform-random gather moves (ncu, committed summary), or None."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "gather_dram_bytes.json")))
+    except (OSError, ValueError):
+        return None
+    return rec["dram_bytes_per_gather"] if rec.get("kernel_digest") == gather_source_digest() else None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
@@ -366,6 +382,14 @@ def run_ours(args):
     gather = None
     if not args.no_gather:
         gather = gather_roofline(torch, mcl, dev, stream, int(wl.map.values.nbytes), elem, value)
+        per_gather = gather_dram_bytes()
+        if traffic is not None and per_gather is not None:
+            # DRAM-traffic form: the sensor kernel's DRAM bytes/s against the DRAM
+            # bytes/s that uniform-random gathers sustain at the map footprint
+            sensor_gbs = traffic / (sensor_ms / 1e3) / 1e9
+            gather_gbs = gather["map_footprint"]["gathers_per_s"] * per_gather / 1e9
+            gather.update({"dram_bytes_per_gather": per_gather, "gather_dram_gbs": gather_gbs,
+                           "sensor_dram_gbs": sensor_gbs, "frac_dram": sensor_gbs / gather_gbs})
 
     # end to end through the C ABI with host buffers (pinned), copies in the region
     e2e = None
