@@ -254,6 +254,74 @@ mcl_status mcl_motion_update(float* particles, int64_t P, const float delta[6],
                              const float sigma[6], uint64_t seed, uint64_t step,
                              mcl_stream_t stream);
 
+/* ------------------------------------------------------------------ batched update */
+
+/* One session of a batched step: a robot's particle set and its latest scan
+ * against its map, with the outputs of mcl_sensor_update and, if
+ * resample_idx is not NULL, of mcl_resample (offset set per run with
+ * mcl_batch_set_offsets). All pointers are device pointers that stay fixed
+ * for the life of the batch; the caller writes new particles and scans into
+ * the same buffers between runs. */
+typedef struct mcl_session_update {
+  uint32_t struct_size;    /* sizeof(mcl_session_update) */
+  mcl_map_t map;
+  const float* particles;  /* P x 6 */
+  int64_t P;
+  const float* scan;       /* N x 3 */
+  int64_t N;
+  float sigma_hit;
+  int32_t mode;            /* MCL_LOGPROD or MCL_SUM */
+  uint32_t flags;          /* MCL_NEGLECT_OUTSIDE or 0 */
+  float* logw;             /* P, may be NULL if w is not */
+  float* w;                /* P, may be NULL */
+  int32_t* resample_idx;   /* P, NULL: no resampling */
+  float* particles_out;    /* P x 6, NULL: indices only (must not alias particles) */
+} mcl_session_update;
+
+/* Shape of a batched step. points_per_chunk and lanes_per_particle fix the
+ * summation order as in mcl_sensor_params: every session's results equal
+ * those of mcl_sensor_update with the same two values. use_graph = 1
+ * captures the whole step into a CUDA graph at the first run and replays it
+ * afterwards (the plan owns all scratch, so the graph stays valid). */
+typedef struct mcl_batch_params {
+  uint32_t struct_size;
+  int32_t points_per_chunk, lanes_per_particle, particles_per_item, unroll, pipeline;
+  int32_t particle_order;
+  int32_t use_graph;
+} mcl_batch_params;
+
+typedef struct mcl_batch_s* mcl_batch_t;
+
+/* Plans a batched step over n sessions (Sec. V-B: every particle evaluated
+ * in parallel, here across robots too): sessions are grouped by map and score
+ * constants; each group runs as one persistent kernel over (session, point
+ * chunk, particle block) work items of uneven size. Allocates the plan's
+ * device scratch. EINVAL for any invalid session (as mcl_sensor_update). */
+mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
+                            const mcl_batch_params* params, mcl_batch_t* out);
+
+/* Resampling offsets r_s in [0, 1) for the next runs (host array of n, in
+ * session order), copied to the device on `stream`. */
+mcl_status mcl_batch_set_offsets(mcl_batch_t b, const double* r, mcl_stream_t stream);
+
+/* Enqueues one step for every session on `stream`: pose matrices, scan
+ * packing, the grouped sensor kernels, log-weights, normalisation and the
+ * requested resampling. */
+mcl_status mcl_batch_run(mcl_batch_t b, mcl_stream_t stream);
+
+/* Work items and launches of the plan (for reporting). */
+typedef struct mcl_batch_info {
+  uint32_t struct_size;
+  int32_t n_sessions, n_groups;
+  int64_t n_items, total_evals, workspace_bytes;
+  int32_t kernels_per_run, graph_captured;
+} mcl_batch_info;
+
+mcl_status mcl_batch_get_info(mcl_batch_t b, mcl_batch_info* out);
+
+/* Waits for the plan's work on every stream, frees its scratch and graph. */
+mcl_status mcl_batch_destroy(mcl_batch_t b);
+
 /* ------------------------------------------------------------------ gather roofline */
 
 /* Microbenchmark of the map look-up pattern (Sec. VI-C: random TSDF reads

@@ -128,10 +128,11 @@ __global__ void __launch_bounds__(kRT) k_tile_offsets(double* __restrict__ tile_
 
 __global__ void k_systematic(const double* __restrict__ cum, const double* __restrict__ tile_off,
                              const long long* __restrict__ tile_last, int P, int ntiles, double r,
-                             int32_t* __restrict__ idx, const float* __restrict__ pin,
-                             float* __restrict__ pout) {
+                             const double* __restrict__ r_dev, int32_t* __restrict__ idx,
+                             const float* __restrict__ pin, float* __restrict__ pout) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P) return;
+  if (r_dev) r = *r_dev;
   const double S = tile_off[ntiles];
   int res;
   if (!(S > 0.0)) {
@@ -215,15 +216,16 @@ cudaError_t launch_resample_static(const float* w, int P, double r, int32_t* idx
 
 cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             const float* particles_in, float* particles_out, double* cum,
-                            double* tile_total, long long* tile_last, cudaStream_t s) {
+                            double* tile_total, long long* tile_last, cudaStream_t s,
+                            const double* r_dev) {
   const int ntiles = resample_tiles(P);
   k_tile_scan<<<ntiles, kRT, 0, s>>>(w, P, cum, tile_total, tile_last);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_tile_offsets<<<1, kRT, 0, s>>>(tile_total, tile_last, ntiles);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_systematic<<<(P + 255) / 256, 256, 0, s>>>(cum, tile_total, tile_last, P, ntiles, r, idx,
-                                               particles_in, particles_out);
+  k_systematic<<<(P + 255) / 256, 256, 0, s>>>(cum, tile_total, tile_last, P, ntiles, r, r_dev,
+                                               idx, particles_in, particles_out);
   return cudaGetLastError();
 }
 

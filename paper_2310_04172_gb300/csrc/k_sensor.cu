@@ -25,16 +25,16 @@
 
 namespace mcl {
 
-void* sensor_kernel_f32(int kind, int layout, int mode, const SensorShape& sh);
-void* sensor_kernel_f16(int kind, int layout, int mode, const SensorShape& sh);
-void* sensor_kernel_i16(int kind, int layout, int mode, const SensorShape& sh);
+void* sensor_kernel_f32(int kind, int layout, int mode, const SensorShape& sh, bool batch);
+void* sensor_kernel_f16(int kind, int layout, int mode, const SensorShape& sh, bool batch);
+void* sensor_kernel_i16(int kind, int layout, int mode, const SensorShape& sh, bool batch);
 
 namespace {
 
-void* pick(int kind, int layout, int dtype, int mode, const SensorShape& sh) {
-  if (dtype == MCL_F32) return sensor_kernel_f32(kind, layout, mode, sh);
-  if (dtype == MCL_F16) return sensor_kernel_f16(kind, layout, mode, sh);
-  if (dtype == MCL_I16) return sensor_kernel_i16(kind, layout, mode, sh);
+void* pick(int kind, int layout, int dtype, int mode, const SensorShape& sh, bool batch = false) {
+  if (dtype == MCL_F32) return sensor_kernel_f32(kind, layout, mode, sh, batch);
+  if (dtype == MCL_F16) return sensor_kernel_f16(kind, layout, mode, sh, batch);
+  if (dtype == MCL_I16) return sensor_kernel_i16(kind, layout, mode, sh, batch);
   return nullptr;
 }
 
@@ -67,6 +67,27 @@ cudaError_t launch_sensor(int kind, int layout, int dtype, const SensorArgs& a,
   cudaError_t e = prepare(f, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<SensorArgs*>(&a)};
+  return cudaLaunchKernel(f, dim3(sh.grid), dim3(sh.threads), args, (size_t)smem, s);
+}
+
+cudaError_t sensor_batch_occupancy(int kind, int layout, int dtype, int mode, const SensorShape& sh,
+                                   int* blocks_per_sm) {
+  void* f = pick(kind, layout, dtype, mode, sh, true);
+  if (!f) return cudaErrorInvalidValue;
+  const int smem = sensor_smem_bytes(sh);
+  cudaError_t e = prepare(f, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, sh.threads, smem);
+}
+
+cudaError_t launch_sensor_batch(int kind, int layout, int dtype, const BatchArgs& b,
+                                const SensorShape& sh, cudaStream_t s) {
+  void* f = pick(kind, layout, dtype, b.base.mode, sh, true);
+  if (!f) return cudaErrorInvalidValue;
+  const int smem = sensor_smem_bytes(sh);
+  cudaError_t e = prepare(f, smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<BatchArgs*>(&b)};
   return cudaLaunchKernel(f, dim3(sh.grid), dim3(sh.threads), args, (size_t)smem, s);
 }
 

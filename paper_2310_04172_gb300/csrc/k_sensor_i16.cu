@@ -4,8 +4,8 @@
 
 namespace mcl {
 
-void* sensor_kernel_i16(int kind, int layout, int mode, const SensorShape& sh) {
-  return sensor::pick_dtype<MCL_I16>(kind, layout, mode, sh);
+void* sensor_kernel_i16(int kind, int layout, int mode, const SensorShape& sh, bool batch) {
+  return sensor::pick_dtype<MCL_I16>(kind, layout, mode, sh, batch);
 }
 
 }  // namespace mcl

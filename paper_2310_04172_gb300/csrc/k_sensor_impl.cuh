@@ -254,114 +254,166 @@ struct MinBlocks {
   static constexpr int value = U == 8 ? 3 : 5;
 };
 
-template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
-__global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const SensorArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  float4* sscan = reinterpret_cast<float4*>(smem);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)a.chunk * sizeof(float4));
-  const uint32_t bar_s = smem_addr(bar);
+// Stage `cnt` scan points starting at `src` into shared memory with one bulk
+// copy; every thread of the CTA calls this. Returns false (after recording the
+// error and letting an in-flight copy land) if the bounded wait ran out.
+__device__ __forceinline__ bool stage_chunk(float4* sscan, uint32_t bar_s, const float4* src,
+                                            int cnt, uint32_t& parity, unsigned* status) {
+  __syncthreads();  // every group is done with the previous chunk
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(float4);
+    mbar_expect_tx(bar_s, bytes);
+    bulk_copy_g2s(smem_addr(sscan), src, bytes, bar_s);
+  }
+  const bool ok = mbar_wait_bounded(bar_s, parity);
+  parity ^= 1u;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, kDevErrTimeout);
+      mbar_wait_bounded(bar_s, parity ^ 1u);
+    }
+    return false;
+  }
+  return true;
+}
 
+// Particles [p0, p0 + pn) of one session against the staged chunk c (cnt
+// points): each lane group takes a particle, sums its chunk terms and writes
+// the chunk sum to partial[c * P + p].
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+__device__ __forceinline__ void process_block(const SensorArgs& a, const float4* __restrict__ sscan,
+                                              const float4* __restrict__ mats,
+                                              float* __restrict__ partial, int P, int c, int p0,
+                                              int pn, int cnt) {
   constexpr int GPW = 32 / G;  // groups per warp
   constexpr int STEP = G * U;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gid = lane / G, glane = lane % G;
   const int ngroups = (blockDim.x >> 5) * GPW;
+  const int full_end = (cnt / STEP) * STEP;
+  for (int i0 = warp * GPW; i0 < pn; i0 += ngroups) {
+    const int i = i0 + gid;
+    const bool gvalid = i < pn;
+    if (G == 32 && !gvalid) continue;  // warp-uniform for whole-warp groups
+    const size_t p = (size_t)p0 + (gvalid ? i : 0);
+    const float4 r0 = __ldg(mats + 3 * p), r1 = __ldg(mats + 3 * p + 1), r2 = __ldg(mats + 3 * p + 2);
+    typename Raw<DTYPE, MODE>::acc acc = 0;
+    int base = 0;
+    if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
+      eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, full_end, glane, r0, r1, r2, acc);
+      base = full_end;
+    }
+    for (; base < cnt; base += STEP)
+      eval_checked<KIND, DTYPE, MODE, G, U>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, acc);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+      acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+    if (glane == 0 && gvalid) partial[(size_t)c * P + p] = __fmul_rn(acc, a.store_scale);
+  }
+}
 
+__device__ __forceinline__ void init_barrier(uint32_t bar_s) {
   if (threadIdx.x == 0) {
     mbar_init(bar_s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+}
 
+// One session: items (chunk c, particle block) strided over a persistent grid.
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+__global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const SensorArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float4* sscan = reinterpret_cast<float4*>(smem);
+  const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
+  init_barrier(bar_s);
   int loaded = -1;
   uint32_t parity = 0;
   for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int c = (int)(item / a.nblk);
     const int p0 = (int)(item % a.nblk) * a.ppi;
     const int pn = min(a.ppi, a.P - p0);
-    const int j0 = c * a.chunk;
-    const int cnt = min(a.chunk, a.N - j0);
-
+    const int cnt = min(a.chunk, a.N - c * a.chunk);
     if (c != loaded) {  // uniform over the CTA: every thread walks the same items
-      __syncthreads();  // every group is done with the staged chunk
-      if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(float4);
-        mbar_expect_tx(bar_s, bytes);
-        bulk_copy_g2s(smem_addr(sscan), a.scan + j0, bytes, bar_s);
-      }
-      const bool ok = mbar_wait_bounded(bar_s, parity);
-      parity ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-          atomicOr(a.status, kDevErrTimeout);
-          mbar_wait_bounded(bar_s, parity ^ 1u);  // let an in-flight copy land
-        }
-        return;
-      }
+      if (!stage_chunk(sscan, bar_s, a.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
       loaded = c;
     }
+    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, a.mats, a.partial, a.P, c, p0, pn, cnt);
+  }
+}
 
-    const int full_end = (cnt / STEP) * STEP;
-    for (int i0 = warp * GPW; i0 < pn; i0 += ngroups) {
-      const int i = i0 + gid;
-      const bool gvalid = i < pn;
-      if (G == 32 && !gvalid) continue;  // warp-uniform for whole-warp groups
-      const size_t p = (size_t)p0 + (gvalid ? i : 0);
-      const float4 r0 = __ldg(a.mats + 3 * p), r1 = __ldg(a.mats + 3 * p + 1),
-                   r2 = __ldg(a.mats + 3 * p + 2);
-      typename Raw<DTYPE, MODE>::acc acc = 0;
-      int base = 0;
-      if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
-        eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, full_end, glane, r0, r1, r2, acc);
-        base = full_end;
-      }
-      for (; base < cnt; base += STEP)
-        eval_checked<KIND, DTYPE, MODE, G, U>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, acc);
-#pragma unroll
-      for (int off = G / 2; off > 0; off >>= 1)
-        acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
-      if (glane == 0 && gvalid) a.partial[(size_t)c * a.P + p] = __fmul_rn(acc, a.store_scale);
+// Many sessions on one map with one set of score constants: items (session,
+// chunk, particle block) of uneven sizes, numbered session by session
+// (item_begin[s] is the first item of session s), strided over a persistent
+// grid. Each session's results are the ones the single-session kernel gives.
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+__global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor_batch(const BatchArgs b) {
+  const SensorArgs& a = b.base;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float4* sscan = reinterpret_cast<float4*>(smem);
+  const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
+  init_barrier(bar_s);
+  long long loaded = -1;
+  uint32_t parity = 0;
+  for (long long item = blockIdx.x; item < b.n_items; item += gridDim.x) {
+    int lo = 0, hi = b.n_sessions - 1;  // session whose item range holds `item`
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(b.item_begin + mid) <= item) lo = mid; else hi = mid - 1;
     }
+    const BatchSession S = b.sessions[lo];
+    const long long local = item - __ldg(b.item_begin + lo);
+    const int c = (int)(local / S.nblk);
+    const int p0 = (int)(local % S.nblk) * a.ppi;
+    const int pn = min(a.ppi, S.P - p0);
+    const int cnt = min(a.chunk, S.N - c * a.chunk);
+    const long long key = ((long long)lo << 32) | (unsigned)c;
+    if (key != loaded) {
+      if (!stage_chunk(sscan, bar_s, S.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
+      loaded = key;
+    }
+    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, S.mats, S.partial, S.P, c, p0, pn, cnt);
   }
 }
 
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
-void* kernel_ptr() {
-  return reinterpret_cast<void*>(&k_sensor<KIND, DTYPE, MODE, G, U, PIPE>);
+void* kernel_ptr(bool batch) {
+  return batch ? reinterpret_cast<void*>(&k_sensor_batch<KIND, DTYPE, MODE, G, U, PIPE>)
+               : reinterpret_cast<void*>(&k_sensor<KIND, DTYPE, MODE, G, U, PIPE>);
 }
 
 // Kernel for one storage type, or NULL for an unsupported shape. Shapes:
 // G = 32 with U = 2 or 4 (plain or pipelined) or U = 8 (plain); G = 16 or 8
 // with U = 4 (plain).
 template <int KIND, int DTYPE, int MODE>
-void* pick_shape(const SensorShape& sh) {
+void* pick_shape(const SensorShape& sh, bool batch) {
   const bool pipe = sh.pipeline != 0;
   if (sh.lanes == 32) {
-    if (sh.unroll == 2) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 2, true>()
-                                    : kernel_ptr<KIND, DTYPE, MODE, 32, 2, false>();
-    if (sh.unroll == 4) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 4, true>()
-                                    : kernel_ptr<KIND, DTYPE, MODE, 32, 4, false>();
-    if (sh.unroll == 8 && !pipe) return kernel_ptr<KIND, DTYPE, MODE, 32, 8, false>();
+    if (sh.unroll == 2) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 2, true>(batch)
+                                    : kernel_ptr<KIND, DTYPE, MODE, 32, 2, false>(batch);
+    if (sh.unroll == 4) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 4, true>(batch)
+                                    : kernel_ptr<KIND, DTYPE, MODE, 32, 4, false>(batch);
+    if (sh.unroll == 8 && !pipe) return kernel_ptr<KIND, DTYPE, MODE, 32, 8, false>(batch);
     return nullptr;
   }
   if (pipe || sh.unroll != 4) return nullptr;
-  if (sh.lanes == 16) return kernel_ptr<KIND, DTYPE, MODE, 16, 4, false>();
-  if (sh.lanes == 8) return kernel_ptr<KIND, DTYPE, MODE, 8, 4, false>();
+  if (sh.lanes == 16) return kernel_ptr<KIND, DTYPE, MODE, 16, 4, false>(batch);
+  if (sh.lanes == 8) return kernel_ptr<KIND, DTYPE, MODE, 8, 4, false>(batch);
   return nullptr;
 }
 
 template <int DTYPE>
-void* pick_dtype(int kind, int layout, int mode, const SensorShape& sh) {
+void* pick_dtype(int kind, int layout, int mode, const SensorShape& sh, bool batch) {
   if (kind == MCL_MAP_DENSE)
-    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_DENSE, DTYPE, MCL_LOGPROD>(sh)
-                               : pick_shape<MCL_MAP_DENSE, DTYPE, MCL_SUM>(sh);
+    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_DENSE, DTYPE, MCL_LOGPROD>(sh, batch)
+                               : pick_shape<MCL_MAP_DENSE, DTYPE, MCL_SUM>(sh, batch);
   if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_LINEAR)
-    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_BRICK, DTYPE, MCL_LOGPROD>(sh)
-                               : pick_shape<MCL_MAP_BRICK, DTYPE, MCL_SUM>(sh);
+    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_BRICK, DTYPE, MCL_LOGPROD>(sh, batch)
+                               : pick_shape<MCL_MAP_BRICK, DTYPE, MCL_SUM>(sh, batch);
   if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)
-    return mode == MCL_LOGPROD ? pick_shape<kKindBrickBlock4, DTYPE, MCL_LOGPROD>(sh)
-                               : pick_shape<kKindBrickBlock4, DTYPE, MCL_SUM>(sh);
+    return mode == MCL_LOGPROD ? pick_shape<kKindBrickBlock4, DTYPE, MCL_LOGPROD>(sh, batch)
+                               : pick_shape<kKindBrickBlock4, DTYPE, MCL_SUM>(sh, batch);
   return nullptr;
 }
 

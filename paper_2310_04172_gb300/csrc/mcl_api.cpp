@@ -12,13 +12,13 @@
 #include <utility>
 #include <vector>
 
-#include "mcl_internal.h"
+#include "runtime.h"
 
-using namespace mcl;
+namespace mcl {
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
 mcl_status fail(mcl_status s, const char* fmt, ...) {
   char buf[512];
@@ -36,22 +36,11 @@ mcl_status cuda_fail(cudaError_t e, const char* what) {
   return fail(MCL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define MCL_CUDA(call)                                  \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-constexpr int64_t kMaxCount = 2147483647LL;
-
-struct DeviceState {
-  unsigned* status = nullptr;
-  int sms = 0;
-};
-
+namespace {
 std::mutex g_mu;
 std::map<int, DeviceState> g_dev;
 std::map<std::pair<int, uintptr_t>, std::pair<void*, size_t>> g_ws;
+}  // namespace
 
 mcl_status device_state(int* dev_out, DeviceState* out) {
   int dev = 0;
@@ -92,11 +81,8 @@ mcl_status workspace(cudaStream_t s, size_t bytes, void** out) {
   return MCL_OK;
 }
 
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
 // ---------------------------------------------------------------- profiling
+namespace {
 struct PhaseEvents {
   int phase, kernels;
   cudaEvent_t a, b;
@@ -104,8 +90,9 @@ struct PhaseEvents {
 bool g_prof_on = false;
 std::vector<PhaseEvents> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
+}  // namespace
 
-cudaEvent_t take_event() {
+static cudaEvent_t take_event() {
   if (!g_event_pool.empty()) {
     cudaEvent_t e = g_event_pool.back();
     g_event_pool.pop_back();
@@ -116,40 +103,24 @@ cudaEvent_t take_event() {
   return e;
 }
 
-// Brackets one launch with events when profiling is on.
-struct PhaseScope {
-  int phase, kernels;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr, b = nullptr;
-  PhaseScope(int ph, cudaStream_t st, int nk = 1) : phase(ph), kernels(nk), s(st) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_prof_on) return;
-    a = take_event();
-    b = take_event();
-    cudaEventRecord(a, s);
-  }
-  ~PhaseScope() {
-    if (!a) return;
-    cudaEventRecord(b, s);
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_prof.push_back({phase, kernels, a, b});
-  }
-};
+PhaseScope::PhaseScope(int ph, cudaStream_t st, int nk) : phase_(ph), kernels_(nk), s_(st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_prof_on) return;
+  a_ = take_event();
+  b_ = take_event();
+  cudaEventRecord(a_, s_);
+}
 
-// ---------------------------------------------------------------- helpers
-bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+PhaseScope::~PhaseScope() {
+  if (!a_) return;
+  cudaEventRecord(b_, s_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof.push_back({phase_, kernels_, a_, b_});
+}
 
-}  // namespace
+}  // namespace mcl
 
-struct mcl_map_s {
-  int device = 0;
-  int kind = 0, dtype = 0;
-  MapView view{};
-  void* d_values = nullptr;
-  uint2* d_table = nullptr;
-  int64_t bytes = 0, n_bricks = 0, capacity = 0;
-  int max_probe = 0;
-};
+using namespace mcl;
 
 extern "C" {
 
@@ -338,12 +309,20 @@ mcl_status mcl_map_get_info(mcl_map_t m, mcl_map_info* out) {
   return MCL_OK;
 }
 
-static mcl_status check_device(mcl_map_t m) {
+}  // extern "C"
+
+namespace mcl {
+
+mcl_status check_device(mcl_map_t m) {
   int dev = 0;
   MCL_CUDA(cudaGetDevice(&dev));
   if (dev != m->device) return fail(MCL_EINVAL, "map lives on device %d, current device is %d", m->device, dev);
   return MCL_OK;
 }
+
+}  // namespace mcl
+
+extern "C" {
 
 mcl_status mcl_map_lookup(mcl_map_t m, const float* pts, int64_t N, int64_t* out_index,
                           float* out_value, mcl_stream_t stream) {
@@ -359,7 +338,11 @@ mcl_status mcl_map_lookup(mcl_map_t m, const float* pts, int64_t N, int64_t* out
 }
 
 // ---------------------------------------------------------------- sensor update
-static mcl_status check_params(const mcl_sensor_params* p) {
+}  // extern "C"
+
+namespace mcl {
+
+mcl_status check_params(const mcl_sensor_params* p) {
   if (!p) return fail(MCL_EINVAL, "sensor params: NULL");
   if (p->struct_size < sizeof(mcl_sensor_params)) return fail(MCL_EINVAL, "sensor params: struct_size");
   if (!finite_pos(p->sigma_hit)) return fail(MCL_EINVAL, "sensor params: sigma_hit must be finite and > 0");
@@ -380,20 +363,11 @@ static mcl_status check_params(const mcl_sensor_params* p) {
   return MCL_OK;
 }
 
-struct Plan {
-  SensorShape sh;
-  int K, nblk, blocks_per_sm, sms;
-  bool spatial;
-  long long n_items;
-  size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, off_key, off_rank,
-      off_hist, total;
-};
-
 // Particles are evaluated in spatial order unless told otherwise (or too few
 // to matter).
 constexpr int64_t kSpatialOrderMinParticles = 4096;
 
-static mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p, Plan* pl) {
+mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p, Plan* pl) {
   DeviceState st;
   if (mcl_status rc = device_state(nullptr, &st)) return rc;
   SensorShape& sh = pl->sh;
@@ -443,6 +417,10 @@ static mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_
   pl->total = o;
   return MCL_OK;
 }
+
+}  // namespace mcl
+
+extern "C" {
 
 mcl_status mcl_sensor_plan_get(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p,
                                mcl_sensor_plan* out) {

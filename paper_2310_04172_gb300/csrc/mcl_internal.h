@@ -160,6 +160,27 @@ struct SensorArgs {
 };
 
 // Pose rows -> [R | t]; with rank, particle p's matrix goes to slot rank[p].
+// Batched sensor update: sessions sharing one map and score constants.
+struct BatchSession {
+  const float4* mats;  // P x 3 rows
+  const float4* scan;  // N packed points
+  float* partial;      // K x P chunk sums
+  int P, N, nblk;
+};
+
+struct BatchArgs {
+  SensorArgs base;                 // map, score constants, chunk, ppi, status
+  const BatchSession* sessions;    // device table
+  const long long* item_begin;     // device, n_sessions + 1 prefix of item counts
+  int n_sessions;
+  long long n_items;
+};
+
+cudaError_t launch_sensor_batch(int kind, int layout, int dtype, const BatchArgs& b,
+                                const SensorShape& sh, cudaStream_t s);
+cudaError_t sensor_batch_occupancy(int kind, int layout, int dtype, int mode, const SensorShape& sh,
+                                   int* blocks_per_sm);
+
 cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
                                   cudaStream_t s);
 
@@ -193,9 +214,11 @@ cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float
 
 // Resampling scratch: C (P doubles), per-tile totals and last positive index.
 int resample_tiles(int P);
+// r_dev (device, optional) overrides r: the offset is read when the kernel runs.
 cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             const float* particles_in, float* particles_out, double* cum,
-                            double* tile_total, long long* tile_last, cudaStream_t s);
+                            double* tile_total, long long* tile_last, cudaStream_t s,
+                            const double* r_dev = nullptr);
 
 // Resampling with scratch in a static device array (no allocation), for at
 // most kStaticMaxParticles particles.

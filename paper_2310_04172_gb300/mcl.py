@@ -61,6 +61,25 @@ class mcl_profile(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("launches", _i64 * 8), ("ms", ctypes.c_double * 8)]
 
 
+class mcl_session_update(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("particles", _c_void_p), ("P", _i64),
+                ("scan", _c_void_p), ("N", _i64), ("sigma_hit", ctypes.c_float), ("mode", _i32),
+                ("flags", _u32), ("logw", _c_void_p), ("w", _c_void_p), ("resample_idx", _c_void_p),
+                ("particles_out", _c_void_p)]
+
+
+class mcl_batch_params(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
+                ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
+                ("particle_order", _i32), ("use_graph", _i32)]
+
+
+class mcl_batch_info(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("n_sessions", _i32), ("n_groups", _i32), ("n_items", _i64),
+                ("total_evals", _i64), ("workspace_bytes", _i64), ("kernels_per_run", _i32),
+                ("graph_captured", _i32)]
+
+
 class MclError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"mcl status {status}: {message}")
@@ -90,6 +109,12 @@ SIGNATURES = {
     "mcl_resample_noalloc": (_i32, [_c_void_p, _i64, ctypes.c_double, _c_void_p, _c_void_p,
                                     _c_void_p, _c_void_p]),
     "mcl_motion_update": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p, _u64, _u64, _c_void_p]),
+    "mcl_batch_create": (_i32, [ctypes.POINTER(mcl_session_update), _i32,
+                                ctypes.POINTER(mcl_batch_params), ctypes.POINTER(_c_void_p)]),
+    "mcl_batch_set_offsets": (_i32, [_c_void_p, _c_void_p, _c_void_p]),
+    "mcl_batch_run": (_i32, [_c_void_p, _c_void_p]),
+    "mcl_batch_get_info": (_i32, [_c_void_p, ctypes.POINTER(mcl_batch_info)]),
+    "mcl_batch_destroy": (_i32, [_c_void_p]),
     "mcl_gather_bench": (_i32, [_c_void_p, _i64, _i32, _i32, _i32, _u64, _c_void_p]),
     "mcl_workspace_release": (_i32, [_c_void_p]),
     "mcl_profile_begin": (_i32, []),
@@ -297,6 +322,89 @@ def mcl_motion_update(particles, delta, sigma, seed: int, step: int, stream=None
                                    particles.shape[0], d, s, int(seed) & (2**64 - 1),
                                    int(step) & (2**64 - 1), _stream(stream)))
     return particles
+
+
+class Batch:
+    """Owning handle of a batched step plan (mcl_batch_t). `sessions` is a list of
+    dicts with keys map, particles, scan, logw, w, and optionally sigma_hit,
+    mode, flags, resample_idx, particles_out (CUDA tensors stay referenced)."""
+
+    def __init__(self, sessions, points_per_chunk=0, lanes_per_particle=0, particles_per_item=0,
+                 unroll=0, pipeline=0, particle_order=0, use_graph=False):
+        import torch
+        arr = (mcl_session_update * len(sessions))()
+        self._keep = []
+        for i, s in enumerate(sessions):
+            u = arr[i]
+            u.struct_size = ctypes.sizeof(mcl_session_update)
+            u.map = s["map"].handle
+            u.particles = _dev_ptr(s["particles"], torch.float32, 6, "particles")
+            u.P = s["particles"].shape[0]
+            u.scan = _dev_ptr(s["scan"], torch.float32, 3, "scan")
+            u.N = s["scan"].shape[0]
+            u.sigma_hit = float(s.get("sigma_hit", 0.1))
+            u.mode = int(s.get("mode", MCL_LOGPROD))
+            u.flags = int(s.get("flags", 0))
+            u.logw = _dev_ptr(s.get("logw"), torch.float32, None, "logw")
+            u.w = _dev_ptr(s.get("w"), torch.float32, None, "w")
+            u.resample_idx = _dev_ptr(s.get("resample_idx"), torch.int32, None, "resample_idx")
+            u.particles_out = _dev_ptr(s.get("particles_out"), torch.float32, 6, "particles_out")
+            self._keep.append(s)
+        bp = mcl_batch_params(struct_size=ctypes.sizeof(mcl_batch_params),
+                              points_per_chunk=points_per_chunk, lanes_per_particle=lanes_per_particle,
+                              particles_per_item=particles_per_item, unroll=unroll, pipeline=pipeline,
+                              particle_order=particle_order, use_graph=int(bool(use_graph)))
+        h = ctypes.c_void_p()
+        _check(lib().mcl_batch_create(arr, len(sessions), ctypes.byref(bp), ctypes.byref(h)))
+        self.handle = h
+        self.n = len(sessions)
+
+    def set_offsets(self, r, stream=None):
+        buf = np.ascontiguousarray(r, np.float64)
+        if buf.shape != (self.n,):
+            raise ValueError(f"need {self.n} offsets")
+        _check(lib().mcl_batch_set_offsets(self.handle, buf.ctypes.data_as(ctypes.c_void_p),
+                                           _stream(stream)))
+        self._r = buf  # the copy may still read the host buffer
+
+    def run(self, stream=None):
+        _check(lib().mcl_batch_run(self.handle, _stream(stream)))
+
+    def info(self) -> dict:
+        inf = mcl_batch_info(struct_size=ctypes.sizeof(mcl_batch_info))
+        _check(lib().mcl_batch_get_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in mcl_batch_info._fields_ if k != "struct_size"}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().mcl_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mcl_batch_create(sessions, **kw) -> Batch:
+    return Batch(sessions, **kw)
+
+
+def mcl_batch_run(batch: Batch, stream=None):
+    batch.run(stream)
+
+
+def mcl_batch_set_offsets(batch: Batch, r, stream=None):
+    batch.set_offsets(r, stream)
+
+
+def mcl_batch_get_info(batch: Batch) -> dict:
+    return batch.info()
+
+
+def mcl_batch_destroy(batch: Batch):
+    batch.close()
 
 
 def mcl_gather_bench(buf, blocks: int, iters: int, seed: int = 1, stream=None) -> int:

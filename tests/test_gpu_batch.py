@@ -1,0 +1,137 @@
+"""Batched step (one persistent kernel per map over (session, chunk, particle
+block) items of uneven size): every session's log-weights, weights and
+resampled indices are identical, bit for bit, to the single-session calls with
+the same chunk and lane split — alone or in the mix, plain or replayed from a
+CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2310_04172_gb300 import _build, mcl
+    _build.build()
+    mcl.lib()
+    torch.cuda.set_device(0)
+    room = scenes.room_plain(P=1000)
+    hall = scenes.vlp16_multiroom(P=3000, dtype=scenes.F16)
+    bld = scenes.os064_building(P=5000, dtype=scenes.I16)
+    room_i16 = scenes.voxelize_bricks(room.scene, (0, 0, 0), 0.05, (128, 128, 64), 0.3, scenes.I16)
+    maps = {"room": mcl.map_from_scene(room.map), "room_i16": mcl.map_from_scene(room_i16),
+            "hall": mcl.map_from_scene(hall.map), "bld": mcl.map_from_scene(bld.map)}
+    yield torch, mcl, room, hall, bld, maps
+    for m in maps.values():
+        m.close()
+
+
+def make_sessions(torch, room, hall, bld, maps, rng):
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    specs = [
+        ("room", room.particles, room.scan, 0, True),
+        ("room_i16", room.particles[:700], room.scan, 0, False),
+        ("hall", hall.particles, hall.scan, 0, True),
+        ("bld", bld.particles, bld.scan, 0, True),
+        ("room", room.particles[::-1].copy(), room.scan[:777], 0, False),   # same map, ragged N
+        ("room", room.particles[:333], room.scan, 1, True),                 # SUM mode: own group
+    ]
+    sessions = []
+    for name, parts, scan, mode, res in specs:
+        P = len(parts)
+        s = {"map": maps[name], "particles": t(parts), "scan": t(scan), "sigma_hit": 0.1,
+             "mode": mode, "logw": torch.empty(P, device="cuda"), "w": torch.empty(P, device="cuda")}
+        if res:
+            s["resample_idx"] = torch.empty(P, dtype=torch.int32, device="cuda")
+            s["particles_out"] = torch.empty((P, 6), device="cuda")
+        sessions.append(s)
+    return sessions
+
+
+def single(torch, mcl, s, r, chunk, lanes):
+    P = s["particles"].shape[0]
+    logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+    prm = mcl.sensor_params(s["sigma_hit"], mode=s["mode"], points_per_chunk=chunk,
+                            lanes_per_particle=lanes)
+    mcl.mcl_sensor_update(s["map"], s["particles"], s["scan"], prm, logw, w)
+    out = [logw.cpu().numpy(), w.cpu().numpy()]
+    if "resample_idx" in s:
+        idx = torch.empty(P, dtype=torch.int32, device="cuda")
+        po = torch.empty((P, 6), device="cuda")
+        mcl.mcl_resample(w, r, idx, s["particles"], po)
+        out += [idx.cpu().numpy(), po.cpu().numpy()]
+    mcl.mcl_sync()
+    return out
+
+
+def batch_outputs(s):
+    out = [s["logw"].cpu().numpy(), s["w"].cpu().numpy()]
+    if "resample_idx" in s:
+        out += [s["resample_idx"].cpu().numpy(), s["particles_out"].cpu().numpy()]
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("chunk,lanes", [(2048, 32), (1024, 16)])
+def test_batch_matches_single_sessions(env, use_graph, chunk, lanes):
+    torch, mcl, room, hall, bld, maps = env
+    rng = np.random.default_rng(11)
+    sessions = make_sessions(torch, room, hall, bld, maps, rng)
+    b = mcl.Batch(sessions, points_per_chunk=chunk, lanes_per_particle=lanes, use_graph=use_graph)
+    info = b.info()
+    assert info["n_sessions"] == 6 and info["n_groups"] == 5  # two sessions share the room group
+    for run in range(2):
+        r = rng.uniform(0, 1, len(sessions))
+        if run == 1:  # new particles in the same buffers, as a filter step would write them
+            for s in sessions:
+                s["particles"][:, :3] += 0.05 * torch.randn_like(s["particles"][:, :3])
+        b.set_offsets(r)
+        b.run()
+        mcl.mcl_sync()
+        for k, s in enumerate(sessions):
+            got = batch_outputs(s)
+            ref = single(torch, mcl, s, float(r[k]), chunk, lanes)
+            for g, e in zip(got, ref):
+                assert np.array_equal(g, e), f"session {k} run {run}"
+    assert b.info()["graph_captured"] == int(use_graph)
+    b.close()
+
+
+def test_batch_against_oracle(env):
+    torch, mcl, room, hall, bld, maps = env
+    sessions = make_sessions(torch, room, hall, bld, maps, np.random.default_rng(3))
+    b = mcl.Batch(sessions)
+    b.set_offsets(np.full(len(sessions), 0.5))
+    b.run()
+    mcl.mcl_sync()
+    for s, sm, scan in ((sessions[0], room.map, room.scan), (sessions[2], hall.map, hall.scan)):
+        L = oracle.sensor_update(oracle.Map.from_scene_map(sm), s["particles"].cpu().numpy(), scan, 0.1)
+        Lg = s["logw"].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(Lg - L) / np.maximum(1, np.abs(L))) <= 1e-5
+        idx, _ = oracle.resample(s["w"].cpu().numpy(), 0.5)
+        assert np.array_equal(s["resample_idx"].cpu().numpy(), idx)
+    b.close()
+
+
+def test_batch_rejects_bad_sessions(env):
+    torch, mcl, room, hall, bld, maps = env
+    parts = torch.from_numpy(room.particles).cuda()
+    scan = torch.from_numpy(room.scan).cuda()
+    ok = {"map": maps["room"], "particles": parts, "scan": scan, "logw": torch.empty(1000, device="cuda")}
+    with pytest.raises(mcl.MclError):   # resampling needs the normalised weights
+        mcl.Batch([dict(ok, resample_idx=torch.empty(1000, dtype=torch.int32, device="cuda"))])
+    with pytest.raises(mcl.MclError):   # no output at all
+        mcl.Batch([{"map": maps["room"], "particles": parts, "scan": scan}])
+    with pytest.raises(mcl.MclError):
+        mcl.Batch([dict(ok, sigma_hit=-1.0)])
+    b = mcl.Batch([ok])
+    with pytest.raises(mcl.MclError):
+        b.set_offsets([1.0])
+    b.close()
