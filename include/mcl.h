@@ -208,6 +208,41 @@ typedef struct mcl_sensor_plan {
 mcl_status mcl_sensor_plan_get(mcl_map_t map, int64_t P, int64_t N,
                                const mcl_sensor_params* params, mcl_sensor_plan* out);
 
+/* ------------------------------------------------------------------ autotuner */
+
+/* Autotuner of the launch shape (the paper has none; the shape is a GB300
+ * choice). Times candidates with CUDA events on the caller's particles (the
+ * first max_particles of them) and scan, by coordinate descent over particles
+ * per item, unroll, pipeline and particle order, and with tune_summation = 1
+ * also over points_per_chunk in {1024, 2048, 4096} and lanes_per_particle in
+ * {32, 16} (those two fix the FP32 summation order: keep a tuned pair fixed
+ * for a session). The winner is appended to the JSON-lines cache at
+ * cache_path (NULL: $MCL_TUNE_CACHE) when use_cache = 1, keyed by GPU name,
+ * map kind, layout, storage type, score mode and the power-of-two buckets of P
+ * and N; a later call with the same key returns it without timing. Synchronous:
+ * returns after timing. Allocates a scratch buffer of max_particles floats. */
+typedef struct mcl_tune_params {
+  uint32_t struct_size;
+  int32_t max_particles;   /* 0 = 65536 */
+  int32_t repeats;         /* timed runs per candidate, best kept; 0 = 3 */
+  int32_t use_cache;       /* 1: read and append the cache file */
+  int32_t tune_summation;  /* 1: also tune points_per_chunk and lanes_per_particle */
+  const char* cache_path;
+} mcl_tune_params;
+
+typedef struct mcl_tune_result {
+  uint32_t struct_size;
+  mcl_sensor_params best;  /* base with the tuned fields filled in */
+  double best_ms;          /* per call on the timing subset */
+  double default_ms;       /* the base shape on the same subset */
+  int32_t candidates;      /* shapes timed (0 when served from the cache) */
+  int32_t from_cache;
+} mcl_tune_result;
+
+mcl_status mcl_autotune(mcl_map_t map, const float* particles, int64_t P, const float* scan,
+                        int64_t N, const mcl_sensor_params* base, const mcl_tune_params* tune,
+                        mcl_tune_result* out, mcl_stream_t stream);
+
 /* ------------------------------------------------------------------ resampling */
 
 /* Systematic resampling (Sec. III: a new set drawn from the old one in

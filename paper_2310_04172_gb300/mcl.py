@@ -61,6 +61,16 @@ class mcl_profile(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("launches", _i64 * 8), ("ms", ctypes.c_double * 8)]
 
 
+class mcl_tune_params(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("max_particles", _i32), ("repeats", _i32),
+                ("use_cache", _i32), ("tune_summation", _i32), ("cache_path", ctypes.c_char_p)]
+
+
+class mcl_tune_result(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("best", mcl_sensor_params), ("best_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("candidates", _i32), ("from_cache", _i32)]
+
+
 class mcl_session_update(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("particles", _c_void_p), ("P", _i64),
                 ("scan", _c_void_p), ("N", _i64), ("sigma_hit", ctypes.c_float), ("mode", _i32),
@@ -109,6 +119,9 @@ SIGNATURES = {
     "mcl_resample_noalloc": (_i32, [_c_void_p, _i64, ctypes.c_double, _c_void_p, _c_void_p,
                                     _c_void_p, _c_void_p]),
     "mcl_motion_update": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p, _u64, _u64, _c_void_p]),
+    "mcl_autotune": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _i64,
+                            ctypes.POINTER(mcl_sensor_params), ctypes.POINTER(mcl_tune_params),
+                            ctypes.POINTER(mcl_tune_result), _c_void_p]),
     "mcl_batch_create": (_i32, [ctypes.POINTER(mcl_session_update), _i32,
                                 ctypes.POINTER(mcl_batch_params), ctypes.POINTER(_c_void_p)]),
     "mcl_batch_set_offsets": (_i32, [_c_void_p, _c_void_p, _c_void_p]),
@@ -322,6 +335,30 @@ def mcl_motion_update(particles, delta, sigma, seed: int, step: int, stream=None
                                    particles.shape[0], d, s, int(seed) & (2**64 - 1),
                                    int(step) & (2**64 - 1), _stream(stream)))
     return particles
+
+
+def mcl_autotune(m: Map, particles, scan, base: mcl_sensor_params, max_particles: int = 0,
+                 repeats: int = 0, cache_path: str | None = None, tune_summation: bool = False,
+                 stream=None):
+    """Tuned launch shape (mcl_sensor_params) and the timing record as a dict."""
+    import torch
+    tp = mcl_tune_params(struct_size=ctypes.sizeof(mcl_tune_params), max_particles=max_particles,
+                         repeats=repeats, use_cache=int(cache_path is not None),
+                         tune_summation=int(bool(tune_summation)),
+                         cache_path=cache_path.encode() if cache_path else None)
+    res = mcl_tune_result(struct_size=ctypes.sizeof(mcl_tune_result))
+    _check(lib().mcl_autotune(m.handle, _dev_ptr(particles, torch.float32, 6, "particles"),
+                              particles.shape[0], _dev_ptr(scan, torch.float32, 3, "scan"),
+                              scan.shape[0], ctypes.byref(base), ctypes.byref(tp), ctypes.byref(res),
+                              _stream(stream)))
+    best = mcl_sensor_params()
+    ctypes.pointer(best)[0] = res.best
+    info = {"best_ms": res.best_ms, "default_ms": res.default_ms, "candidates": res.candidates,
+            "from_cache": bool(res.from_cache),
+            "shape": {k: getattr(res.best, k) for k in ("points_per_chunk", "lanes_per_particle",
+                                                         "particles_per_item", "unroll", "pipeline",
+                                                         "particle_order")}}
+    return best, info
 
 
 class Batch:

@@ -54,7 +54,9 @@ def test_binding_covers_every_symbol_and_loads(lib_path):
 def test_struct_layouts_match_c(tmp_path):
     from paper_2310_04172_gb300 import mcl
     src = tmp_path / "sz.c"
-    structs = ["mcl_map_desc", "mcl_map_info", "mcl_sensor_params", "mcl_sensor_plan", "mcl_profile"]
+    structs = sorted(n for n, v in vars(mcl).items()
+                     if n.startswith("mcl_") and isinstance(v, type) and issubclass(v, ctypes.Structure))
+    assert len(structs) >= 10
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcl.h"', "int main(void){"]
     for s in structs:
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
