@@ -357,6 +357,99 @@ mcl_status mcl_batch_get_info(mcl_batch_t b, mcl_batch_info* out);
 /* Waits for the plan's work on every stream, frees its scratch and graph. */
 mcl_status mcl_batch_destroy(mcl_batch_t b);
 
+/* ------------------------------------------------------------------ serving */
+
+/* A server keeps robot sessions on the device (particles, weights, scan
+ * buffer, scratch) and runs one filter step per submitted scan: optional
+ * motion update with the scan's odometry increment, sensor update,
+ * normalisation and systematic resampling (Sec. III: motion, sensor,
+ * resampling steps). A scheduler thread batches the pending scans of all
+ * sessions that are not already on the GPU into one batched step as soon as
+ * one of max_in_flight slots (each with its own stream) is free, so scans
+ * that arrive while others run are admitted and their work overlaps on the
+ * device (continuous batching). Each session keeps at most one queued scan:
+ * a newer scan supersedes a queued, unstarted one (its ticket completes as
+ * MCL_RESULT_SUPERSEDED). Latency is measured from submission to the host
+ * seeing the step complete. */
+typedef struct mcl_server_s* mcl_server_t;
+typedef struct mcl_session_s* mcl_session_t;
+typedef uint64_t mcl_ticket_t;
+
+typedef struct mcl_server_desc {
+  uint32_t struct_size;
+  int64_t hbm_budget_bytes; /* device bytes all sessions may hold (maps not included) */
+  int32_t max_sessions;     /* open sessions at most */
+  int32_t max_in_flight;    /* batched steps on the GPU at once, >= 1 (2 recommended) */
+  int32_t max_batch;        /* sessions per batched step at most (0 = max_sessions) */
+  mcl_batch_params shape;   /* launch shape of every step (use_graph must be 0) */
+} mcl_server_desc;
+
+mcl_status mcl_server_create(const mcl_server_desc* desc, mcl_server_t* out);
+
+/* Opens a session of P particles (host array P x 6, copied) on `map`, for
+ * scans of at most max_N points. EBUSY: max_sessions reached. ENOMEM: the
+ * session's device bytes would exceed the budget (or the device is full). */
+typedef struct mcl_session_desc {
+  uint32_t struct_size;
+  mcl_map_t map;
+  int64_t P, max_N;
+  const float* particles;   /* host, P x 6 */
+  float sigma_hit;
+  int32_t mode;
+  uint32_t flags;
+  float motion_sigma[6];    /* noise of the motion update */
+  uint64_t seed;            /* motion noise and resampling offsets */
+} mcl_session_desc;
+
+mcl_status mcl_session_open(mcl_server_t s, const mcl_session_desc* desc, mcl_session_t* out);
+
+/* Queues one scan (host, N x 3, copied before return) with an optional
+ * odometry increment (host, 6 values, NULL = none). */
+mcl_status mcl_submit_scan(mcl_session_t ss, const float* scan, int64_t N, const float* delta,
+                           mcl_ticket_t* out);
+
+enum { MCL_RESULT_DONE = 0, MCL_RESULT_SUPERSEDED = 1, MCL_RESULT_CLOSED = 2 };
+
+typedef struct mcl_result {
+  uint32_t struct_size;
+  int32_t status;           /* MCL_RESULT_* */
+  double latency_ms;        /* submission to completion seen by the host */
+  int64_t evals;            /* P x N of the step */
+  int64_t step;             /* the session's step counter after this step */
+} mcl_result;
+
+/* Waits up to timeout_ms (< 0: forever) for a ticket. ETIMEDOUT if it has
+ * not completed; EINVAL for an unknown ticket (each completed ticket can be
+ * collected once). */
+mcl_status mcl_wait(mcl_server_t s, mcl_ticket_t t, int32_t timeout_ms, mcl_result* out);
+
+/* Copies the session's current particles (P x 6) and weights (P) to host
+ * arrays (either may be NULL), after its queued and running steps finished. */
+mcl_status mcl_session_read(mcl_session_t ss, float* particles, float* w, int32_t timeout_ms);
+
+/* Closes a session after its running step (a queued scan completes as
+ * MCL_RESULT_CLOSED) and returns its device bytes to the budget. */
+mcl_status mcl_session_close(mcl_session_t ss);
+
+typedef struct mcl_server_stats {
+  uint32_t struct_size;
+  int64_t completed, superseded, batches, evals;
+  double p50_ms, p99_ms, max_ms, mean_batch_sessions;
+  double wall_s;            /* since creation or the last reset */
+  double evals_per_s;
+  int64_t bytes_in_use;
+  int32_t sessions, in_flight;
+} mcl_server_stats;
+
+mcl_status mcl_server_get_stats(mcl_server_t s, int32_t reset, mcl_server_stats* out);
+
+/* Holds (1) or releases (0) the scheduler: held, no new step starts (for
+ * tests of queueing and timeouts). */
+mcl_status mcl_server_pause(mcl_server_t s, int32_t pause);
+
+/* Stops the scheduler after the running steps, closes every session. */
+mcl_status mcl_server_destroy(mcl_server_t s);
+
 /* ------------------------------------------------------------------ gather roofline */
 
 /* Microbenchmark of the map look-up pattern (Sec. VI-C: random TSDF reads

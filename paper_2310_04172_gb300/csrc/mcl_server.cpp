@@ -1,0 +1,610 @@
+// Serving loop (C ABI in include/mcl.h): device-resident robot sessions,
+// admission by device-memory budget, latest-scan-wins queues and continuous
+// batching of pending scans into batched filter steps on max_in_flight slots.
+//
+// Threads: client calls take the server mutex to queue scans and collect
+// tickets; one scheduler thread forms batches and enqueues their work; a host
+// function at the end of each slot's stream marks the slot done (it makes no
+// CUDA call) and wakes the scheduler, which completes the slot's tickets.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace mcl;
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Resampling offset of (seed, step): SplitMix64 finaliser as a counter hash.
+double offset_of(uint64_t seed, uint64_t step) {
+  uint64_t z = seed ^ (step * 0x9E3779B97F4A7C15ull);
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+struct Ticket {
+  int status = -1;  // -1 pending, else MCL_RESULT_*
+  double t_submit = 0, latency_ms = 0;
+  int64_t evals = 0, step = 0;
+};
+
+struct Slot;
+
+}  // namespace
+
+struct mcl_session_s {
+  mcl_server_s* srv = nullptr;
+  mcl_map_t map = nullptr;
+  int64_t P = 0, max_N = 0;
+  float sigma = 0.1f;
+  int mode = 0;
+  uint32_t flags = 0;
+  float msig[6] = {0, 0, 0, 0, 0, 0};
+  uint64_t seed = 0;
+  int64_t step = 0;
+  int cur = 0;
+  float* d_part[2] = {nullptr, nullptr};
+  float *d_scan = nullptr, *d_logw = nullptr, *d_w = nullptr;
+  int32_t* d_idx = nullptr;
+  char* d_ws = nullptr;
+  Plan pl{};
+  size_t off_cum = 0, off_tot = 0, off_last = 0;
+  float* h_stage[2] = {nullptr, nullptr};  // pinned scan staging: queued / running
+  int stage_next = 0;
+  // queued scan
+  bool pending = false;
+  int64_t pending_N = 0;
+  bool pending_delta = false;
+  float delta[6] = {0, 0, 0, 0, 0, 0};
+  mcl_ticket_t pending_ticket = 0;
+  // running step
+  bool in_flight = false;
+  bool closing = false;
+  int64_t bytes = 0;
+};
+
+namespace {
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  char* d_tab = nullptr;  // device session tables and item offsets of the step
+  char* h_tab = nullptr;  // pinned staging of the same
+  size_t tab_bytes = 0;
+  bool busy = false;
+  std::atomic<bool> done{false};
+  mcl_server_s* srv = nullptr;
+  std::vector<mcl_session_s*> sessions;
+  std::vector<mcl_ticket_t> tickets;
+};
+
+}  // namespace
+
+struct mcl_server_s {
+  int device = 0;
+  mcl_server_desc desc{};
+  DeviceState dev{};
+  std::mutex mu;
+  std::condition_variable cv;       // wakes the scheduler
+  std::condition_variable cv_done;  // wakes clients
+  std::vector<mcl_session_s*> sessions;
+  std::map<mcl_ticket_t, Ticket> tickets;
+  mcl_ticket_t next_ticket = 1;
+  std::vector<Slot*> slots;
+  std::thread th;
+  bool stop = false, paused = false;
+  int64_t bytes_in_use = 0;
+  // statistics since creation or reset
+  std::vector<double> lat;
+  int64_t completed = 0, superseded = 0, batches = 0, evals = 0, batch_sessions = 0;
+  double t0 = 0;
+  std::string sched_error;
+};
+
+namespace {
+
+// Runs on a CUDA driver thread when the slot's stream reaches it: no CUDA
+// call and no lock here (the scheduler also polls every 2 ms).
+void CUDART_CB on_slot_done(void* p) {
+  Slot* sl = static_cast<Slot*>(p);
+  sl->done.store(true);
+  sl->srv->cv.notify_all();
+}
+
+void free_session(mcl_session_s* ss) {
+  cudaFree(ss->d_part[0]);
+  cudaFree(ss->d_part[1]);
+  cudaFree(ss->d_scan);
+  cudaFree(ss->d_logw);
+  cudaFree(ss->d_w);
+  cudaFree(ss->d_idx);
+  cudaFree(ss->d_ws);
+  cudaFreeHost(ss->h_stage[0]);
+  cudaFreeHost(ss->h_stage[1]);
+  delete ss;
+}
+
+// Enqueues one batched filter step for the slot's sessions on its stream.
+mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& Ns,
+                        const std::vector<int>& stages, const std::vector<bool>& deltas,
+                        const std::vector<std::array<float, 6>>& dvals) {
+  cudaStream_t st = sl->st;
+  const size_t n = sl->sessions.size();
+  for (size_t i = 0; i < n; ++i) {
+    mcl_session_s* ss = sl->sessions[i];
+    MCL_CUDA(cudaMemcpyAsync(ss->d_scan, ss->h_stage[stages[i]], (size_t)Ns[i] * 3 * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    float* part = ss->d_part[ss->cur];
+    if (deltas[i])
+      MCL_CUDA(launch_motion(part, (int)ss->P, dvals[i].data(), ss->msig, ss->seed, (uint64_t)ss->step, st));
+    const Plan& pl = ss->pl;
+    int* rank = pl.spatial ? (int*)(ss->d_ws + pl.off_rank) : nullptr;
+    if (pl.spatial)
+      MCL_CUDA(launch_particle_order(part, (int)ss->P, ss->map->view, (uint32_t*)(ss->d_ws + pl.off_key),
+                                     (uint32_t*)(ss->d_ws + pl.off_hist), rank, st));
+    MCL_CUDA(launch_pose_to_matrix(part, (int)ss->P, (float4*)(ss->d_ws + pl.off_mats), rank, st));
+    MCL_CUDA(launch_scan_pack(ss->d_scan, (int)Ns[i], (float4*)(ss->d_ws + pl.off_scan), st));
+  }
+  // group the slot's sessions by map and score constants; tables go to the slot buffer
+  struct G {
+    mcl_map_t map;
+    int mode, neglect;
+    float sigma;
+    std::vector<size_t> idx;
+  };
+  std::vector<G> groups;
+  for (size_t i = 0; i < n; ++i) {
+    mcl_session_s* ss = sl->sessions[i];
+    const int neglect = (ss->flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
+    G* g = nullptr;
+    for (auto& x : groups)
+      if (x.map == ss->map && x.mode == ss->mode && x.neglect == neglect && x.sigma == ss->sigma) g = &x;
+    if (!g) {
+      groups.push_back(G{ss->map, ss->mode, neglect, ss->sigma, {}});
+      g = &groups.back();
+    }
+    g->idx.push_back(i);
+  }
+  size_t off = 0;
+  std::vector<BatchArgs> args(groups.size());
+  std::vector<SensorShape> shapes(groups.size());
+  for (size_t k = 0; k < groups.size(); ++k) {
+    const G& g = groups[k];
+    BatchSession* tab = (BatchSession*)(sl->h_tab + off);
+    const size_t off_tab = off;
+    off = align256(off + g.idx.size() * sizeof(BatchSession));
+    long long* beg = (long long*)(sl->h_tab + off);
+    const size_t off_beg = off;
+    off = align256(off + (g.idx.size() + 1) * sizeof(long long));
+    if (off > sl->tab_bytes) return fail(MCL_EINTERNAL, "server: step tables exceed the slot buffer");
+    beg[0] = 0;
+    SensorShape sh{};
+    for (size_t q = 0; q < g.idx.size(); ++q) {
+      mcl_session_s* ss = sl->sessions[g.idx[q]];
+      const int64_t N = Ns[g.idx[q]];
+      sh = ss->pl.sh;
+      const int K = (int)((N + sh.chunk - 1) / sh.chunk);
+      tab[q] = BatchSession{(const float4*)(ss->d_ws + ss->pl.off_mats),
+                            (const float4*)(ss->d_ws + ss->pl.off_scan),
+                            (float*)(ss->d_ws + ss->pl.off_partial), (int)ss->P, (int)N, ss->pl.nblk};
+      beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
+    }
+    int bps = 0;
+    MCL_CUDA(sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype, g.mode, sh, &bps));
+    sh.grid = (int)std::min<long long>(beg[g.idx.size()], (long long)S->dev.sms * std::max(bps, 1));
+    shapes[k] = sh;
+    BatchArgs& b = args[k];
+    b = BatchArgs{};
+    SensorArgs& a = b.base;
+    a.map = g.map->view;
+    a.status = S->dev.status;
+    a.chunk = sh.chunk;
+    a.ppi = sh.ppi;
+    a.mode = g.mode;
+    a.neglect = g.neglect;
+    const double sig = (double)g.sigma, scale = (double)g.map->view.scale;
+    const bool q16 = g.map->dtype == MCL_I16;
+    a.vout = q16 ? 32767.0f : g.map->view.tau;
+    a.cs = (float)(-0.5 / (sig * sig) * (q16 ? scale * scale : 1.0));
+    a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
+    b.sessions = (const BatchSession*)(sl->d_tab + off_tab);
+    b.item_begin = (const long long*)(sl->d_tab + off_beg);
+    b.n_sessions = (int)g.idx.size();
+    b.n_items = beg[g.idx.size()];
+  }
+  MCL_CUDA(cudaMemcpyAsync(sl->d_tab, sl->h_tab, off, cudaMemcpyHostToDevice, st));
+  for (size_t k = 0; k < groups.size(); ++k)
+    MCL_CUDA(launch_sensor_batch(groups[k].map->kind, groups[k].map->view.layout, groups[k].map->dtype,
+                                 args[k], shapes[k], st));
+  for (size_t i = 0; i < n; ++i) {
+    mcl_session_s* ss = sl->sessions[i];
+    const Plan& pl = ss->pl;
+    const int P = (int)ss->P;
+    const int K = (int)((Ns[i] + pl.sh.chunk - 1) / pl.sh.chunk);
+    int* rank = pl.spatial ? (int*)(ss->d_ws + pl.off_rank) : nullptr;
+    const double sig = (double)ss->sigma;
+    const float c = (float)(-0.5 / (sig * sig));
+    const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
+    MCL_CUDA(launch_finish_and_normalise((float*)(ss->d_ws + pl.off_partial), rank, P, K, ss->mode, c, k,
+                                         ss->d_logw, ss->d_w, (float2*)(ss->d_ws + pl.off_stats),
+                                         normalise_blocks(P), (float*)(ss->d_ws + pl.off_ostats), st));
+    MCL_CUDA(launch_resample(ss->d_w, P, offset_of(ss->seed, (uint64_t)ss->step), ss->d_idx,
+                             ss->d_part[ss->cur], ss->d_part[1 - ss->cur], (double*)(ss->d_ws + ss->off_cum),
+                             (double*)(ss->d_ws + ss->off_tot), (long long*)(ss->d_ws + ss->off_last), st));
+  }
+  MCL_CUDA(cudaLaunchHostFunc(st, on_slot_done, sl));
+  return MCL_OK;
+}
+
+// Completes a finished slot's tickets (server mutex held).
+void finalize(mcl_server_s* S, Slot* sl) {
+  const double t = now_s();
+  for (size_t i = 0; i < sl->sessions.size(); ++i) {
+    mcl_session_s* ss = sl->sessions[i];
+    ss->in_flight = false;
+    auto it = S->tickets.find(sl->tickets[i]);
+    if (it != S->tickets.end()) {
+      it->second.status = MCL_RESULT_DONE;
+      it->second.latency_ms = 1e3 * (t - it->second.t_submit);
+      S->lat.push_back(it->second.latency_ms);
+      S->evals += it->second.evals;
+    }
+    ++S->completed;
+  }
+  S->batch_sessions += (int64_t)sl->sessions.size();
+  ++S->batches;
+  sl->sessions.clear();
+  sl->tickets.clear();
+  sl->busy = false;
+  sl->done.store(false);
+  S->cv_done.notify_all();
+}
+
+void scheduler(mcl_server_s* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    bool any_busy = false;
+    for (Slot* sl : S->slots) {
+      if (sl->busy && sl->done.load()) finalize(S, sl);
+      any_busy = any_busy || sl->busy;
+    }
+    if (S->stop && !any_busy) break;
+    Slot* free_slot = nullptr;
+    for (Slot* sl : S->slots)
+      if (!sl->busy) free_slot = sl;
+    std::vector<mcl_session_s*> take;
+    if (!S->stop && !S->paused && free_slot) {
+      const int cap = S->desc.max_batch > 0 ? S->desc.max_batch : S->desc.max_sessions;
+      for (mcl_session_s* ss : S->sessions)
+        if (ss->pending && !ss->in_flight && !ss->closing && (int)take.size() < cap) take.push_back(ss);
+    }
+    if (take.empty()) {
+      S->cv.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    // move the queued scans into the slot
+    Slot* sl = free_slot;
+    sl->busy = true;
+    std::vector<int64_t> Ns;
+    std::vector<int> stages;
+    std::vector<bool> deltas;
+    std::vector<std::array<float, 6>> dvals;
+    for (mcl_session_s* ss : take) {
+      ss->pending = false;
+      ss->in_flight = true;
+      Ns.push_back(ss->pending_N);
+      stages.push_back(1 - ss->stage_next);  // the buffer the queued scan was written to
+      deltas.push_back(ss->pending_delta);
+      std::array<float, 6> d;
+      std::copy(ss->delta, ss->delta + 6, d.begin());
+      dvals.push_back(d);
+      sl->sessions.push_back(ss);
+      sl->tickets.push_back(ss->pending_ticket);
+      auto it = S->tickets.find(ss->pending_ticket);
+      if (it != S->tickets.end()) {
+        it->second.evals = ss->P * ss->pending_N;
+        it->second.step = ss->step + 1;
+      }
+    }
+    mcl_status rc = enqueue_step(S, sl, Ns, stages, deltas, dvals);
+    for (mcl_session_s* ss : take) {
+      ++ss->step;
+      ss->cur = 1 - ss->cur;  // the resampled set is the next step's input
+    }
+    if (rc != MCL_OK) {
+      S->sched_error = mcl_last_error();
+      sl->done.store(true);  // complete the tickets so no client waits forever
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+mcl_status mcl_server_create(const mcl_server_desc* d, mcl_server_t* out) {
+  if (!d || !out || d->struct_size < sizeof(mcl_server_desc)) return fail(MCL_EINVAL, "server_create: bad desc");
+  *out = nullptr;
+  if (d->max_sessions < 1 || d->max_in_flight < 1 || d->max_in_flight > 8 || d->hbm_budget_bytes <= 0 ||
+      d->max_batch < 0)
+    return fail(MCL_EINVAL, "server_create: max_sessions, max_in_flight (1..8), budget must be positive");
+  if (d->shape.use_graph) return fail(MCL_EINVAL, "server_create: steps are not graph-captured");
+  auto* S = new mcl_server_s();
+  S->desc = *d;
+  if (mcl_status rc = device_state(&S->device, &S->dev)) {
+    delete S;
+    return rc;
+  }
+  const int cap = d->max_batch > 0 ? d->max_batch : d->max_sessions;
+  for (int i = 0; i < d->max_in_flight; ++i) {
+    Slot* sl = new Slot();
+    sl->srv = S;
+    // per group: align256(n * sizeof(BatchSession)) + align256((n + 1) * 8) <= 48 n + 526
+    sl->tab_bytes = (size_t)cap * (48 + 528) + 4096;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&sl->d_tab, sl->tab_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&sl->h_tab, sl->tab_bytes);
+    S->slots.push_back(sl);
+    if (e != cudaSuccess) {
+      mcl_server_destroy(S);
+      return cuda_fail(e, "server_create slots");
+    }
+  }
+  S->t0 = now_s();
+  S->th = std::thread(scheduler, S);
+  *out = S;
+  return MCL_OK;
+}
+
+mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_session_t* out) {
+  if (!S || !d || !out || d->struct_size < sizeof(mcl_session_desc)) return fail(MCL_EINVAL, "session_open: bad argument");
+  *out = nullptr;
+  if (!d->map || !d->particles || d->P < 1 || d->P > kMaxCount || d->max_N < 1 || d->max_N > kMaxCount)
+    return fail(MCL_EINVAL, "session_open: map, particles, P or max_N");
+  for (int k = 0; k < 6; ++k)
+    if (!(d->motion_sigma[k] >= 0.f && d->motion_sigma[k] < 1e30f)) return fail(MCL_EINVAL, "session_open: motion_sigma");
+  mcl_sensor_params prm{sizeof(mcl_sensor_params), d->sigma_hit, d->mode, d->flags,
+                        S->desc.shape.points_per_chunk, S->desc.shape.lanes_per_particle,
+                        S->desc.shape.particles_per_item, S->desc.shape.unroll, S->desc.shape.pipeline,
+                        S->desc.shape.particle_order};
+  if (mcl_status rc = check_params(&prm)) return rc;
+  int dev = 0;
+  MCL_CUDA(cudaGetDevice(&dev));
+  if (dev != S->device || d->map->device != S->device) return fail(MCL_EINVAL, "session_open: map on another device");
+  auto* ss = new mcl_session_s();
+  ss->srv = S;
+  ss->map = d->map;
+  ss->P = d->P;
+  ss->max_N = d->max_N;
+  ss->sigma = d->sigma_hit;
+  ss->mode = d->mode;
+  ss->flags = d->flags;
+  std::copy(d->motion_sigma, d->motion_sigma + 6, ss->msig);
+  ss->seed = d->seed;
+  if (mcl_status rc = make_plan(d->map, d->P, d->max_N, &prm, &ss->pl)) {
+    delete ss;
+    return rc;
+  }
+  const int nt = resample_tiles((int)d->P);
+  size_t o = ss->pl.total;
+  ss->off_cum = o;
+  o = align256(o + (size_t)d->P * 8);
+  ss->off_tot = o;
+  o = align256(o + (size_t)(nt + 1) * 8);
+  ss->off_last = o;
+  o = align256(o + (size_t)(nt + 1) * 8);
+  const int64_t P = d->P;
+  ss->bytes = (int64_t)o + 2 * P * 24 + d->max_N * 12 + P * 12;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if ((int)S->sessions.size() >= S->desc.max_sessions) {
+      delete ss;
+      return fail(MCL_EBUSY, "session_open: %d sessions open (max_sessions)", S->desc.max_sessions);
+    }
+    if (S->bytes_in_use + ss->bytes > S->desc.hbm_budget_bytes) {
+      const long long need = (long long)ss->bytes, used = (long long)S->bytes_in_use;
+      delete ss;
+      return fail(MCL_ENOMEM, "session_open: needs %lld bytes, %lld of %lld in use", need, used,
+                  (long long)S->desc.hbm_budget_bytes);
+    }
+    S->bytes_in_use += ss->bytes;  // reserved before allocating
+  }
+  cudaError_t e = cudaMalloc(&ss->d_part[0], (size_t)P * 24);
+  if (e == cudaSuccess) e = cudaMalloc(&ss->d_part[1], (size_t)P * 24);
+  if (e == cudaSuccess) e = cudaMalloc(&ss->d_scan, (size_t)d->max_N * 12);
+  if (e == cudaSuccess) e = cudaMalloc(&ss->d_logw, (size_t)P * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&ss->d_w, (size_t)P * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&ss->d_idx, (size_t)P * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&ss->d_ws, o);
+  if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stage[0], (size_t)d->max_N * 12);
+  if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stage[1], (size_t)d->max_N * 12);
+  if (e == cudaSuccess) e = cudaMemcpy(ss->d_part[0], d->particles, (size_t)P * 24, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->bytes_in_use -= ss->bytes;
+    }
+    free_session(ss);
+    return cuda_fail(e, "session_open");
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->sessions.push_back(ss);
+  *out = ss;
+  return MCL_OK;
+}
+
+mcl_status mcl_submit_scan(mcl_session_t ss, const float* scan, int64_t N, const float* delta,
+                           mcl_ticket_t* out) {
+  if (!ss || !scan || !out) return fail(MCL_EINVAL, "submit_scan: NULL argument");
+  if (N < 1 || N > ss->max_N) return fail(MCL_EINVAL, "submit_scan: N = %lld outside [1, max_N]", (long long)N);
+  if (delta)
+    for (int k = 0; k < 6; ++k)
+      if (!(delta[k] == delta[k]) || std::fabs(delta[k]) > 1e30f) return fail(MCL_EINVAL, "submit_scan: delta");
+  mcl_server_s* S = ss->srv;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (ss->closing) return fail(MCL_EINVAL, "submit_scan: session is closing");
+  if (ss->pending) {  // latest scan wins: the queued, unstarted one is superseded
+    auto it = S->tickets.find(ss->pending_ticket);
+    if (it != S->tickets.end()) it->second.status = MCL_RESULT_SUPERSEDED;
+    ++S->superseded;
+  } else {
+    ss->stage_next = 1 - ss->stage_next;  // the other buffer may be in use by the running step
+  }
+  // the queued scan lives in h_stage[1 - stage_next]
+  std::memcpy(ss->h_stage[1 - ss->stage_next], scan, (size_t)N * 12);
+  ss->pending = true;
+  ss->pending_N = N;
+  ss->pending_delta = delta != nullptr;
+  if (delta) std::copy(delta, delta + 6, ss->delta);
+  const mcl_ticket_t t = S->next_ticket++;
+  Ticket tk;
+  tk.t_submit = now_s();
+  S->tickets[t] = tk;
+  ss->pending_ticket = t;
+  *out = t;
+  S->cv.notify_all();
+  S->cv_done.notify_all();
+  return MCL_OK;
+}
+
+mcl_status mcl_wait(mcl_server_t S, mcl_ticket_t t, int32_t timeout_ms, mcl_result* out) {
+  if (!S || !out || out->struct_size < sizeof(mcl_result)) return fail(MCL_EINVAL, "wait: bad argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->tickets.find(t);
+  if (it == S->tickets.end()) return fail(MCL_EINVAL, "wait: unknown ticket %llu", (unsigned long long)t);
+  auto ready = [&] {
+    auto i2 = S->tickets.find(t);
+    return i2 == S->tickets.end() || i2->second.status >= 0;
+  };
+  if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+    return fail(MCL_ETIMEDOUT, "wait: ticket %llu not done after %d ms", (unsigned long long)t, timeout_ms);
+  it = S->tickets.find(t);
+  if (it == S->tickets.end()) return fail(MCL_EINVAL, "wait: ticket %llu vanished", (unsigned long long)t);
+  out->status = it->second.status;
+  out->latency_ms = it->second.latency_ms;
+  out->evals = it->second.evals;
+  out->step = it->second.step;
+  S->tickets.erase(it);
+  if (!S->sched_error.empty()) return fail(MCL_ECUDA, "server step failed: %s", S->sched_error.c_str());
+  return MCL_OK;
+}
+
+mcl_status mcl_session_read(mcl_session_t ss, float* particles, float* w, int32_t timeout_ms) {
+  if (!ss) return fail(MCL_EINVAL, "session_read: NULL session");
+  mcl_server_s* S = ss->srv;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto idle = [&] { return !ss->pending && !ss->in_flight; };
+  if (timeout_ms < 0) S->cv_done.wait(lk, idle);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle))
+    return fail(MCL_ETIMEDOUT, "session_read: session busy after %d ms", timeout_ms);
+  if (particles) MCL_CUDA(cudaMemcpy(particles, ss->d_part[ss->cur], (size_t)ss->P * 24, cudaMemcpyDeviceToHost));
+  if (w) MCL_CUDA(cudaMemcpy(w, ss->d_w, (size_t)ss->P * 4, cudaMemcpyDeviceToHost));
+  return MCL_OK;
+}
+
+mcl_status mcl_session_close(mcl_session_t ss) {
+  if (!ss) return MCL_OK;
+  mcl_server_s* S = ss->srv;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    ss->closing = true;
+    if (ss->pending) {
+      auto it = S->tickets.find(ss->pending_ticket);
+      if (it != S->tickets.end()) it->second.status = MCL_RESULT_CLOSED;
+      ss->pending = false;
+    }
+    S->cv_done.notify_all();
+    S->cv_done.wait(lk, [&] { return !ss->in_flight; });
+    S->sessions.erase(std::remove(S->sessions.begin(), S->sessions.end(), ss), S->sessions.end());
+    S->bytes_in_use -= ss->bytes;
+  }
+  free_session(ss);
+  return MCL_OK;
+}
+
+mcl_status mcl_server_get_stats(mcl_server_t S, int32_t reset, mcl_server_stats* out) {
+  if (!S || !out || out->struct_size < sizeof(mcl_server_stats)) return fail(MCL_EINVAL, "server_get_stats: bad argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::vector<double> l = S->lat;
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    size_t k = (size_t)std::min<double>((double)l.size() - 1, std::floor(q * (double)(l.size() - 1) + 0.5));
+    std::nth_element(l.begin(), l.begin() + k, l.end());
+    return l[k];
+  };
+  out->completed = S->completed;
+  out->superseded = S->superseded;
+  out->batches = S->batches;
+  out->evals = S->evals;
+  out->p50_ms = pct(0.5);
+  out->p99_ms = pct(0.99);
+  out->max_ms = l.empty() ? 0.0 : *std::max_element(l.begin(), l.end());
+  out->mean_batch_sessions = S->batches ? (double)S->batch_sessions / (double)S->batches : 0.0;
+  out->wall_s = now_s() - S->t0;
+  out->evals_per_s = out->wall_s > 0 ? (double)S->evals / out->wall_s : 0.0;
+  out->bytes_in_use = S->bytes_in_use;
+  out->sessions = (int32_t)S->sessions.size();
+  int busy = 0;
+  for (Slot* sl : S->slots) busy += sl->busy ? 1 : 0;
+  out->in_flight = busy;
+  if (reset) {
+    S->lat.clear();
+    S->completed = S->superseded = S->batches = S->evals = S->batch_sessions = 0;
+    S->t0 = now_s();
+  }
+  return MCL_OK;
+}
+
+mcl_status mcl_server_pause(mcl_server_t S, int32_t pause) {
+  if (!S) return fail(MCL_EINVAL, "server_pause: NULL server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->paused = pause != 0;
+  S->cv.notify_all();
+  return MCL_OK;
+}
+
+mcl_status mcl_server_destroy(mcl_server_t S) {
+  if (!S) return MCL_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->paused = false;
+    S->cv.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  std::vector<mcl_session_s*> open;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    open = S->sessions;
+  }
+  for (mcl_session_s* ss : open) mcl_session_close(ss);
+  for (Slot* sl : S->slots) {
+    if (sl->st) cudaStreamSynchronize(sl->st);
+    if (sl->st) cudaStreamDestroy(sl->st);
+    cudaFree(sl->d_tab);
+    cudaFreeHost(sl->h_tab);
+    delete sl;
+  }
+  delete S;
+  return MCL_OK;
+}
+
+}  // extern "C"

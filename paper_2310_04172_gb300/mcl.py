@@ -90,6 +90,30 @@ class mcl_batch_info(ctypes.Structure):
                 ("graph_captured", _i32)]
 
 
+class mcl_server_desc(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("hbm_budget_bytes", _i64), ("max_sessions", _i32),
+                ("max_in_flight", _i32), ("max_batch", _i32), ("shape", mcl_batch_params)]
+
+
+class mcl_session_desc(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("P", _i64), ("max_N", _i64),
+                ("particles", _c_void_p), ("sigma_hit", ctypes.c_float), ("mode", _i32),
+                ("flags", _u32), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64)]
+
+
+class mcl_result(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("status", _i32), ("latency_ms", ctypes.c_double),
+                ("evals", _i64), ("step", _i64)]
+
+
+class mcl_server_stats(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("completed", _i64), ("superseded", _i64), ("batches", _i64),
+                ("evals", _i64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_batch_sessions", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("evals_per_s", ctypes.c_double),
+                ("bytes_in_use", _i64), ("sessions", _i32), ("in_flight", _i32)]
+
+
 class MclError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"mcl status {status}: {message}")
@@ -128,6 +152,15 @@ SIGNATURES = {
     "mcl_batch_run": (_i32, [_c_void_p, _c_void_p]),
     "mcl_batch_get_info": (_i32, [_c_void_p, ctypes.POINTER(mcl_batch_info)]),
     "mcl_batch_destroy": (_i32, [_c_void_p]),
+    "mcl_server_create": (_i32, [ctypes.POINTER(mcl_server_desc), ctypes.POINTER(_c_void_p)]),
+    "mcl_session_open": (_i32, [_c_void_p, ctypes.POINTER(mcl_session_desc), ctypes.POINTER(_c_void_p)]),
+    "mcl_submit_scan": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, ctypes.POINTER(_u64)]),
+    "mcl_wait": (_i32, [_c_void_p, _u64, _i32, ctypes.POINTER(mcl_result)]),
+    "mcl_session_read": (_i32, [_c_void_p, _c_void_p, _c_void_p, _i32]),
+    "mcl_session_close": (_i32, [_c_void_p]),
+    "mcl_server_get_stats": (_i32, [_c_void_p, _i32, ctypes.POINTER(mcl_server_stats)]),
+    "mcl_server_pause": (_i32, [_c_void_p, _i32]),
+    "mcl_server_destroy": (_i32, [_c_void_p]),
     "mcl_gather_bench": (_i32, [_c_void_p, _i64, _i32, _i32, _i32, _u64, _c_void_p]),
     "mcl_workspace_release": (_i32, [_c_void_p]),
     "mcl_profile_begin": (_i32, []),
@@ -442,6 +475,120 @@ def mcl_batch_get_info(batch: Batch) -> dict:
 
 def mcl_batch_destroy(batch: Batch):
     batch.close()
+
+
+MCL_RESULT_DONE, MCL_RESULT_SUPERSEDED, MCL_RESULT_CLOSED = 0, 1, 2
+
+
+class Server:
+    """Serving loop handle (mcl_server_t): device-resident sessions, continuous batching."""
+
+    def __init__(self, hbm_budget_bytes: int, max_sessions: int, max_in_flight: int = 2,
+                 max_batch: int = 0, **shape):
+        d = mcl_server_desc(struct_size=ctypes.sizeof(mcl_server_desc),
+                            hbm_budget_bytes=int(hbm_budget_bytes), max_sessions=max_sessions,
+                            max_in_flight=max_in_flight, max_batch=max_batch)
+        d.shape = mcl_batch_params(struct_size=ctypes.sizeof(mcl_batch_params), **shape)
+        h = ctypes.c_void_p()
+        _check(lib().mcl_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    def open(self, m: Map, particles: np.ndarray, max_N: int, sigma_hit: float = 0.1,
+             mode: int = MCL_LOGPROD, flags: int = 0, motion_sigma=(0,) * 6, seed: int = 0):
+        parts = np.ascontiguousarray(particles, np.float32).reshape(-1, 6)
+        d = mcl_session_desc(struct_size=ctypes.sizeof(mcl_session_desc), map=m.handle, P=len(parts),
+                             max_N=int(max_N), particles=parts.ctypes.data_as(ctypes.c_void_p),
+                             sigma_hit=sigma_hit, mode=mode, flags=flags, seed=int(seed))
+        d.motion_sigma[:] = [float(x) for x in motion_sigma]
+        h = ctypes.c_void_p()
+        _check(lib().mcl_session_open(self.handle, ctypes.byref(d), ctypes.byref(h)))
+        return Session(self, h, len(parts))
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = mcl_result(struct_size=ctypes.sizeof(mcl_result))
+        _check(lib().mcl_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r)))
+        return {"status": r.status, "latency_ms": r.latency_ms, "evals": r.evals, "step": r.step}
+
+    def stats(self, reset: bool = False) -> dict:
+        st = mcl_server_stats(struct_size=ctypes.sizeof(mcl_server_stats))
+        _check(lib().mcl_server_get_stats(self.handle, int(bool(reset)), ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in mcl_server_stats._fields_ if k != "struct_size"}
+
+    def pause(self, on: bool = True):
+        _check(lib().mcl_server_pause(self.handle, int(bool(on))))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().mcl_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Session:
+    def __init__(self, server: Server, handle, P: int):
+        self.server, self.handle, self.P = server, handle, P
+
+    def submit(self, scan: np.ndarray, delta=None) -> int:
+        sc = np.ascontiguousarray(scan, np.float32).reshape(-1, 3)
+        dl = None if delta is None else np.ascontiguousarray(delta, np.float32).reshape(6)
+        t = ctypes.c_uint64()
+        _check(lib().mcl_submit_scan(self.handle, sc.ctypes.data_as(ctypes.c_void_p), len(sc),
+                                     None if dl is None else dl.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(t)))
+        return t.value
+
+    def read(self, timeout_ms: int = -1):
+        parts = np.empty((self.P, 6), np.float32)
+        w = np.empty(self.P, np.float32)
+        _check(lib().mcl_session_read(self.handle, parts.ctypes.data_as(ctypes.c_void_p),
+                                      w.ctypes.data_as(ctypes.c_void_p), int(timeout_ms)))
+        return parts, w
+
+    def close(self):
+        if self.handle:
+            _check(lib().mcl_session_close(self.handle))
+            self.handle = None
+
+
+def mcl_server_create(hbm_budget_bytes, max_sessions, **kw) -> Server:
+    return Server(hbm_budget_bytes, max_sessions, **kw)
+
+
+def mcl_session_open(server: Server, m: Map, particles, max_N, **kw) -> Session:
+    return server.open(m, particles, max_N, **kw)
+
+
+def mcl_submit_scan(session: Session, scan, delta=None) -> int:
+    return session.submit(scan, delta)
+
+
+def mcl_wait(server: Server, ticket: int, timeout_ms: int = -1) -> dict:
+    return server.wait(ticket, timeout_ms)
+
+
+def mcl_session_read(session: Session, timeout_ms: int = -1):
+    return session.read(timeout_ms)
+
+
+def mcl_session_close(session: Session):
+    session.close()
+
+
+def mcl_server_get_stats(server: Server, reset: bool = False) -> dict:
+    return server.stats(reset)
+
+
+def mcl_server_pause(server: Server, on: bool = True):
+    server.pause(on)
+
+
+def mcl_server_destroy(server: Server):
+    server.close()
 
 
 def mcl_gather_bench(buf, blocks: int, iters: int, seed: int = 1, stream=None) -> int:

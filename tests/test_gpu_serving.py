@@ -1,0 +1,148 @@
+"""Serving loop: sessions resident on the device, admission by budget and slot
+count, latest-scan-wins queues, continuous batching; a session's result is the
+same alone and in the mix, and matches the oracle."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+MASK = (1 << 64) - 1
+
+
+def offset_of(seed: int, step: int) -> float:
+    """The server's resampling offset for (seed, step): SplitMix64 finaliser."""
+    z = (seed ^ ((step * 0x9E3779B97F4A7C15) & MASK)) & MASK
+    z = (z + 0x9E3779B97F4A7C15) & MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK
+    z ^= z >> 31
+    return (z >> 11) * 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2310_04172_gb300 import _build, mcl
+    _build.build()
+    mcl.lib()
+    torch.cuda.set_device(0)
+    room = scenes.room_plain(P=1000)
+    hall = scenes.vlp16_multiroom(P=4000, dtype=scenes.F16)
+    bld = scenes.os064_building(P=6000, dtype=scenes.I16)
+    maps = {"room": mcl.map_from_scene(room.map), "hall": mcl.map_from_scene(hall.map),
+            "bld": mcl.map_from_scene(bld.map)}
+    yield mcl, room, hall, bld, maps
+    for m in maps.values():
+        m.close()
+
+
+def test_same_alone_and_in_the_mix_and_against_the_oracle(env):
+    mcl, room, hall, bld, maps = env
+    seed = 1234
+    alone = mcl.Server(4 << 30, 8)
+    s = alone.open(maps["room"], room.particles, 2048, seed=seed)
+    t = s.submit(room.scan)
+    res = alone.wait(t, 10_000)
+    assert res["status"] == mcl.MCL_RESULT_DONE and res["evals"] == 1000 * 1024
+    parts_alone, w_alone = s.read()
+    alone.close()
+
+    mix = mcl.Server(8 << 30, 8, max_in_flight=2)
+    mix.pause(True)
+    others = [mix.open(maps["hall"], hall.particles, 28800, seed=5),
+              mix.open(maps["bld"], bld.particles, 65536, seed=6),
+              mix.open(maps["room"], room.particles[::-1].copy(), 2048, seed=7)]
+    s2 = mix.open(maps["room"], room.particles, 2048, seed=seed)
+    tickets = [o.submit(sc) for o, sc in zip(others, (hall.scan, bld.scan, room.scan[:900]))]
+    t2 = s2.submit(room.scan)
+    mix.pause(False)
+    for tk in tickets + [t2]:
+        assert mix.wait(tk, 30_000)["status"] == mcl.MCL_RESULT_DONE
+    parts_mix, w_mix = s2.read()
+    assert mix.stats()["mean_batch_sessions"] == 4.0  # all four went as one batched step
+    assert np.array_equal(parts_alone, parts_mix) and np.array_equal(w_alone, w_mix)
+    # against the oracle: weights of the step's input, then systematic resampling
+    L = oracle.sensor_update(oracle.Map.from_scene_map(room.map), room.particles, room.scan, 0.1)
+    wo, M, _, _ = oracle.normalise(L)
+    sel = wo >= 1e-30
+    assert abs(w_mix.astype(np.float64).sum() - 1) <= 1e-5
+    bound = 1e-5 * (np.maximum(1, np.abs(L[sel])) + max(1, abs(M)))
+    assert np.all(np.abs(np.log(w_mix[sel].astype(np.float64)) - np.log(wo[sel])) <= bound)
+    idx, _ = oracle.resample(w_mix, offset_of(seed, 0))
+    assert np.array_equal(parts_mix, room.particles[idx])
+    mix.close()
+
+
+def test_continuous_batching_under_load(env):
+    mcl, room, hall, bld, maps = env
+    srv = mcl.Server(16 << 30, 16, max_in_flight=2)
+    rng = np.random.default_rng(0)
+    sess = []
+    for k in range(12):
+        if k % 3 == 0:
+            sess.append((srv.open(maps["bld"], bld.particles[: 1000 + 400 * k], 65536, seed=k), bld.scan))
+        elif k % 3 == 1:
+            sess.append((srv.open(maps["hall"], hall.particles[: 500 + 300 * k], 28800, seed=k), hall.scan))
+        else:
+            sess.append((srv.open(maps["room"], room.particles, 2048, seed=k), room.scan))
+    stop = time.time() + 2.0
+    results, lock = [], threading.Lock()
+
+    def client(session, scan, seed):
+        r = np.random.default_rng(seed)
+        while time.time() < stop:
+            t = session.submit(scan, delta=[0.01, 0, 0, 0, 0, 0.001])
+            res = srv.wait(t, 20_000)
+            with lock:
+                results.append(res["status"])
+            time.sleep(r.exponential(0.01))
+
+    th = [threading.Thread(target=client, args=(s, sc, i)) for i, (s, sc) in enumerate(sess)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    st = srv.stats()
+    assert st["completed"] >= 24 and all(r == mcl.MCL_RESULT_DONE for r in results)
+    assert st["mean_batch_sessions"] > 1.0       # scans of several sessions share steps
+    assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    assert st["evals_per_s"] > 0 and st["sessions"] == 12
+    srv.close()
+
+
+def test_admission_supersede_timeout_and_close(env):
+    mcl, room, hall, bld, maps = env
+    srv = mcl.Server(1 << 30, 2, max_in_flight=2)
+    a = srv.open(maps["room"], room.particles, 2048, seed=1)
+    b = srv.open(maps["room"], room.particles, 2048, seed=2)
+    with pytest.raises(mcl.MclError) as e:               # no slot left
+        srv.open(maps["room"], room.particles, 2048)
+    assert e.value.status == mcl.MCL_EBUSY
+    b.close()
+    with pytest.raises(mcl.MclError) as e:               # over the device-memory budget
+        srv.open(maps["bld"], np.tile(bld.particles, (1000, 1)), 65536)
+    assert e.value.status == mcl.MCL_ENOMEM
+    srv.pause(True)
+    t1 = a.submit(room.scan)
+    t2 = a.submit(room.scan[:512])                       # supersedes t1 (not started)
+    assert srv.wait(t1, 1000)["status"] == mcl.MCL_RESULT_SUPERSEDED
+    with pytest.raises(mcl.MclError) as e:               # held scheduler: the wait runs out
+        srv.wait(t2, 50)
+    assert e.value.status == mcl.MCL_ETIMEDOUT
+    srv.pause(False)
+    r = srv.wait(t2, 10_000)
+    assert r["status"] == mcl.MCL_RESULT_DONE and r["evals"] == 1000 * 512
+    srv.pause(True)
+    t3 = a.submit(room.scan)
+    a.close()                                            # queued scan completes as closed
+    assert srv.wait(t3, 1000)["status"] == mcl.MCL_RESULT_CLOSED
+    with pytest.raises(mcl.MclError):
+        srv.wait(12345678, 0)                            # unknown ticket
+    srv.close()
