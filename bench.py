@@ -54,6 +54,12 @@ def parse_args(argv=None):
     ap.add_argument("--pipeline", type=int, default=0, help="0 auto, 1 off, 2 on")
     ap.add_argument("--order", type=int, default=0, help="particle order: 0 auto, 1 given, 2 spatial")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
+    ap.add_argument("--mode", default="headline", choices=["headline", "serving", "precision", "vlp16"],
+                    help="headline: 1M x 65,536 int16 step (+ serving probe); serving: 64 sessions over "
+                         "8 maps; precision: f32/f16/i16 sweep with oracle weight error; vlp16: plain vs "
+                         "batched graph-captured form on the VLP-16 tracking workload")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving probe of the headline")
+    ap.add_argument("--serving-seconds", type=float, default=8.0)
     return ap.parse_args(argv)
 
 
@@ -404,6 +410,10 @@ def run_ours(args):
                "sample": f"{n} of {P} particles x {N} points, sensor update + normalise + "
                          f"resample, {dt:.1f} s (FP64, OpenMP over particles)"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_probe(mcl, m, wl, capacity=value, seconds=args.serving_seconds)
+
     if rank == 0:
         cfg = config_dict(args, wl)
         cfg["launch"] = plan
@@ -413,7 +423,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roof, "gather_roofline": gather, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(), "serving": serving,
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["launches"]},
         }
         print(json.dumps(line), flush=True)
@@ -492,10 +502,287 @@ def end_to_end(torch, mcl, m, parts_np, scan_np, prm, offsets, args, dev, dist):
             "ms_per_step": 1e3 * dt / args.steps}
 
 
+# ------------------------------------------------------------------ serving
+def run_clients(mcl, srv, sessions, seconds, rate_scale, seed):
+    """Poisson scan streams (one thread per session) for `seconds`; returns results."""
+    import threading
+    import numpy as np
+    deadline = time.time() + seconds
+    tickets, lock = [], threading.Lock()
+
+    def client(k, sess, scan, rate):
+        r = np.random.default_rng(seed + k)
+        while True:
+            time.sleep(r.exponential(1.0 / (rate * rate_scale)))
+            if time.time() >= deadline:
+                return
+            t = sess.submit(scan)
+            with lock:
+                tickets.append(t)
+
+    th = [threading.Thread(target=client, args=(k, s, sc, rt)) for k, (s, sc, rt) in enumerate(sessions)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    res = [srv.wait(t, 120_000) for t in tickets]
+    return res
+
+
+def serving_measure(mcl, srv, sessions, seconds, rate_scale, seed):
+    import numpy as np
+    srv.stats(reset=True)
+    res = run_clients(mcl, srv, sessions, seconds, rate_scale, seed)
+    st = srv.stats()
+    lat = np.array([r["latency_ms"] for r in res if r["status"] == mcl.MCL_RESULT_DONE])
+    offered = sum(rt * rate_scale * s.P * len(sc) for s, sc, rt in sessions)
+    return {"offered_evals_per_s": offered, "achieved_evals_per_s": st["evals_per_s"],
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "max_ms": float(lat.max()) if len(lat) else None,
+            "completed": int(st["completed"]), "superseded": int(st["superseded"]),
+            "supersede_rate": st["superseded"] / max(1, len(res)),
+            "mean_batch_sessions": st["mean_batch_sessions"], "seconds": seconds}
+
+
+def serving_sessions(mcl, srv, maps, n, p_lo, p_hi, seed):
+    """n sessions round-robin over (map, scene, scan) entries, P log-uniform, 10-20 Hz."""
+    import numpy as np
+    import scenes
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        m, sc, scan = maps[k % len(maps)]
+        P = int(round(math.exp(rng.uniform(math.log(p_lo), math.log(p_hi)))))
+        parts = scenes.particles_free(sc, P, 0.1, 10.0, seed * 1000 + k)
+        sess = srv.open(m, parts, len(scan), seed=seed * 1000 + k,
+                        motion_sigma=(0.02, 0.02, 0.01, 0.002, 0.002, 0.01))
+        out.append((sess, scan, float(rng.uniform(10.0, 20.0))))
+    return out
+
+
+def serving_probe(mcl, m_bld, wl, capacity, seconds):
+    """Short continuous-batching run beside the headline: 16 sessions over the
+    building map and a dense FP16 hall (VLP-16 scans), P log-uniform in
+    [1e3, 2e5], Poisson 10-20 Hz scaled so the offered load is 70 % of the
+    measured step throughput."""
+    import scenes
+    hall = scenes.vlp16_multiroom(P=16, dtype=scenes.F16, seed=12)
+    m_hall = mcl.map_from_scene(hall.map)
+    srv = mcl.Server(64 << 30, 64, max_in_flight=2)
+    sess = serving_sessions(mcl, srv, [(m_bld, wl.scene, wl.scan), (m_hall, hall.scene, hall.scan)],
+                            16, 1e3, 2e5, 21)
+    offered = sum(rt * s.P * len(sc) for s, sc, rt in sess)
+    scale = 0.7 * capacity / offered
+    out = serving_measure(mcl, srv, sess, seconds, scale, 5)
+    out.update({"sessions": 16, "maps": 2, "rate_scale": scale,
+                "load": "Poisson, 10-20 Hz per session scaled to 70% of the measured step throughput"})
+    for s, _, _ in sess:
+        s.close()
+    srv.close()
+    m_hall.close()
+    return out
+
+
+def run_serving(args):
+    """64 robot sessions over 8 maps (4 dense 512x512x128 FP16 halls, 4 brick int16
+    160x160x20 m buildings), P log-uniform in [1e3, 1e6], scans of 28,800 (halls)
+    and 65,536 (buildings) points, Poisson 10-20 Hz per session: first at the
+    nominal rates (offered load far above capacity: latest scan wins), then
+    scaled to 70 % of the achieved throughput."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import scenes
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    maps = []
+    for k in range(4):
+        hall = scenes.vlp16_multiroom(P=16, dtype=scenes.F16, seed=11 + k)
+        maps.append((mcl.map_from_scene(hall.map), hall.scene, hall.scan))
+        bld = scenes.os064_building(P=16, dtype=scenes.I16, seed=15 + k)
+        maps.append((mcl.map_from_scene(bld.map), bld.scene, bld.scan))
+    srv = mcl.Server(200 << 30, 64, max_in_flight=2)
+    sess = serving_sessions(mcl, srv, maps, 64, 1e3, 1e6, 31)
+    nominal = serving_measure(mcl, srv, sess, args.serving_seconds * 2, 1.0, 7)
+    scale = 0.7 * nominal["achieved_evals_per_s"] / nominal["offered_evals_per_s"]
+    scaled = serving_measure(mcl, srv, sess, args.serving_seconds * 2, scale, 9)
+    line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
+            "value": scaled["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "64 sessions over 4 dense FP16 halls + 4 int16 brick buildings",
+                       "particles_total": int(sum(s.P for s, _, _ in sess))},
+            "nominal_load": nominal, "scaled_load_70pct": dict(scaled, rate_scale=scale)}
+    print(json.dumps(line), flush=True)
+    for s, _, _ in sess:
+        s.close()
+    srv.close()
+    for m, _, _ in maps:
+        m.close()
+    return 0
+
+
+# ------------------------------------------------------------------ precision sweep
+def run_precision(args):
+    """The building workload stored as FP32, FP16 and int16: step throughput for
+    1M x 65,536, and weight error / top-100 agreement against the FP64 oracle
+    (quality mode, FP32 reference values) on a seeded 10,000-particle subset;
+    then the plain FP32 per-session form against the int16 batched
+    graph-captured form on four 250,000-particle sessions."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import scenes
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    wl = scenes.os064_building(P=args.particles, dtype=scenes.F32,
+                               dtypes=(scenes.F32, scenes.F16, scenes.I16))
+    maps = wl.info["maps"]
+    P, N = len(wl.particles), len(wl.scan)
+    parts = torch.from_numpy(wl.particles).cuda()
+    scan = torch.from_numpy(wl.scan).cuda()
+    rng = np.random.default_rng(4)
+    sub = np.sort(rng.choice(P, 10_000, replace=False))
+    L_ref = oracle.sensor_update(oracle.Map.from_scene_map(maps[scenes.F32]), wl.particles[sub], wl.scan,
+                                 wl.sigma_hit, parity=False)
+    w_ref, *_ = oracle.normalise(L_ref)
+    top_ref = set(np.argsort(-L_ref)[:100].tolist())
+    out = {}
+    handles = {}
+    for dt, name in ((scenes.F32, "f32"), (scenes.F16, "f16"), (scenes.I16, "i16")):
+        m = mcl.map_from_scene(maps[dt])
+        handles[name] = m
+        logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+        prm = mcl.sensor_params(wl.sigma_hit)
+        mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(args.steps):
+            mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+        e.record()
+        e.synchronize()
+        ms = a.elapsed_time(e) / args.steps
+        ls = torch.empty(len(sub), device="cuda")
+        mcl.mcl_sensor_update(m, parts[torch.from_numpy(sub).cuda()].contiguous(), scan, prm, ls)
+        Lg = ls.cpu().numpy().astype(np.float64)
+        wg, *_ = oracle.normalise(Lg)
+        sel = w_ref >= 1e-6 * w_ref.max()
+        out[name] = {"ms_per_update": ms, "evals_per_s": P * N / (ms / 1e3),
+                     "map_bytes": int(maps[dt].values.nbytes),
+                     "max_rel_logw_err": float(np.max(np.abs(Lg - L_ref) / np.maximum(1, np.abs(L_ref)))),
+                     "max_rel_w_err_top": float(np.max(np.abs(wg[sel] - w_ref[sel]) / w_ref[sel])),
+                     "top100_agreement": len(top_ref & set(np.argsort(-Lg)[:100].tolist())) / 100.0}
+    # plain FP32 per-session form vs int16 batched graph-captured form, 4 sessions
+    S = 4
+    per = P // S
+    sess_parts = [parts[k * per:(k + 1) * per].contiguous() for k in range(S)]
+    outs = [(torch.empty(per, device="cuda"), torch.empty(per, device="cuda")) for _ in range(S)]
+    plain = mcl.sensor_params(wl.sigma_hit, particle_order=1)
+
+    def plain_step():
+        for k in range(S):
+            mcl.mcl_sensor_update(handles["f32"], sess_parts[k], scan, plain, outs[k][0], outs[k][1])
+
+    batch = mcl.Batch([{"map": handles["i16"], "particles": sess_parts[k], "scan": scan,
+                        "logw": outs[k][0], "w": outs[k][1]} for k in range(S)], use_graph=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        e.synchronize()
+        return a.elapsed_time(e) / reps
+
+    ms_plain = timed(plain_step, args.steps)
+    ms_batch = timed(batch.run, args.steps)
+    batch.close()
+    line = {"mode": "precision", "metric": METRIC, "value": out["i16"]["evals_per_s"], "unit": UNIT,
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": wl.name, "subset": 10_000,
+                       "reference": "FP64 oracle, quality mode, FP32 map values"},
+            "storage": out,
+            "plain_f32_per_session": {"sessions": S, "evals_per_s": P * N / (ms_plain / 1e3),
+                                      "ms": ms_plain},
+            "i16_batched_graph": {"sessions": S, "evals_per_s": P * N / (ms_batch / 1e3), "ms": ms_batch,
+                                  "max_rel_logw_err": out["i16"]["max_rel_logw_err"]}}
+    print(json.dumps(line), flush=True)
+    for m in handles.values():
+        m.close()
+    return 0
+
+
+# ------------------------------------------------------------------ VLP-16 tracking
+def run_vlp16(args):
+    """Dense 512x512x128 FP32 hall, 50,000 Gaussian particles x 28,800 points:
+    the plain per-call form against the batched, graph-captured form."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import scenes
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    wl = scenes.vlp16_multiroom(P=50_000, dtype=scenes.F32)
+    m = mcl.map_from_scene(wl.map)
+    parts = torch.from_numpy(wl.particles).cuda()
+    nxt = torch.empty_like(parts)
+    scan = torch.from_numpy(wl.scan).cuda()
+    P, N = parts.shape[0], scan.shape[0]
+    logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+    idx = torch.empty(P, dtype=torch.int32, device="cuda")
+    prm = mcl.sensor_params(wl.sigma_hit)
+
+    def plain():
+        mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+        mcl.mcl_resample(w, 0.5, idx, parts, nxt)
+
+    batch = mcl.Batch([{"map": m, "particles": parts, "scan": scan, "logw": logw, "w": w,
+                        "resample_idx": idx, "particles_out": nxt}], use_graph=True)
+    batch.set_offsets([0.5])
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        e.synchronize()
+        return a.elapsed_time(e) / reps
+
+    reps = max(args.steps, 20)
+    ms_plain = timed(plain, reps)
+    ms_batch = timed(batch.run, reps)
+    line = {"mode": "vlp16", "metric": "particle×point evals/s (50,000×28,800, FP32 dense TSDF)",
+            "value": P * N / (ms_batch / 1e3), "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32", "config": {"workload": wl.name},
+            "plain": {"ms_per_step": ms_plain, "evals_per_s": P * N / (ms_plain / 1e3)},
+            "batched_graph": {"ms_per_step": ms_batch, "evals_per_s": P * N / (ms_batch / 1e3),
+                              "kernels_per_step": batch.info()["kernels_per_run"]}}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    m.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "serving":
+        return run_serving(args)
+    if args.mode == "precision":
+        return run_precision(args)
+    if args.mode == "vlp16":
+        return run_vlp16(args)
     return run_ours(args)
 
 
