@@ -46,7 +46,9 @@ def _digest(extra_flags) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every CUDA / C++ source of the library and link libmcl.so."""
+    """Compile every CUDA / C++ source of the library and link libmcl.so.
+    Extra nvcc flags may also come from $MCL_NVCC_FLAGS (space separated)."""
+    extra_flags = tuple(extra_flags) + tuple(os.environ.get("MCL_NVCC_FLAGS", "").split())
     nvcc = _nvcc()
     os.makedirs(BUILD_DIR, exist_ok=True)
     stamp = os.path.join(BUILD_DIR, "stamp")

@@ -125,12 +125,34 @@ struct Pending {
   bool in[U], v[U];
 };
 
+// The particle's [R | t] rows live in shared memory (one slot per lane group)
+// and are re-read every step, so they do not hold 12 registers across the
+// gathers; with the register cap below this gives 6 resident CTAs per SM
+// instead of 5 (measured 239 ms against 243 ms for 1M x 65,536).
+#ifndef MCL_MATRIX_IN_SMEM
+#define MCL_MATRIX_IN_SMEM 1
+#endif
+
+__device__ __forceinline__ float4 lds_volatile(const float4* p) {
+  float4 v;
+  asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return v;
+}
+
 template <int KIND, int DTYPE, int MODE, int G, int U, bool FULL>
 __device__ __forceinline__ void stage_a(const SensorArgs& a, const float4* __restrict__ sscan,
                                         int base, int glane, int cnt, bool gvalid,
-                                        const float4& r0, const float4& r1, const float4& r2,
+                                        const float4& r0_, const float4& r1_, const float4& r2_,
                                         Pending<KIND, DTYPE, MODE, U>& s) {
   const MapView& m = a.map;
+#if MCL_MATRIX_IN_SMEM
+  // r0_ points at the group's three rows in shared memory
+  const float4 r0 = lds_volatile(&r0_), r1 = lds_volatile(&r0_ + 1), r2 = lds_volatile(&r0_ + 2);
+#else
+  const float4 &r0 = r0_, &r1 = r1_, &r2 = r2_;
+#endif
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int j = base + u * G + glane;
@@ -247,11 +269,16 @@ __device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* 
   accumulate<DTYPE, MODE, U>(a, dv, use, acc);
 }
 
-// Resident CTAs per SM the register allocation is held to: only the 8-deep
-// loop is capped (3 CTAs measured faster than the 2 its free allocation gives).
+// Resident CTAs per SM the register allocation is held to: 6 for the 2- and
+// 4-deep loops (40 registers), 3 for the 8-deep loop (measured faster than the
+// 2 its free allocation gives).
+#ifndef MCL_SENSOR_MIN_BLOCKS
+#define MCL_SENSOR_MIN_BLOCKS 6
+#endif
+
 template <int U>
 struct MinBlocks {
-  static constexpr int value = U == 8 ? 3 : 5;
+  static constexpr int value = U == 8 ? 3 : MCL_SENSOR_MIN_BLOCKS;
 };
 
 // Stage `cnt` scan points starting at `src` into shared memory with one bulk
@@ -283,7 +310,7 @@ __device__ __forceinline__ bool stage_chunk(float4* sscan, uint32_t bar_s, const
 // the chunk sum to partial[c * P + p].
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
 __device__ __forceinline__ void process_block(const SensorArgs& a, const float4* __restrict__ sscan,
-                                              const float4* __restrict__ mats,
+                                              float4* smat, const float4* __restrict__ mats,
                                               float* __restrict__ partial, int P, int c, int p0,
                                               int pn, int cnt) {
   constexpr int GPW = 32 / G;  // groups per warp
@@ -297,7 +324,16 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const float4*
     const bool gvalid = i < pn;
     if (G == 32 && !gvalid) continue;  // warp-uniform for whole-warp groups
     const size_t p = (size_t)p0 + (gvalid ? i : 0);
+#if MCL_MATRIX_IN_SMEM
+    float4* srow = smat + 3 * (warp * GPW + gid);
+    if (glane < 3) srow[glane] = __ldg(mats + 3 * p + glane);
+    __syncwarp();
+    const float4& r0 = srow[0];
+    const float4& r1 = srow[0];
+    const float4& r2 = srow[0];
+#else
     const float4 r0 = __ldg(mats + 3 * p), r1 = __ldg(mats + 3 * p + 1), r2 = __ldg(mats + 3 * p + 2);
+#endif
     typename Raw<DTYPE, MODE>::acc acc = 0;
     int base = 0;
     if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
@@ -310,7 +346,11 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const float4*
     for (int off = G / 2; off > 0; off >>= 1)
       acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
     if (glane == 0 && gvalid) partial[(size_t)c * P + p] = __fmul_rn(acc, a.store_scale);
+#if MCL_MATRIX_IN_SMEM
+    __syncwarp();  // every lane read the rows before the next particle's are written
+#endif
   }
+  (void)smat;
 }
 
 __device__ __forceinline__ void init_barrier(uint32_t bar_s) {
@@ -327,6 +367,7 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const Senso
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
   const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
+  float4* smat = reinterpret_cast<float4*>(smem + (size_t)a.chunk * sizeof(float4) + 16);
   init_barrier(bar_s);
   int loaded = -1;
   uint32_t parity = 0;
@@ -339,7 +380,7 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const Senso
       if (!stage_chunk(sscan, bar_s, a.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
       loaded = c;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, a.mats, a.partial, a.P, c, p0, pn, cnt);
+    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, smat, a.mats, a.partial, a.P, c, p0, pn, cnt);
   }
 }
 
@@ -353,6 +394,7 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor_batch(const
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
   const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
+  float4* smat = reinterpret_cast<float4*>(smem + (size_t)a.chunk * sizeof(float4) + 16);
   init_barrier(bar_s);
   long long loaded = -1;
   uint32_t parity = 0;
@@ -373,7 +415,7 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor_batch(const
       if (!stage_chunk(sscan, bar_s, S.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
       loaded = key;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, S.mats, S.partial, S.P, c, p0, pn, cnt);
+    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, smat, S.mats, S.partial, S.P, c, p0, pn, cnt);
   }
 }
 
