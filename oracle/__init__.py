@@ -11,6 +11,7 @@ with the readings listed in ``oracle.c``; each is pinned in
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -212,3 +213,83 @@ def motion_update(poses, delta, sigma, seed: int, step: int) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_L().ora_num_threads())
+
+
+def _quat_of_pose(poses: np.ndarray) -> np.ndarray:
+    """Unit quaternion (w, x, y, z) of R = Rz(yaw) Ry(pitch) Rx(roll) in FP64:
+    the product q_z(yaw) * q_y(pitch) * q_x(roll) of the three elementary
+    half-angle quaternions (Sec. III pose s = (x, y, z, phi, psi, theta))."""
+    h = 0.5 * poses[:, 3:6].astype(np.float64)
+    cr, sr = np.cos(h[:, 0]), np.sin(h[:, 0])
+    cp, sp = np.cos(h[:, 1]), np.sin(h[:, 1])
+    cy, sy = np.cos(h[:, 2]), np.sin(h[:, 2])
+    return np.stack([cy * cp * cr + sy * sp * sr,
+                     cy * cp * sr - sy * sp * cr,
+                     cy * sp * cr + sy * cp * sr,
+                     sy * cp * cr - cy * sp * sr], axis=1)
+
+
+def pose_estimate(poses, w) -> dict:
+    """Pose estimate of a weighted particle set (Sec. III: the weighted average
+    of the particles, or the particle with the highest weight; Sec. V: the
+    weights give the weighted sum of the poses). FP64 on the FP32 inputs:
+
+      W         = sum_p w_p
+      mean_pose = sum_p w_p s_p / W, each of the six components as a number
+                  (the literal weighted average; its angles are meaningful only
+                  while the particles' angles stay away from the +-pi wrap)
+      quat      = unit eigenvector of the largest eigenvalue lambda of
+                  Q = sum_p w_p q_p q_p^T / W, q_p the quaternion of R(s_p):
+                  the rotation that minimises sum_p w_p ||R - R(s_p)||_F^2
+                  (||R - R_p||^2 = 8 - 8 (q . q_p)^2); sign: first non-zero
+                  component of (w, x, y, z) positive
+      rpy       = that rotation as (roll, pitch, yaw), R = Rz Ry Rx
+      concentration = lambda, in [1/4, 1]; 1 iff all weighted rotations agree
+      n_eff     = W^2 / sum_p w_p^2 (0 if W = 0)
+      argmax    = lowest p with the largest w_p (NaN weights ignored; -1 if
+                  every weight is NaN), best_pose its row, best_w its weight.
+    W = 0 gives NaN means."""
+    s = np.ascontiguousarray(poses, np.float32).reshape(-1, 6)
+    wf = np.ascontiguousarray(w, np.float32).reshape(-1)
+    wd = wf.astype(np.float64)
+    W = float(wd.sum())
+    W2 = float((wd * wd).sum())
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mean = (wd[:, None] * s.astype(np.float64)).sum(0) / W
+    q = _quat_of_pose(s)
+    Q = np.einsum("p,pi,pj->ij", wd, q, q)
+    if W != 0.0 and np.all(np.isfinite(Q)):
+        Q = Q / W
+        lam, vec = np.linalg.eigh(Q)
+        v = vec[:, -1].copy()
+        nz = np.flatnonzero(v != 0.0)
+        if len(nz) and v[nz[0]] < 0:
+            v = -v
+        qw, qx, qy, qz = v
+        r21 = 2.0 * (qy * qz + qw * qx)
+        r22 = 1.0 - 2.0 * (qx * qx + qy * qy)
+        r20 = 2.0 * (qx * qz - qw * qy)
+        r10 = 2.0 * (qx * qy + qw * qz)
+        r00 = 1.0 - 2.0 * (qy * qy + qz * qz)
+        rpy = np.array([math.atan2(r21, r22), math.asin(min(1.0, max(-1.0, -r20))),
+                        math.atan2(r10, r00)])
+        conc = float(lam[-1])
+    else:
+        v = np.full(4, np.nan)
+        rpy = np.full(3, np.nan)
+        conc = float("nan")
+    if np.all(np.isnan(wf)):
+        am = -1
+    else:
+        am = int(np.nanargmax(wf))
+    return {
+        "weight_sum": W,
+        "n_eff": W * W / W2 if W2 > 0 else 0.0,
+        "mean_pose": mean,
+        "quat": v,
+        "rpy": rpy,
+        "concentration": conc,
+        "argmax": am,
+        "best_pose": s[am].copy() if am >= 0 else np.full(6, np.nan, np.float32),
+        "best_w": float(wf[am]) if am >= 0 else float("nan"),
+    }
