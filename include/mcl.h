@@ -185,6 +185,54 @@ mcl_status mcl_sensor_update(mcl_map_t map, const float* particles, int64_t P, c
 mcl_status mcl_normalise(const float* logw, int64_t P, float* w, float* out_stats,
                          mcl_stream_t stream);
 
+/* Pose estimate of a weighted particle set (Sec. III: the pose is the
+ * weighted average of the particles or the particle with the highest weight;
+ * Sec. V: after the weights, the weighted sum of the poses). Written to
+ * device memory by mcl_pose_estimate and mcl_sensor_update_estimate; sums in
+ * FP64 in a fixed order (bit-reproducible), quaternions of the particles in
+ * FP32. With W = sum of w_p:
+ *   mean_pose     sum w_p s_p / W, each of the six pose components as a
+ *                 number (the literal weighted average: its angles are
+ *                 meaningful only while the particles' angles stay away from
+ *                 the +-pi wrap);
+ *   quat          (w, x, y, z): unit eigenvector of the largest eigenvalue of
+ *                 Q = sum w_p q_p q_p^T / W, q_p the quaternion of R(s_p) -
+ *                 the rotation R minimising sum w_p ||R - R(s_p)||_F^2 (no
+ *                 wrap problem); sign: first non-zero component positive;
+ *   rpy           that rotation as (roll, pitch, yaw), R = Rz Ry Rx;
+ *   concentration that eigenvalue, in [1/4, 1]: 1 iff all weighted
+ *                 rotations coincide;
+ *   n_eff         W^2 / sum w_p^2 (0 if W = 0);
+ *   argmax        lowest p with the largest w_p (NaN weights ignored; -1 if
+ *                 all are NaN), best_pose its row, best_w its weight.
+ * W = 0 (or non-finite sums) gives NaN means, quat, rpy and concentration. */
+typedef struct mcl_estimate {
+  double weight_sum;
+  double n_eff;
+  double mean_pose[6];
+  double quat[4];
+  double rpy[3];
+  double concentration;
+  int64_t argmax;
+  float best_pose[6];
+  float best_w;
+  int32_t reserved;
+} mcl_estimate;
+
+/* Estimate from given weights: particles (device, P x 6 FP32), w (device, P
+ * FP32, normalised or not), out (device, one mcl_estimate, 8-byte aligned).
+ * EINVAL: P outside [1, 2^31 - 1], a NULL pointer, misalignment. */
+mcl_status mcl_pose_estimate(const float* particles, const float* w, int64_t P, mcl_estimate* out,
+                             mcl_stream_t stream);
+
+/* mcl_sensor_update with the pose estimate fused into the normalisation
+ * pass (the estimate of the normalised weights it writes, identical bit for
+ * bit to mcl_pose_estimate on those weights). w and out are required. */
+mcl_status mcl_sensor_update_estimate(mcl_map_t map, const float* particles, int64_t P,
+                                      const float* scan, int64_t N,
+                                      const mcl_sensor_params* params, float* logw, float* w,
+                                      mcl_estimate* out, mcl_stream_t stream);
+
 /* Pose rows -> [R | t] (device, P x 12 FP32, rows [R_i0 R_i1 R_i2 t_i]):
  * R = Rz(yaw) Ry(pitch) Rx(roll) evaluated in FP64 in the fixed order
  * a = cy*sp, b = sy*sp, R = [[cy*cp, a*sr - sy*cr, a*cr + sy*sr],
@@ -294,7 +342,8 @@ mcl_status mcl_motion_update(float* particles, int64_t P, const float delta[6],
 /* One session of a batched step: a robot's particle set and its latest scan
  * against its map, with the outputs of mcl_sensor_update and, if
  * resample_idx is not NULL, of mcl_resample (offset set per run with
- * mcl_batch_set_offsets). All pointers are device pointers that stay fixed
+ * mcl_batch_set_offsets), and if estimate is not NULL, of
+ * mcl_sensor_update_estimate. All pointers are device pointers that stay fixed
  * for the life of the batch; the caller writes new particles and scans into
  * the same buffers between runs. */
 typedef struct mcl_session_update {
@@ -311,6 +360,8 @@ typedef struct mcl_session_update {
   float* w;                /* P, may be NULL */
   int32_t* resample_idx;   /* P, NULL: no resampling */
   float* particles_out;    /* P x 6, NULL: indices only (must not alias particles) */
+  mcl_estimate* estimate;  /* NULL, or the pose estimate of the weighted particles (before
+                              resampling), as mcl_sensor_update_estimate; needs w */
 } mcl_session_update;
 
 /* Shape of a batched step. points_per_chunk and lanes_per_particle fix the

@@ -8,6 +8,7 @@
 // and S bit for bit) and writes w = exp(L - M) / S for its range. FP32
 // throughout; max-subtracted so nothing overflows.
 #include <cfloat>
+#include <climits>
 
 #include "mcl_internal.h"
 
@@ -75,10 +76,100 @@ __global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ pa
   if (threadIdx.x == 0) stats[blockIdx.x] = make_float2(m, m > -INFINITY ? s : 0.f);
 }
 
+// ---------------------------------------------------------------- pose estimate
+// Per-particle terms of the estimate: W, sum w^2, sum w s_k, sum w q_i q_j.
+// The quaternion of R(s) = Rz(yaw) Ry(pitch) Rx(roll) is the product of the
+// three half-angle quaternions, evaluated in FP32; the sums are FP64.
+struct EstAcc {
+  double v[kEstSums];
+  float bw;
+  int bp;
+};
+
+__device__ __forceinline__ void est_init(EstAcc& a) {
+#pragma unroll
+  for (int i = 0; i < kEstSums; ++i) a.v[i] = 0.0;
+  a.bw = -INFINITY;
+  a.bp = INT_MAX;
+}
+
+// (w, p) beats (bw, bp): larger weight, or equal weight and lower index.
+__device__ __forceinline__ void est_best(EstAcc& a, float w, int p) {
+  if (w > a.bw || (w == a.bw && p < a.bp)) {
+    a.bw = w;
+    a.bp = p;
+  }
+}
+
+__device__ __forceinline__ void est_add(EstAcc& a, const float* __restrict__ particles, float w,
+                                        int p) {
+  const float* s = particles + (size_t)p * 6;
+  float sv[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sv[k] = __ldg(s + k);
+  float sr, cr, sp, cp, sy, cy;
+  sincosf(0.5f * sv[3], &sr, &cr);
+  sincosf(0.5f * sv[4], &sp, &cp);
+  sincosf(0.5f * sv[5], &sy, &cy);
+  const float q[4] = {cy * cp * cr + sy * sp * sr, cy * cp * sr - sy * sp * cr,
+                      cy * sp * cr + sy * cp * sr, sy * cp * cr - cy * sp * sr};
+  const double wd = (double)w;
+  a.v[0] += wd;
+  a.v[1] = fma(wd, wd, a.v[1]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) a.v[2 + k] = fma(wd, (double)sv[k], a.v[2 + k]);
+  int o = 8;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double wq = wd * (double)q[i];
+#pragma unroll
+    for (int j = i; j < 4; ++j) {
+      a.v[o] = fma(wq, (double)q[j], a.v[o]);
+      ++o;
+    }
+  }
+  est_best(a, w, p);
+}
+
+__device__ __forceinline__ void est_warp_reduce(EstAcc& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int i = 0; i < kEstSums; ++i) a.v[i] += __shfl_xor_sync(0xffffffffu, a.v[i], off);
+    const float ow = __shfl_xor_sync(0xffffffffu, a.bw, off);
+    const int op = __shfl_xor_sync(0xffffffffu, a.bp, off);
+    est_best(a, ow, op);
+  }
+}
+
+// Fixed tree over the block; the result is thread 0's.
+__device__ void est_block_reduce(EstAcc& a, EstAcc* sh) {
+  est_warp_reduce(a);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = a;
+  __syncthreads();
+  if (warp == 0) {
+    if (lane < (int)(blockDim.x >> 5)) a = sh[lane];
+    else est_init(a);
+    est_warp_reduce(a);
+  }
+}
+
+__device__ __forceinline__ void est_store(const EstAcc& a, EstPartial* out) {
+#pragma unroll
+  for (int i = 0; i < kEstSums; ++i) out->v[i] = a.v[i];
+  out->best_w = a.bw;
+  out->best_p = a.bp;
+}
+
+template <bool EST>
 __global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw, int P,
                                                   float* __restrict__ w,
                                                   const float2* __restrict__ stats, int nb,
-                                                  int range, float* __restrict__ out_stats) {
+                                                  int range, float* __restrict__ out_stats,
+                                                  const float* __restrict__ particles,
+                                                  EstPartial* __restrict__ part) {
   __shared__ float sh[32];
   float m = -INFINITY;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmaxf(m, stats[i].x);
@@ -93,12 +184,150 @@ __global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw
   const float S = block_sum(s, sh);
   const int start = blockIdx.x * range, end = min(P, start + range);
   const float uni = 1.0f / (float)P;
-  for (int p = start + threadIdx.x; p < end; p += blockDim.x)
-    w[p] = degenerate ? uni : __fdiv_rn(expf(__fsub_rn(logw[p], M)), S);
+  EstAcc acc;
+  if (EST) est_init(acc);
+  for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
+    const float wp = degenerate ? uni : __fdiv_rn(expf(__fsub_rn(logw[p], M)), S);
+    w[p] = wp;
+    if (EST) est_add(acc, particles, wp, p);
+  }
   if (out_stats && blockIdx.x == 0 && threadIdx.x == 0) {
     out_stats[0] = M;
     out_stats[1] = degenerate ? 0.f : S;
   }
+  if (EST) {
+    __shared__ EstAcc esh[kT / 32];
+    est_block_reduce(acc, esh);
+    if (threadIdx.x == 0) est_store(acc, part + blockIdx.x);
+  }
+}
+
+// The same per-block terms from weights in memory (same ranges, same order).
+__global__ void __launch_bounds__(kT) k_estimate_blocks(const float* __restrict__ particles,
+                                                        const float* __restrict__ w, int P,
+                                                        int range, EstPartial* __restrict__ part) {
+  __shared__ EstAcc esh[kT / 32];
+  EstAcc acc;
+  est_init(acc);
+  const int start = blockIdx.x * range, end = min(P, start + range);
+  for (int p = start + threadIdx.x; p < end; p += blockDim.x) est_add(acc, particles, w[p], p);
+  est_block_reduce(acc, esh);
+  if (threadIdx.x == 0) est_store(acc, part + blockIdx.x);
+}
+
+// Cyclic Jacobi rotations on a symmetric 4 x 4 matrix (FP64): A becomes
+// diagonal (the eigenvalues), V collects the rotations (columns = unit
+// eigenvectors). Stops when the off-diagonal mass is negligible.
+__device__ void jacobi4(double A[4][4], double V[4][4]) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        all += A[i][j] * A[i][j];
+        if (i != j) off += A[i][j] * A[i][j];
+      }
+    if (!(off > 1e-34 * all)) break;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p + 1; q < 4; ++q) {
+        const double apq = A[p][q];
+        if (apq == 0.0) continue;
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 4; ++k) {  // A <- A J
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 4; ++k) {  // A <- J^T A
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 4; ++k) {  // V <- V J
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// One block of kTF threads: partials are combined in a fixed order (thread
+// i takes i, i + kTF, ..., then the block tree), then thread 0 solves the
+// 4 x 4 eigenproblem.
+constexpr int kTF = 256;
+
+__global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __restrict__ part, int nb,
+                                                        const float* __restrict__ particles,
+                                                        mcl_estimate* __restrict__ out) {
+  __shared__ EstAcc esh[kTF / 32];
+  EstAcc acc;
+  est_init(acc);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const EstPartial& e = part[i];
+#pragma unroll
+    for (int k = 0; k < kEstSums; ++k) acc.v[k] += e.v[k];
+    est_best(acc, e.best_w, e.best_p);
+  }
+  est_block_reduce(acc, esh);
+  if (threadIdx.x != 0) return;
+  const double W = acc.v[0], W2 = acc.v[1];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  out->weight_sum = W;
+  out->n_eff = W2 > 0.0 ? W * W / W2 : 0.0;
+  for (int k = 0; k < 6; ++k) out->mean_pose[k] = acc.v[2 + k] / W;
+  double A[4][4];
+  bool finite = W != 0.0;
+  {
+    int o = 8;
+    for (int i = 0; i < 4; ++i)
+      for (int j = i; j < 4; ++j) {
+        const double qij = acc.v[o++] / W;
+        finite = finite && isfinite(qij);
+        A[i][j] = qij;
+        A[j][i] = qij;
+      }
+  }
+  if (finite) {
+    double V[4][4];
+    jacobi4(A, V);
+    int b = 0;
+    for (int i = 1; i < 4; ++i)
+      if (A[i][i] > A[b][b]) b = i;
+    double q[4] = {V[0][b], V[1][b], V[2][b], V[3][b]};
+    const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    int f = 0;
+    while (f < 3 && q[f] == 0.0) ++f;
+    const double sg = q[f] < 0.0 ? -1.0 / n : 1.0 / n;
+    for (int i = 0; i < 4; ++i) q[i] *= sg;
+    const double r21 = 2.0 * (q[2] * q[3] + q[0] * q[1]);
+    const double r22 = 1.0 - 2.0 * (q[1] * q[1] + q[2] * q[2]);
+    const double r20 = 2.0 * (q[1] * q[3] - q[0] * q[2]);
+    const double r10 = 2.0 * (q[1] * q[2] + q[0] * q[3]);
+    const double r00 = 1.0 - 2.0 * (q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) out->quat[i] = q[i];
+    out->rpy[0] = atan2(r21, r22);
+    out->rpy[1] = asin(fmin(1.0, fmax(-1.0, -r20)));
+    out->rpy[2] = atan2(r10, r00);
+    out->concentration = A[b][b];
+  } else {
+    for (int i = 0; i < 4; ++i) out->quat[i] = nan;
+    for (int i = 0; i < 3; ++i) out->rpy[i] = nan;
+    out->concentration = nan;
+  }
+  if (acc.bp != INT_MAX) {
+    out->argmax = acc.bp;
+    for (int k = 0; k < 6; ++k) out->best_pose[k] = particles[(size_t)acc.bp * 6 + k];
+    out->best_w = acc.bw;
+  } else {
+    out->argmax = -1;
+    for (int k = 0; k < 6; ++k) out->best_pose[k] = __int_as_float(0x7fc00000);
+    out->best_w = __int_as_float(0x7fc00000);
+  }
+  out->reserved = 0;
 }
 
 inline int range_of(int P, int nb) { return (P + nb - 1) / nb; }
@@ -118,7 +347,35 @@ cudaError_t launch_finish_and_normalise(const float* partial, const int* rank, i
   k_block_stats<<<nblocks, kT, 0, s>>>(partial, rank, P, K, mode, c, k, logw, block_stats, range);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !w) return e;
-  k_normalise<<<nblocks, kT, 0, s>>>(logw, P, w, block_stats, nblocks, range, out_stats);
+  return launch_normalise_from_stats(logw, P, w, block_stats, nblocks, out_stats, nullptr, nullptr,
+                                     nullptr, s);
+}
+
+cudaError_t launch_normalise_from_stats(const float* logw, int P, float* w,
+                                        const float2* block_stats, int nblocks, float* out_stats,
+                                        const float* particles, EstPartial* part,
+                                        mcl_estimate* est, cudaStream_t s) {
+  const int range = range_of(P, nblocks);
+  if (!est) {
+    k_normalise<false><<<nblocks, kT, 0, s>>>(logw, P, w, block_stats, nblocks, range, out_stats,
+                                              nullptr, nullptr);
+    return cudaGetLastError();
+  }
+  k_normalise<true><<<nblocks, kT, 0, s>>>(logw, P, w, block_stats, nblocks, range, out_stats,
+                                           particles, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_estimate_final<<<1, kTF, 0, s>>>(part, nblocks, particles, est);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pose_estimate(const float* particles, const float* w, int P, EstPartial* part,
+                                 mcl_estimate* est, cudaStream_t s) {
+  const int nb = normalise_blocks(P);
+  k_estimate_blocks<<<nb, kT, 0, s>>>(particles, w, P, range_of(P, nb), part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_estimate_final<<<1, kTF, 0, s>>>(part, nb, particles, est);
   return cudaGetLastError();
 }
 

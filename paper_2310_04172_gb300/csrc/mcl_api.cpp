@@ -408,6 +408,8 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   o = align256(o + (size_t)normalise_blocks((int)P) * sizeof(float2));
   pl->off_ostats = o;
   o = align256(o + 2 * sizeof(float));
+  pl->off_est = o;
+  o = align256(o + (size_t)normalise_blocks((int)P) * sizeof(EstPartial));
   pl->off_key = o;
   o = align256(o + (pl->spatial ? (size_t)P * sizeof(uint32_t) : 0));
   pl->off_rank = o;
@@ -446,9 +448,14 @@ mcl_status mcl_sensor_plan_get(mcl_map_t m, int64_t P, int64_t N, const mcl_sens
   return MCL_OK;
 }
 
-mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, const float* scan,
-                             int64_t N, const mcl_sensor_params* p, float* logw, float* w,
-                             mcl_stream_t stream) {
+}  // extern "C"
+
+namespace mcl {
+namespace {
+
+mcl_status sensor_update(mcl_map_t m, const float* particles, int64_t P, const float* scan,
+                         int64_t N, const mcl_sensor_params* p, float* logw, float* w,
+                         mcl_estimate* est, cudaStream_t s) {
   if (!m || !particles || !scan) return fail(MCL_EINVAL, "sensor_update: NULL map, particles or scan");
   if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "sensor_update: P = %lld", (long long)P);
   if (N < 1 || N > kMaxCount) return fail(MCL_EINVAL, "sensor_update: N = %lld", (long long)N);
@@ -457,7 +464,6 @@ mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, con
     return fail(MCL_EINVAL, "sensor_update: pointers need 4-byte alignment");
   if (mcl_status rc = check_params(p)) return rc;
   if (mcl_status rc = check_device(m)) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
   DeviceState st;
   if (mcl_status rc = device_state(nullptr, &st)) return rc;
   Plan pl;
@@ -517,8 +523,43 @@ mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, con
   }
   if (w) {
     PhaseScope ps(MCL_PHASE_NORMALISE, s);
-    MCL_CUDA(launch_normalise(L, (int)P, w, bstats, nb, ostats, s));
+    MCL_CUDA(launch_normalise_from_stats(L, (int)P, w, bstats, nb, ostats, particles,
+                                         (EstPartial*)(ws + pl.off_est), est, s));
   }
+  return MCL_OK;
+}
+
+}  // namespace
+}  // namespace mcl
+
+extern "C" {
+
+mcl_status mcl_sensor_update(mcl_map_t m, const float* particles, int64_t P, const float* scan,
+                             int64_t N, const mcl_sensor_params* p, float* logw, float* w,
+                             mcl_stream_t stream) {
+  return sensor_update(m, particles, P, scan, N, p, logw, w, nullptr, (cudaStream_t)stream);
+}
+
+mcl_status mcl_sensor_update_estimate(mcl_map_t m, const float* particles, int64_t P,
+                                      const float* scan, int64_t N, const mcl_sensor_params* p,
+                                      float* logw, float* w, mcl_estimate* out,
+                                      mcl_stream_t stream) {
+  if (!w || !out) return fail(MCL_EINVAL, "sensor_update_estimate: NULL w or out");
+  if (!aligned(out, 8)) return fail(MCL_EINVAL, "sensor_update_estimate: out needs 8-byte alignment");
+  return sensor_update(m, particles, P, scan, N, p, logw, w, out, (cudaStream_t)stream);
+}
+
+mcl_status mcl_pose_estimate(const float* particles, const float* w, int64_t P, mcl_estimate* out,
+                             mcl_stream_t stream) {
+  if (!particles || !w || !out) return fail(MCL_EINVAL, "pose_estimate: NULL pointer");
+  if (P < 1 || P > kMaxCount) return fail(MCL_EINVAL, "pose_estimate: P = %lld", (long long)P);
+  if (!aligned(particles, 4) || !aligned(w, 4) || !aligned(out, 8))
+    return fail(MCL_EINVAL, "pose_estimate: misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  if (mcl_status rc = workspace(s, (size_t)normalise_blocks((int)P) * sizeof(EstPartial), &ws)) return rc;
+  PhaseScope ps(MCL_PHASE_NORMALISE, s);
+  MCL_CUDA(launch_pose_estimate(particles, w, (int)P, (EstPartial*)ws, out, s));
   return MCL_OK;
 }
 

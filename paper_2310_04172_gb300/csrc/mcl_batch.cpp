@@ -99,9 +99,14 @@ mcl_status enqueue(mcl_batch_s* b, cudaStream_t st, bool profile) {
     const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
     const int nb = normalise_blocks(P);
     MCL_CUDA(launch_finish_and_normalise((float*)(ws + pl.off_partial), rank, P, pl.K, sp.u.mode,
-                                         sensor_c(sp.u.sigma_hit), k, L, sp.u.w,
+                                         sensor_c(sp.u.sigma_hit), k, L,
+                                         sp.u.estimate ? nullptr : sp.u.w,
                                          (float2*)(ws + pl.off_stats), nb, (float*)(ws + pl.off_ostats),
                                          st));
+    if (sp.u.estimate)
+      MCL_CUDA(launch_normalise_from_stats(L, P, sp.u.w, (float2*)(ws + pl.off_stats), nb,
+                                           (float*)(ws + pl.off_ostats), sp.u.particles,
+                                           (EstPartial*)(ws + pl.off_est), sp.u.estimate, st));
     if (sp.u.resample_idx)
       MCL_CUDA(launch_resample(sp.u.w, P, 0.0, sp.u.resample_idx,
                                sp.u.particles_out ? sp.u.particles : nullptr, sp.u.particles_out,
@@ -145,6 +150,8 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       return bail(fail(MCL_EINVAL, "session %d: P or N out of range", i));
     if (!u.logw && !u.w) return bail(fail(MCL_EINVAL, "session %d: both outputs NULL", i));
     if (u.resample_idx && !u.w) return bail(fail(MCL_EINVAL, "session %d: resampling needs w", i));
+    if (u.estimate && !u.w) return bail(fail(MCL_EINVAL, "session %d: the estimate needs w", i));
+    if (!aligned(u.estimate, 8)) return bail(fail(MCL_EINVAL, "session %d: estimate needs 8-byte alignment", i));
     if (u.particles_out && (!u.resample_idx || u.particles_out == u.particles))
       return bail(fail(MCL_EINVAL, "session %d: particles_out needs resample_idx and must not alias", i));
     for (const void* p : {(const void*)u.particles, (const void*)u.scan, (const void*)u.logw,

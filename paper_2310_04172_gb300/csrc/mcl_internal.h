@@ -209,6 +209,25 @@ cudaError_t launch_normalise(const float* logw, int P, float* w, float2* block_s
                              float* out_stats, cudaStream_t s);
 int normalise_blocks(int P);
 
+// Pose estimate (k_normalise.cu): per-block FP64 sums of the weighted pose
+// terms and the block's largest weight, then one block that combines them.
+constexpr int kEstSums = 18;  // W, sum w^2, 6 x sum w s_k, 10 x sum w q_i q_j (i <= j)
+struct EstPartial {
+  double v[kEstSums];
+  float best_w;
+  int best_p;
+};
+// Normalisation from block statistics already computed for logw (by
+// launch_finish_and_normalise); with est, the estimate of the weighted
+// particles (P x 6, original order) is accumulated in the same pass.
+cudaError_t launch_normalise_from_stats(const float* logw, int P, float* w,
+                                        const float2* block_stats, int nblocks, float* out_stats,
+                                        const float* particles, EstPartial* part,
+                                        mcl_estimate* est, cudaStream_t s);
+// Estimate from given weights (same blocks and order as the fused pass).
+cudaError_t launch_pose_estimate(const float* particles, const float* w, int P, EstPartial* part,
+                                 mcl_estimate* est, cudaStream_t s);
+
 cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float* pts, int N,
                               long long* out_index, float* out_value, cudaStream_t s);
 

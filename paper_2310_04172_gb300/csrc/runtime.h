@@ -51,8 +51,8 @@ struct Plan {
   int K, nblk, blocks_per_sm, sms;
   bool spatial;
   long long n_items;
-  size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, off_key, off_rank,
-      off_hist, total;
+  size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, off_est, off_key,
+      off_rank, off_hist, total;
 };
 
 mcl_status check_params(const mcl_sensor_params* p);

@@ -75,7 +75,7 @@ class mcl_session_update(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("particles", _c_void_p), ("P", _i64),
                 ("scan", _c_void_p), ("N", _i64), ("sigma_hit", ctypes.c_float), ("mode", _i32),
                 ("flags", _u32), ("logw", _c_void_p), ("w", _c_void_p), ("resample_idx", _c_void_p),
-                ("particles_out", _c_void_p)]
+                ("particles_out", _c_void_p), ("estimate", _c_void_p)]
 
 
 class mcl_batch_params(ctypes.Structure):
@@ -114,6 +114,17 @@ class mcl_server_stats(ctypes.Structure):
                 ("bytes_in_use", _i64), ("sessions", _i32), ("in_flight", _i32)]
 
 
+class mcl_estimate(ctypes.Structure):
+    _fields_ = [("weight_sum", ctypes.c_double), ("n_eff", ctypes.c_double),
+                ("mean_pose", ctypes.c_double * 6), ("quat", ctypes.c_double * 4),
+                ("rpy", ctypes.c_double * 3), ("concentration", ctypes.c_double),
+                ("argmax", _i64), ("best_pose", ctypes.c_float * 6), ("best_w", ctypes.c_float),
+                ("reserved", _i32)]
+
+
+ESTIMATE_BYTES = ctypes.sizeof(mcl_estimate)
+
+
 class MclError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"mcl status {status}: {message}")
@@ -135,6 +146,10 @@ SIGNATURES = {
     "mcl_sensor_update": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _i64,
                                  ctypes.POINTER(mcl_sensor_params), _c_void_p, _c_void_p, _c_void_p]),
     "mcl_normalise": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p]),
+    "mcl_pose_estimate": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _c_void_p]),
+    "mcl_sensor_update_estimate": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _i64,
+                                          ctypes.POINTER(mcl_sensor_params), _c_void_p, _c_void_p,
+                                          _c_void_p, _c_void_p]),
     "mcl_pose_to_matrix": (_i32, [_c_void_p, _i64, _c_void_p, _c_void_p]),
     "mcl_sensor_plan_get": (_i32, [_c_void_p, _i64, _i64, ctypes.POINTER(mcl_sensor_params),
                                    ctypes.POINTER(mcl_sensor_plan)]),
@@ -317,6 +332,56 @@ def mcl_sensor_update(m: Map, particles, scan, params: mcl_sensor_params, logw=N
     return logw, w
 
 
+def estimate_buffer(device=None):
+    """Device buffer for one mcl_estimate (uint8 tensor of ESTIMATE_BYTES)."""
+    import torch
+    return torch.zeros(ESTIMATE_BYTES, dtype=torch.uint8, device=device or "cuda")
+
+
+def estimate_to_dict(buf) -> dict:
+    """Reads an mcl_estimate from a device (or host) buffer into a dict of
+    numpy values (synchronises with the buffer's producer through .cpu())."""
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    e = mcl_estimate.from_buffer_copy(raw[:ESTIMATE_BYTES])
+    return {
+        "weight_sum": e.weight_sum, "n_eff": e.n_eff,
+        "mean_pose": np.array(e.mean_pose[:], np.float64), "quat": np.array(e.quat[:], np.float64),
+        "rpy": np.array(e.rpy[:], np.float64), "concentration": e.concentration,
+        "argmax": int(e.argmax), "best_pose": np.array(e.best_pose[:], np.float32),
+        "best_w": float(np.float32(e.best_w)),
+    }
+
+
+def _est_ptr(out):
+    import torch
+    if out is None:
+        return None
+    p = _dev_ptr(out, torch.uint8, None, "out")
+    if out.numel() < ESTIMATE_BYTES:
+        raise ValueError(f"out must hold {ESTIMATE_BYTES} bytes")
+    return p
+
+
+def mcl_pose_estimate(particles, w, out, stream=None):
+    import torch
+    _check(lib().mcl_pose_estimate(_dev_ptr(particles, torch.float32, 6, "particles"),
+                                   _dev_ptr(w, torch.float32, None, "w"), particles.shape[0],
+                                   _est_ptr(out), _stream(stream)))
+    return out
+
+
+def mcl_sensor_update_estimate(m: Map, particles, scan, params: mcl_sensor_params, logw, w, out,
+                               stream=None):
+    import torch
+    P, N = particles.shape[0], scan.shape[0]
+    _check(lib().mcl_sensor_update_estimate(
+        m.handle, _dev_ptr(particles, torch.float32, 6, "particles"), P,
+        _dev_ptr(scan, torch.float32, 3, "scan"), N, ctypes.byref(params),
+        _dev_ptr(logw, torch.float32, None, "logw"), _dev_ptr(w, torch.float32, None, "w"),
+        _est_ptr(out), _stream(stream)))
+    return logw, w, out
+
+
 def mcl_sensor_plan_get(m: Map, P: int, N: int, params: mcl_sensor_params) -> dict:
     pl = mcl_sensor_plan(struct_size=ctypes.sizeof(mcl_sensor_plan))
     _check(lib().mcl_sensor_plan_get(m.handle, P, N, ctypes.byref(params), ctypes.byref(pl)))
@@ -397,7 +462,8 @@ def mcl_autotune(m: Map, particles, scan, base: mcl_sensor_params, max_particles
 class Batch:
     """Owning handle of a batched step plan (mcl_batch_t). `sessions` is a list of
     dicts with keys map, particles, scan, logw, w, and optionally sigma_hit,
-    mode, flags, resample_idx, particles_out (CUDA tensors stay referenced)."""
+    mode, flags, resample_idx, particles_out, estimate (a buffer from
+    estimate_buffer()); the CUDA tensors stay referenced."""
 
     def __init__(self, sessions, points_per_chunk=0, lanes_per_particle=0, particles_per_item=0,
                  unroll=0, pipeline=0, particle_order=0, use_graph=False):
@@ -419,6 +485,7 @@ class Batch:
             u.w = _dev_ptr(s.get("w"), torch.float32, None, "w")
             u.resample_idx = _dev_ptr(s.get("resample_idx"), torch.int32, None, "resample_idx")
             u.particles_out = _dev_ptr(s.get("particles_out"), torch.float32, 6, "particles_out")
+            u.estimate = _est_ptr(s.get("estimate"))
             self._keep.append(s)
         bp = mcl_batch_params(struct_size=ctypes.sizeof(mcl_batch_params),
                               points_per_chunk=points_per_chunk, lanes_per_particle=lanes_per_particle,

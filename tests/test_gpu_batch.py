@@ -1,6 +1,6 @@
 """Batched step (one persistent kernel per map over (session, chunk, particle
 block) items of uneven size): every session's log-weights, weights and
-resampled indices are identical, bit for bit, to the single-session calls with
+resampled indices (and pose estimates) are identical, bit for bit, to the single-session calls with
 the same chunk and lane split — alone or in the mix, plain or replayed from a
 CUDA graph."""
 import numpy as np
@@ -60,13 +60,19 @@ def single(torch, mcl, s, r, chunk, lanes):
     logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
     prm = mcl.sensor_params(s["sigma_hit"], mode=s["mode"], points_per_chunk=chunk,
                             lanes_per_particle=lanes)
-    mcl.mcl_sensor_update(s["map"], s["particles"], s["scan"], prm, logw, w)
+    if "estimate" in s:
+        est = mcl.estimate_buffer()
+        mcl.mcl_sensor_update_estimate(s["map"], s["particles"], s["scan"], prm, logw, w, est)
+    else:
+        mcl.mcl_sensor_update(s["map"], s["particles"], s["scan"], prm, logw, w)
     out = [logw.cpu().numpy(), w.cpu().numpy()]
     if "resample_idx" in s:
         idx = torch.empty(P, dtype=torch.int32, device="cuda")
         po = torch.empty((P, 6), device="cuda")
         mcl.mcl_resample(w, r, idx, s["particles"], po)
         out += [idx.cpu().numpy(), po.cpu().numpy()]
+    if "estimate" in s:
+        out.append(est.cpu().numpy())
     mcl.mcl_sync()
     return out
 
@@ -75,6 +81,8 @@ def batch_outputs(s):
     out = [s["logw"].cpu().numpy(), s["w"].cpu().numpy()]
     if "resample_idx" in s:
         out += [s["resample_idx"].cpu().numpy(), s["particles_out"].cpu().numpy()]
+    if "estimate" in s:
+        out.append(s["estimate"].cpu().numpy())
     return out
 
 
@@ -84,6 +92,8 @@ def test_batch_matches_single_sessions(env, use_graph, chunk, lanes):
     torch, mcl, room, hall, bld, maps = env
     rng = np.random.default_rng(11)
     sessions = make_sessions(torch, room, hall, bld, maps, rng)
+    for k in (0, 3, 4):  # pose estimates fused into the batched normalisation
+        sessions[k]["estimate"] = mcl.estimate_buffer()
     b = mcl.Batch(sessions, points_per_chunk=chunk, lanes_per_particle=lanes, use_graph=use_graph)
     info = b.info()
     assert info["n_sessions"] == 6 and info["n_groups"] == 5  # two sessions share the room group
