@@ -408,6 +408,82 @@ mcl_status mcl_batch_get_info(mcl_batch_t b, mcl_batch_info* out);
 /* Waits for the plan's work on every stream, frees its scratch and graph. */
 mcl_status mcl_batch_destroy(mcl_batch_t b);
 
+/* ------------------------------------------------------------------ filter */
+
+/* A particle filter for one robot that keeps its particles on the device and
+ * runs a whole step of the method per call (Sec. III: motion update, sensor
+ * update with weights, pose estimate, resampling). Step k (k = 0, 1, ...)
+ * enqueues exactly the work of these calls, with equal results bit for bit:
+ *   mcl_motion_update(particles, P, delta, motion_sigma, seed, k)  (skipped
+ *     when delta is NULL),
+ *   mcl_sensor_update_estimate(map, particles, P, scan, N, &sensor, logw, w,
+ *     estimate),
+ *   mcl_resample(w, P, r_k, idx, particles, particles') and particles =
+ *     particles', with r_k = the SplitMix64 finaliser of
+ *     (seed ^ k * 0x9E3779B97F4A7C15) as 53 bits in [0, 1) - the offsets of a
+ *     serving session with the same seed.
+ * The paper runs the motion update and resampling on the CPU between GPU
+ * calls; here with use_graph = 1 the step for each scan size is captured
+ * into a CUDA graph at its first use and replayed: the per-step values
+ * (increment, counter, offset) are read from device memory when the graph
+ * runs, so a step costs one 48-byte copy, one scan copy and a graph launch. */
+typedef struct mcl_filter_desc {
+  uint32_t struct_size;       /* sizeof(mcl_filter_desc) */
+  mcl_map_t map;
+  int64_t P;                  /* particles, [1, 2^31 - 1] */
+  int64_t max_points;         /* largest scan, [1, 2^31 - 1] */
+  mcl_sensor_params sensor;   /* sigma_hit, mode, flags, launch shape */
+  float motion_sigma[6];      /* noise sigma of the increment, >= 0 */
+  uint64_t seed;              /* motion-noise key and resampling offsets */
+  int32_t use_graph;          /* 1: replay each scan size's step from a CUDA graph */
+  int32_t max_graphs;         /* graphs kept, least recently used evicted; 0 = 8 */
+} mcl_filter_desc;
+
+typedef struct mcl_filter_s* mcl_filter_t;
+
+/* Creates a filter on the current device from P particles (device, P x 6
+ * FP32, copied before return). The filter owns its device memory, sized at
+ * creation for max_points, so steps allocate nothing. EINVAL: bad
+ * description; ENOMEM: out of device memory. */
+mcl_status mcl_filter_create(const mcl_filter_desc* desc, const float* particles,
+                             mcl_filter_t* out);
+
+/* One step: delta (host, 6 FP32, NULL = no motion update), scan (device,
+ * N x 3 FP32, 1 <= N <= max_points, copied into the filter on `stream`), out
+ * (device mcl_estimate, 8-byte aligned, or NULL) gets the estimate of this
+ * step's weighted particles (before resampling). Asynchronous; the caller
+ * may reuse delta at once and scan after the stream's work. Steps on one
+ * filter must be issued from one host thread at a time. */
+mcl_status mcl_filter_step(mcl_filter_t f, const float* delta, const float* scan, int64_t N,
+                           mcl_estimate* out, mcl_stream_t stream);
+
+/* Replaces the particles (device, P x 6, copied on `stream`), e.g. for a
+ * global relocalisation; the step counter continues. */
+mcl_status mcl_filter_reset(mcl_filter_t f, const float* particles, mcl_stream_t stream);
+
+/* The filter's device arrays (valid until mcl_filter_destroy; read them after
+ * the stream's work finished) and counters. */
+typedef struct mcl_filter_state {
+  uint32_t struct_size;
+  const float* particles;        /* P x 6, after the last resampling */
+  const float* logw;             /* P, of the last sensor update */
+  const float* w;                /* P, of the last sensor update */
+  const int32_t* idx;            /* P, the last resampling's draw */
+  const mcl_estimate* estimate;  /* the last step's estimate */
+  int64_t P;
+  int64_t steps;                 /* steps enqueued */
+  int64_t graph_launches;        /* steps replayed from a graph */
+  double last_r;                 /* resampling offset of the last step */
+  int64_t device_bytes;          /* device memory the filter holds */
+  int32_t graphs;                /* graphs instantiated and kept */
+  int32_t reserved;
+} mcl_filter_state;
+
+mcl_status mcl_filter_get_state(mcl_filter_t f, mcl_filter_state* out);
+
+/* Waits for the filter's work on the device, then frees it. NULL is a no-op. */
+mcl_status mcl_filter_destroy(mcl_filter_t f);
+
 /* ------------------------------------------------------------------ serving */
 
 /* A server keeps robot sessions on the device (particles, weights, scan

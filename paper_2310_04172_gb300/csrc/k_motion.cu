@@ -50,10 +50,16 @@ __device__ __forceinline__ void rpy(double roll, double pitch, double yaw, doubl
   R[8] = __dmul_rn(cp, cr);
 }
 
-__global__ void k_motion(float* __restrict__ poses, int P, const MotionArgs a, uint64_t seed,
-                         uint64_t step) {
+__global__ void k_motion(float* __restrict__ poses, int P, MotionArgs a, uint64_t seed,
+                         uint64_t step, const StepIn* __restrict__ in) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
+  if (in) {
+    if (!in->motion) return;
+    step = in->step;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.delta[k] = in->delta[k];
+  }
   double n[6];
 #pragma unroll
   for (uint32_t b = 0; b < 3; ++b) {
@@ -98,13 +104,13 @@ __global__ void k_motion(float* __restrict__ poses, int P, const MotionArgs a, u
 }  // namespace
 
 cudaError_t launch_motion(float* particles, int P, const float delta[6], const float sigma[6],
-                          uint64_t seed, uint64_t step, cudaStream_t s) {
+                          uint64_t seed, uint64_t step, cudaStream_t s, const StepIn* in) {
   MotionArgs a;
   for (int k = 0; k < 6; ++k) {
-    a.delta[k] = delta[k];
+    a.delta[k] = delta ? delta[k] : 0.f;
     a.sigma[k] = sigma[k];
   }
-  k_motion<<<(P + 255) / 256, 256, 0, s>>>(particles, P, a, seed, step);
+  k_motion<<<(P + 255) / 256, 256, 0, s>>>(particles, P, a, seed, step, in);
   return cudaGetLastError();
 }
 

@@ -103,7 +103,13 @@ static cudaEvent_t take_event() {
   return e;
 }
 
+thread_local bool t_no_profile = false;
+
+NoProfileScope::NoProfileScope() : prev_(t_no_profile) { t_no_profile = true; }
+NoProfileScope::~NoProfileScope() { t_no_profile = prev_; }
+
 PhaseScope::PhaseScope(int ph, cudaStream_t st, int nk) : phase_(ph), kernels_(nk), s_(st) {
+  if (t_no_profile) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_prof_on) return;
   a_ = take_event();
@@ -470,6 +476,15 @@ mcl_status sensor_update(mcl_map_t m, const float* particles, int64_t P, const f
   if (mcl_status rc = make_plan(m, P, N, p, &pl)) return rc;
   char* ws = nullptr;
   if (mcl_status rc = workspace(s, pl.total, (void**)&ws)) return rc;
+  return enqueue_sensor(m, particles, P, scan, N, p, logw, w, est, pl, ws, st.status, s);
+}
+
+}  // namespace
+
+mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const float* scan,
+                          int64_t N, const mcl_sensor_params* p, float* logw, float* w,
+                          mcl_estimate* est, const Plan& pl, char* ws, unsigned* status,
+                          cudaStream_t s) {
   float4* mats = (float4*)(ws + pl.off_mats);
   float4* packed = (float4*)(ws + pl.off_scan);
   float* partial = (float*)(ws + pl.off_partial);
@@ -494,7 +509,7 @@ mcl_status sensor_update(mcl_map_t m, const float* particles, int64_t P, const f
   a.mats = mats;
   a.scan = packed;
   a.partial = partial;
-  a.status = st.status;
+  a.status = status;
   a.P = (int)P;
   a.N = (int)N;
   a.chunk = pl.sh.chunk;
@@ -529,7 +544,6 @@ mcl_status sensor_update(mcl_map_t m, const float* particles, int64_t P, const f
   return MCL_OK;
 }
 
-}  // namespace
 }  // namespace mcl
 
 extern "C" {

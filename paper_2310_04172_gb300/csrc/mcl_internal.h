@@ -246,8 +246,21 @@ constexpr int kMaxDevices = 64;
 cudaError_t launch_resample_static(const float* w, int P, double r, int32_t* idx,
                                    const float* particles_in, float* particles_out, cudaStream_t s);
 
+// Inputs of one filter step read from device memory when the kernels run,
+// so that a captured graph replays with each step's values.
+struct StepIn {
+  float delta[6];           // odometry increment
+  int motion;               // 0: no motion update this step
+  int pad;
+  unsigned long long step;  // motion-noise counter
+  double r;                 // resampling offset
+};
+
+// With in, delta and step come from in (read at run time) and the update is
+// skipped when in->motion is 0.
 cudaError_t launch_motion(float* particles, int P, const float delta[6], const float sigma[6],
-                          uint64_t seed, uint64_t step, cudaStream_t s);
+                          uint64_t seed, uint64_t step, cudaStream_t s,
+                          const StepIn* in = nullptr);
 
 cudaError_t launch_gather_bench(const void* buf, long long n_elems, int elem_bytes, int blocks,
                                 int iters, unsigned long long seed, float* sink, cudaStream_t s);

@@ -29,16 +29,6 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Resampling offset of (seed, step): SplitMix64 finaliser as a counter hash.
-double offset_of(uint64_t seed, uint64_t step) {
-  uint64_t z = seed ^ (step * 0x9E3779B97F4A7C15ull);
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return (double)(z >> 11) * 0x1.0p-53;
-}
-
 struct Ticket {
   int status = -1;  // -1 pending, else MCL_RESULT_*
   double t_submit = 0, latency_ms = 0;
@@ -244,7 +234,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     MCL_CUDA(launch_finish_and_normalise((float*)(ss->d_ws + pl.off_partial), rank, P, K, ss->mode, c, k,
                                          ss->d_logw, ss->d_w, (float2*)(ss->d_ws + pl.off_stats),
                                          normalise_blocks(P), (float*)(ss->d_ws + pl.off_ostats), st));
-    MCL_CUDA(launch_resample(ss->d_w, P, offset_of(ss->seed, (uint64_t)ss->step), ss->d_idx,
+    MCL_CUDA(launch_resample(ss->d_w, P, resample_offset(ss->seed, (uint64_t)ss->step), ss->d_idx,
                              ss->d_part[ss->cur], ss->d_part[1 - ss->cur], (double*)(ss->d_ws + ss->off_cum),
                              (double*)(ss->d_ws + ss->off_tot), (long long*)(ss->d_ws + ss->off_last), st));
   }

@@ -55,6 +55,36 @@ struct Plan {
       off_rank, off_hist, total;
 };
 
+// Enqueues one sensor update (pose matrices, scan packing, sensor kernel,
+// log-weights, normalisation with the optional fused estimate) on s, with the
+// plan's workspace at ws. Arguments must already be validated.
+mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const float* scan,
+                          int64_t N, const mcl_sensor_params* p, float* logw, float* w,
+                          mcl_estimate* est, const Plan& pl, char* ws, unsigned* status,
+                          cudaStream_t s);
+
+// While one is alive on a thread, PhaseScope records nothing on that thread
+// (work enqueued into a stream that is being captured into a graph).
+class NoProfileScope {
+ public:
+  NoProfileScope();
+  ~NoProfileScope();
+
+ private:
+  bool prev_;
+};
+
+// Resampling offset r in [0, 1) of a filter step: the SplitMix64 finaliser of
+// (seed, step) as a counter hash, 53 bits.
+inline double resample_offset(uint64_t seed, uint64_t step) {
+  uint64_t z = seed ^ (step * 0x9E3779B97F4A7C15ull);
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
 mcl_status check_params(const mcl_sensor_params* p);
 mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p, Plan* pl);
 mcl_status check_device(mcl_map_t m);

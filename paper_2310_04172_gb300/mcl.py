@@ -125,6 +125,19 @@ class mcl_estimate(ctypes.Structure):
 ESTIMATE_BYTES = ctypes.sizeof(mcl_estimate)
 
 
+class mcl_filter_desc(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("P", _i64), ("max_points", _i64),
+                ("sensor", mcl_sensor_params), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64),
+                ("use_graph", _i32), ("max_graphs", _i32)]
+
+
+class mcl_filter_state(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("particles", _c_void_p), ("logw", _c_void_p),
+                ("w", _c_void_p), ("idx", _c_void_p), ("estimate", _c_void_p), ("P", _i64),
+                ("steps", _i64), ("graph_launches", _i64), ("last_r", ctypes.c_double),
+                ("device_bytes", _i64), ("graphs", _i32), ("reserved", _i32)]
+
+
 class MclError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"mcl status {status}: {message}")
@@ -167,6 +180,11 @@ SIGNATURES = {
     "mcl_batch_run": (_i32, [_c_void_p, _c_void_p]),
     "mcl_batch_get_info": (_i32, [_c_void_p, ctypes.POINTER(mcl_batch_info)]),
     "mcl_batch_destroy": (_i32, [_c_void_p]),
+    "mcl_filter_create": (_i32, [ctypes.POINTER(mcl_filter_desc), _c_void_p, ctypes.POINTER(_c_void_p)]),
+    "mcl_filter_step": (_i32, [_c_void_p, _c_void_p, _c_void_p, _i64, _c_void_p, _c_void_p]),
+    "mcl_filter_reset": (_i32, [_c_void_p, _c_void_p, _c_void_p]),
+    "mcl_filter_get_state": (_i32, [_c_void_p, ctypes.POINTER(mcl_filter_state)]),
+    "mcl_filter_destroy": (_i32, [_c_void_p]),
     "mcl_server_create": (_i32, [ctypes.POINTER(mcl_server_desc), ctypes.POINTER(_c_void_p)]),
     "mcl_session_open": (_i32, [_c_void_p, ctypes.POINTER(mcl_session_desc), ctypes.POINTER(_c_void_p)]),
     "mcl_submit_scan": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, ctypes.POINTER(_u64)]),
@@ -545,6 +563,103 @@ def mcl_batch_destroy(batch: Batch):
 
 
 MCL_RESULT_DONE, MCL_RESULT_SUPERSEDED, MCL_RESULT_CLOSED = 0, 1, 2
+
+
+class Filter:
+    """Owning handle of a device-resident particle filter (mcl_filter_t): one
+    call runs motion update, sensor update with pose estimate and resampling.
+    `particles` is a CUDA float32 (P, 6) tensor (copied)."""
+
+    def __init__(self, m: Map, particles, max_points: int, params: mcl_sensor_params = None,
+                 motion_sigma=(0.0,) * 6, seed: int = 0, use_graph: bool = True,
+                 max_graphs: int = 0):
+        import torch
+        d = mcl_filter_desc(struct_size=ctypes.sizeof(mcl_filter_desc), map=m.handle,
+                            P=particles.shape[0], max_points=int(max_points),
+                            sensor=params if params is not None else sensor_params(),
+                            seed=int(seed), use_graph=int(bool(use_graph)), max_graphs=max_graphs)
+        for k in range(6):
+            d.motion_sigma[k] = float(motion_sigma[k])
+        h = ctypes.c_void_p()
+        _check(lib().mcl_filter_create(ctypes.byref(d), _dev_ptr(particles, torch.float32, 6, "particles"),
+                                       ctypes.byref(h)))
+        self.handle = h
+        self.map = m
+        self.P = particles.shape[0]
+
+    def step(self, scan, delta=None, out=None, stream=None):
+        import torch
+        dv = None
+        if delta is not None:
+            dv = (ctypes.c_float * 6)(*[float(x) for x in np.asarray(delta, np.float32).reshape(6)])
+        _check(lib().mcl_filter_step(self.handle, dv, _dev_ptr(scan, torch.float32, 3, "scan"),
+                                     scan.shape[0], _est_ptr(out), _stream(stream)))
+        return out
+
+    def reset(self, particles, stream=None):
+        import torch
+        _check(lib().mcl_filter_reset(self.handle, _dev_ptr(particles, torch.float32, 6, "particles"),
+                                      _stream(stream)))
+
+    def state(self) -> dict:
+        st = mcl_filter_state(struct_size=ctypes.sizeof(mcl_filter_state))
+        _check(lib().mcl_filter_get_state(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in mcl_filter_state._fields_ if k != "struct_size"}
+
+    def tensors(self) -> dict:
+        """Torch views of the filter's device arrays (no copy; valid while the
+        filter lives; read them after the stream's work finished)."""
+        import torch
+        st = self.state()
+        P = self.P
+        out = {name: _device_view(st[name], shape, dt)
+               for name, shape, dt in (("particles", (P, 6), torch.float32), ("logw", (P,), torch.float32),
+                                       ("w", (P,), torch.float32), ("idx", (P,), torch.int32))}
+        out["estimate"] = _device_view(st["estimate"], (ESTIMATE_BYTES,), torch.uint8)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().mcl_filter_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(ptr: int, shape, dtype):
+    """A torch tensor viewing device memory owned by the library (no copy),
+    through the CUDA array interface."""
+    import torch
+    typestr = {torch.float32: "<f4", torch.int32: "<i4", torch.uint8: "|u1"}[dtype]
+
+    class _Iface:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                    "data": (int(ptr), False), "version": 3, "strides": None}
+    return torch.as_tensor(_Iface(), device="cuda")
+
+
+def mcl_filter_create(m: Map, particles, max_points: int, **kw) -> Filter:
+    return Filter(m, particles, max_points, **kw)
+
+
+def mcl_filter_step(f: Filter, scan, delta=None, out=None, stream=None):
+    return f.step(scan, delta, out, stream)
+
+
+def mcl_filter_reset(f: Filter, particles, stream=None):
+    f.reset(particles, stream)
+
+
+def mcl_filter_get_state(f: Filter) -> dict:
+    return f.state()
+
+
+def mcl_filter_destroy(f: Filter):
+    f.close()
 
 
 class Server:

@@ -287,6 +287,59 @@ def true_pose(scene: Scene, seed: int, scan_kw: dict, clearance: float = 0.5,
     raise RuntimeError("true_pose: no pose with a full scan")
 
 
+def _rot(rpy):
+    """R = Rz(yaw) Ry(pitch) Rx(roll) (FP64, the pose convention of the inputs)."""
+    r, p, y = rpy
+    cr, sr, cp, sp, cy, sy = math.cos(r), math.sin(r), math.cos(p), math.sin(p), math.cos(y), math.sin(y)
+    return np.array([[cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr],
+                     [sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr],
+                     [-sp, cp * sr, cp * cr]])
+
+
+def trajectory(scene: Scene, start, steps: int, seed: int, step_len: float = 0.1,
+               clearance: float = 0.4):
+    """A seeded robot path through free space: each step moves step_len
+    forward in the body frame and turns by a yaw increment chosen from a
+    small set (the first in a seeded order that keeps the new position and
+    the midpoint more than `clearance` from every surface; else it turns in
+    place by 90 degrees). Returns the true poses (steps + 1, 6) in FP64 and
+    the odometry increments (steps, 6) FP32 in the body frame: the simulated
+    sensor input of a motion update."""
+    u = uniform(seed, 200, steps)
+    turns = np.radians([0.0, 5.0, -5.0, 15.0, -15.0, 40.0, -40.0])
+    poses = [np.asarray(start, np.float64).copy()]
+    deltas = []
+    for k in range(steps):
+        cur = poses[-1]
+        R = _rot(cur[3:])
+        order = np.roll(np.arange(len(turns)), int(u[k] * 3)) if u[k] < 0.5 else np.arange(len(turns))
+        step = None
+        for i in order:
+            fwd = R @ np.array([step_len, 0.0, 0.0])
+            mid, new = cur[:3] + 0.5 * fwd, cur[:3] + fwd
+            if sdf(scene, mid)[0] > clearance and sdf(scene, new)[0] > clearance:
+                step = np.array([step_len, 0.0, 0.0, 0.0, 0.0, turns[i]])
+                break
+        if step is None:
+            step = np.array([0.0, 0.0, 0.0, 0.0, 0.0, math.pi / 2])
+        R2 = R @ _rot(step[3:])
+        t2 = cur[:3] + R @ step[:3]
+        rpy = np.array([math.atan2(R2[2, 1], R2[2, 2]), math.asin(max(-1.0, min(1.0, -R2[2, 0]))),
+                        math.atan2(R2[1, 0], R2[0, 0])])
+        poses.append(np.concatenate([t2, rpy]))
+        deltas.append(step.astype(np.float32))
+    return np.array(poses), np.array(deltas, np.float32).reshape(steps, 6)
+
+
+def trajectory_scans(scene: Scene, poses, scan_kw: dict, seed: int):
+    """Scans raycast from each true pose; rays without a hit are dropped, so N varies."""
+    out = []
+    for k, pose in enumerate(poses):
+        pts, hit = raycast(scene, pose, seed=seed + 7919 * k, **scan_kw)
+        out.append(np.ascontiguousarray(pts[hit]))
+    return out
+
+
 # ------------------------------------------------------------------ workloads
 @dataclass
 class Workload:
