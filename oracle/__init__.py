@@ -55,7 +55,7 @@ def _L():
             lib.ora_pose_to_matrix.argtypes = [P, i64, cint, P]
             lib.ora_sensor_update.argtypes = [P, P, i64, P, i64, dbl, cint, cint, cint, P]
             lib.ora_sensor_update_mat.argtypes = [P, P, i64, P, i64, dbl, cint, cint, cint, P]
-            lib.ora_eval_points.argtypes = [P, P, P, i64, cint, P, P, P]
+            lib.ora_eval_points.argtypes = [P, P, P, i64, cint, cint, P, P, P]
             lib.ora_eval_points.restype = i64
             lib.ora_map_lookup.argtypes = [P, P, i64, P, P]
             lib.ora_normalise.argtypes = [P, i64, P, P, P]
@@ -132,36 +132,45 @@ def pose_to_matrix(poses, parity: bool = True) -> np.ndarray:
     return out
 
 
+def _flags(neglect: bool, trilinear: bool) -> int:
+    return int(bool(neglect)) | (2 if trilinear else 0)
+
+
 def sensor_update(m: Map, poses, scan, sigma: float, mode: int = LOGPROD, neglect: bool = False,
-                  parity: bool = True) -> np.ndarray:
+                  parity: bool = True, trilinear: bool = False) -> np.ndarray:
     """Particle log-weights L_p (FP64) for one scan."""
     poses = _f32(poses).reshape(-1, 6)
     scan = _f32(scan).reshape(-1, 3)
     out = np.empty(len(poses), np.float64)
     _L().ora_sensor_update(m._h, _p(poses), len(poses), _p(scan), len(scan),
-                           float(np.float32(sigma)), mode, int(neglect), int(parity), _p(out))
+                           float(np.float32(sigma)), mode, _flags(neglect, trilinear), int(parity),
+                           _p(out))
     return out
 
 
 def sensor_update_mat(m: Map, mats, scan, sigma: float, mode: int = LOGPROD,
-                      neglect: bool = False, parity: bool = False) -> np.ndarray:
+                      neglect: bool = False, parity: bool = False,
+                      trilinear: bool = False) -> np.ndarray:
     """Particle log-weights for poses given as FP64 [R | t] matrices (P, 3, 4)."""
     mats = np.ascontiguousarray(mats, np.float64).reshape(-1, 12)
     scan = _f32(scan).reshape(-1, 3)
     out = np.empty(len(mats), np.float64)
     _L().ora_sensor_update_mat(m._h, _p(mats), len(mats), _p(scan), len(scan),
-                               float(np.float32(sigma)), mode, int(neglect), int(parity), _p(out))
+                               float(np.float32(sigma)), mode, _flags(neglect, trilinear),
+                               int(parity), _p(out))
     return out
 
 
-def eval_points(m: Map, pose, scan, parity: bool = True):
-    """World points, read values d, voxel indices (-1 outside) and count of stored reads."""
+def eval_points(m: Map, pose, scan, parity: bool = True, trilinear: bool = False):
+    """World points, read values d, voxel indices (-1 outside; the lower corner
+    with trilinear) and count of stored reads."""
     pose = _f32(pose).reshape(6)
     scan = _f32(scan).reshape(-1, 3)
     x = np.empty((len(scan), 3), np.float64)
     d = np.empty(len(scan), np.float64)
     idx = np.empty((len(scan), 3), np.int64)
-    n = _L().ora_eval_points(m._h, _p(pose), _p(scan), len(scan), int(parity), _p(x), _p(d), _p(idx))
+    n = _L().ora_eval_points(m._h, _p(pose), _p(scan), len(scan), int(parity), int(trilinear),
+                             _p(x), _p(d), _p(idx))
     return x, d, idx, int(n)
 
 

@@ -13,6 +13,8 @@
  *   sensor model p_hit = exp(-m^2 / (2 sigma^2)) / sqrt(2 pi sigma^2)   Eq. 3
  *   m(x, z) = TSDF value read at the voxel containing the scan point
  *             seen from the particle's pose                    Sec. III
+ *             (or interpolated trilinearly between the voxel centres
+ *             around it: "pseudo-continuous via interpolation", Sec. III)
  *   cells without stored values are clamped to the truncation value Sec. III
  *   weights summed for normalisation                          Sec. V-A
  *   resampling draws a new set in proportion to the weights   Sec. III
@@ -202,13 +204,75 @@ void ora_pose_to_matrix(const float* poses, int64_t P, int parity, double* out) 
 
 /* ------------------------------------------------------------------ look-up of one point */
 
+/* Value of voxel (ix, iy, iz): 1 and *d = the stored value if the voxel is
+ * inside the grid and (brick maps) in an allocated brick, else 0 and
+ * *d = +tau (Sec. III clamping). */
+static int voxel_value(const ora_map* m, int64_t ix, int64_t iy, int64_t iz, double* d) {
+  *d = (double)m->tau_f;
+  if (ix < 0 || iy < 0 || iz < 0 || ix >= m->dims[0] || iy >= m->dims[1] || iz >= m->dims[2]) return 0;
+  if (m->kind == ORA_DENSE) {
+    *d = stored_value(m, (iz * m->dims[1] + iy) * m->dims[0] + ix);
+    return 1;
+  }
+  int64_t c = ((iz / BRICK_EDGE) * m->nb[1] + iy / BRICK_EDGE) * m->nb[0] + ix / BRICK_EDGE;
+  int32_t slot = m->coarse[c];
+  if (slot < 0) return 0;
+  int64_t local = ((iz % BRICK_EDGE) * BRICK_EDGE + iy % BRICK_EDGE) * BRICK_EDGE + ix % BRICK_EDGE;
+  *d = stored_value(m, (int64_t)slot * BRICK_EDGE * BRICK_EDGE * BRICK_EDGE + local);
+  return 1;
+}
+
+/* Trilinear read at world point x (Sec. III: a pseudo-continuous value by
+ * interpolation). Voxel i's value is the SDF at its centre o + (i + 1/2) r, so
+ * with f = u - 1/2 per axis (u the index-rule coordinate; parity mode: u and
+ * f in FP32) the eight centres around x are i0 + c, c in {0, 1}^3,
+ * i0 = floor(f), a = f - i0, and
+ *   d = sum_c prod_k (c_k ? a_k : 1 - a_k) * value(i0 + c)      (FP64)
+ * with +tau for corners outside the grid or in no brick. Returns 1 if any
+ * corner holds a stored value. idx3 gets i0 (or -1s if no corner is inside). */
+static int trilinear_read(const ora_map* m, const double x[3], int parity, double* d,
+                          int64_t idx3[3]) {
+  int64_t i0[3];
+  double a[3];
+  idx3[0] = idx3[1] = idx3[2] = -1;
+  *d = (double)m->tau_f;
+  for (int k = 0; k < 3; ++k) {
+    if (parity) {
+      float u = ((float)x[k] - m->origin_f[k]) * m->inv_voxel_f;
+      float f = u - 0.5f;
+      if (!(f >= -1.0f && f < (float)m->dims[k])) return 0;
+      float fl = floorf(f);
+      i0[k] = (int64_t)fl;
+      a[k] = (double)(f - fl);
+    } else {
+      double f = (x[k] - (double)m->origin_f[k]) / (double)m->voxel_f - 0.5;
+      if (!(f >= -1.0 && f < (double)m->dims[k])) return 0;
+      double fl = floor(f);
+      i0[k] = (int64_t)fl;
+      a[k] = f - fl;
+    }
+  }
+  double acc = 0.0;
+  int any = 0;
+  for (int c = 0; c < 8; ++c) {
+    int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    double v;
+    any |= voxel_value(m, i0[0] + cx, i0[1] + cy, i0[2] + cz, &v);
+    double wgt = (cx ? a[0] : 1.0 - a[0]) * (cy ? a[1] : 1.0 - a[1]) * (cz ? a[2] : 1.0 - a[2]);
+    acc += wgt * v;
+  }
+  *d = acc;
+  for (int k = 0; k < 3; ++k) idx3[k] = i0[k];
+  return any;
+}
+
 /* Scan point z seen from the pose [R | t]: world point x = R z + t.
  * Parity: x_i = fmaf(R_i0, z0, fmaf(R_i1, z1, fmaf(R_i2, z2, t_i))) in FP32.
  * Then the voxel containing x, the value stored there and whether it exists.
  * Returns 1 if a stored value was read (d set), 0 if outside the grid or in an
  * unallocated brick (d = +tau). idx3 gets the voxel index or -1s. */
 static int lookup_point(const ora_map* m, const double M[12], const float z[3], int parity,
-                        double x[3], double* d, int64_t idx3[3]) {
+                        int interp, double x[3], double* d, int64_t idx3[3]) {
   idx3[0] = idx3[1] = idx3[2] = -1;
   if (parity) {
     float xf[3];
@@ -227,6 +291,7 @@ static int lookup_point(const ora_map* m, const double M[12], const float z[3], 
     *d = v > tau ? tau : (v < -tau ? -tau : v);
     return 1;
   }
+  if (interp) return trilinear_read(m, x, parity, d, idx3);
   int64_t ix[3];
   for (int k = 0; k < 3; ++k) {
     if (parity) {
@@ -264,16 +329,21 @@ static double point_score(double d, double sigma, int mode) {
   return exp(e) / sqrt(2.0 * M_PI * sigma * sigma);
 }
 
+/* Flags of the sensor update: bit 0 leaves points without a stored value
+ * out (neglect), bit 1 reads the TSDF by trilinear interpolation. */
+#define ORA_NEGLECT 1
+#define ORA_TRILINEAR 2
+
 /* Log-weight of one particle with pose matrix M (Sec. III): LOGPROD sums the
- * per-point log scores, SUM takes the log of the summed p_hit. With `neglect`
- * points without a stored value are left out. */
+ * per-point log scores, SUM takes the log of the summed p_hit. With the
+ * neglect flag points without a stored value are left out. */
 static double particle_log_weight(const ora_map* m, const double M[12], const float* scan,
-                                  int64_t N, double sigma, int mode, int neglect, int parity) {
+                                  int64_t N, double sigma, int mode, int flags, int parity) {
   double x[3], d, acc = 0.0;
   int64_t idx3[3];
   for (int64_t j = 0; j < N; ++j) {
-    int stored = lookup_point(m, M, scan + 3 * j, parity, x, &d, idx3);
-    if (!stored && neglect) continue;
+    int stored = lookup_point(m, M, scan + 3 * j, parity, (flags & ORA_TRILINEAR) != 0, x, &d, idx3);
+    if (!stored && (flags & ORA_NEGLECT)) continue;
     acc += point_score(d, sigma, mode);
   }
   return (mode == ORA_LOGPROD) ? acc : log(acc);
@@ -282,39 +352,39 @@ static double particle_log_weight(const ora_map* m, const double M[12], const fl
 /* Log-weights L_p of all particles for one scan. Particles are split into
  * contiguous per-thread groups (the CPU design of Sec. V-A) when OpenMP is on. */
 void ora_sensor_update(const ora_map* m, const float* poses, int64_t P, const float* scan,
-                       int64_t N, double sigma, int mode, int neglect, int parity, double* out_L) {
+                       int64_t N, double sigma, int mode, int flags, int parity, double* out_L) {
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < P; ++p) {
     double M[12];
     pose_matrix(poses + 6 * p, parity, M);
-    out_L[p] = particle_log_weight(m, M, scan, N, sigma, mode, neglect, parity);
+    out_L[p] = particle_log_weight(m, M, scan, N, sigma, mode, flags, parity);
   }
 }
 
 /* Same with the poses given as FP64 [R | t] rows (12 per particle). Parity
  * mode rounds the given entries to FP32. */
 void ora_sensor_update_mat(const ora_map* m, const double* mats, int64_t P, const float* scan,
-                           int64_t N, double sigma, int mode, int neglect, int parity,
+                           int64_t N, double sigma, int mode, int flags, int parity,
                            double* out_L) {
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < P; ++p) {
     double M[12];
     for (int k = 0; k < 12; ++k) M[k] = parity ? (double)(float)mats[12 * p + k] : mats[12 * p + k];
-    out_L[p] = particle_log_weight(m, M, scan, N, sigma, mode, neglect, parity);
+    out_L[p] = particle_log_weight(m, M, scan, N, sigma, mode, flags, parity);
   }
 }
 
 /* Per-point detail for one pose: world coordinates, read value d and the
  * voxel index (-1 where outside). Returns the number of stored reads. */
 int64_t ora_eval_points(const ora_map* m, const float pose[6], const float* scan, int64_t N,
-                        int parity, double* out_x, double* out_d, int64_t* out_idx) {
+                        int parity, int interp, double* out_x, double* out_d, int64_t* out_idx) {
   double M[12];
   int64_t n_stored = 0;
   pose_matrix(pose, parity, M);
   for (int64_t j = 0; j < N; ++j) {
     double x[3], d;
     int64_t idx3[3];
-    n_stored += lookup_point(m, M, scan + 3 * j, parity, x, &d, idx3);
+    n_stored += lookup_point(m, M, scan + 3 * j, parity, interp, x, &d, idx3);
     if (out_x) memcpy(out_x + 3 * j, x, sizeof(x));
     if (out_d) out_d[j] = d;
     if (out_idx) memcpy(out_idx + 3 * j, idx3, sizeof(idx3));
@@ -331,7 +401,7 @@ void ora_map_lookup(const ora_map* m, const float* pts, int64_t n, int64_t* out_
   for (int64_t j = 0; j < n; ++j) {
     double x[3], d;
     int64_t idx3[3];
-    lookup_point(m, I, pts + 3 * j, 1, x, &d, idx3);
+    lookup_point(m, I, pts + 3 * j, 1, 0, x, &d, idx3);
     out_index[j] = idx3[0] < 0 ? -1 : (idx3[2] * m->dims[1] + idx3[1]) * m->dims[0] + idx3[0];
     out_value[j] = d;
   }
