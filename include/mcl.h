@@ -133,6 +133,7 @@ mcl_status mcl_map_lookup(mcl_map_t map, const float* points, int64_t N, int64_t
 
 enum { MCL_LOGPROD = 0, MCL_SUM = 1 };
 #define MCL_NEGLECT_OUTSIDE 1u /* points without a stored value are left out */
+#define MCL_TRILINEAR 2u       /* read the TSDF by trilinear interpolation (see below) */
 
 /* Sensor-model parameters (Sec. III, Eq. 3).
  * mode LOGPROD: per-point score -d^2 / (2 sigma^2) (log of Eq. 3 without its
@@ -140,6 +141,14 @@ enum { MCL_LOGPROD = 0, MCL_SUM = 1 };
  * mode SUM: per-point score p_hit of Eq. 3, L = log(sum of p_hit).
  * A point outside the grid or in a voxel of no brick reads d = +truncation
  * (Sec. III clamping), or with MCL_NEGLECT_OUTSIDE contributes nothing.
+ * MCL_TRILINEAR (Sec. III: a pseudo-continuous value by interpolation)
+ * replaces the containing voxel's value by the trilinear interpolation of the
+ * eight voxel centres around the point: with u as in the index rule and
+ * f = u - 1/2 (FP32), corners i0 + {0, 1} per axis, i0 = floor(f), weights
+ * a = f - i0 and 1 - a; a corner outside the grid or in no brick reads
+ * +truncation, and the point counts as stored (for MCL_NEGLECT_OUTSIDE) if
+ * any corner is. Interpolated in FP32 along x, then y, then z. Needs
+ * lanes_per_particle 0 or 32; unroll and pipeline are ignored.
  * points_per_chunk and lanes_per_particle fix the FP32 summation order
  * (points of one particle are split in chunks of points_per_chunk, each
  * summed by lanes_per_particle lanes and a shuffle tree, chunks added in

@@ -269,6 +269,121 @@ __device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* 
   accumulate<DTYPE, MODE, U>(a, dv, use, acc);
 }
 
+// ---------------------------------------------------------------- trilinear read
+// MCL_TRILINEAR (Sec. III: a pseudo-continuous value by interpolation). The
+// stored value of voxel i is the SDF at its centre o + (i + 1/2) r, so with
+// u = (x - o) * inv as in the index rule and f = u - 1/2 (FP32), the eight
+// centres around x are i0 + {0, 1} per axis, i0 = floor(f), with weights
+// a = f - i0 and 1 - a. A corner outside the grid or in no brick reads the
+// same value as an unstored voxel. The point counts as stored if any corner
+// is. Interpolation in FP32: along x for the four (y, z) corner pairs, then
+// y, then z, each step fma(a, v1 - v0, v0).
+template <int KIND, int DTYPE, int MODE>
+__device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y, float z,
+                                          bool& stored) {
+  const MapView& m = a.map;
+  const float fx = __fsub_rn(__fmul_rn(__fsub_rn(x, m.ox), m.inv), 0.5f);
+  const float fy = __fsub_rn(__fmul_rn(__fsub_rn(y, m.oy), m.inv), 0.5f);
+  const float fz = __fsub_rn(__fmul_rn(__fsub_rn(z, m.oz), m.inv), 0.5f);
+  stored = false;
+  // Some corner is inside iff -1 <= f < n on every axis (NaN fails).
+  if (!((fx >= -1.f) & (fx < m.fnx) & (fy >= -1.f) & (fy < m.fny) & (fz >= -1.f) & (fz < m.fnz)))
+    return a.vout;
+  const float flx = floorf(fx), fly = floorf(fy), flz = floorf(fz);
+  const int x0 = (int)flx, y0 = (int)fly, z0 = (int)flz;
+  const float ax = __fsub_rn(fx, flx), ay = __fsub_rn(fy, fly), az = __fsub_rn(fz, flz);
+  const bool inx[2] = {x0 >= 0, x0 + 1 < m.nx};
+  const bool iny[2] = {y0 >= 0, y0 + 1 < m.ny};
+  const bool inz[2] = {z0 >= 0, z0 + 1 < m.nz};
+  float v[8];
+  if constexpr (KIND == MCL_MAP_DENSE) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+      const bool in = inx[cx] & iny[cy] & inz[cz];
+      const size_t lin = ((size_t)(z0 + cz) * (size_t)m.ny + (size_t)(y0 + cy)) * (size_t)m.nx +
+                         (size_t)(x0 + cx);
+      v[c] = in ? load_raw<DTYPE, MODE>(m.values, lin) : a.vout;
+      stored |= in;
+    }
+  } else {
+    uint32_t key[8], slot[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+      key[c] = ((uint32_t)((z0 + cz) >> 4) * m.nby + (uint32_t)((y0 + cy) >> 4)) * m.nbx +
+               (uint32_t)((x0 + cx) >> 4);
+    }
+    // One probe per distinct brick: a corner reuses the slot of a neighbouring
+    // corner (lower along x, else y, else z) in the same brick.
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+      const bool in = inx[cx] & iny[cy] & inz[cz];
+      slot[c] = kNoSlot;
+      if (!in) continue;
+      int r = -1;
+      if (cx && (inx[0] & iny[cy] & inz[cz]) && key[c ^ 1] == key[c]) r = c ^ 1;
+      else if (cy && (inx[cx] & iny[0] & inz[cz]) && key[c ^ 2] == key[c]) r = c ^ 2;
+      else if (cz && (inx[cx] & iny[cy] & inz[0]) && key[c ^ 4] == key[c]) r = c ^ 4;
+      if (r >= 0) {
+        slot[c] = slot[r];
+      } else {
+        const uint32_t h = brick_hash(key[c], m.hash_shift);
+        const uint2 e = __ldg(m.table + h);
+        slot[c] = e.x == key[c] ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key[c], h));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+      const bool st = slot[c] != kNoSlot;
+      v[c] = st ? load_raw<DTYPE, MODE>(m.values, (size_t)slot[c] * kBrickVoxels +
+                                                     brick_local<KIND>(x0 + cx, y0 + cy, z0 + cz))
+                : a.vout;
+      stored |= st;
+    }
+  }
+  const float c00 = fmaf(ax, __fsub_rn(v[1], v[0]), v[0]);
+  const float c10 = fmaf(ax, __fsub_rn(v[3], v[2]), v[2]);
+  const float c01 = fmaf(ax, __fsub_rn(v[5], v[4]), v[4]);
+  const float c11 = fmaf(ax, __fsub_rn(v[7], v[6]), v[6]);
+  const float c0 = fmaf(ay, __fsub_rn(c10, c00), c00);
+  const float c1 = fmaf(ay, __fsub_rn(c11, c01), c01);
+  return fmaf(az, __fsub_rn(c1, c0), c0);
+}
+
+// One particle's points of the staged chunk with the trilinear read: lane
+// glane takes points glane, glane + G, ... in order (the summation order of
+// the nearest-voxel path), two per loop step.
+template <int KIND, int DTYPE, int MODE, int G>
+__device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __restrict__ sscan,
+                                         int glane, int cnt, const float4& r0, const float4& r1,
+                                         const float4& r2, float& acc) {
+  int j = glane;
+  for (; j + G < cnt; j += 2 * G) {
+    float d[2];
+    bool use[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      float x, y, w;
+      transform_point(r0, r1, r2, sscan[j + u * G], x, y, w);
+      bool st;
+      d[u] = tri_read<KIND, DTYPE, MODE>(a, x, y, w, st);
+      use[u] = st || !a.neglect;
+    }
+    accumulate<DTYPE, MODE, 2>(a, d, use, acc);
+  }
+  if (j < cnt) {
+    float x, y, w;
+    transform_point(r0, r1, r2, sscan[j], x, y, w);
+    bool st;
+    float d = tri_read<KIND, DTYPE, MODE>(a, x, y, w, st);
+    bool use = st || !a.neglect;
+    accumulate<DTYPE, MODE, 1>(a, &d, &use, acc);
+  }
+}
+
 // Resident CTAs per SM the register allocation is held to: 6 for the 2- and
 // 4-deep loops (40 registers), 3 for the 8-deep loop (measured faster than the
 // 2 its free allocation gives).
@@ -276,9 +391,9 @@ __device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* 
 #define MCL_SENSOR_MIN_BLOCKS 6
 #endif
 
-template <int U>
+template <int U, bool TRI = false>
 struct MinBlocks {
-  static constexpr int value = U == 8 ? 3 : MCL_SENSOR_MIN_BLOCKS;
+  static constexpr int value = TRI ? 3 : (U == 8 ? 3 : MCL_SENSOR_MIN_BLOCKS);
 };
 
 // Stage `cnt` scan points starting at `src` into shared memory with one bulk
@@ -308,7 +423,7 @@ __device__ __forceinline__ bool stage_chunk(float4* sscan, uint32_t bar_s, const
 // Particles [p0, p0 + pn) of one session against the staged chunk c (cnt
 // points): each lane group takes a particle, sums its chunk terms and writes
 // the chunk sum to partial[c * P + p].
-template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
 __device__ __forceinline__ void process_block(const SensorArgs& a, const float4* __restrict__ sscan,
                                               float4* smat, const float4* __restrict__ mats,
                                               float* __restrict__ partial, int P, int c, int p0,
@@ -335,13 +450,23 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const float4*
     const float4 r0 = __ldg(mats + 3 * p), r1 = __ldg(mats + 3 * p + 1), r2 = __ldg(mats + 3 * p + 2);
 #endif
     typename Raw<DTYPE, MODE>::acc acc = 0;
-    int base = 0;
-    if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
-      eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, full_end, glane, r0, r1, r2, acc);
-      base = full_end;
+    if constexpr (TRI) {
+      static_assert(G == 32, "the trilinear read uses whole-warp groups");
+#if MCL_MATRIX_IN_SMEM
+      const float4 q0 = lds_volatile(&r0), q1 = lds_volatile(&r0 + 1), q2 = lds_volatile(&r0 + 2);
+#else
+      const float4 q0 = r0, q1 = r1, q2 = r2;
+#endif
+      eval_tri<KIND, DTYPE, MODE, G>(a, sscan, glane, cnt, q0, q1, q2, acc);
+    } else {
+      int base = 0;
+      if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
+        eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, full_end, glane, r0, r1, r2, acc);
+        base = full_end;
+      }
+      for (; base < cnt; base += STEP)
+        eval_checked<KIND, DTYPE, MODE, G, U>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, acc);
     }
-    for (; base < cnt; base += STEP)
-      eval_checked<KIND, DTYPE, MODE, G, U>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, acc);
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1)
       acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
@@ -362,8 +487,8 @@ __device__ __forceinline__ void init_barrier(uint32_t bar_s) {
 }
 
 // One session: items (chunk c, particle block) strided over a persistent grid.
-template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
-__global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const SensorArgs a) {
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
+__global__ void __launch_bounds__(256, (MinBlocks<U, TRI>::value)) k_sensor(const SensorArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
   const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
@@ -380,7 +505,8 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const Senso
       if (!stage_chunk(sscan, bar_s, a.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
       loaded = c;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, smat, a.mats, a.partial, a.P, c, p0, pn, cnt);
+    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, sscan, smat, a.mats, a.partial, a.P, c, p0,
+                                                      pn, cnt);
   }
 }
 
@@ -388,8 +514,8 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor(const Senso
 // chunk, particle block) of uneven sizes, numbered session by session
 // (item_begin[s] is the first item of session s), strided over a persistent
 // grid. Each session's results are the ones the single-session kernel gives.
-template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
-__global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor_batch(const BatchArgs b) {
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
+__global__ void __launch_bounds__(256, (MinBlocks<U, TRI>::value)) k_sensor_batch(const BatchArgs b) {
   const SensorArgs& a = b.base;
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
@@ -415,21 +541,23 @@ __global__ void __launch_bounds__(256, MinBlocks<U>::value) k_sensor_batch(const
       if (!stage_chunk(sscan, bar_s, S.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
       loaded = key;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, smat, S.mats, S.partial, S.P, c, p0, pn, cnt);
+    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, sscan, smat, S.mats, S.partial, S.P, c, p0,
+                                                      pn, cnt);
   }
 }
 
-template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI = false>
 void* kernel_ptr(bool batch) {
-  return batch ? reinterpret_cast<void*>(&k_sensor_batch<KIND, DTYPE, MODE, G, U, PIPE>)
-               : reinterpret_cast<void*>(&k_sensor<KIND, DTYPE, MODE, G, U, PIPE>);
+  return batch ? reinterpret_cast<void*>(&k_sensor_batch<KIND, DTYPE, MODE, G, U, PIPE, TRI>)
+               : reinterpret_cast<void*>(&k_sensor<KIND, DTYPE, MODE, G, U, PIPE, TRI>);
 }
 
 // Kernel for one storage type, or NULL for an unsupported shape. Shapes:
 // G = 32 with U = 2 or 4 (plain or pipelined) or U = 8 (plain); G = 16 or 8
-// with U = 4 (plain).
+// with U = 4 (plain); the trilinear read with G = 32.
 template <int KIND, int DTYPE, int MODE>
 void* pick_shape(const SensorShape& sh, bool batch) {
+  if (sh.interp) return sh.lanes == 32 ? kernel_ptr<KIND, DTYPE, MODE, 32, 2, false, true>(batch) : nullptr;
   const bool pipe = sh.pipeline != 0;
   if (sh.lanes == 32) {
     if (sh.unroll == 2) return pipe ? kernel_ptr<KIND, DTYPE, MODE, 32, 2, true>(batch)

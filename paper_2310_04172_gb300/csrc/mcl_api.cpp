@@ -353,7 +353,10 @@ mcl_status check_params(const mcl_sensor_params* p) {
   if (p->struct_size < sizeof(mcl_sensor_params)) return fail(MCL_EINVAL, "sensor params: struct_size");
   if (!finite_pos(p->sigma_hit)) return fail(MCL_EINVAL, "sensor params: sigma_hit must be finite and > 0");
   if (p->mode != MCL_LOGPROD && p->mode != MCL_SUM) return fail(MCL_EINVAL, "sensor params: mode %d", p->mode);
-  if (p->flags & ~MCL_NEGLECT_OUTSIDE) return fail(MCL_EINVAL, "sensor params: unknown flags 0x%x", p->flags);
+  if (p->flags & ~(MCL_NEGLECT_OUTSIDE | MCL_TRILINEAR))
+    return fail(MCL_EINVAL, "sensor params: unknown flags 0x%x", p->flags);
+  if ((p->flags & MCL_TRILINEAR) && p->lanes_per_particle != 0 && p->lanes_per_particle != 32)
+    return fail(MCL_EINVAL, "sensor params: the trilinear read needs 32 lanes per particle");
   const int c = p->points_per_chunk;
   if (c != 0 && (c < 32 || c > 8192 || c % 32))
     return fail(MCL_EINVAL, "sensor params: points_per_chunk %d", c);
@@ -388,6 +391,11 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
     sh.unroll = 4;
     sh.pipeline = 0;
   } else if (sh.unroll == 8) {
+    sh.pipeline = 0;
+  }
+  sh.interp = (p->flags & MCL_TRILINEAR) ? 1 : 0;
+  if (sh.interp) {  // two points per lane per step, no pipelining
+    sh.unroll = 2;
     sh.pipeline = 0;
   }
   sh.threads = 256;

@@ -30,6 +30,7 @@ struct SessionPlan {
 struct Group {
   mcl_map_t map;
   int mode, neglect;
+  uint32_t flags;
   float sigma;
   std::vector<int> sessions;
   SensorShape sh;
@@ -175,11 +176,11 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     sp.off_last = o;
     o = align256(o + (u.resample_idx ? (size_t)(nt + 1) * 8 : 0));
     off = align256(off + o);
-    // group by map and score constants
+    // group by map, score constants and read rule
     const int neglect = (u.flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
     int gi = -1;
     for (size_t k = 0; k < b->g.size(); ++k)
-      if (b->g[k].map == u.map && b->g[k].mode == u.mode && b->g[k].neglect == neglect &&
+      if (b->g[k].map == u.map && b->g[k].mode == u.mode && b->g[k].flags == u.flags &&
           b->g[k].sigma == u.sigma_hit)
         gi = (int)k;
     if (gi < 0) {
@@ -187,6 +188,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       g.map = u.map;
       g.mode = u.mode;
       g.neglect = neglect;
+      g.flags = u.flags;
       g.sigma = u.sigma_hit;
       g.sh = sp.pl.sh;
       b->g.push_back(g);

@@ -141,6 +141,7 @@ struct SensorShape {
   int ppi;        // particles per work item
   int unroll;     // points per lane per loop step
   int pipeline;   // 1: next step's index look-ups overlap this step's gathers
+  int interp;     // 1: trilinear read (MCL_TRILINEAR)
   int threads;    // threads per CTA
   int grid;       // CTAs (persistent)
 };

@@ -155,6 +155,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
   struct G {
     mcl_map_t map;
     int mode, neglect;
+    uint32_t flags;
     float sigma;
     std::vector<size_t> idx;
   };
@@ -164,9 +165,9 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     const int neglect = (ss->flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
     G* g = nullptr;
     for (auto& x : groups)
-      if (x.map == ss->map && x.mode == ss->mode && x.neglect == neglect && x.sigma == ss->sigma) g = &x;
+      if (x.map == ss->map && x.mode == ss->mode && x.flags == ss->flags && x.sigma == ss->sigma) g = &x;
     if (!g) {
-      groups.push_back(G{ss->map, ss->mode, neglect, ss->sigma, {}});
+      groups.push_back(G{ss->map, ss->mode, neglect, ss->flags, ss->sigma, {}});
       g = &groups.back();
     }
     g->idx.push_back(i);

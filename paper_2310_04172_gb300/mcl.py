@@ -23,6 +23,7 @@ MCL_F32, MCL_F16, MCL_I16 = 0, 1, 2
 MCL_LAYOUT_LINEAR, MCL_LAYOUT_BLOCK4 = 0, 1
 MCL_LOGPROD, MCL_SUM = 0, 1
 MCL_NEGLECT_OUTSIDE = 1
+MCL_TRILINEAR = 2
 PHASES = ("pose", "pack", "sensor", "reduce", "normalise", "resample", "motion", "other")
 
 _c_void_p, _i64, _i32, _u32, _u64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
