@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LOGPROD, SUM = 0, 1
+LOGPROD, SUM, SCORE = 0, 1, 2
 DENSE, BRICK, ANALYTIC = 0, 1, 2
 PLANE, SPHERE, BOX = 0, 1, 2
 
@@ -52,6 +52,7 @@ def _L():
             lib.ora_map_create_analytic.argtypes = [i64, P, flt]
             lib.ora_map_create_analytic.restype = P
             lib.ora_map_destroy.argtypes = [P]
+            lib.ora_map_set_outside.argtypes = [P, dbl]
             lib.ora_pose_to_matrix.argtypes = [P, i64, cint, P]
             lib.ora_sensor_update.argtypes = [P, P, i64, P, i64, dbl, cint, cint, cint, P]
             lib.ora_sensor_update_mat.argtypes = [P, P, i64, P, i64, dbl, cint, cint, cint, P]
@@ -110,6 +111,11 @@ class Map:
         if not h:
             raise ValueError("oracle map: bad map description")
         return cls(h, keep)
+
+    def set_outside(self, value: float) -> "Map":
+        """Value read where nothing is stored (default +tau)."""
+        _L().ora_map_set_outside(self._h, float(value))
+        return self
 
     @classmethod
     def analytic(cls, prims, tau: float) -> "Map":
@@ -302,3 +308,31 @@ def pose_estimate(poses, w) -> dict:
         "best_pose": s[am].copy() if am >= 0 else np.full(6, np.nan, np.float32),
         "best_w": float(wf[am]) if am >= 0 else float("nan"),
     }
+
+
+def _dequantised(values, dtype: int, tau: float) -> np.ndarray:
+    """Stored values as the real numbers they stand for (FP64); scaled int16
+    stands for q * tau / 32767 (tau as FP32)."""
+    v = np.asarray(values)
+    if dtype == 2:
+        return v.astype(np.float64) * (float(np.float32(tau)) / 32767.0)
+    return v.astype(np.float64)
+
+
+def score_of(d, sigma: float, dtype: int = 1) -> np.ndarray:
+    """Per-voxel score exp(-d^2 / (2 sigma^2)) of Eq. 3 without its constant
+    (Sec. III: the exponential evaluated once per map entry before the
+    scans), in FP64 and rounded once to the storage type (FP16 or FP32,
+    nearest even). sigma is read as FP32."""
+    sig = float(np.float32(sigma))
+    d = np.asarray(d, np.float64)
+    e = np.exp(-(d * d) / (2.0 * sig * sig))
+    return e.astype(np.float16 if dtype == 1 else np.float32)
+
+
+def score_map(scene_map, sigma: float, dtype: int = 1):
+    """(values, outside): the score map's stored values (same layout as the
+    TSDF's) and the score read where nothing is stored (that of +tau)."""
+    vals = score_of(_dequantised(scene_map.values, scene_map.dtype, scene_map.tau), sigma, dtype)
+    outside = score_of(float(np.float32(scene_map.tau)), sigma, dtype)
+    return vals, float(outside)

@@ -53,7 +53,7 @@
 
 enum { ORA_DENSE = 0, ORA_BRICK = 1, ORA_ANALYTIC = 2 };
 enum { ORA_F32 = 0, ORA_F16 = 1, ORA_I16 = 2 };
-enum { ORA_LOGPROD = 0, ORA_SUM = 1 };
+enum { ORA_LOGPROD = 0, ORA_SUM = 1, ORA_SCORE = 2 };
 enum { ORA_PRIM_PLANE = 0, ORA_PRIM_SPHERE = 1, ORA_PRIM_BOX = 2 };
 
 #define BRICK_EDGE 16
@@ -61,6 +61,7 @@ enum { ORA_PRIM_PLANE = 0, ORA_PRIM_SPHERE = 1, ORA_PRIM_BOX = 2 };
 typedef struct {
   int kind, dtype;
   float origin_f[3], voxel_f, inv_voxel_f, tau_f;
+  double outside; /* value read where nothing is stored: +tau, or the score of +tau for a score map */
   int64_t dims[3];
   const void* values; /* dense: dims[2]*dims[1]*dims[0]; brick: n_bricks * 4096 */
   int64_t n_bricks;
@@ -85,6 +86,7 @@ ora_map* ora_map_create(int kind, int dtype, const float origin[3], float voxel,
   m->voxel_f = voxel;
   m->inv_voxel_f = inv_voxel;
   m->tau_f = tau;
+  m->outside = (double)tau;
   m->values = values;
   if (kind == ORA_BRICK) {
     for (int k = 0; k < 3; ++k) {
@@ -123,6 +125,11 @@ ora_map* ora_map_create_analytic(int64_t n_prims, const double* prims, float tau
   memcpy(m->prims, prims, (size_t)n_prims * 8 * sizeof(double));
   return m;
 }
+
+/* Score maps (Sec. III: the exponential of Eq. 3 evaluated once per map
+ * entry before the scans): their values are per-voxel scores, and a point
+ * where nothing is stored reads the score of +tau, set here. */
+void ora_map_set_outside(ora_map* m, double outside) { m->outside = outside; }
 
 void ora_map_destroy(ora_map* m) {
   if (!m) return;
@@ -208,7 +215,7 @@ void ora_pose_to_matrix(const float* poses, int64_t P, int parity, double* out) 
  * inside the grid and (brick maps) in an allocated brick, else 0 and
  * *d = +tau (Sec. III clamping). */
 static int voxel_value(const ora_map* m, int64_t ix, int64_t iy, int64_t iz, double* d) {
-  *d = (double)m->tau_f;
+  *d = m->outside;
   if (ix < 0 || iy < 0 || iz < 0 || ix >= m->dims[0] || iy >= m->dims[1] || iz >= m->dims[2]) return 0;
   if (m->kind == ORA_DENSE) {
     *d = stored_value(m, (iz * m->dims[1] + iy) * m->dims[0] + ix);
@@ -235,7 +242,7 @@ static int trilinear_read(const ora_map* m, const double x[3], int parity, doubl
   int64_t i0[3];
   double a[3];
   idx3[0] = idx3[1] = idx3[2] = -1;
-  *d = (double)m->tau_f;
+  *d = m->outside;
   for (int k = 0; k < 3; ++k) {
     if (parity) {
       float u = ((float)x[k] - m->origin_f[k]) * m->inv_voxel_f;
@@ -298,11 +305,11 @@ static int lookup_point(const ora_map* m, const double M[12], const float z[3], 
       /* u = (x - o) * (1/r), two FP32 roundings; inside iff 0 <= u < n (NaN fails) */
       float diff = (float)x[k] - m->origin_f[k];
       float u = diff * m->inv_voxel_f;
-      if (!(u >= 0.0f && u < (float)m->dims[k])) { *d = (double)m->tau_f; return 0; }
+      if (!(u >= 0.0f && u < (float)m->dims[k])) { *d = m->outside; return 0; }
       ix[k] = (int64_t)floorf(u);
     } else {
       double u = floor((x[k] - (double)m->origin_f[k]) / (double)m->voxel_f);
-      if (!(u >= 0.0 && u < (double)m->dims[k])) { *d = (double)m->tau_f; return 0; }
+      if (!(u >= 0.0 && u < (double)m->dims[k])) { *d = m->outside; return 0; }
       ix[k] = (int64_t)u;
     }
   }
@@ -313,7 +320,7 @@ static int lookup_point(const ora_map* m, const double M[12], const float z[3], 
   }
   int64_t c = ((ix[2] / BRICK_EDGE) * m->nb[1] + ix[1] / BRICK_EDGE) * m->nb[0] + ix[0] / BRICK_EDGE;
   int32_t slot = m->coarse[c];
-  if (slot < 0) { *d = (double)m->tau_f; return 0; }
+  if (slot < 0) { *d = m->outside; return 0; }
   int64_t local = ((ix[2] % BRICK_EDGE) * BRICK_EDGE + ix[1] % BRICK_EDGE) * BRICK_EDGE + ix[0] % BRICK_EDGE;
   *d = stored_value(m, (int64_t)slot * BRICK_EDGE * BRICK_EDGE * BRICK_EDGE + local);
   return 1;
@@ -322,8 +329,11 @@ static int lookup_point(const ora_map* m, const double M[12], const float z[3], 
 /* ------------------------------------------------------------------ sensor update */
 
 /* Per-point score of Eq. 3. LOGPROD: log p_hit without the constant,
- * -d^2 / (2 sigma^2). SUM: p_hit itself. */
+ * -d^2 / (2 sigma^2). SUM: p_hit itself. SCORE (a score map, mode SUM):
+ * the stored value is exp(-d^2 / (2 sigma^2)), so p_hit = value times the
+ * constant of Eq. 3. */
 static double point_score(double d, double sigma, int mode) {
+  if (mode == ORA_SCORE) return d / sqrt(2.0 * M_PI * sigma * sigma); /* d is the stored score */
   double e = -(d * d) / (2.0 * sigma * sigma);
   if (mode == ORA_LOGPROD) return e;
   return exp(e) / sqrt(2.0 * M_PI * sigma * sigma);
