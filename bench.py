@@ -54,10 +54,14 @@ def parse_args(argv=None):
     ap.add_argument("--pipeline", type=int, default=0, help="0 auto, 1 off, 2 on")
     ap.add_argument("--order", type=int, default=0, help="particle order: 0 auto, 1 given, 2 spatial")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
-    ap.add_argument("--mode", default="headline", choices=["headline", "serving", "precision", "vlp16"],
+    ap.add_argument("--mode", default="headline",
+                    choices=["headline", "serving", "precision", "vlp16", "filter", "trilinear"],
                     help="headline: 1M x 65,536 int16 step (+ serving probe); serving: 64 sessions over "
                          "8 maps; precision: f32/f16/i16 sweep with oracle weight error; vlp16: plain vs "
-                         "batched graph-captured form on the VLP-16 tracking workload")
+                         "batched graph-captured form on the VLP-16 tracking workload; filter: whole "
+                         "filter steps (motion, sensor, estimate, resampling) as separate calls, as one "
+                         "call and replayed from a CUDA graph; trilinear: the 1M x 65,536 step with the "
+                         "trilinear read")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving probe of the headline")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     return ap.parse_args(argv)
@@ -773,6 +777,134 @@ def run_vlp16(args):
     return 0
 
 
+# ------------------------------------------------------------------ whole filter steps
+def run_filter(args):
+    """Whole filter steps on two tracking workloads: the 1,000-particle room
+    (VLP-16 shape, 1,024 points: launch-bound) and the 50,000-particle hall
+    (28,800 points). Three forms of the same step: separate C-ABI calls
+    (motion, sensor update with estimate, resampling, copy back), one filter
+    call per step, and the filter replayed from a CUDA graph."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import scenes
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    sigma_m = np.array([0.02, 0.02, 0.01, 0.005, 0.005, 0.01], np.float32)
+    delta = np.array([0.05, 0.0, 0.0, 0.0, 0.0, 0.01], np.float32)
+    reps = max(args.steps, 50)
+
+    def timed(fn, n):
+        for k in range(5):
+            fn(k)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for k in range(n):
+            fn(k)
+        e.record()
+        e.synchronize()
+        return a.elapsed_time(e) / n
+
+    out = {}
+    for label, wl in (("room_1000x1024", scenes.room_plain(P=1000)),
+                      ("hall_50000x28800", scenes.vlp16_multiroom(P=50_000, dtype=scenes.F32))):
+        m = mcl.map_from_scene(wl.map)
+        P, N = wl.particles.shape[0], wl.scan.shape[0]
+        prm = mcl.sensor_params(wl.sigma_hit)
+        scan = torch.from_numpy(wl.scan).cuda()
+        parts = torch.from_numpy(wl.particles).cuda()
+        nxt = torch.empty_like(parts)
+        logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+        idx = torch.empty(P, dtype=torch.int32, device="cuda")
+        est = mcl.estimate_buffer()
+
+        def calls(k):
+            mcl.mcl_motion_update(parts, delta, sigma_m, 7, k)
+            mcl.mcl_sensor_update_estimate(m, parts, scan, prm, logw, w, est)
+            mcl.mcl_resample(w, 0.5, idx, parts, nxt)
+            parts.copy_(nxt)
+
+        res = {"particles": P, "points": N}
+        res["separate_calls_ms"] = timed(calls, reps)
+        for name, graph in (("filter_call_ms", False), ("filter_graph_ms", True)):
+            f = mcl.Filter(m, torch.from_numpy(wl.particles).cuda(), max_points=N, params=prm,
+                           motion_sigma=sigma_m, seed=7, use_graph=graph)
+            res[name] = timed(lambda k: f.step(scan, delta, est), reps)
+            f.close()
+        # cost of the fused estimate: the sensor update with and without it
+        res["sensor_update_ms"] = timed(lambda k: mcl.mcl_sensor_update(m, parts, scan, prm, logw, w), reps)
+        res["sensor_update_estimate_ms"] = timed(
+            lambda k: mcl.mcl_sensor_update_estimate(m, parts, scan, prm, logw, w, est), reps)
+        res["graph_steps_per_s"] = 1e3 / res["filter_graph_ms"]
+        res["graph_evals_per_s"] = P * N / (res["filter_graph_ms"] / 1e3)
+        out[label] = res
+        m.close()
+    hall = out["hall_50000x28800"]
+    line = {"mode": "filter", "metric": "particle×point evals/s of whole filter steps (50,000×28,800)",
+            "value": hall["graph_evals_per_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32", "steps": reps,
+            "config": {"workload": "room_plain_128x128x64_1024pts, vlp16_multiroom_512x512x128_28800pts",
+                       "step": "motion update, sensor update + pose estimate, systematic resampling"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ trilinear read
+def run_trilinear(args):
+    """The headline step (1M x 65,536, int16 bricks) with the trilinear read:
+    eight corner values per evaluation (one brick-index probe per distinct
+    brick), against the nearest-voxel read in the same run."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    wl = make_workload(args, 0)
+    m = mcl.map_from_scene(wl.map)
+    P, N = wl.particles.shape[0], wl.scan.shape[0]
+    parts = torch.from_numpy(wl.particles).cuda()
+    scan = torch.from_numpy(np.ascontiguousarray(wl.scan)).cuda()
+    logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+    elem = 4 if args.dtype == "f32" else 2
+    peak, peak_src = peaks()
+    out = {}
+    steps = max(1, min(args.steps, 5))
+    for name, flags in (("nearest", 0), ("trilinear", mcl.MCL_TRILINEAR)):
+        prm = mcl.sensor_params(wl.sigma_hit, flags=flags)
+        for _ in range(max(args.warmup, 3)):
+            mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        mcl.mcl_profile_begin()
+        a.record()
+        for _ in range(steps):
+            mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+        e.record()
+        e.synchronize()
+        prof = mcl.mcl_profile_end()
+        ms = a.elapsed_time(e) / steps
+        kms = prof["sensor"]["ms"] / max(1, prof["sensor"]["launches"])
+        per_eval = (8 if flags else 1) * elem + 8
+        abytes = P * N * per_eval + P * 52 + N * 16
+        out[name] = {"ms_per_step": ms, "kernel_ms": kms, "evals_per_s": P * N / (ms / 1e3),
+                     "roofline": {"bound": "hbm", "achieved": abytes / (kms / 1e3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": abytes / (kms / 1e3) / 1e9 / peak,
+                                  "peak_source": peak_src, "bytes_per_eval": per_eval}}
+    line = {"mode": "trilinear", "metric": "particle×point evals/s (1M×65,536, int16 TSDF, trilinear read)",
+            "value": out["trilinear"]["evals_per_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32", "steps": steps,
+            "config": {"workload": config_dict(args, wl)["workload"],
+                       "bytes_per_eval": "trilinear: 8 int16 corner values + one 8-byte brick-index entry"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    m.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -783,6 +915,10 @@ def main(argv=None):
         return run_precision(args)
     if args.mode == "vlp16":
         return run_vlp16(args)
+    if args.mode == "filter":
+        return run_filter(args)
+    if args.mode == "trilinear":
+        return run_trilinear(args)
     return run_ours(args)
 
 

@@ -117,9 +117,24 @@ typedef struct mcl_map_info {
   int64_t hash_capacity;  /* BRICK: hash table entries (power of two) */
   int32_t hash_max_probe; /* BRICK: longest probe sequence of a stored brick */
   int32_t device;         /* CUDA device that holds the map */
+  float score_sigma;      /* > 0: a score map made for this sigma (mcl_map_create_score) */
+  float score_outside;    /* score map: the score read where nothing is stored */
 } mcl_map_info;
 
 mcl_status mcl_map_get_info(mcl_map_t map, mcl_map_info* out);
+
+/* Score map (Sec. III: all entries of the map can be computed before the
+ * scans, so the exponential of Eq. 3 is not evaluated per point). Makes, on
+ * the source map's device, a map of the same kind, grid and bricks whose
+ * values are the scores s = exp(-d^2 / (2 sigma^2)) of the source's values d
+ * (dequantised; computed in FP64 and rounded once, to nearest even, to
+ * dtype MCL_F16 or MCL_F32); a point where nothing is stored reads the score
+ * of +truncation. A sensor update on a score map must use mode MCL_SUM, the
+ * same sigma_hit (bit for bit) and no MCL_TRILINEAR; it sums the stored
+ * scores: L = log(k * sum s), k the constant of Eq. 3. mcl_map_lookup on a
+ * score map returns the scores. EINVAL: sigma not finite and > 0, another
+ * dtype, a score map as source. The new map owns its memory. */
+mcl_status mcl_map_create_score(mcl_map_t src, float sigma_hit, int32_t dtype, mcl_map_t* out);
 
 /* Map query at N world points (device, N x 3 FP32): out_index (device, N
  * int64) gets the linear voxel index (iz * dims[1] + iy) * dims[0] + ix or -1

@@ -215,39 +215,50 @@ __global__ void __launch_bounds__(kT) k_estimate_blocks(const float* __restrict_
   if (threadIdx.x == 0) est_store(acc, part + blockIdx.x);
 }
 
-// Cyclic Jacobi rotations on a symmetric 4 x 4 matrix (FP64): A becomes
+// Cyclic Jacobi rotations on a symmetric 4 x 4 matrix in FP32: A becomes
 // diagonal (the eigenvalues), V collects the rotations (columns = unit
-// eigenvectors). Stops when the off-diagonal mass is negligible.
-__device__ void jacobi4(double A[4][4], double V[4][4]) {
+// eigenvectors). FP32 because this runs on one thread, where the long
+// latency of FP64 arithmetic on this part would dominate the whole estimate;
+// the FP64 polish below restores the precision.
+__device__ void jacobi4f(float A[4][4], float V[4][4]) {
+#pragma unroll
   for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) V[i][j] = i == j ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 16; ++sweep) {
-    double off = 0.0, all = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) V[i][j] = i == j ? 1.f : 0.f;
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    float off = 0.f, all = 0.f;
+#pragma unroll
     for (int i = 0; i < 4; ++i)
+#pragma unroll
       for (int j = 0; j < 4; ++j) {
         all += A[i][j] * A[i][j];
         if (i != j) off += A[i][j] * A[i][j];
       }
-    if (!(off > 1e-34 * all)) break;
+    if (!(off > 1e-14f * all)) break;
+#pragma unroll
     for (int p = 0; p < 3; ++p)
+#pragma unroll
       for (int q = p + 1; q < 4; ++q) {
-        const double apq = A[p][q];
-        if (apq == 0.0) continue;
-        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        const float apq = A[p][q];
+        if (apq == 0.f) continue;
+        const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
+        const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+        const float c = rsqrtf(t * t + 1.f), s = t * c;
+#pragma unroll
         for (int k = 0; k < 4; ++k) {  // A <- A J
-          const double akp = A[k][p], akq = A[k][q];
+          const float akp = A[k][p], akq = A[k][q];
           A[k][p] = c * akp - s * akq;
           A[k][q] = s * akp + c * akq;
         }
+#pragma unroll
         for (int k = 0; k < 4; ++k) {  // A <- J^T A
-          const double apk = A[p][k], aqk = A[q][k];
+          const float apk = A[p][k], aqk = A[q][k];
           A[p][k] = c * apk - s * aqk;
           A[q][k] = s * apk + c * aqk;
         }
+#pragma unroll
         for (int k = 0; k < 4; ++k) {  // V <- V J
-          const double vkp = V[k][p], vkq = V[k][q];
+          const float vkp = V[k][p], vkq = V[k][q];
           V[k][p] = c * vkp - s * vkq;
           V[k][q] = s * vkp + c * vkq;
         }
@@ -292,17 +303,29 @@ __global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __rest
       }
   }
   if (finite) {
-    double V[4][4];
-    jacobi4(A, V);
+    // Dominant eigenvector of Q: FP32 Jacobi, then two FP64 power steps
+    // v <- Q v / |Q v| (each shrinks the error by lambda_2 / lambda_1).
+    float Af[4][4], Vf[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) Af[i][j] = (float)A[i][j];
+    jacobi4f(Af, Vf);
     int b = 0;
     for (int i = 1; i < 4; ++i)
-      if (A[i][i] > A[b][b]) b = i;
-    double q[4] = {V[0][b], V[1][b], V[2][b], V[3][b]};
-    const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+      if (Af[i][i] > Af[b][b]) b = i;
+    double q[4] = {Vf[0][b], Vf[1][b], Vf[2][b], Vf[3][b]};
+    for (int it = 0; it < 2; ++it) {
+      double y[4];
+      for (int i = 0; i < 4; ++i) y[i] = A[i][0] * q[0] + A[i][1] * q[1] + A[i][2] * q[2] + A[i][3] * q[3];
+      const double inv = rsqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+      for (int i = 0; i < 4; ++i) q[i] = y[i] * inv;
+    }
     int f = 0;
     while (f < 3 && q[f] == 0.0) ++f;
-    const double sg = q[f] < 0.0 ? -1.0 / n : 1.0 / n;
-    for (int i = 0; i < 4; ++i) q[i] *= sg;
+    if (q[f] < 0.0)
+      for (int i = 0; i < 4; ++i) q[i] = -q[i];
+    double lam = 0.0;
+    for (int i = 0; i < 4; ++i)
+      lam += q[i] * (A[i][0] * q[0] + A[i][1] * q[1] + A[i][2] * q[2] + A[i][3] * q[3]);
     const double r21 = 2.0 * (q[2] * q[3] + q[0] * q[1]);
     const double r22 = 1.0 - 2.0 * (q[1] * q[1] + q[2] * q[2]);
     const double r20 = 2.0 * (q[1] * q[3] - q[0] * q[2]);
@@ -312,7 +335,7 @@ __global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __rest
     out->rpy[0] = atan2(r21, r22);
     out->rpy[1] = asin(fmin(1.0, fmax(-1.0, -r20)));
     out->rpy[2] = atan2(r10, r00);
-    out->concentration = A[b][b];
+    out->concentration = lam;
   } else {
     for (int i = 0; i < 4; ++i) out->quat[i] = nan;
     for (int i = 0; i < 3; ++i) out->rpy[i] = nan;

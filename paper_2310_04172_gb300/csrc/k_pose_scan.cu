@@ -1,4 +1,6 @@
 // Per-particle pose matrices, scan packing and the map query kernel.
+#include <algorithm>
+
 #include "mcl_internal.h"
 
 namespace mcl {
@@ -71,6 +73,24 @@ __global__ void k_brick_to_block4(const T* __restrict__ src, T* __restrict__ dst
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
+// Score map values (Sec. III: the exponential of Eq. 3 evaluated once per map
+// entry): s = exp(-d^2 / (2 sigma^2)) in FP64, rounded once to the output type.
+template <int SRC>
+__global__ void k_score_values(const void* __restrict__ src, long long n, double tau, double sigma,
+                               void* __restrict__ dst, int dst_f16) {
+  const double c = 2.0 * sigma * sigma;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double d;
+    if constexpr (SRC == MCL_F32) d = (double)static_cast<const float*>(src)[i];
+    else if constexpr (SRC == MCL_F16) d = (double)__half2float(static_cast<const __half*>(src)[i]);
+    else d = (double)static_cast<const short*>(src)[i] * (tau / 32767.0);
+    const double e = exp(-(d * d) / c);
+    if (dst_f16) static_cast<__half*>(dst)[i] = __double2half(e);  // round to nearest even
+    else static_cast<float*>(dst)[i] = __double2float_rn(e);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
@@ -92,6 +112,17 @@ cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_brick
     k_brick_to_block4<<<blocks_for(n, 256), 256, 0, s>>>((const short*)src, (short*)dst, n);
   else
     k_brick_to_block4<<<blocks_for(n, 256), 256, 0, s>>>((const float*)src, (float*)dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_score_values(const void* src, int src_dtype, long long n, double tau,
+                                double sigma, void* dst, int dst_dtype, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int g = (int)std::min<long long>(blocks_for(n, 256), 152LL * 64);
+  const int f16 = dst_dtype == MCL_F16;
+  if (src_dtype == MCL_F32) k_score_values<MCL_F32><<<g, 256, 0, s>>>(src, n, tau, sigma, dst, f16);
+  else if (src_dtype == MCL_F16) k_score_values<MCL_F16><<<g, 256, 0, s>>>(src, n, tau, sigma, dst, f16);
+  else k_score_values<MCL_I16><<<g, 256, 0, s>>>(src, n, tau, sigma, dst, f16);
   return cudaGetLastError();
 }
 

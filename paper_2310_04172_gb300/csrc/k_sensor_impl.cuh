@@ -215,6 +215,10 @@ __device__ __forceinline__ void accumulate(const SensorArgs& a,
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (use[u]) acc = fmaf(dv[u], dv[u], acc);
+  } else if constexpr (MODE == kModeScore) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (use[u]) acc = __fadd_rn(acc, dv[u]);
   } else {
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -573,8 +577,37 @@ void* pick_shape(const SensorShape& sh, bool batch) {
   return nullptr;
 }
 
+// Score maps (FP16 or FP32 values that are already scores): the plain
+// shapes, nearest-voxel read only.
+template <int KIND, int DTYPE>
+void* pick_score_shape(const SensorShape& sh, bool batch) {
+  if (sh.interp || sh.pipeline) return nullptr;
+  if (sh.lanes == 32) {
+    if (sh.unroll == 2) return kernel_ptr<KIND, DTYPE, kModeScore, 32, 2, false>(batch);
+    if (sh.unroll == 4) return kernel_ptr<KIND, DTYPE, kModeScore, 32, 4, false>(batch);
+    if (sh.unroll == 8) return kernel_ptr<KIND, DTYPE, kModeScore, 32, 8, false>(batch);
+    return nullptr;
+  }
+  if (sh.unroll != 4) return nullptr;
+  if (sh.lanes == 16) return kernel_ptr<KIND, DTYPE, kModeScore, 16, 4, false>(batch);
+  if (sh.lanes == 8) return kernel_ptr<KIND, DTYPE, kModeScore, 8, 4, false>(batch);
+  return nullptr;
+}
+
 template <int DTYPE>
 void* pick_dtype(int kind, int layout, int mode, const SensorShape& sh, bool batch) {
+  if (mode == kModeScore) {
+    if constexpr (DTYPE == MCL_I16) {
+      return nullptr;
+    } else {
+      if (kind == MCL_MAP_DENSE) return pick_score_shape<MCL_MAP_DENSE, DTYPE>(sh, batch);
+      if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_LINEAR)
+        return pick_score_shape<MCL_MAP_BRICK, DTYPE>(sh, batch);
+      if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)
+        return pick_score_shape<kKindBrickBlock4, DTYPE>(sh, batch);
+      return nullptr;
+    }
+  }
   if (kind == MCL_MAP_DENSE)
     return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_DENSE, DTYPE, MCL_LOGPROD>(sh, batch)
                                : pick_shape<MCL_MAP_DENSE, DTYPE, MCL_SUM>(sh, batch);

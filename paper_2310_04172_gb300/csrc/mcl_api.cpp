@@ -12,6 +12,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "runtime.h"
 
 namespace mcl {
@@ -291,6 +293,51 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
   return MCL_OK;
 }
 
+mcl_status mcl_map_create_score(mcl_map_t src, float sigma, int32_t dtype, mcl_map_t* out) {
+  if (!src || !out) return fail(MCL_EINVAL, "map_create_score: NULL source or out");
+  *out = nullptr;
+  if (!finite_pos(sigma)) return fail(MCL_EINVAL, "map_create_score: sigma must be finite and > 0");
+  if (dtype != MCL_F16 && dtype != MCL_F32) return fail(MCL_EINVAL, "map_create_score: dtype %d", dtype);
+  if (src->score_sigma > 0.f) return fail(MCL_EINVAL, "map_create_score: the source is a score map");
+  if (mcl_status rc = check_device(src)) return rc;
+  const int64_t n = src->kind == MCL_MAP_DENSE
+                        ? (int64_t)src->view.nx * src->view.ny * src->view.nz
+                        : src->n_bricks * (int64_t)kBrickVoxels;
+  const size_t es = dtype == MCL_F32 ? 4 : 2;
+  mcl_map_s* m = new mcl_map_s(*src);
+  m->dtype = dtype;
+  m->d_values = nullptr;
+  m->d_table = nullptr;
+  auto cleanup = [&](mcl_status st) {
+    if (m->d_values) cudaFree(m->d_values);
+    if (m->d_table) cudaFree(m->d_table);
+    delete m;
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&m->d_values, std::max((size_t)n * es, (size_t)256));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create_score values"));
+  const double tau = (double)src->view.tau;
+  e = launch_score_values(src->d_values, src->dtype, n, tau, (double)sigma, m->d_values, dtype, nullptr);
+  if (e == cudaSuccess && src->d_table) {
+    e = cudaMalloc((void**)&m->d_table, (size_t)src->capacity * sizeof(uint2));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m->d_table, src->d_table, (size_t)src->capacity * sizeof(uint2),
+                     cudaMemcpyDeviceToDevice);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create_score"));
+  // The score of +tau, computed the same way (FP64, one rounding).
+  const double eo = std::exp(-(tau * tau) / (2.0 * (double)sigma * (double)sigma));
+  m->score_outside = dtype == MCL_F16 ? __half2float(__double2half(eo)) : (float)eo;
+  m->score_sigma = sigma;
+  m->view.values = m->d_values;
+  m->view.table = m->d_table;
+  m->view.tau = m->score_outside;  // what a look-up reads where nothing is stored
+  m->bytes = (int64_t)n * (int64_t)es + (m->d_table ? m->capacity * (int64_t)sizeof(uint2) : 0);
+  *out = m;
+  return MCL_OK;
+}
+
 mcl_status mcl_map_destroy(mcl_map_t m) {
   if (!m) return MCL_OK;
   int cur = 0;
@@ -312,6 +359,8 @@ mcl_status mcl_map_get_info(mcl_map_t m, mcl_map_info* out) {
   out->hash_capacity = m->capacity;
   out->hash_max_probe = m->max_probe;
   out->device = m->device;
+  out->score_sigma = m->score_sigma;
+  out->score_outside = m->score_outside;
   return MCL_OK;
 }
 
@@ -372,6 +421,17 @@ mcl_status check_params(const mcl_sensor_params* p) {
   return MCL_OK;
 }
 
+mcl_status check_map_params(mcl_map_t m, const mcl_sensor_params* p) {
+  if (m->score_sigma > 0.f) {
+    if (p->mode != MCL_SUM) return fail(MCL_EINVAL, "score map: mode must be MCL_SUM");
+    if (p->sigma_hit != m->score_sigma)
+      return fail(MCL_EINVAL, "score map: sigma_hit %g differs from the map's %g", p->sigma_hit, m->score_sigma);
+    if (p->flags & MCL_TRILINEAR) return fail(MCL_EINVAL, "score map: no trilinear read");
+    if (p->pipeline == 2) return fail(MCL_EINVAL, "score map: no pipelined loop");
+  }
+  return MCL_OK;
+}
+
 // Particles are evaluated in spatial order unless told otherwise (or too few
 // to matter).
 constexpr int64_t kSpatialOrderMinParticles = 4096;
@@ -393,6 +453,8 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   } else if (sh.unroll == 8) {
     sh.pipeline = 0;
   }
+  if (mcl_status rc = check_map_params(m, p)) return rc;
+  if (m->score_sigma > 0.f) sh.pipeline = 0;
   sh.interp = (p->flags & MCL_TRILINEAR) ? 1 : 0;
   if (sh.interp) {  // two points per lane per step, no pipelining
     sh.unroll = 2;
@@ -400,7 +462,7 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   }
   sh.threads = 256;
   int bps = 0;
-  MCL_CUDA(sensor_occupancy(m->kind, m->view.layout, m->dtype, p->mode, sh, &bps));
+  MCL_CUDA(sensor_occupancy(m->kind, m->view.layout, m->dtype, kernel_mode(m, p->mode), sh, &bps));
   if (bps < 1) return fail(MCL_EINVAL, "sensor plan: launch shape does not fit on an SM");
   pl->spatial = p->particle_order == 2 || (p->particle_order == 0 && P >= kSpatialOrderMinParticles);
   pl->K = (int)((N + sh.chunk - 1) / sh.chunk);
@@ -525,12 +587,12 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   a.ppi = pl.sh.ppi;
   a.nblk = pl.nblk;
   a.n_items = pl.n_items;
-  a.mode = p->mode;
+  a.mode = kernel_mode(m, p->mode);
   a.neglect = (p->flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
   const float c = (float)(-0.5 / (sig * sig));
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
-  a.vout = q16 ? 32767.0f : m->view.tau;
+  a.vout = outside_raw(m);
   a.cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : c;
   a.store_scale = (q16 && p->mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
   {

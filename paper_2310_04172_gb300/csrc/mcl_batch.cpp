@@ -44,7 +44,7 @@ void score_constants(const mcl_map_s* m, float sigma, int mode, SensorArgs* a) {
   const double sig = (double)sigma;
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
-  a->vout = q16 ? 32767.0f : m->view.tau;
+  a->vout = outside_raw(const_cast<mcl_map_t>(m));
   a->cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : sensor_c(sigma);
   a->store_scale = (q16 && mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
 }
@@ -231,7 +231,8 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       e = cudaMemcpy(b->ws + off_beg[k], beg.data(), beg.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch_create tables"));
     int bps = 0;
-    e = sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype, g.mode, g.sh, &bps);
+    e = sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype, kernel_mode(g.map, g.mode),
+                               g.sh, &bps);
     if (e != cudaSuccess || bps < 1) return bail(cuda_fail(e, "batch_create occupancy"));
     g.sh.grid = (int)std::min<long long>(beg.back(), (long long)st.sms * bps);
     SensorArgs& a = g.args.base;
@@ -240,7 +241,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     a.status = st.status;
     a.chunk = g.sh.chunk;
     a.ppi = g.sh.ppi;
-    a.mode = g.mode;
+    a.mode = kernel_mode(g.map, g.mode);
     a.neglect = g.neglect;
     score_constants(g.map, g.sigma, g.mode, &a);
     g.args.sessions = (const BatchSession*)(b->ws + off_tab[k]);

@@ -16,6 +16,7 @@ constexpr int kBrickVoxels = kBrick * kBrick * kBrick;
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr int kKindBrickBlock4 = 2;  // internal kind: brick map stored in 4x4x4 blocks
+constexpr int kModeScore = 2;        // internal mode: SUM on a score map (stored values are scores)
 
 // Bits of the per-device status word that kernels set instead of faulting.
 enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
@@ -199,6 +200,12 @@ cudaError_t sensor_occupancy(int kind, int layout, int dtype, int mode, const Se
 // Map upload helper: x-fastest bricks (src) -> 4x4x4-block layout (dst).
 cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_bricks, int elem_bytes,
                                    cudaStream_t s);
+
+// Score map values: s = exp(-d^2 / (2 sigma^2)) of n stored values (src of
+// src_dtype, int16 scaled by tau / 32767), FP64, rounded once to dst_dtype
+// (MCL_F16 or MCL_F32).
+cudaError_t launch_score_values(const void* src, int src_dtype, long long n, double tau,
+                                double sigma, void* dst, int dst_dtype, cudaStream_t s);
 
 // Finishing pass: L_p from the chunk partials, then block max / sum-exp.
 // With rank, particle p's chunk sums sit in slot rank[p] of partial.

@@ -197,7 +197,8 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
     }
     int bps = 0;
-    MCL_CUDA(sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype, g.mode, sh, &bps));
+    MCL_CUDA(sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype,
+                                    kernel_mode(g.map, g.mode), sh, &bps));
     sh.grid = (int)std::min<long long>(beg[g.idx.size()], (long long)S->dev.sms * std::max(bps, 1));
     shapes[k] = sh;
     BatchArgs& b = args[k];
@@ -207,11 +208,11 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     a.status = S->dev.status;
     a.chunk = sh.chunk;
     a.ppi = sh.ppi;
-    a.mode = g.mode;
+    a.mode = kernel_mode(g.map, g.mode);
     a.neglect = g.neglect;
     const double sig = (double)g.sigma, scale = (double)g.map->view.scale;
     const bool q16 = g.map->dtype == MCL_I16;
-    a.vout = q16 ? 32767.0f : g.map->view.tau;
+    a.vout = outside_raw(g.map);
     a.cs = (float)(-0.5 / (sig * sig) * (q16 ? scale * scale : 1.0));
     a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
     b.sessions = (const BatchSession*)(sl->d_tab + off_tab);

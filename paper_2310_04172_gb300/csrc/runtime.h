@@ -99,5 +99,21 @@ struct mcl_map_s {
   uint2* d_table = nullptr;
   int64_t bytes = 0, n_bricks = 0, capacity = 0;
   int max_probe = 0;
+  float score_sigma = 0.f;    // > 0: values are scores for this sigma
+  float score_outside = 0.f;  // score map: value read where nothing is stored
 };
 
+namespace mcl {
+
+// Kernel mode and the value read where nothing is stored (storage units)
+// of a sensor update on map m with the caller's mode.
+inline int kernel_mode(mcl_map_t m, int mode) { return m->score_sigma > 0.f ? kModeScore : mode; }
+inline float outside_raw(mcl_map_t m) {
+  if (m->score_sigma > 0.f) return m->score_outside;
+  return m->dtype == MCL_I16 ? 32767.0f : m->view.tau;
+}
+// EINVAL unless the parameters fit the map (a score map needs SUM, its own
+// sigma and the nearest-voxel read).
+mcl_status check_map_params(mcl_map_t m, const mcl_sensor_params* p);
+
+}  // namespace mcl

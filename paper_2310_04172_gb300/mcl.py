@@ -40,7 +40,8 @@ class mcl_map_desc(ctypes.Structure):
 
 class mcl_map_info(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("device_bytes", _i64), ("n_bricks", _i64),
-                ("hash_capacity", _i64), ("hash_max_probe", _i32), ("device", _i32)]
+                ("hash_capacity", _i64), ("hash_max_probe", _i32), ("device", _i32),
+                ("score_sigma", ctypes.c_float), ("score_outside", ctypes.c_float)]
 
 
 class mcl_sensor_params(ctypes.Structure):
@@ -155,6 +156,7 @@ SIGNATURES = {
     "mcl_sync": (_i32, [_c_void_p]),
     "mcl_map_create": (_i32, [ctypes.POINTER(mcl_map_desc), _c_void_p, ctypes.POINTER(_c_void_p)]),
     "mcl_map_destroy": (_i32, [_c_void_p]),
+    "mcl_map_create_score": (_i32, [_c_void_p, ctypes.c_float, _i32, ctypes.POINTER(_c_void_p)]),
     "mcl_map_get_info": (_i32, [_c_void_p, ctypes.POINTER(mcl_map_info)]),
     "mcl_map_lookup": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p]),
     "mcl_sensor_update": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, _i64,
@@ -310,6 +312,13 @@ def map_from_scene(m, device_layout: int = MCL_LAYOUT_LINEAR) -> Map:
     return mcl_map_create(MCL_MAP_BRICK, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
                           m.dims, m.values, m.coords, inv_voxel=m.inv_voxel,
                           device_layout=device_layout)
+
+
+def mcl_map_create_score(m: Map, sigma_hit: float, dtype: int = MCL_F16) -> Map:
+    """Score map of `m` for sigma_hit (values exp(-d^2 / (2 sigma^2)), FP16 or FP32)."""
+    h = ctypes.c_void_p()
+    _check(lib().mcl_map_create_score(m.handle, float(sigma_hit), int(dtype), ctypes.byref(h)))
+    return Map(h, ("score", m.desc, float(sigma_hit), int(dtype)))
 
 
 def mcl_map_destroy(m: Map):
