@@ -55,13 +55,13 @@ def parse_args(argv=None):
     ap.add_argument("--order", type=int, default=0, help="particle order: 0 auto, 1 given, 2 spatial")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
     ap.add_argument("--mode", default="headline",
-                    choices=["headline", "serving", "precision", "vlp16", "filter", "trilinear"],
+                    choices=["headline", "serving", "precision", "vlp16", "filter", "variants", "trilinear"],
                     help="headline: 1M x 65,536 int16 step (+ serving probe); serving: 64 sessions over "
                          "8 maps; precision: f32/f16/i16 sweep with oracle weight error; vlp16: plain vs "
                          "batched graph-captured form on the VLP-16 tracking workload; filter: whole "
                          "filter steps (motion, sensor, estimate, resampling) as separate calls, as one "
-                         "call and replayed from a CUDA graph; trilinear: the 1M x 65,536 step with the "
-                         "trilinear read")
+                         "call and replayed from a CUDA graph; variants (or trilinear): the 1M x 65,536 "
+                         "step with SUM on the TSDF, SUM on an FP16 score map and the trilinear read")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving probe of the headline")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     return ap.parse_args(argv)
@@ -832,6 +832,13 @@ def run_filter(args):
             f = mcl.Filter(m, torch.from_numpy(wl.particles).cuda(), max_points=N, params=prm,
                            motion_sigma=sigma_m, seed=7, use_graph=graph)
             res[name] = timed(lambda k: f.step(scan, delta, est), reps)
+            if not graph:  # where a step's device time goes (events around each phase)
+                mcl.mcl_profile_begin()
+                for k in range(10):
+                    f.step(scan, delta, est)
+                torch.cuda.synchronize()
+                prof = mcl.mcl_profile_end()
+                res["phases_ms_per_step"] = {k: v["ms"] / 10 for k, v in prof.items() if v["launches"]}
             f.close()
         # cost of the fused estimate: the sensor update with and without it
         res["sensor_update_ms"] = timed(lambda k: mcl.mcl_sensor_update(m, parts, scan, prm, logw, w), reps)
@@ -852,11 +859,13 @@ def run_filter(args):
     return 0
 
 
-# ------------------------------------------------------------------ trilinear read
-def run_trilinear(args):
-    """The headline step (1M x 65,536, int16 bricks) with the trilinear read:
-    eight corner values per evaluation (one brick-index probe per distinct
-    brick), against the nearest-voxel read in the same run."""
+# ------------------------------------------------------------------ read and score variants
+def run_variants(args):
+    """The headline step size (1M x 65,536, int16 bricks) with each variant of
+    the read and the score: nearest-voxel LOGPROD (the headline), SUM on the
+    TSDF (exp per evaluation), SUM on an FP16 score map (the exponential
+    precomputed per voxel), and the trilinear read (eight corner values per
+    evaluation, one brick-index probe per distinct brick)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -865,6 +874,9 @@ def run_trilinear(args):
     torch.cuda.set_device(0)
     wl = make_workload(args, 0)
     m = mcl.map_from_scene(wl.map)
+    t0 = time.time()
+    sc = mcl.mcl_map_create_score(m, wl.sigma_hit, mcl.MCL_F16)
+    score_build_s = time.time() - t0
     P, N = wl.particles.shape[0], wl.scan.shape[0]
     parts = torch.from_numpy(wl.particles).cuda()
     scan = torch.from_numpy(np.ascontiguousarray(wl.scan)).cuda()
@@ -873,34 +885,40 @@ def run_trilinear(args):
     peak, peak_src = peaks()
     out = {}
     steps = max(1, min(args.steps, 5))
-    for name, flags in (("nearest", 0), ("trilinear", mcl.MCL_TRILINEAR)):
-        prm = mcl.sensor_params(wl.sigma_hit, flags=flags)
+    variants = (("nearest_logprod", m, mcl.MCL_LOGPROD, 0, 1),
+                ("nearest_sum_tsdf", m, mcl.MCL_SUM, 0, 1),
+                ("nearest_sum_score_f16", sc, mcl.MCL_SUM, 0, 1),
+                ("trilinear_logprod", m, mcl.MCL_LOGPROD, mcl.MCL_TRILINEAR, 8))
+    for name, mm, mode, flags, corners in variants:
+        prm = mcl.sensor_params(wl.sigma_hit, mode=mode, flags=flags)
         for _ in range(max(args.warmup, 3)):
-            mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+            mcl.mcl_sensor_update(mm, parts, scan, prm, logw, w)
         torch.cuda.synchronize()
         a, e = torch.cuda.Event(True), torch.cuda.Event(True)
         mcl.mcl_profile_begin()
         a.record()
         for _ in range(steps):
-            mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
+            mcl.mcl_sensor_update(mm, parts, scan, prm, logw, w)
         e.record()
         e.synchronize()
         prof = mcl.mcl_profile_end()
         ms = a.elapsed_time(e) / steps
         kms = prof["sensor"]["ms"] / max(1, prof["sensor"]["launches"])
-        per_eval = (8 if flags else 1) * elem + 8
+        per_eval = corners * elem + 8
         abytes = P * N * per_eval + P * 52 + N * 16
         out[name] = {"ms_per_step": ms, "kernel_ms": kms, "evals_per_s": P * N / (ms / 1e3),
                      "roofline": {"bound": "hbm", "achieved": abytes / (kms / 1e3) / 1e9, "peak": peak,
                                   "unit": "GB/s", "frac": abytes / (kms / 1e3) / 1e9 / peak,
                                   "peak_source": peak_src, "bytes_per_eval": per_eval}}
-    line = {"mode": "trilinear", "metric": "particle×point evals/s (1M×65,536, int16 TSDF, trilinear read)",
-            "value": out["trilinear"]["evals_per_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
-            "data": "synthetic", "dtype": "f32", "steps": steps,
+    line = {"mode": "variants", "metric": "particle×point evals/s (1M×65,536, int16 TSDF, trilinear read)",
+            "value": out["trilinear_logprod"]["evals_per_s"], "unit": UNIT, "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32", "steps": steps,
             "config": {"workload": config_dict(args, wl)["workload"],
-                       "bytes_per_eval": "trilinear: 8 int16 corner values + one 8-byte brick-index entry"},
+                       "bytes_per_eval": "corner values x element bytes + one 8-byte brick-index entry",
+                       "score_map_build_s": score_build_s},
             "results": out}
     print(json.dumps(line), flush=True)
+    sc.close()
     m.close()
     return 0
 
@@ -917,8 +935,8 @@ def main(argv=None):
         return run_vlp16(args)
     if args.mode == "filter":
         return run_filter(args)
-    if args.mode == "trilinear":
-        return run_trilinear(args)
+    if args.mode in ("variants", "trilinear"):
+        return run_variants(args)
     return run_ours(args)
 
 
