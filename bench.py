@@ -54,6 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--pipeline", type=int, default=0, help="0 auto, 1 off, 2 on")
     ap.add_argument("--order", type=int, default=0, help="particle order: 0 auto, 1 given, 2 spatial")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
+    ap.add_argument("--index", type=int, default=0, help="brick index: 0 auto, 1 hash, 2 cell grid")
     ap.add_argument("--mode", default="headline",
                     choices=["headline", "serving", "precision", "vlp16", "filter", "variants", "trilinear"],
                     help="headline: 1M x 65,536 int16 step (+ serving probe); serving: 64 sessions over "
@@ -175,16 +176,17 @@ def rank_particles(wl, rank: int):
     return scenes.particles_free(wl.scene, len(wl.particles), 0.1, 10.0, 1000 + rank)
 
 
-def algorithmic_bytes(P: int, N: int, elem: int, brick: bool) -> int:
+def algorithmic_bytes(P: int, N: int, elem: int, index_entry: int) -> int:
     """Bytes the sensor kernel must move per launch: one map element per
-    (particle, point) evaluation plus one 8-byte brick-index entry for a
-    brick map; each pose record (48 B), scan point (16 B) and weight (4 B) once."""
-    return P * N * (elem + (8 if brick else 0)) + P * 48 + N * 16 + P * 4
+    (particle, point) evaluation plus one brick-index entry for a brick map
+    (4 B in the cell grid, 8 B in the hash table); each pose record (48 B),
+    scan point (16 B) and weight (4 B) once."""
+    return P * N * (elem + index_entry) + P * 48 + N * 16 + P * 4
 
 
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16.cu", "mcl_internal.h"):
+    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16_grid.cu", "mcl_internal.h"):
         with open(os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -326,7 +328,7 @@ def run_ours(args):
     wl = make_workload(args, rank)
     parts_np = rank_particles(wl, rank)
     P, N = len(parts_np), len(wl.scan)
-    m = mcl.map_from_scene(wl.map, args.layout)
+    m = mcl.map_from_scene(wl.map, args.layout, args.index)
     elem = 4 if args.dtype == "f32" else 2
     stream = torch.cuda.Stream(device=dev)
     parts = torch.from_numpy(parts_np).to(dev)
@@ -378,7 +380,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel, timed live in the region above
     sensor_ms = prof["sensor"]["ms"] / max(1, prof["sensor"]["launches"])
-    abytes = algorithmic_bytes(P, N, elem, True)
+    index_entry = {1: 8, 2: 4}.get(m.info()["index"], 0)
+    abytes = algorithmic_bytes(P, N, elem, index_entry)
     achieved = abytes / (sensor_ms / 1e3) / 1e9
     peak, peak_src = peaks()
     traffic = measured_traffic(P, N)
@@ -386,7 +389,7 @@ def run_ours(args):
             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
             "kernel": "k_sensor", "kernel_ms": sensor_ms,
             "algorithmic_bytes_per_launch": abytes,
-            "bytes_per_eval": elem + 8}
+            "bytes_per_eval": elem + index_entry}
 
     # gather roofline: uniform-random element reads over a buffer of the map's size
     gather = None
@@ -420,6 +423,9 @@ def run_ours(args):
 
     if rank == 0:
         cfg = config_dict(args, wl)
+        info = m.info()
+        cfg["map"]["index"] = {1: "hash", 2: "cell grid"}.get(info["index"], "none")
+        cfg["map"]["index_bytes"] = info["index_bytes"]
         cfg["launch"] = plan
         cfg["parallelism"] = f"replicas{world}" if world > 1 else "single"
         line = {
@@ -904,7 +910,7 @@ def run_variants(args):
         prof = mcl.mcl_profile_end()
         ms = a.elapsed_time(e) / steps
         kms = prof["sensor"]["ms"] / max(1, prof["sensor"]["launches"])
-        per_eval = corners * elem + 8
+        per_eval = corners * elem + {1: 8, 2: 4}.get(mm.info()["index"], 0)
         abytes = P * N * per_eval + P * 52 + N * 16
         out[name] = {"ms_per_step": ms, "kernel_ms": kms, "evals_per_s": P * N / (ms / 1e3),
                      "roofline": {"bound": "hbm", "achieved": abytes / (kms / 1e3) / 1e9, "peak": peak,
@@ -914,7 +920,8 @@ def run_variants(args):
             "value": out["trilinear_logprod"]["evals_per_s"], "unit": UNIT, "higher_is_better": True,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32", "steps": steps,
             "config": {"workload": config_dict(args, wl)["workload"],
-                       "bytes_per_eval": "corner values x element bytes + one 8-byte brick-index entry",
+                       "bytes_per_eval": "corner values x element bytes + one brick-index entry "
+                                         "(4 B cell grid, 8 B hash)",
                        "score_map_build_s": score_build_s},
             "results": out}
     print(json.dumps(line), flush=True)

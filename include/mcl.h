@@ -61,6 +61,7 @@ mcl_status mcl_sync(mcl_stream_t stream);
 enum { MCL_MAP_DENSE = 0, MCL_MAP_BRICK = 1 };
 enum { MCL_F32 = 0, MCL_F16 = 1, MCL_I16 = 2 };
 enum { MCL_LAYOUT_LINEAR = 0, MCL_LAYOUT_BLOCK4 = 1 };
+enum { MCL_INDEX_AUTO = 0, MCL_INDEX_HASH = 1, MCL_INDEX_GRID = 2 };
 
 /* TSDF map description (Sec. III: a TSDF volume; the sparse form keeps fine
  * blocks only where values lie within the truncation distance, every other
@@ -84,7 +85,15 @@ enum { MCL_LAYOUT_LINEAR = 0, MCL_LAYOUT_BLOCK4 = 1 };
  * device: MCL_LAYOUT_LINEAR keeps the x-fastest order, MCL_LAYOUT_BLOCK4
  * stores 4x4x4 blocks (block-major, each block z-major) so that neighbouring
  * voxels in x and y share memory sectors. host_values are always x-fastest;
- * results do not depend on the layout. */
+ * results do not depend on the layout.
+ * index (BRICK) chooses how a brick cell finds its brick (the coarse level
+ * of Sec. III's coarse/fine split): MCL_INDEX_GRID keeps a dense array of
+ * one 32-bit slot per brick cell (4 bytes x cells; neighbouring cells are
+ * neighbours in memory), MCL_INDEX_HASH an open-addressing hash table of
+ * 8-byte entries, at least 4 per brick (for sparse maps of a huge extent).
+ * MCL_INDEX_AUTO takes the grid for the linear layout when it needs at most
+ * 512 MB, else the hash. The grid is only built with MCL_LAYOUT_LINEAR.
+ * Results do not depend on the index. */
 typedef struct mcl_map_desc {
   uint32_t struct_size; /* sizeof(mcl_map_desc) */
   int32_t kind;         /* MCL_MAP_DENSE or MCL_MAP_BRICK */
@@ -97,7 +106,7 @@ typedef struct mcl_map_desc {
   int64_t n_bricks;     /* BRICK: number of bricks */
   const int32_t* brick_coords; /* BRICK: (host) n_bricks x 3 int32 */
   int32_t device_layout;       /* BRICK: MCL_LAYOUT_LINEAR or MCL_LAYOUT_BLOCK4 */
-  int32_t reserved;            /* 0 */
+  int32_t index;               /* BRICK: MCL_INDEX_AUTO (0), MCL_INDEX_HASH or MCL_INDEX_GRID */
 } mcl_map_desc;
 
 typedef struct mcl_map_s* mcl_map_t;
@@ -114,11 +123,14 @@ typedef struct mcl_map_info {
   uint32_t struct_size;
   int64_t device_bytes;   /* values + index bytes held on the device */
   int64_t n_bricks;       /* BRICK: bricks stored; DENSE: 0 */
-  int64_t hash_capacity;  /* BRICK: hash table entries (power of two) */
-  int32_t hash_max_probe; /* BRICK: longest probe sequence of a stored brick */
+  int64_t hash_capacity;  /* BRICK with the hash index: table entries (power of two) */
+  int32_t hash_max_probe; /* BRICK with the hash index: longest probe sequence of a stored brick */
   int32_t device;         /* CUDA device that holds the map */
   float score_sigma;      /* > 0: a score map made for this sigma (mcl_map_create_score) */
   float score_outside;    /* score map: the score read where nothing is stored */
+  int32_t index;          /* BRICK: MCL_INDEX_HASH or MCL_INDEX_GRID; DENSE: 0 */
+  int32_t reserved;
+  int64_t index_bytes;    /* BRICK: device bytes of the brick index */
 } mcl_map_info;
 
 mcl_status mcl_map_get_info(mcl_map_t map, mcl_map_info* out);

@@ -137,6 +137,9 @@ cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F32)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F16)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_I16)
+  MCL_LOOKUP_CASE(kKindBrickGrid, MCL_F32)
+  MCL_LOOKUP_CASE(kKindBrickGrid, MCL_F16)
+  MCL_LOOKUP_CASE(kKindBrickGrid, MCL_I16)
 #undef MCL_LOOKUP_CASE
   return cudaErrorInvalidValue;
 }

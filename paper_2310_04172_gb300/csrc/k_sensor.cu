@@ -25,16 +25,30 @@
 
 namespace mcl {
 
-void* sensor_kernel_f32(int kind, int layout, int mode, const SensorShape& sh, bool batch);
-void* sensor_kernel_f16(int kind, int layout, int mode, const SensorShape& sh, bool batch);
-void* sensor_kernel_i16(int kind, int layout, int mode, const SensorShape& sh, bool batch);
+#define MCL_SENSOR_UNIT(d, k) void* sensor_kernel_##d##_##k(int mode, const SensorShape& sh, bool batch);
+#define MCL_SENSOR_UNITS(d) \
+  MCL_SENSOR_UNIT(d, dense) MCL_SENSOR_UNIT(d, hash) MCL_SENSOR_UNIT(d, block4) MCL_SENSOR_UNIT(d, grid)
+MCL_SENSOR_UNITS(f32)
+MCL_SENSOR_UNITS(f16)
+MCL_SENSOR_UNITS(i16)
+#undef MCL_SENSOR_UNITS
+#undef MCL_SENSOR_UNIT
 
 namespace {
 
+// Kernel for (map kind, brick layout, storage type, mode, shape), or NULL.
 void* pick(int kind, int layout, int dtype, int mode, const SensorShape& sh, bool batch = false) {
-  if (dtype == MCL_F32) return sensor_kernel_f32(kind, layout, mode, sh, batch);
-  if (dtype == MCL_F16) return sensor_kernel_f16(kind, layout, mode, sh, batch);
-  if (dtype == MCL_I16) return sensor_kernel_i16(kind, layout, mode, sh, batch);
+#define MCL_PICK(d)                                                                     \
+  if (kind == MCL_MAP_DENSE) return sensor_kernel_##d##_dense(mode, sh, batch);         \
+  if (kind == kKindBrickGrid) return sensor_kernel_##d##_grid(mode, sh, batch);         \
+  if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)                             \
+    return sensor_kernel_##d##_block4(mode, sh, batch);                                 \
+  if (kind == MCL_MAP_BRICK) return sensor_kernel_##d##_hash(mode, sh, batch);          \
+  return nullptr;
+  if (dtype == MCL_F32) { MCL_PICK(f32) }
+  if (dtype == MCL_F16) { MCL_PICK(f16) }
+  if (dtype == MCL_I16) { MCL_PICK(i16) }
+#undef MCL_PICK
   return nullptr;
 }
 

@@ -1,0 +1,11 @@
+// Sensor kernel instances for f32 brick maps with the grid index (one unit per storage type
+// and map kind, so they compile in parallel).
+#include "k_sensor_impl.cuh"
+
+namespace mcl {
+
+void* sensor_kernel_f32_grid(int mode, const SensorShape& sh, bool batch) {
+  return sensor::pick_kind<kKindBrickGrid, MCL_F32>(mode, sh, batch);
+}
+
+}  // namespace mcl

@@ -1,0 +1,11 @@
+// Sensor kernel instances for i16 brick maps with the hash index (linear bricks) (one unit per storage type
+// and map kind, so they compile in parallel).
+#include "k_sensor_impl.cuh"
+
+namespace mcl {
+
+void* sensor_kernel_i16_hash(int mode, const SensorShape& sh, bool batch) {
+  return sensor::pick_kind<MCL_MAP_BRICK, MCL_I16>(mode, sh, batch);
+}
+
+}  // namespace mcl

@@ -173,6 +173,8 @@ __device__ __forceinline__ void stage_a(const SensorArgs& a, const float4* __res
   for (int u = 0; u < U; ++u) {
     if constexpr (KIND == MCL_MAP_DENSE) {
       s.dv[u] = s.in[u] ? load_raw<DTYPE, MODE>(m.values, s.key[u]) : outside_value<DTYPE, MODE>(a);
+    } else if constexpr (KIND == kKindBrickGrid) {
+      s.e[u].y = s.in[u] ? __ldg(m.grid + s.key[u]) : kNoSlot;
     } else {
       s.e[u] = s.in[u] ? __ldg(m.table + brick_hash(s.key[u], m.hash_shift))
                        : make_uint2(kEmptyKey, 0u);
@@ -194,7 +196,9 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
       use[u] = s.v[u] && (s.in[u] || !a.neglect);
     } else {
       uint32_t slot = kNoSlot;
-      if (s.in[u]) {
+      if constexpr (KIND == kKindBrickGrid) {
+        slot = s.e[u].y;  // kNoSlot outside the grid or in an empty cell
+      } else if (s.in[u]) {
         if (s.e[u].x == s.key[u]) slot = s.e[u].y;
         else if (s.e[u].x != kEmptyKey)
           slot = probe_rest(m, s.key[u], brick_hash(s.key[u], m.hash_shift));
@@ -332,6 +336,8 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
       else if (cz && (inx[cx] & iny[cy] & inz[0]) && key[c ^ 4] == key[c]) r = c ^ 4;
       if (r >= 0) {
         slot[c] = slot[r];
+      } else if constexpr (KIND == kKindBrickGrid) {
+        slot[c] = __ldg(m.grid + key[c]);
       } else {
         const uint32_t h = brick_hash(key[c], m.hash_shift);
         const uint2 e = __ldg(m.table + h);
@@ -594,30 +600,15 @@ void* pick_score_shape(const SensorShape& sh, bool batch) {
   return nullptr;
 }
 
-template <int DTYPE>
-void* pick_dtype(int kind, int layout, int mode, const SensorShape& sh, bool batch) {
+// Kernel of one map kind and storage type for a score mode and shape, or NULL.
+template <int KIND, int DTYPE>
+void* pick_kind(int mode, const SensorShape& sh, bool batch) {
   if (mode == kModeScore) {
-    if constexpr (DTYPE == MCL_I16) {
-      return nullptr;
-    } else {
-      if (kind == MCL_MAP_DENSE) return pick_score_shape<MCL_MAP_DENSE, DTYPE>(sh, batch);
-      if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_LINEAR)
-        return pick_score_shape<MCL_MAP_BRICK, DTYPE>(sh, batch);
-      if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)
-        return pick_score_shape<kKindBrickBlock4, DTYPE>(sh, batch);
-      return nullptr;
-    }
+    if constexpr (DTYPE == MCL_I16) return nullptr;
+    else return pick_score_shape<KIND, DTYPE>(sh, batch);
   }
-  if (kind == MCL_MAP_DENSE)
-    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_DENSE, DTYPE, MCL_LOGPROD>(sh, batch)
-                               : pick_shape<MCL_MAP_DENSE, DTYPE, MCL_SUM>(sh, batch);
-  if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_LINEAR)
-    return mode == MCL_LOGPROD ? pick_shape<MCL_MAP_BRICK, DTYPE, MCL_LOGPROD>(sh, batch)
-                               : pick_shape<MCL_MAP_BRICK, DTYPE, MCL_SUM>(sh, batch);
-  if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)
-    return mode == MCL_LOGPROD ? pick_shape<kKindBrickBlock4, DTYPE, MCL_LOGPROD>(sh, batch)
-                               : pick_shape<kKindBrickBlock4, DTYPE, MCL_SUM>(sh, batch);
-  return nullptr;
+  return mode == MCL_LOGPROD ? pick_shape<KIND, DTYPE, MCL_LOGPROD>(sh, batch)
+                             : pick_shape<KIND, DTYPE, MCL_SUM>(sh, batch);
 }
 
 }  // namespace sensor

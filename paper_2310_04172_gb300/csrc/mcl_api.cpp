@@ -174,6 +174,10 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     return fail(MCL_EINVAL, "map_create: device_layout %d", d->device_layout);
   if (d->kind == MCL_MAP_DENSE && d->device_layout != MCL_LAYOUT_LINEAR)
     return fail(MCL_EINVAL, "map_create: dense maps are stored linearly");
+  if (d->index < MCL_INDEX_AUTO || d->index > MCL_INDEX_GRID)
+    return fail(MCL_EINVAL, "map_create: index %d", d->index);
+  if (d->kind == MCL_MAP_BRICK && d->index == MCL_INDEX_GRID && d->device_layout != MCL_LAYOUT_LINEAR)
+    return fail(MCL_EINVAL, "map_create: the grid index is built for the linear layout only");
   float inv = d->inv_voxel == 0.f ? (float)(1.0 / (double)d->voxel) : d->inv_voxel;
   if (!finite_pos(inv)) return fail(MCL_EINVAL, "map_create: inv_voxel must be finite and > 0");
   const size_t es = d->dtype == MCL_F32 ? 4 : 2;
@@ -202,6 +206,7 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
   auto cleanup = [&](mcl_status s) {
     if (m->d_values) cudaFree(m->d_values);
     if (m->d_table) cudaFree(m->d_table);
+    if (m->d_grid) cudaFree(m->d_grid);
     delete m;
     return s;
   };
@@ -273,20 +278,41 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
       cudaFree(stage);
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create block layout"));
     }
-    e = cudaMalloc(&m->d_table, (size_t)cap * sizeof(uint2));
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table"));
-    e = cudaMemcpy(m->d_table, table.data(), (size_t)cap * sizeof(uint2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table upload"));
-    v.table = m->d_table;
+    const uint64_t cells = nbx * nby * nbz;
+    const bool grid = d->index == MCL_INDEX_GRID ||
+                      (d->index == MCL_INDEX_AUTO && v.layout == MCL_LAYOUT_LINEAR &&
+                       cells * sizeof(uint32_t) <= (512ull << 20));
     v.nbx = (uint32_t)nbx;
     v.nby = (uint32_t)nby;
-    v.hash_mask = (uint32_t)(cap - 1);
-    v.hash_shift = shift;
-    v.max_probe = max_probe;
     m->n_bricks = nb;
-    m->capacity = cap;
-    m->max_probe = max_probe;
-    m->bytes = (int64_t)vbytes + cap * (int64_t)sizeof(uint2);
+    if (grid) {
+      // coarse level as a dense array: brick cell -> slot (the duplicates and
+      // ranges were checked while the hash was filled above)
+      std::vector<uint32_t> cell_slot((size_t)cells, kNoSlot);
+      for (int64_t b = 0; b < nb; ++b) {
+        const int32_t* c = d->brick_coords + 3 * b;
+        cell_slot[((uint64_t)c[2] * nby + (uint64_t)c[1]) * nbx + (uint64_t)c[0]] = (uint32_t)b;
+      }
+      e = cudaMalloc((void**)&m->d_grid, (size_t)cells * sizeof(uint32_t));
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create grid index"));
+      e = cudaMemcpy(m->d_grid, cell_slot.data(), (size_t)cells * sizeof(uint32_t), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create grid upload"));
+      v.grid = m->d_grid;
+      m->grid_cells = (int64_t)cells;
+      m->bytes = (int64_t)vbytes + (int64_t)cells * (int64_t)sizeof(uint32_t);
+    } else {
+      e = cudaMalloc(&m->d_table, (size_t)cap * sizeof(uint2));
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table"));
+      e = cudaMemcpy(m->d_table, table.data(), (size_t)cap * sizeof(uint2), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create table upload"));
+      v.table = m->d_table;
+      v.hash_mask = (uint32_t)(cap - 1);
+      v.hash_shift = shift;
+      v.max_probe = max_probe;
+      m->capacity = cap;
+      m->max_probe = max_probe;
+      m->bytes = (int64_t)vbytes + cap * (int64_t)sizeof(uint2);
+    }
   }
   v.values = m->d_values;
   *out = m;
@@ -308,9 +334,11 @@ mcl_status mcl_map_create_score(mcl_map_t src, float sigma, int32_t dtype, mcl_m
   m->dtype = dtype;
   m->d_values = nullptr;
   m->d_table = nullptr;
+  m->d_grid = nullptr;
   auto cleanup = [&](mcl_status st) {
     if (m->d_values) cudaFree(m->d_values);
     if (m->d_table) cudaFree(m->d_table);
+    if (m->d_grid) cudaFree(m->d_grid);
     delete m;
     return st;
   };
@@ -324,6 +352,12 @@ mcl_status mcl_map_create_score(mcl_map_t src, float sigma, int32_t dtype, mcl_m
       e = cudaMemcpy(m->d_table, src->d_table, (size_t)src->capacity * sizeof(uint2),
                      cudaMemcpyDeviceToDevice);
   }
+  if (e == cudaSuccess && src->d_grid) {
+    e = cudaMalloc((void**)&m->d_grid, (size_t)src->grid_cells * sizeof(uint32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m->d_grid, src->d_grid, (size_t)src->grid_cells * sizeof(uint32_t),
+                     cudaMemcpyDeviceToDevice);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create_score"));
   // The score of +tau, computed the same way (FP64, one rounding).
@@ -332,8 +366,10 @@ mcl_status mcl_map_create_score(mcl_map_t src, float sigma, int32_t dtype, mcl_m
   m->score_sigma = sigma;
   m->view.values = m->d_values;
   m->view.table = m->d_table;
+  m->view.grid = m->d_grid;
   m->view.tau = m->score_outside;  // what a look-up reads where nothing is stored
-  m->bytes = (int64_t)n * (int64_t)es + (m->d_table ? m->capacity * (int64_t)sizeof(uint2) : 0);
+  m->bytes = (int64_t)n * (int64_t)es + (m->d_table ? m->capacity * (int64_t)sizeof(uint2) : 0) +
+             (m->d_grid ? m->grid_cells * (int64_t)sizeof(uint32_t) : 0);
   *out = m;
   return MCL_OK;
 }
@@ -346,6 +382,7 @@ mcl_status mcl_map_destroy(mcl_map_t m) {
   cudaDeviceSynchronize();
   if (m->d_values) cudaFree(m->d_values);
   if (m->d_table) cudaFree(m->d_table);
+  if (m->d_grid) cudaFree(m->d_grid);
   cudaSetDevice(cur);
   delete m;
   return MCL_OK;
@@ -361,6 +398,10 @@ mcl_status mcl_map_get_info(mcl_map_t m, mcl_map_info* out) {
   out->device = m->device;
   out->score_sigma = m->score_sigma;
   out->score_outside = m->score_outside;
+  out->index = m->kind == MCL_MAP_BRICK ? (m->d_grid ? MCL_INDEX_GRID : MCL_INDEX_HASH) : 0;
+  out->reserved = 0;
+  out->index_bytes = m->d_grid ? m->grid_cells * (int64_t)sizeof(uint32_t)
+                               : m->capacity * (int64_t)sizeof(uint2);
   return MCL_OK;
 }
 
@@ -387,7 +428,7 @@ mcl_status mcl_map_lookup(mcl_map_t m, const float* pts, int64_t N, int64_t* out
     return fail(MCL_EINVAL, "map_lookup: misaligned pointer");
   if (mcl_status rc = check_device(m)) return rc;
   PhaseScope ps(MCL_PHASE_OTHER, (cudaStream_t)stream);
-  MCL_CUDA(launch_map_lookup(m->kind, m->dtype, m->view, pts, (int)N, (long long*)out_index,
+  MCL_CUDA(launch_map_lookup(kernel_kind(m), m->dtype, m->view, pts, (int)N, (long long*)out_index,
                              out_value, (cudaStream_t)stream));
   return MCL_OK;
 }
@@ -462,7 +503,7 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   }
   sh.threads = 256;
   int bps = 0;
-  MCL_CUDA(sensor_occupancy(m->kind, m->view.layout, m->dtype, kernel_mode(m, p->mode), sh, &bps));
+  MCL_CUDA(sensor_occupancy(kernel_kind(m), m->view.layout, m->dtype, kernel_mode(m, p->mode), sh, &bps));
   if (bps < 1) return fail(MCL_EINVAL, "sensor plan: launch shape does not fit on an SM");
   pl->spatial = p->particle_order == 2 || (p->particle_order == 0 && P >= kSpatialOrderMinParticles);
   pl->K = (int)((N + sh.chunk - 1) / sh.chunk);
@@ -597,7 +638,7 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   a.store_scale = (q16 && p->mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
   {
     PhaseScope ps(MCL_PHASE_SENSOR, s);
-    MCL_CUDA(launch_sensor(m->kind, m->view.layout, m->dtype, a, pl.sh, s));
+    MCL_CUDA(launch_sensor(kernel_kind(m), m->view.layout, m->dtype, a, pl.sh, s));
   }
   const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
   const int nb = normalise_blocks((int)P);

@@ -44,7 +44,7 @@ void score_constants(const mcl_map_s* m, float sigma, int mode, SensorArgs* a) {
   const double sig = (double)sigma;
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
-  a->vout = outside_raw(const_cast<mcl_map_t>(m));
+  a->vout = outside_raw(m);
   a->cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : sensor_c(sigma);
   a->store_scale = (q16 && mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
 }
@@ -84,9 +84,9 @@ mcl_status enqueue(mcl_batch_s* b, cudaStream_t st, bool profile) {
   for (auto& g : b->g) {
     if (profile) {
       PhaseScope ps(MCL_PHASE_SENSOR, st);
-      MCL_CUDA(launch_sensor_batch(g.map->kind, g.map->view.layout, g.map->dtype, g.args, g.sh, st));
+      MCL_CUDA(launch_sensor_batch(kernel_kind(g.map), g.map->view.layout, g.map->dtype, g.args, g.sh, st));
     } else {
-      MCL_CUDA(launch_sensor_batch(g.map->kind, g.map->view.layout, g.map->dtype, g.args, g.sh, st));
+      MCL_CUDA(launch_sensor_batch(kernel_kind(g.map), g.map->view.layout, g.map->dtype, g.args, g.sh, st));
     }
   }
   for (size_t i = 0; i < b->s.size(); ++i) {
@@ -231,7 +231,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       e = cudaMemcpy(b->ws + off_beg[k], beg.data(), beg.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch_create tables"));
     int bps = 0;
-    e = sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype, kernel_mode(g.map, g.mode),
+    e = sensor_batch_occupancy(kernel_kind(g.map), g.map->view.layout, g.map->dtype, kernel_mode(g.map, g.mode),
                                g.sh, &bps);
     if (e != cudaSuccess || bps < 1) return bail(cuda_fail(e, "batch_create occupancy"));
     g.sh.grid = (int)std::min<long long>(beg.back(), (long long)st.sms * bps);

@@ -17,6 +17,7 @@ constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr int kKindBrickBlock4 = 2;  // internal kind: brick map stored in 4x4x4 blocks
 constexpr int kModeScore = 2;        // internal mode: SUM on a score map (stored values are scores)
+constexpr int kKindBrickGrid = 3;    // internal kind: brick map (linear layout) with the cell grid index
 
 // Bits of the per-device status word that kernels set instead of faulting.
 enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
@@ -24,7 +25,8 @@ enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
 // Device view of a TSDF map (Sec. III). Passed by value to the kernels.
 struct MapView {
   const void* values;   // dense grid or brick-major values
-  const uint2* table;   // BRICK: open-addressing hash (key, slot), capacity 2^bits
+  const uint2* table;   // BRICK, hash index: open-addressing hash (key, slot), capacity 2^bits
+  const uint32_t* grid; // BRICK, grid index: slot of each brick cell (kNoSlot if none)
   float ox, oy, oz;     // grid corner
   float inv;            // 1 / voxel as used by the index rule
   float fnx, fny, fnz;  // dims as FP32 for the inside test
@@ -122,11 +124,15 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
     d = load_value<DTYPE>(m, (size_t)linear);
     return true;
   } else {
-    uint32_t key, local;
+    uint32_t key, local, slot;
     brick_key(m, ix, iy, iz, key, local);
-    uint32_t h = brick_hash(key, m.hash_shift);
-    uint2 e = __ldg(m.table + h);
-    uint32_t slot = e.x == key ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key, h));
+    if constexpr (KIND == kKindBrickGrid) {
+      slot = __ldg(m.grid + key);
+    } else {
+      uint32_t h = brick_hash(key, m.hash_shift);
+      uint2 e = __ldg(m.table + h);
+      slot = e.x == key ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key, h));
+    }
     if (slot == kNoSlot) return false;
     d = load_value<DTYPE>(m, (size_t)slot * kBrickVoxels + local);
     return true;

@@ -197,7 +197,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
     }
     int bps = 0;
-    MCL_CUDA(sensor_batch_occupancy(g.map->kind, g.map->view.layout, g.map->dtype,
+    MCL_CUDA(sensor_batch_occupancy(kernel_kind(g.map), g.map->view.layout, g.map->dtype,
                                     kernel_mode(g.map, g.mode), sh, &bps));
     sh.grid = (int)std::min<long long>(beg[g.idx.size()], (long long)S->dev.sms * std::max(bps, 1));
     shapes[k] = sh;
@@ -222,7 +222,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
   }
   MCL_CUDA(cudaMemcpyAsync(sl->d_tab, sl->h_tab, off, cudaMemcpyHostToDevice, st));
   for (size_t k = 0; k < groups.size(); ++k)
-    MCL_CUDA(launch_sensor_batch(groups[k].map->kind, groups[k].map->view.layout, groups[k].map->dtype,
+    MCL_CUDA(launch_sensor_batch(kernel_kind(groups[k].map), groups[k].map->view.layout, groups[k].map->dtype,
                                  args[k], shapes[k], st));
   for (size_t i = 0; i < n; ++i) {
     mcl_session_s* ss = sl->sessions[i];

@@ -38,7 +38,7 @@ std::string tune_key(const mcl_map_s* m, int mode, int64_t P, int64_t N, bool su
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, m->device);
   char buf[256];
-  snprintf(buf, sizeof buf, "%s|k%d|l%d|d%d|m%d|P%d|N%d|s%d", prop.name, m->kind, m->view.layout,
+  snprintf(buf, sizeof buf, "%s|k%d|l%d|d%d|m%d|P%d|N%d|s%d", prop.name, kernel_kind(m), m->view.layout,
            m->dtype, mode, log2_bucket(P), log2_bucket(N), summation ? 1 : 0);
   std::string s(buf);
   for (char& c : s)

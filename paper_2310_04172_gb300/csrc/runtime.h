@@ -96,7 +96,9 @@ struct mcl_map_s {
   int kind = 0, dtype = 0;
   mcl::MapView view{};
   void* d_values = nullptr;
-  uint2* d_table = nullptr;
+  uint2* d_table = nullptr;     // hash index
+  uint32_t* d_grid = nullptr;   // grid index
+  int64_t grid_cells = 0;
   int64_t bytes = 0, n_bricks = 0, capacity = 0;
   int max_probe = 0;
   float score_sigma = 0.f;    // > 0: values are scores for this sigma
@@ -105,10 +107,14 @@ struct mcl_map_s {
 
 namespace mcl {
 
+// Kernel kind of a map: dense, brick with the hash index (layout chosen at
+// run time) or brick with the grid index.
+inline int kernel_kind(const mcl_map_s* m) { return m->d_grid ? kKindBrickGrid : m->kind; }
+
 // Kernel mode and the value read where nothing is stored (storage units)
 // of a sensor update on map m with the caller's mode.
-inline int kernel_mode(mcl_map_t m, int mode) { return m->score_sigma > 0.f ? kModeScore : mode; }
-inline float outside_raw(mcl_map_t m) {
+inline int kernel_mode(const mcl_map_s* m, int mode) { return m->score_sigma > 0.f ? kModeScore : mode; }
+inline float outside_raw(const mcl_map_s* m) {
   if (m->score_sigma > 0.f) return m->score_outside;
   return m->dtype == MCL_I16 ? 32767.0f : m->view.tau;
 }

@@ -21,6 +21,7 @@ MCL_OK, MCL_EINVAL, MCL_ENOMEM, MCL_EBUSY, MCL_ETIMEDOUT, MCL_ECUDA, MCL_EINTERN
 MCL_MAP_DENSE, MCL_MAP_BRICK = 0, 1
 MCL_F32, MCL_F16, MCL_I16 = 0, 1, 2
 MCL_LAYOUT_LINEAR, MCL_LAYOUT_BLOCK4 = 0, 1
+MCL_INDEX_AUTO, MCL_INDEX_HASH, MCL_INDEX_GRID = 0, 1, 2
 MCL_LOGPROD, MCL_SUM = 0, 1
 MCL_NEGLECT_OUTSIDE = 1
 MCL_TRILINEAR = 2
@@ -35,13 +36,14 @@ class mcl_map_desc(ctypes.Structure):
                 ("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float),
                 ("inv_voxel", ctypes.c_float), ("truncation", ctypes.c_float),
                 ("dims", _i64 * 3), ("n_bricks", _i64), ("brick_coords", _c_void_p),
-                ("device_layout", _i32), ("reserved", _i32)]
+                ("device_layout", _i32), ("index", _i32)]
 
 
 class mcl_map_info(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("device_bytes", _i64), ("n_bricks", _i64),
                 ("hash_capacity", _i64), ("hash_max_probe", _i32), ("device", _i32),
-                ("score_sigma", ctypes.c_float), ("score_outside", ctypes.c_float)]
+                ("score_sigma", ctypes.c_float), ("score_outside", ctypes.c_float),
+                ("index", _i32), ("reserved", _i32), ("index_bytes", _i64)]
 
 
 class mcl_sensor_params(ctypes.Structure):
@@ -285,7 +287,8 @@ class Map:
 
 def mcl_map_create(kind: int, dtype: int, origin, voxel: float, truncation: float, dims,
                    values: np.ndarray, brick_coords: np.ndarray | None = None,
-                   inv_voxel: float = 0.0, device_layout: int = MCL_LAYOUT_LINEAR) -> Map:
+                   inv_voxel: float = 0.0, device_layout: int = MCL_LAYOUT_LINEAR,
+                   index: int = MCL_INDEX_AUTO) -> Map:
     """Upload a dense or brick TSDF (host arrays) to the current device."""
     values = np.ascontiguousarray(values)
     d = mcl_map_desc(struct_size=ctypes.sizeof(mcl_map_desc), kind=kind, dtype=dtype)
@@ -299,19 +302,20 @@ def mcl_map_create(kind: int, dtype: int, origin, voxel: float, truncation: floa
         d.n_bricks = len(bc)
         d.brick_coords = bc.ctypes.data_as(ctypes.c_void_p)
         d.device_layout = device_layout
+        d.index = index
     h = ctypes.c_void_p()
     _check(lib().mcl_map_create(ctypes.byref(d), values.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
     return Map(h, d)
 
 
-def map_from_scene(m, device_layout: int = MCL_LAYOUT_LINEAR) -> Map:
+def map_from_scene(m, device_layout: int = MCL_LAYOUT_LINEAR, index: int = MCL_INDEX_AUTO) -> Map:
     """Upload a ``scenes.DenseMap`` / ``scenes.BrickMap`` (input generator objects)."""
     if m.kind == "dense":
         return mcl_map_create(MCL_MAP_DENSE, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
                               m.dims, m.values, inv_voxel=m.inv_voxel)
     return mcl_map_create(MCL_MAP_BRICK, m.dtype, m.origin, np.float32(m.voxel), np.float32(m.tau),
                           m.dims, m.values, m.coords, inv_voxel=m.inv_voxel,
-                          device_layout=device_layout)
+                          device_layout=device_layout, index=index)
 
 
 def mcl_map_create_score(m: Map, sigma_hit: float, dtype: int = MCL_F16) -> Map:

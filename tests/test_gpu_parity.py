@@ -114,11 +114,14 @@ def lookup_points(rng, m, n=200_000):
     return pts
 
 
-KINDS = ["dense", "brick", "brick_block4"]
+# brick: automatic index (the cell grid for these maps); brick_hash: the hash
+# index; brick_block4: 4x4x4-block bricks (hash index)
+KINDS = ["dense", "brick", "brick_hash", "brick_block4"]
 
 
 def upload(mcl, sm, kind):
-    return mcl.map_from_scene(sm, mcl.MCL_LAYOUT_BLOCK4 if kind == "brick_block4" else 0)
+    return mcl.map_from_scene(sm, mcl.MCL_LAYOUT_BLOCK4 if kind == "brick_block4" else 0,
+                              mcl.MCL_INDEX_HASH if kind == "brick_hash" else mcl.MCL_INDEX_AUTO)
 
 
 def room_map(sc, kind, dtype):
@@ -232,11 +235,12 @@ def building_i16():
     return scenes.os064_building(P=1_000_000, dtype=scenes.I16)
 
 
-@pytest.mark.parametrize("layout", [0, 1])
-def test_building_os064_parity_subset(torch_cuda, mcl, building_i16, layout):
+@pytest.mark.parametrize("layout,index", [(0, 0), (0, 1), (1, 0)])
+def test_building_os064_parity_subset(torch_cuda, mcl, building_i16, layout, index):
     torch = torch_cuda
     wl = building_i16
-    m = mcl.map_from_scene(wl.map, layout)
+    m = mcl.map_from_scene(wl.map, layout, index)
+    assert m.info()["index"] == (2 if (layout, index) == (0, 0) else 1)
     parts = wl.particles[:3000]
     Lg, wg = run_sensor(torch, mcl, m, parts, wl.scan, wl.sigma_hit)
     Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), parts, wl.scan, wl.sigma_hit)
@@ -260,16 +264,22 @@ def test_particle_order_gives_identical_bits(torch_cuda, mcl, room, building_i16
 
 
 def test_brick_layouts_give_identical_bits(torch_cuda, mcl, room):
-    """The device layout only moves values: same reads, same sums, same bits."""
+    """The device layout and the brick index only move values and change how
+    a brick is found: same reads, same sums, same bits."""
     torch = torch_cuda
     for dtype in (scenes.F32, scenes.F16, scenes.I16):
         sm = room_map(room.scene, "brick", dtype)
         res = []
-        for layout in (0, 1):
-            m = mcl.map_from_scene(sm, layout)
+        for layout, index in ((0, 2), (0, 1), (1, 1)):
+            m = mcl.map_from_scene(sm, layout, index)
             res.append(run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit))
+            for flags in (mcl.MCL_TRILINEAR, mcl.MCL_NEGLECT_OUTSIDE):
+                res[-1] += run_sensor(torch, mcl, m, room.particles, room.scan, room.sigma_hit, 0, flags)
             m.close()
-        assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+        for r in res[1:]:
+            assert all(np.array_equal(x, y) for x, y in zip(res[0], r))
+    with pytest.raises(mcl.MclError):  # the grid index is built for linear bricks only
+        mcl.map_from_scene(sm, 1, 2)
 
 
 def test_building_full_size_sampled(torch_cuda, mcl, building_i16):
