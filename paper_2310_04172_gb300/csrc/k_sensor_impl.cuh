@@ -394,16 +394,23 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
   }
 }
 
-// Resident CTAs per SM the register allocation is held to: 6 for the 2- and
-// 4-deep loops (40 registers), 3 for the 8-deep loop (measured faster than the
-// 2 its free allocation gives).
+// Resident CTAs per SM the register allocation is held to (measured on the
+// 1M x 65,536 building step): with the hash index 6 for the 2- and 4-deep
+// loops (40 registers; 5 or 4 were slower), with the cell-grid index 4 (64
+// registers, no spills: 189 ms against 206 ms at 6), 3 for the 8-deep loop
+// and the trilinear read.
 #ifndef MCL_SENSOR_MIN_BLOCKS
 #define MCL_SENSOR_MIN_BLOCKS 6
 #endif
+#ifndef MCL_SENSOR_MIN_BLOCKS_GRID
+#define MCL_SENSOR_MIN_BLOCKS_GRID 4
+#endif
 
-template <int U, bool TRI = false>
+template <int KIND, int U, bool TRI = false>
 struct MinBlocks {
-  static constexpr int value = TRI ? 3 : (U == 8 ? 3 : MCL_SENSOR_MIN_BLOCKS);
+  static constexpr int value = (TRI || U == 8) ? 3
+                               : KIND == kKindBrickGrid ? MCL_SENSOR_MIN_BLOCKS_GRID
+                                                        : MCL_SENSOR_MIN_BLOCKS;
 };
 
 // Stage `cnt` scan points starting at `src` into shared memory with one bulk
@@ -498,7 +505,7 @@ __device__ __forceinline__ void init_barrier(uint32_t bar_s) {
 
 // One session: items (chunk c, particle block) strided over a persistent grid.
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
-__global__ void __launch_bounds__(256, (MinBlocks<U, TRI>::value)) k_sensor(const SensorArgs a) {
+__global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_sensor(const SensorArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
   const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
@@ -525,7 +532,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<U, TRI>::value)) k_sensor(cons
 // (item_begin[s] is the first item of session s), strided over a persistent
 // grid. Each session's results are the ones the single-session kernel gives.
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
-__global__ void __launch_bounds__(256, (MinBlocks<U, TRI>::value)) k_sensor_batch(const BatchArgs b) {
+__global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_sensor_batch(const BatchArgs b) {
   const SensorArgs& a = b.base;
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
