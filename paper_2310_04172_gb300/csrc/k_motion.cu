@@ -110,7 +110,11 @@ cudaError_t launch_motion(float* particles, int P, const float delta[6], const f
     a.delta[k] = delta ? delta[k] : 0.f;
     a.sigma[k] = sigma[k];
   }
-  k_motion<<<(P + 255) / 256, 256, 0, s>>>(particles, P, a, seed, step, in);
+  // FP64-heavy per particle: small sets use small blocks so that they still
+  // spread over many SMs (one block of 256 would load a single SM).
+  int threads = 256;
+  while (threads > 32 && (P + threads - 1) / threads < 2 * 152) threads >>= 1;
+  k_motion<<<(P + threads - 1) / threads, threads, 0, s>>>(particles, P, a, seed, step, in);
   return cudaGetLastError();
 }
 

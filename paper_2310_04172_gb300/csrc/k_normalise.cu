@@ -2,7 +2,7 @@
 // weights are summed for normalisation; Sec. V-B: a GPU reduction).
 //
 // The paper reduces with repeated pairwise-halving launches. Here two
-// launches suffice: each of up to 1024 blocks owns a contiguous particle range
+// launches suffice: each of up to 1024 blocks of 256 threads owns a contiguous particle range
 // and writes its (max, sum exp(L - max)); every block of the second launch
 // combines all block pairs in the same fixed order (so all blocks agree on M
 // and S bit for bit) and writes w = exp(L - M) / S for its range. FP32
@@ -15,7 +15,10 @@
 namespace mcl {
 namespace {
 
-constexpr int kT = 1024;
+// 256 threads per block: small particle sets still spread over several SMs,
+// which matters for the FP64 sums of the estimate (FP64 throughput per SM is
+// low on this part).
+constexpr int kT = 256;
 
 __device__ __forceinline__ float block_max(float v, float* sh) {
 #pragma unroll

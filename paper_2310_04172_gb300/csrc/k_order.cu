@@ -3,8 +3,9 @@
 //
 // Particles are bucketed by position into a 64 x 64 x 64 grid over the map's
 // extent, buckets ordered along a Morton (Z-order) curve, and each particle
-// gets a slot rank[p] in that order (counting sort: histogram, one-block
-// exclusive scan, scatter). The sensor kernel then works on the particles slot
+// gets a slot rank[p] in that order (counting sort: histogram, exclusive
+// scan of the bucket counts in tiles of 1024 plus a scan of the tile totals,
+// scatter). The sensor kernel then works on the particles slot
 // by slot, so the CTAs running at the same time hold particles that are close
 // in space and read the same map bricks from L2. Each particle's result
 // depends only on its own pose, never on its slot, so the order within a
@@ -16,7 +17,8 @@ namespace {
 
 constexpr int kOrderBits = 6;                         // cells per axis = 64
 constexpr int kOrderBuckets = 1 << (3 * kOrderBits);  // 262144
-constexpr int kScanThreads = 1024;
+constexpr int kScanTile = 1024;                          // buckets per scan block
+constexpr int kScanTiles = kOrderBuckets / kScanTile;  // 256
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   uint32_t r = 0;
@@ -42,55 +44,72 @@ __global__ void k_order_keys(const float* __restrict__ poses, int P, float3 o, f
   atomicAdd(hist + k, 1u);
 }
 
-// One block: exclusive prefix of the bucket counts, in place.
-__global__ void __launch_bounds__(kScanThreads) k_order_scan(uint32_t* __restrict__ hist) {
-  constexpr int per = kOrderBuckets / kScanThreads;
-  __shared__ uint32_t warp_tot[32];
-  uint32_t* mine = hist + threadIdx.x * per;
-  uint32_t local = 0;
-  for (int i = 0; i < per; ++i) local += mine[i];
-  // inclusive scan of the per-thread totals
+// Inclusive scan over a block of 1024 threads (warp shuffles, then the warp
+// totals); returns this thread's inclusive prefix and the block total.
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = local;
+  uint32_t incl = v;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += v;
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += u;
   }
   if (lane == 31) warp_tot[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t t = warp_tot[lane];
+    const int nw = (int)(blockDim.x >> 5);
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, t, off);
-      if (lane >= off) t += v;
+      const uint32_t u = __shfl_up_sync(0xffffffffu, t, off);
+      if (lane >= off) t += u;
     }
     warp_tot[lane] = t;
   }
   __syncthreads();
-  uint32_t run = incl - local + (warp > 0 ? warp_tot[warp - 1] : 0u);
-  for (int i = 0; i < per; ++i) {
-    const uint32_t c = mine[i];
-    mine[i] = run;
-    run += c;
-  }
+  total = warp_tot[(blockDim.x >> 5) - 1];
+  return incl + (warp > 0 ? warp_tot[warp - 1] : 0u);
+}
+
+// Tile b: exclusive prefix of its 1024 bucket counts in place (coalesced),
+// its total to tile_off[b].
+__global__ void __launch_bounds__(kScanTile) k_order_scan_tiles(uint32_t* __restrict__ hist,
+                                                                 uint32_t* __restrict__ tile_off) {
+  __shared__ uint32_t warp_tot[32];
+  const size_t i = (size_t)blockIdx.x * kScanTile + threadIdx.x;
+  const uint32_t v = hist[i];
+  uint32_t total;
+  const uint32_t incl = block_incl_scan(v, warp_tot, total);
+  hist[i] = incl - v;
+  if (threadIdx.x == 0) tile_off[blockIdx.x] = total;
+}
+
+// Exclusive prefix of the tile totals in place (one block of kScanTiles).
+__global__ void __launch_bounds__(kScanTiles) k_order_scan_totals(uint32_t* __restrict__ tile_off) {
+  __shared__ uint32_t warp_tot[32];
+  const uint32_t v = tile_off[threadIdx.x];
+  uint32_t total;
+  const uint32_t incl = block_incl_scan(v, warp_tot, total);
+  tile_off[threadIdx.x] = incl - v;
 }
 
 __global__ void k_order_scatter(const uint32_t* __restrict__ key, int P,
-                                uint32_t* __restrict__ cursor, int* __restrict__ rank) {
+                                uint32_t* __restrict__ cursor, const uint32_t* __restrict__ tile_off,
+                                int* __restrict__ rank) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  rank[p] = (int)atomicAdd(cursor + key[p], 1u);
+  const uint32_t k = key[p];
+  rank[p] = (int)(__ldg(tile_off + k / kScanTile) + atomicAdd(cursor + k, 1u));
 }
 
 }  // namespace
 
-size_t order_hist_bytes() { return (size_t)kOrderBuckets * sizeof(uint32_t); }
+// bucket counts / cursors, then the tile offsets
+size_t order_hist_bytes() { return (size_t)(kOrderBuckets + kScanTiles) * sizeof(uint32_t); }
 
 cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, uint32_t* key,
                                   uint32_t* hist, int* rank, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(hist, 0, order_hist_bytes(), s);
+  cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)kOrderBuckets * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const float cells = (float)(1 << kOrderBits);
   const float ex = m.fnx / m.inv, ey = m.fny / m.inv, ez = m.fnz / m.inv;  // extent in metres
@@ -99,9 +118,12 @@ cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, u
   const int g = (P + 255) / 256;
   k_order_keys<<<g, 256, 0, s>>>(poses, P, o, sc, key, hist);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_order_scan<<<1, kScanThreads, 0, s>>>(hist);
+  uint32_t* tile_off = hist + kOrderBuckets;
+  k_order_scan_tiles<<<kScanTiles, kScanTile, 0, s>>>(hist, tile_off);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_order_scatter<<<g, 256, 0, s>>>(key, P, hist, rank);
+  k_order_scan_totals<<<1, kScanTiles, 0, s>>>(tile_off);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_order_scatter<<<g, 256, 0, s>>>(key, P, hist, tile_off, rank);
   return cudaGetLastError();
 }
 

@@ -604,7 +604,7 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   float* ostats = (float*)(ws + pl.off_ostats);
   int* rank = pl.spatial ? (int*)(ws + pl.off_rank) : nullptr;
   {
-    PhaseScope ps(MCL_PHASE_POSE, s, pl.spatial ? 4 : 1);
+    PhaseScope ps(MCL_PHASE_POSE, s, pl.spatial ? 5 : 1);
     if (pl.spatial)
       MCL_CUDA(launch_particle_order(particles, (int)P, m->view, (uint32_t*)(ws + pl.off_key),
                                      (uint32_t*)(ws + pl.off_hist), rank, s));
