@@ -298,7 +298,7 @@ def config_dict(args, wl):
     return {
         "workload": wl.name, "particles": int(len(wl.particles)), "points": int(len(wl.scan)),
         "scan": f"64 rings (+-45 deg) x {args.azimuths} azimuths, sigma 0.02 m",
-        "map": {"kind": "brick16", "index": "hash", "dtype": args.dtype,
+        "map": {"kind": "brick16", "dtype": args.dtype,
                 "layout": ["linear", "block4"][args.layout],
                 "extent_m": [args.building, args.building, 5.0 * args.floors], "voxel_m": 0.05,
                 "dims": list(m.dims), "bricks": int(len(m.coords)), "bytes": int(m.values.nbytes),
@@ -424,9 +424,8 @@ def run_ours(args):
     if rank == 0:
         cfg = config_dict(args, wl)
         info = m.info()
-        cfg["map"]["index"] = {1: "hash", 2: "cell grid"}.get(info["index"], "none")
-        cfg["map"]["index_bytes"] = info["index_bytes"]
-        cfg["launch"] = plan
+        cfg["launch"] = dict(plan, brick_index={1: "hash", 2: "cell grid"}.get(info["index"], "none"),
+                             brick_index_bytes=info["index_bytes"])
         cfg["parallelism"] = f"replicas{world}" if world > 1 else "single"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
