@@ -56,6 +56,16 @@ int32_t mcl_version(void);
  * that ran out, an index check that failed); the status word is cleared. */
 mcl_status mcl_sync(mcl_stream_t stream);
 
+/* Self-test of the library's failure path (the paper has no counterpart):
+ * launches one CTA that waits, with the same bounded wait the sensor kernel
+ * uses for its scan copies, on a barrier phase that nothing completes. The
+ * wait gives up after about one second, the kernel records the timeout in
+ * the device status word and returns; this call waits for it (synchronous),
+ * checks that the timeout was recorded, clears the status word and writes
+ * the time the kernel waited to waited_s (host, may be NULL). MCL_OK if the
+ * failure path worked; MCL_EINTERNAL if the timeout was not recorded. */
+mcl_status mcl_selftest_wait(double* waited_s, mcl_stream_t stream);
+
 /* ------------------------------------------------------------------ maps */
 
 enum { MCL_MAP_DENSE = 0, MCL_MAP_BRICK = 1 };

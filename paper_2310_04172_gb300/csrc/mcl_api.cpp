@@ -153,6 +153,29 @@ mcl_status mcl_sync(mcl_stream_t stream) {
   return MCL_OK;
 }
 
+mcl_status mcl_selftest_wait(double* waited_s, mcl_stream_t stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  MCL_CUDA(cudaStreamSynchronize(s));
+  DeviceState st;
+  if (mcl_status rc = device_state(nullptr, &st)) return rc;
+  unsigned v = 0;
+  MCL_CUDA(cudaMemcpy(&v, st.status, sizeof v, cudaMemcpyDeviceToHost));
+  if (v) return fail(MCL_EINTERNAL, "selftest_wait: status word already 0x%x", v);
+  unsigned long long* d_ns = nullptr;
+  MCL_CUDA(cudaMalloc(&d_ns, sizeof(unsigned long long)));
+  unsigned long long ns = 0;
+  cudaError_t e = launch_wait_selftest(st.status, d_ns, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&ns, d_ns, sizeof ns, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, st.status, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(st.status, 0, sizeof v);
+  cudaFree(d_ns);
+  MCL_CUDA(e);
+  if (waited_s) *waited_s = (double)ns * 1e-9;
+  if (!(v & kDevErrTimeout)) return fail(MCL_EINTERNAL, "selftest_wait: the timeout was not recorded");
+  return MCL_OK;
+}
+
 // ---------------------------------------------------------------- maps
 mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_map_t* out) {
   if (!d || !out) return fail(MCL_EINVAL, "map_create: NULL desc or out");

@@ -276,6 +276,9 @@ cudaError_t launch_motion(float* particles, int P, const float delta[6], const f
                           uint64_t seed, uint64_t step, cudaStream_t s,
                           const StepIn* in = nullptr);
 
+// One CTA waits on a barrier phase nothing completes (k_diag.cu).
+cudaError_t launch_wait_selftest(unsigned* status, unsigned long long* waited_ns, cudaStream_t s);
+
 cudaError_t launch_gather_bench(const void* buf, long long n_elems, int elem_bytes, int blocks,
                                 int iters, unsigned long long seed, float* sink, cudaStream_t s);
 

@@ -199,6 +199,7 @@ SIGNATURES = {
     "mcl_server_get_stats": (_i32, [_c_void_p, _i32, ctypes.POINTER(mcl_server_stats)]),
     "mcl_server_pause": (_i32, [_c_void_p, _i32]),
     "mcl_server_destroy": (_i32, [_c_void_p]),
+    "mcl_selftest_wait": (_i32, [ctypes.POINTER(ctypes.c_double), _c_void_p]),
     "mcl_gather_bench": (_i32, [_c_void_p, _i64, _i32, _i32, _i32, _u64, _c_void_p]),
     "mcl_workspace_release": (_i32, [_c_void_p]),
     "mcl_profile_begin": (_i32, []),
@@ -259,6 +260,13 @@ def mcl_version() -> int:
 
 def mcl_sync(stream=None):
     _check(lib().mcl_sync(_stream(stream)))
+
+
+def mcl_selftest_wait(stream=None) -> float:
+    """Runs the bounded-wait failure path on the device; returns the seconds waited."""
+    t = ctypes.c_double()
+    _check(lib().mcl_selftest_wait(ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 class Map:
