@@ -411,18 +411,23 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 // Resident CTAs per SM the register allocation is held to (measured on the
 // 1M x 65,536 building step): with the hash index 6 for the 2- and 4-deep
 // loops (40 registers; 5 or 4 were slower), with the cell-grid index 4 (64
-// registers, no spills: 189 ms against 206 ms at 6), 3 for the 8-deep loop
-// and the trilinear read.
+// registers, no spills: 189 ms against 206 ms at 6), 3 for the 8-deep loop,
+// 4 for the trilinear read (1082 ms against 1112 ms at 3 and 1364 ms at 2; a
+// branch-free corner walk without the per-brick deduplication and a
+// single-brick fast path were both slower).
 #ifndef MCL_SENSOR_MIN_BLOCKS
 #define MCL_SENSOR_MIN_BLOCKS 6
 #endif
 #ifndef MCL_SENSOR_MIN_BLOCKS_GRID
 #define MCL_SENSOR_MIN_BLOCKS_GRID 4
 #endif
+#ifndef MCL_TRI_MIN_BLOCKS
+#define MCL_TRI_MIN_BLOCKS 4
+#endif
 
 template <int KIND, int U, bool TRI = false>
 struct MinBlocks {
-  static constexpr int value = (TRI || U == 8) ? 3
+  static constexpr int value = TRI ? MCL_TRI_MIN_BLOCKS : U == 8 ? 3
                                : KIND == kKindBrickGrid ? MCL_SENSOR_MIN_BLOCKS_GRID
                                                         : MCL_SENSOR_MIN_BLOCKS;
 };
