@@ -97,8 +97,64 @@ struct Raw {
   using acc = float;
 };
 
+#ifndef MCL_VALUE_LOAD_HINT
+#define MCL_VALUE_LOAD_HINT 1
+#endif
+
+// Read-only 16/32-bit gathers of map values. Hint 1 (default): do not
+// allocate in L1 (the values have little reuse there; the brick index and
+// the scan keep L1): 184.5 ms against 189.9 ms with plain read-only loads for
+// 1M x 65,536. Hints 2 and 3 add an L2 evict-first / evict-last policy.
+__device__ __forceinline__ unsigned short ld_u16(const void* p) {
+  unsigned short v;
+#if MCL_VALUE_LOAD_HINT == 1
+  asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+#elif MCL_VALUE_LOAD_HINT == 2 || MCL_VALUE_LOAD_HINT == 3
+  uint64_t pol;
+#if MCL_VALUE_LOAD_HINT == 2
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#else
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#endif
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+#else
+  v = __ldg(static_cast<const unsigned short*>(p));
+#endif
+  return v;
+}
+
+__device__ __forceinline__ float ld_f32(const void* p) {
+  float v;
+#if MCL_VALUE_LOAD_HINT == 1
+  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+#elif MCL_VALUE_LOAD_HINT == 2 || MCL_VALUE_LOAD_HINT == 3
+  uint64_t pol;
+#if MCL_VALUE_LOAD_HINT == 2
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#else
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#endif
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+#else
+  v = __ldg(static_cast<const float*>(p));
+#endif
+  return v;
+}
+
 template <int DTYPE, int MODE>
 __device__ __forceinline__ typename Raw<DTYPE, MODE>::value load_raw(const void* values, size_t i) {
+  if constexpr (DTYPE == MCL_F32) {
+    return ld_f32(static_cast<const float*>(values) + i);
+  } else if constexpr (DTYPE == MCL_F16) {
+    return __half2float(__ushort_as_half(ld_u16(static_cast<const __half*>(values) + i)));
+  } else {
+    return (float)(short)ld_u16(static_cast<const short*>(values) + i);
+  }
+}
+
+// The same through L1: the trilinear read's eight corners share L1 lines.
+template <int DTYPE, int MODE>
+__device__ __forceinline__ typename Raw<DTYPE, MODE>::value load_raw_l1(const void* values, size_t i) {
   if constexpr (DTYPE == MCL_F32) {
     return __ldg(static_cast<const float*>(values) + i);
   } else if constexpr (DTYPE == MCL_F16) {
@@ -325,7 +381,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
       const bool in = inx[cx] & iny[cy] & inz[cz];
       const size_t lin = ((size_t)(z0 + cz) * (size_t)m.ny + (size_t)(y0 + cy)) * (size_t)m.nx +
                          (size_t)(x0 + cx);
-      v[c] = in ? load_raw<DTYPE, MODE>(m.values, lin) : a.vout;
+      v[c] = in ? load_raw_l1<DTYPE, MODE>(m.values, lin) : a.vout;
       stored |= in;
     }
   } else {
@@ -362,7 +418,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
       const bool st = slot[c] != kNoSlot;
-      v[c] = st ? load_raw<DTYPE, MODE>(m.values, (size_t)slot[c] * kBrickVoxels +
+      v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, (size_t)slot[c] * kBrickVoxels +
                                                      brick_local<KIND>(x0 + cx, y0 + cy, z0 + cz))
                 : a.vout;
       stored |= st;
