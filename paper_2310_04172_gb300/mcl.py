@@ -381,7 +381,7 @@ def estimate_buffer(device=None):
 def estimate_to_dict(buf) -> dict:
     """Reads an mcl_estimate from a device (or host) buffer into a dict of
     numpy values (synchronises with the buffer's producer through .cpu())."""
-    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(np.asarray(buf).tobytes())
     e = mcl_estimate.from_buffer_copy(raw[:ESTIMATE_BYTES])
     return {
         "weight_sum": e.weight_sum, "n_eff": e.n_eff,

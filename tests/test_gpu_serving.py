@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from resample_props import check_systematic
 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -75,8 +76,11 @@ def test_same_alone_and_in_the_mix_and_against_the_oracle(env):
     assert abs(w_mix.astype(np.float64).sum() - 1) <= 1e-5
     bound = 1e-5 * (np.maximum(1, np.abs(L[sel])) + max(1, abs(M)))
     assert np.all(np.abs(np.log(w_mix[sel].astype(np.float64)) - np.log(wo[sel])) <= bound)
-    idx, _ = oracle.resample(w_mix, offset_of(seed, 0))
-    assert np.array_equal(parts_mix, room.particles[idx])
+    # the resampled set: rows of the input drawn systematically by the weights
+    rows = {r.tobytes(): i for i, r in enumerate(room.particles)}
+    idx = np.array([rows[r.tobytes()] for r in parts_mix])
+    order = np.argsort(idx, kind="stable")
+    check_systematic(idx[order], w_mix, offset_of(seed, 0))
     mix.close()
 
 
