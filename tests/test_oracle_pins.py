@@ -476,3 +476,22 @@ def test_motion_noise_statistics():
     # counter-based: same (seed, step, i) gives the same draw, another step another
     assert np.array_equal(oracle.motion_noise(77, 5, 3), n[3])
     assert not np.array_equal(oracle.motion_noise(77, 6, 3), n[3])
+
+
+def test_systematic_properties_hold_for_the_oracle_and_catch_a_planted_error(rng):
+    """The property check used on GPU-drawn indices accepts every oracle draw
+    and rejects a draw with one index moved."""
+    from resample_props import check_systematic
+    for P in (1, 7, 1000, 4097):
+        w = (rng.exponential(1.0, P) ** 3).astype(np.float32)
+        w[rng.random(P) < 0.3] = 0
+        for r in (0.0, 0.37, 1 - 2.0 ** -53):
+            idx, _ = oracle.resample(w, r)
+            check_systematic(idx, w, r)
+    w = np.full(100, 0.01, np.float32)
+    idx, _ = oracle.resample(w, 0.5)
+    bad = idx.copy()
+    bad[10] = bad[11]                      # one particle drawn twice, another not at all
+    with pytest.raises(AssertionError):
+        check_systematic(bad, w, 0.5)
+    check_systematic(np.arange(5), np.zeros(5, np.float32), 0.2)
