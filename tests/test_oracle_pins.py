@@ -488,10 +488,20 @@ def test_systematic_properties_hold_for_the_oracle_and_catch_a_planted_error(rng
         for r in (0.0, 0.37, 1 - 2.0 ** -53):
             idx, _ = oracle.resample(w, r)
             check_systematic(idx, w, r)
-    w = np.full(100, 0.01, np.float32)
+    # 10 particles: weight 0.25 (2.5 expected draws) at index 3, zero at 5
+    w = np.array([0.1, 0.05, 0.1, 0.25, 0.1, 0.0, 0.1, 0.1, 0.1, 0.1], np.float32)
     idx, _ = oracle.resample(w, 0.5)
+    check_systematic(idx, w, 0.5)
+    planted = []
     bad = idx.copy()
-    bad[10] = bad[11]                      # one particle drawn twice, another not at all
-    with pytest.raises(AssertionError):
-        check_systematic(bad, w, 0.5)
+    bad[bad == 4] = 5                      # draws of a zero-weight particle
+    planted.append(np.sort(bad))
+    bad = idx.copy()
+    bad[[0, -1]] = bad[[-1, 0]]            # out of order
+    planted.append(bad)
+    bad = np.sort(np.concatenate([idx[idx != 7], [3] * int((idx == 7).sum())]))
+    planted.append(bad)                    # particle 3 drawn 3 + 1 times
+    for b in planted:
+        with pytest.raises(AssertionError):
+            check_systematic(b, w, 0.5)
     check_systematic(np.arange(5), np.zeros(5, np.float32), 0.2)
