@@ -589,6 +589,8 @@ typedef struct mcl_result {
   double latency_ms;        /* submission to completion seen by the host */
   int64_t evals;            /* P x N of the step */
   int64_t step;             /* the session's step counter after this step */
+  mcl_estimate estimate;    /* MCL_RESULT_DONE: the pose estimate of the step's weighted
+                               particles (before resampling), as mcl_pose_estimate */
 } mcl_result;
 
 /* Waits up to timeout_ms (< 0: forever) for a ticket. ETIMEDOUT if it has

@@ -33,6 +33,7 @@ struct Ticket {
   int status = -1;  // -1 pending, else MCL_RESULT_*
   double t_submit = 0, latency_ms = 0;
   int64_t evals = 0, step = 0;
+  mcl_estimate est{};
 };
 
 struct Slot;
@@ -54,6 +55,8 @@ struct mcl_session_s {
   float *d_scan = nullptr, *d_logw = nullptr, *d_w = nullptr;
   int32_t* d_idx = nullptr;
   char* d_ws = nullptr;
+  mcl_estimate* d_est = nullptr;  // the running step's estimate
+  mcl_estimate* h_est = nullptr;  // pinned copy, read when the step completed
   Plan pl{};
   size_t off_cum = 0, off_tot = 0, off_last = 0;
   float* h_stage[2] = {nullptr, nullptr};  // pinned scan staging: queued / running
@@ -125,6 +128,8 @@ void free_session(mcl_session_s* ss) {
   cudaFree(ss->d_w);
   cudaFree(ss->d_idx);
   cudaFree(ss->d_ws);
+  cudaFree(ss->d_est);
+  cudaFreeHost(ss->h_est);
   cudaFreeHost(ss->h_stage[0]);
   cudaFreeHost(ss->h_stage[1]);
   delete ss;
@@ -234,8 +239,13 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     const float c = (float)(-0.5 / (sig * sig));
     const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
     MCL_CUDA(launch_finish_and_normalise((float*)(ss->d_ws + pl.off_partial), rank, P, K, ss->mode, c, k,
-                                         ss->d_logw, ss->d_w, (float2*)(ss->d_ws + pl.off_stats),
-                                         normalise_blocks(P), (float*)(ss->d_ws + pl.off_ostats), st));
+                                         ss->d_logw, nullptr, (float2*)(ss->d_ws + pl.off_stats),
+                                         normalise_blocks(P), nullptr, st));
+    MCL_CUDA(launch_normalise_from_stats(ss->d_logw, P, ss->d_w, (float2*)(ss->d_ws + pl.off_stats),
+                                         normalise_blocks(P), (float*)(ss->d_ws + pl.off_ostats),
+                                         ss->d_part[ss->cur], (EstPartial*)(ss->d_ws + pl.off_est),
+                                         ss->d_est, st));
+    MCL_CUDA(cudaMemcpyAsync(ss->h_est, ss->d_est, sizeof(mcl_estimate), cudaMemcpyDeviceToHost, st));
     MCL_CUDA(launch_resample(ss->d_w, P, resample_offset(ss->seed, (uint64_t)ss->step), ss->d_idx,
                              ss->d_part[ss->cur], ss->d_part[1 - ss->cur], (double*)(ss->d_ws + ss->off_cum),
                              (double*)(ss->d_ws + ss->off_tot), (long long*)(ss->d_ws + ss->off_last), st));
@@ -253,6 +263,7 @@ void finalize(mcl_server_s* S, Slot* sl) {
     auto it = S->tickets.find(sl->tickets[i]);
     if (it != S->tickets.end()) {
       it->second.status = MCL_RESULT_DONE;
+      it->second.est = *ss->h_est;  // the slot's stream has completed
       it->second.latency_ms = 1e3 * (t - it->second.t_submit);
       S->lat.push_back(it->second.latency_ms);
       S->evals += it->second.evals;
@@ -403,7 +414,7 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   ss->off_last = o;
   o = align256(o + (size_t)(nt + 1) * 8);
   const int64_t P = d->P;
-  ss->bytes = (int64_t)o + 2 * P * 24 + d->max_N * 12 + P * 12;
+  ss->bytes = (int64_t)o + 2 * P * 24 + d->max_N * 12 + P * 12 + (int64_t)sizeof(mcl_estimate);
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if ((int)S->sessions.size() >= S->desc.max_sessions) {
@@ -425,6 +436,8 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   if (e == cudaSuccess) e = cudaMalloc(&ss->d_w, (size_t)P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ss->d_idx, (size_t)P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ss->d_ws, o);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ss->d_est, sizeof(mcl_estimate));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ss->h_est, sizeof(mcl_estimate));
   if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stage[0], (size_t)d->max_N * 12);
   if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stage[1], (size_t)d->max_N * 12);
   if (e == cudaSuccess) e = cudaMemcpy(ss->d_part[0], d->particles, (size_t)P * 24, cudaMemcpyHostToDevice);
@@ -494,6 +507,7 @@ mcl_status mcl_wait(mcl_server_t S, mcl_ticket_t t, int32_t timeout_ms, mcl_resu
   out->latency_ms = it->second.latency_ms;
   out->evals = it->second.evals;
   out->step = it->second.step;
+  out->estimate = it->second.est;
   S->tickets.erase(it);
   if (!S->sched_error.empty()) return fail(MCL_ECUDA, "server step failed: %s", S->sched_error.c_str());
   return MCL_OK;

@@ -105,9 +105,7 @@ class mcl_session_desc(ctypes.Structure):
                 ("flags", _u32), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64)]
 
 
-class mcl_result(ctypes.Structure):
-    _fields_ = [("struct_size", _u32), ("status", _i32), ("latency_ms", ctypes.c_double),
-                ("evals", _i64), ("step", _i64)]
+
 
 
 class mcl_server_stats(ctypes.Structure):
@@ -127,6 +125,11 @@ class mcl_estimate(ctypes.Structure):
 
 
 ESTIMATE_BYTES = ctypes.sizeof(mcl_estimate)
+
+
+class mcl_result(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("status", _i32), ("latency_ms", ctypes.c_double),
+                ("evals", _i64), ("step", _i64), ("estimate", mcl_estimate)]
 
 
 class mcl_filter_desc(ctypes.Structure):
@@ -381,7 +384,12 @@ def estimate_buffer(device=None):
 def estimate_to_dict(buf) -> dict:
     """Reads an mcl_estimate from a device (or host) buffer into a dict of
     numpy values (synchronises with the buffer's producer through .cpu())."""
-    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(np.asarray(buf).tobytes())
+    if isinstance(buf, (bytes, bytearray, memoryview)):
+        raw = bytes(buf)
+    elif hasattr(buf, "cpu"):
+        raw = bytes(buf.cpu().numpy().tobytes())
+    else:
+        raw = bytes(np.asarray(buf).tobytes())
     e = mcl_estimate.from_buffer_copy(raw[:ESTIMATE_BYTES])
     return {
         "weight_sum": e.weight_sum, "n_eff": e.n_eff,
@@ -711,7 +719,10 @@ class Server:
     def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
         r = mcl_result(struct_size=ctypes.sizeof(mcl_result))
         _check(lib().mcl_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r)))
-        return {"status": r.status, "latency_ms": r.latency_ms, "evals": r.evals, "step": r.step}
+        out = {"status": r.status, "latency_ms": r.latency_ms, "evals": r.evals, "step": r.step}
+        if r.status == MCL_RESULT_DONE:
+            out["estimate"] = estimate_to_dict(bytes(r.estimate))
+        return out
 
     def stats(self, reset: bool = False) -> dict:
         st = mcl_server_stats(struct_size=ctypes.sizeof(mcl_server_stats))

@@ -64,9 +64,20 @@ def test_same_alone_and_in_the_mix_and_against_the_oracle(env):
     tickets = [o.submit(sc) for o, sc in zip(others, (hall.scan, bld.scan, room.scan[:900]))]
     t2 = s2.submit(room.scan)
     mix.pause(False)
-    for tk in tickets + [t2]:
+    for tk in tickets:
         assert mix.wait(tk, 30_000)["status"] == mcl.MCL_RESULT_DONE
+    res2 = mix.wait(t2, 30_000)
+    assert res2["status"] == mcl.MCL_RESULT_DONE
     parts_mix, w_mix = s2.read()
+    # the step's pose estimate: that of its input particles with its weights
+    import torch
+    ref = mcl.estimate_buffer()
+    mcl.mcl_pose_estimate(torch.from_numpy(room.particles).cuda(), torch.from_numpy(w_mix).cuda(), ref)
+    mcl.mcl_sync()
+    want = mcl.estimate_to_dict(ref)
+    for key in ("mean_pose", "quat", "rpy"):
+        assert np.array_equal(res2["estimate"][key], want[key])
+    assert res2["estimate"]["argmax"] == want["argmax"]
     assert mix.stats()["mean_batch_sessions"] == 4.0  # all four went as one batched step
     assert np.array_equal(parts_alone, parts_mix) and np.array_equal(w_alone, w_mix)
     # against the oracle: weights of the step's input, then systematic resampling
