@@ -9,8 +9,8 @@
 // l of the group takes points l, l + G, l + 2G, ... of the chunk, so
 // neighbouring lanes read neighbouring scan points (neighbouring azimuths of
 // one ring) and their map gathers fall in the same or adjacent sectors. Each
-// lane keeps U look-ups in flight per step (brick-hash entries first, then the
-// values). Per-point terms are summed in FP32 per lane in point order, then
+// lane keeps U look-ups in flight per step (brick-index entries first, then
+// the values). Per-point terms are summed in FP32 per lane in point order, then
 // over the group with a fixed xor-shuffle tree; lane 0 of the group writes the
 // particle's chunk sum to partial[c * P + p]. The summation order depends only
 // on (chunk, G).

@@ -9,8 +9,8 @@
 // l of the group takes points l, l + G, l + 2G, ... of the chunk, so
 // neighbouring lanes read neighbouring scan points (neighbouring azimuths of
 // one ring) and their map gathers fall in the same or adjacent sectors. Each
-// lane keeps U look-ups in flight per step (brick-hash entries first, then the
-// values). Per-point terms are summed in FP32 per lane in point order, then
+// lane keeps U look-ups in flight per step (brick-index entries first, then
+// the values). Per-point terms are summed in FP32 per lane in point order, then
 // over the group with a fixed xor-shuffle tree; lane 0 of the group writes the
 // particle's chunk sum to partial[c * P + p]. The summation order depends only
 // on (chunk, G).
@@ -184,13 +184,14 @@ __device__ __forceinline__ uint32_t brick_local(int ix, int iy, int iz) {
 }
 
 // Stage A of one step of U points per lane: load the points, transform them,
-// find their voxels and issue the first index look-up (brick maps: the hash
-// entry; dense maps: the value itself). FULL: every point index is inside the
-// chunk and the group is valid (no bounds predicates).
+// find their voxels and issue the first index look-up (brick maps: the cell
+// grid's slot or the first hash entry; dense maps: the value itself). FULL:
+// every point index is inside the chunk and the group is valid (no bounds
+// predicates).
 template <int KIND, int DTYPE, int MODE, int U>
 struct Pending {
   uint32_t key[U], loc[U];  // BRICK: brick-cell key, in-brick offset; DENSE: key = linear index
-  uint2 e[U];               // BRICK: first hash entry (EMPTY where not in[u])
+  uint2 e[U];               // BRICK: first hash entry (EMPTY where not in[u]); grid: .y = slot
   typename Raw<DTYPE, MODE>::value dv[U];  // DENSE: value
   bool in[U], v[U];
 };
