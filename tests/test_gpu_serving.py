@@ -161,3 +161,36 @@ def test_admission_supersede_timeout_and_close(env):
     with pytest.raises(mcl.MclError):
         srv.wait(12345678, 0)                            # unknown ticket
     srv.close()
+
+
+def test_score_map_and_trilinear_sessions_match_single_calls(env):
+    """Sessions on a score map (SUM) and with the trilinear read, served in one
+    batch beside a plain session: each session's weights equal the single
+    call's bit for bit."""
+    import torch
+    mcl, room, hall, bld, maps = env
+    sc = mcl.mcl_map_create_score(maps["room"], 0.1)
+    parts = torch.from_numpy(room.particles).cuda()
+    scan = torch.from_numpy(room.scan).cuda()
+    singles = []
+    for m, mode, flags in ((sc, mcl.MCL_SUM, 0), (maps["room"], mcl.MCL_LOGPROD, mcl.MCL_TRILINEAR),
+                           (maps["room"], mcl.MCL_LOGPROD, 0)):
+        w = torch.empty(1000, device="cuda")
+        mcl.mcl_sensor_update(m, parts, scan, mcl.sensor_params(0.1, mode=mode, flags=flags), None, w)
+        singles.append(w.cpu().numpy())
+    srv = mcl.Server(8 << 30, 4)
+    srv.pause(True)
+    sessions = [srv.open(sc, room.particles, 2048, mode=mcl.MCL_SUM, seed=1),
+                srv.open(maps["room"], room.particles, 2048, flags=mcl.MCL_TRILINEAR, seed=2),
+                srv.open(maps["room"], room.particles, 2048, seed=3)]
+    tickets = [s.submit(room.scan) for s in sessions]
+    srv.pause(False)
+    for t in tickets:
+        assert srv.wait(t, 30_000)["status"] == mcl.MCL_RESULT_DONE
+    assert srv.stats()["mean_batch_sessions"] == 3.0
+    for s, ref in zip(sessions, singles):
+        _, w = s.read()
+        assert np.array_equal(w, ref)
+        s.close()
+    srv.close()
+    sc.close()
