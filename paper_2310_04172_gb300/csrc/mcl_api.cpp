@@ -530,6 +530,15 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   if (bps < 1) return fail(MCL_EINVAL, "sensor plan: launch shape does not fit on an SM");
   pl->spatial = p->particle_order == 2 || (p->particle_order == 0 && P >= kSpatialOrderMinParticles);
   pl->K = (int)((N + sh.chunk - 1) / sh.chunk);
+  if (!p->particles_per_item) {
+    // Small sets: shrink the particle block (not below one particle per lane
+    // group of the CTA) until every resident CTA has an item; the block size
+    // changes no result.
+    const int groups = (sh.threads / 32) * (32 / sh.lanes);
+    const long long slots = (long long)st.sms * bps;
+    const long long per = ((long long)P * pl->K + slots - 1) / slots;
+    while (sh.ppi > groups && sh.ppi / 2 >= per) sh.ppi /= 2;
+  }
   pl->nblk = (int)((P + sh.ppi - 1) / sh.ppi);
   pl->n_items = (long long)pl->K * pl->nblk;
   pl->blocks_per_sm = bps;
