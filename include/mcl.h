@@ -245,7 +245,8 @@ mcl_status mcl_normalise(const float* logw, int64_t P, float* w, float* out_stat
  *                 Q = sum w_p q_p q_p^T / W, q_p the quaternion of R(s_p) -
  *                 the rotation R minimising sum w_p ||R - R(s_p)||_F^2 (no
  *                 wrap problem); sign: first non-zero component positive;
- *   rpy           that rotation as (roll, pitch, yaw), R = Rz Ry Rx;
+ *   rpy           that rotation as (roll, pitch, yaw), R = Rz Ry Rx (from the
+ *                 FP64 quaternion, angles evaluated in FP32);
  *   concentration that eigenvalue, in [1/4, 1]: 1 iff all weighted
  *                 rotations coincide;
  *   n_eff         W^2 / sum w_p^2 (0 if W = 0);

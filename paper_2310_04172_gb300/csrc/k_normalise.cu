@@ -335,9 +335,11 @@ __global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __rest
     const double r10 = 2.0 * (q[1] * q[2] + q[0] * q[3]);
     const double r00 = 1.0 - 2.0 * (q[2] * q[2] + q[3] * q[3]);
     for (int i = 0; i < 4; ++i) out->quat[i] = q[i];
-    out->rpy[0] = atan2(r21, r22);
-    out->rpy[1] = asin(fmin(1.0, fmax(-1.0, -r20)));
-    out->rpy[2] = atan2(r10, r00);
+    // angles in FP32 (about 1e-7 rad): FP64 transcendentals on one thread
+    // would dominate the whole estimate on this part
+    out->rpy[0] = (double)atan2f((float)r21, (float)r22);
+    out->rpy[1] = (double)asinf(fminf(1.f, fmaxf(-1.f, (float)-r20)));
+    out->rpy[2] = (double)atan2f((float)r10, (float)r00);
     out->concentration = lam;
   } else {
     for (int i = 0; i < 4; ++i) out->quat[i] = nan;

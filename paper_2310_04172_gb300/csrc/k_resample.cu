@@ -7,7 +7,7 @@
 // same bit for bit whatever the summation order: tiles of 4096 scan locally,
 // one block scans the tile totals, and each output j finds
 // min{p : C_p > t_j}, t_j = ((j + r) / P) S, by a binary search over tile ends
-// and then inside the tile.
+// and then inside the tile. Sets of at most one tile take one fused launch.
 #include <mutex>
 
 #include "mcl_internal.h"
@@ -165,9 +165,67 @@ __global__ void k_systematic(const double* __restrict__ cum, const double* __res
   }
 }
 
+// Sets of at most one tile in one block: the same quantised weights, the
+// same exact prefix (kept in shared memory), the same targets and search, so
+// the same indices as the three-launch path, in one launch.
+__global__ void __launch_bounds__(kRT) k_systematic_small(const float* __restrict__ w, int P,
+                                                          double r, const double* __restrict__ r_dev,
+                                                          int32_t* __restrict__ idx,
+                                                          const float* __restrict__ pin,
+                                                          float* __restrict__ pout) {
+  __shared__ double cs[kTile];
+  __shared__ double sh[32];
+  __shared__ long long shl[32];
+  const int base = threadIdx.x * kRI;
+  double run = 0.0, q[kRI];
+  long long last = -1;
+#pragma unroll
+  for (int i = 0; i < kRI; ++i) {
+    const int p = base + i;
+    double v = 0.0;
+    if (p < P) {
+      v = __dmul_rn(rint(__dmul_rn((double)w[p], 0x1.0p52)), 0x1.0p-52);
+      if (v > 0.0) last = p;
+    }
+    run = __dadd_rn(run, v);
+    q[i] = run;
+  }
+  double S;
+  const double incl = block_incl_scan(run, sh, &S);
+  const double excl = __dsub_rn(incl, run);
+#pragma unroll
+  for (int i = 0; i < kRI; ++i)
+    if (base + i < P) cs[base + i] = __dadd_rn(excl, q[i]);
+  last = block_max_ll(last, shl);
+  __syncthreads();
+  if (r_dev) r = *r_dev;
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    int res;
+    if (!(S > 0.0)) {
+      res = j;  // all weights zero: identity
+    } else {
+      const double t = __dmul_rn(__ddiv_rn(__dadd_rn((double)j, r), (double)P), S);
+      int a = 0, b = P;
+      while (a < b) {
+        const int mid = (a + b) >> 1;
+        if (cs[mid] > t) b = mid; else a = mid + 1;
+      }
+      res = a < P ? a : (int)last;
+    }
+    idx[j] = res;
+    if (pin) {
+      const float* src = pin + 6 * (size_t)res;
+      float* dst = pout + 6 * (size_t)j;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dst[k] = src[k];
+    }
+  }
+}
+
 }  // namespace
 
 int resample_tiles(int P) { return (P + kTile - 1) / kTile; }
+int resample_kernels(int P) { return P <= kTile ? 1 : 3; }
 
 // ---------------------------------------------------------------- static scratch
 // Scratch for the allocation-free entry point (mcl_resample_noalloc), for
@@ -218,6 +276,10 @@ cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             const float* particles_in, float* particles_out, double* cum,
                             double* tile_total, long long* tile_last, cudaStream_t s,
                             const double* r_dev) {
+  if (P <= kTile) {
+    k_systematic_small<<<1, kRT, 0, s>>>(w, P, r, r_dev, idx, particles_in, particles_out);
+    return cudaGetLastError();
+  }
   const int ntiles = resample_tiles(P);
   k_tile_scan<<<ntiles, kRT, 0, s>>>(w, P, cum, tile_total, tile_last);
   cudaError_t e = cudaGetLastError();

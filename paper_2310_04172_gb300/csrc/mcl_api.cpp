@@ -760,7 +760,7 @@ mcl_status mcl_resample(const float* w, int64_t P, double r, int32_t* idx, const
                total = align256(o_last + (size_t)(nt + 1) * 8);
   char* ws = nullptr;
   if (mcl_status rc = workspace(s, total, (void**)&ws)) return rc;
-  PhaseScope ps(MCL_PHASE_RESAMPLE, s, 3);
+  PhaseScope ps(MCL_PHASE_RESAMPLE, s, resample_kernels((int)P));
   MCL_CUDA(launch_resample(w, (int)P, r, idx, pin, pout, (double*)(ws + o_cum), (double*)(ws + o_tot),
                            (long long*)(ws + o_last), s));
   return MCL_OK;

@@ -253,7 +253,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
   int kern = (int)b->g.size();
   for (auto& sp : b->s)
     kern += (sp.pl.spatial ? 4 : 0) + 2 + 1 + (sp.u.w ? 1 : 0) + (sp.u.estimate ? 1 : 0) +
-            (sp.u.resample_idx ? 3 : 0);
+            (sp.u.resample_idx ? resample_kernels((int)sp.u.P) : 0);
   b->kernels_per_run = kern;
   *out = b;
   return MCL_OK;

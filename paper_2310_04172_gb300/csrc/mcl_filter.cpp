@@ -82,7 +82,7 @@ mcl_status enqueue_step(mcl_filter_s* f, int64_t N, cudaStream_t s) {
                                      f->est, pl, f->ws, f->status, s))
     return rc;
   {
-    PhaseScope ps(MCL_PHASE_RESAMPLE, s, 4);
+    PhaseScope ps(MCL_PHASE_RESAMPLE, s, resample_kernels(P));
     MCL_CUDA(launch_resample(f->w, P, 0.0, f->idx, f->part, f->part2, f->cum, f->tot, f->last, s,
                              &f->d_in->r));
     MCL_CUDA(cudaMemcpyAsync(f->part, f->part2, (size_t)P * 6 * sizeof(float),

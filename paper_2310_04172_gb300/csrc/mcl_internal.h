@@ -247,6 +247,7 @@ cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float
 
 // Resampling scratch: C (P doubles), per-tile totals and last positive index.
 int resample_tiles(int P);
+int resample_kernels(int P);  // launches of one resampling call
 // r_dev (device, optional) overrides r: the offset is read when the kernel runs.
 cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             const float* particles_in, float* particles_out, double* cum,
