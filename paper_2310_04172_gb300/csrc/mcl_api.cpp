@@ -134,7 +134,7 @@ extern "C" {
 
 const char* mcl_last_error(void) { return g_err.c_str(); }
 
-int32_t mcl_version(void) { return 100; }
+int32_t mcl_version(void) { return 200; }
 
 mcl_status mcl_sync(mcl_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_binding_covers_every_symbol_and_loads(lib_path):
     from paper_2310_04172_gb300 import mcl
     assert set(declared_functions()) == set(mcl.SIGNATURES)
-    assert mcl.lib() is not None and mcl.mcl_version() == 100
+    assert mcl.lib() is not None and mcl.mcl_version() == 200
 
 
 def test_struct_layouts_match_c(tmp_path):
