@@ -36,8 +36,10 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 
 // Rotation Rz(yaw) Ry(pitch) Rx(roll) in FP64 (row-major 3 x 3).
 __device__ __forceinline__ void rpy(double roll, double pitch, double yaw, double R[9]) {
-  const double cr = cos(roll), sr = sin(roll), cp = cos(pitch), sp = sin(pitch);
-  const double cy = cos(yaw), sy = sin(yaw);
+  double cr, sr, cp, sp, cy, sy;  // one shared range reduction per angle
+  sincos(roll, &sr, &cr);
+  sincos(pitch, &sp, &cp);
+  sincos(yaw, &sy, &cy);
   const double a = __dmul_rn(cy, sp), b = __dmul_rn(sy, sp);
   R[0] = __dmul_rn(cy, cp);
   R[1] = __dsub_rn(__dmul_rn(a, sr), __dmul_rn(sy, cr));
@@ -70,8 +72,10 @@ __global__ void k_motion(float* __restrict__ poses, int P, MotionArgs a, uint64_
     const double u1 = __dmul_rn(__dadd_rn((double)hi, 0.5), 0x1.0p-53);
     const double u2 = __dmul_rn((double)lo, 0x1.0p-53);
     const double rho = sqrt(__dmul_rn(-2.0, log(u1)));
-    n[2 * b] = __dmul_rn(rho, cos(__dmul_rn(6.283185307179586, u2)));
-    n[2 * b + 1] = __dmul_rn(rho, sin(__dmul_rn(6.283185307179586, u2)));
+    double sn, cs;
+    sincos(__dmul_rn(6.283185307179586, u2), &sn, &cs);
+    n[2 * b] = __dmul_rn(rho, cs);
+    n[2 * b + 1] = __dmul_rn(rho, sn);
   }
   double u[6];
 #pragma unroll

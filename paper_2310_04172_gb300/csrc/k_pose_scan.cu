@@ -21,9 +21,10 @@ __global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4*
   const float* s = poses + 6 * (size_t)p;
   const float x = s[0], y = s[1], z = s[2];
   const double roll = (double)s[3], pitch = (double)s[4], yaw = (double)s[5];
-  const double cr = cos(roll), sr = sin(roll);
-  const double cp = cos(pitch), sp = sin(pitch);
-  const double cy = cos(yaw), sy = sin(yaw);
+  double cr, sr, cp, sp, cy, sy;  // one shared range reduction per angle
+  sincos(roll, &sr, &cr);
+  sincos(pitch, &sp, &cp);
+  sincos(yaw, &sy, &cy);
   const double a = __dmul_rn(cy, sp), b = __dmul_rn(sy, sp);
   const double r00 = __dmul_rn(cy, cp);
   const double r01 = __dsub_rn(__dmul_rn(a, sr), __dmul_rn(sy, cr));
