@@ -141,7 +141,7 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self) -> dict:
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         for l in self.lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 8:
@@ -151,13 +151,28 @@ class ClockSampler:
                 smax.append(float(f[1]))
             except ValueError:
                 continue
+            try:
+                power.append(float(f[2]))
+            except ValueError:
+                pass
             for name, val in zip(self.NAMES, f[4:8]):
                 if val.lower() == "active":
                     reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": statistics.median(power) if power else None}
+
+
+def energy(clocks: dict, ms_per_step: float, evals_per_step: float):
+    """GPU board power during the timed region (median of the samples) and
+    what it makes per step: the counterpart of the paper's run time and
+    power figures (Table I)."""
+    pw = clocks.get("power_w")
+    if not pw:
+        return None
+    j = pw * ms_per_step / 1e3
+    return {"power_w": pw, "joules_per_step": j, "evals_per_joule": evals_per_step / j}
 
 
 # ------------------------------------------------------------------ workload
@@ -433,6 +448,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roof, "gather_roofline": gather, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(), "serving": serving,
+            "energy": energy(clocks.summary(), ms_max / args.steps, float(P) * N),
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["launches"]},
         }
         print(json.dumps(line), flush=True)

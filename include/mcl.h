@@ -484,6 +484,8 @@ typedef struct mcl_filter_desc {
   uint64_t seed;              /* motion-noise key and resampling offsets */
   int32_t use_graph;          /* 1: replay each scan size's step from a CUDA graph */
   int32_t max_graphs;         /* graphs kept, least recently used evicted; 0 = 8 */
+  int64_t first_step;         /* step counter to start from: 0, or the steps of a
+                                 checkpoint (mcl_filter_state) to resume it */
 } mcl_filter_desc;
 
 typedef struct mcl_filter_s* mcl_filter_t;
@@ -573,9 +575,26 @@ typedef struct mcl_session_desc {
   uint32_t flags;
   float motion_sigma[6];    /* noise of the motion update */
   uint64_t seed;            /* motion noise and resampling offsets */
+  int64_t first_step;       /* step counter to start from: 0, or the step of a checkpoint
+                               (particles from mcl_session_read, step from
+                               mcl_session_get_info) to resume the same sequence */
 } mcl_session_desc;
 
 mcl_status mcl_session_open(mcl_server_t s, const mcl_session_desc* desc, mcl_session_t* out);
+
+typedef struct mcl_session_info {
+  uint32_t struct_size;
+  int64_t P, max_N;
+  int64_t step;             /* steps completed (the next step's noise counter) */
+  uint64_t seed;
+  int64_t device_bytes;     /* counted against the server's budget */
+} mcl_session_info;
+
+/* The session's counters after its queued and running steps finished
+ * (waits up to timeout_ms; < 0: forever). With mcl_session_read this is a
+ * checkpoint: a session opened with those particles, the same parameters and
+ * first_step = step continues bit for bit. */
+mcl_status mcl_session_get_info(mcl_session_t ss, mcl_session_info* out, int32_t timeout_ms);
 
 /* Queues one scan (host, N x 3, copied before return) with an optional
  * odometry increment (host, 6 values, NULL = none). */
@@ -647,7 +666,9 @@ mcl_status mcl_workspace_release(mcl_stream_t stream);
  * every phase this library enqueues is bracketed by CUDA events recorded on
  * its own stream; mcl_profile_end() waits for them and returns, per phase,
  * the number of kernel launches and the summed elapsed milliseconds. Not for
- * use while a stream is being captured into a graph. */
+ * use while a stream is being captured into a graph. Every phase is also an
+ * NVTX range named "mcl.<phase>" (pose, pack, sensor, reduce, normalise,
+ * resample, motion, other) whether profiling is on or not. */
 enum {
   MCL_PHASE_POSE = 0,     /* pose -> [R | t] */
   MCL_PHASE_PACK = 1,     /* scan packing */

@@ -274,6 +274,12 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
         else if (s.e[u].x != kEmptyKey)
           slot = probe_rest(m, s.key[u], brick_hash(s.key[u], m.hash_shift));
       }
+#if MCL_DEBUG_BOUNDS
+      if (slot != kNoSlot && slot >= m.n_slots) {
+        atomicOr(a.status, kDevErrIndex);
+        slot = kNoSlot;
+      }
+#endif
       const bool st = slot != kNoSlot;
       dv[u] = st ? load_raw<DTYPE, MODE>(m.values, (size_t)slot * kBrickVoxels + s.loc[u])
                  : outside_value<DTYPE, MODE>(a);
@@ -418,6 +424,12 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+#if MCL_DEBUG_BOUNDS
+      if (slot[c] != kNoSlot && slot[c] >= m.n_slots) {
+        atomicOr(a.status, kDevErrIndex);
+        slot[c] = kNoSlot;
+      }
+#endif
       const bool st = slot[c] != kNoSlot;
       v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, (size_t)slot[c] * kBrickVoxels +
                                                      brick_local<KIND>(x0 + cx, y0 + cy, z0 + cz))

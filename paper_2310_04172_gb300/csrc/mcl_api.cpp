@@ -13,6 +13,7 @@
 #include <vector>
 
 #include <cuda_fp16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "runtime.h"
 
@@ -110,7 +111,13 @@ thread_local bool t_no_profile = false;
 NoProfileScope::NoProfileScope() : prev_(t_no_profile) { t_no_profile = true; }
 NoProfileScope::~NoProfileScope() { t_no_profile = prev_; }
 
+// NVTX range names of the phases (seen by nsys / ncu range filters; the
+// calls cost nothing when no tool is attached).
+const char* const kPhaseRange[] = {"mcl.pose",      "mcl.pack",     "mcl.sensor", "mcl.reduce",
+                                   "mcl.normalise", "mcl.resample", "mcl.motion", "mcl.other"};
+
 PhaseScope::PhaseScope(int ph, cudaStream_t st, int nk) : phase_(ph), kernels_(nk), s_(st) {
+  nvtxRangePushA(kPhaseRange[ph >= 0 && ph < MCL_NUM_PHASES ? ph : MCL_PHASE_OTHER]);
   if (t_no_profile) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_prof_on) return;
@@ -120,6 +127,7 @@ PhaseScope::PhaseScope(int ph, cudaStream_t st, int nk) : phase_(ph), kernels_(n
 }
 
 PhaseScope::~PhaseScope() {
+  nvtxRangePop();
   if (!a_) return;
   cudaEventRecord(b_, s_);
   std::lock_guard<std::mutex> lk(g_mu);
@@ -307,6 +315,7 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
                        cells * sizeof(uint32_t) <= (512ull << 20));
     v.nbx = (uint32_t)nbx;
     v.nby = (uint32_t)nby;
+    v.n_slots = (uint32_t)nb;
     m->n_bricks = nb;
     if (grid) {
       // coarse level as a dense array: brick cell -> slot (the duplicates and

@@ -150,6 +150,7 @@ mcl_status mcl_filter_create(const mcl_filter_desc* d, const float* particles, m
   if (d->max_points < 1 || d->max_points > kMaxCount)
     return fail(MCL_EINVAL, "filter_create: max_points = %lld", (long long)d->max_points);
   if (d->max_graphs < 0) return fail(MCL_EINVAL, "filter_create: max_graphs < 0");
+  if (d->first_step < 0) return fail(MCL_EINVAL, "filter_create: first_step < 0");
   for (int k = 0; k < 6; ++k)
     if (!(d->motion_sigma[k] >= 0.f && d->motion_sigma[k] < 3.4e38f))
       return fail(MCL_EINVAL, "filter_create: motion_sigma[%d]", k);
@@ -172,6 +173,7 @@ mcl_status mcl_filter_create(const mcl_filter_desc* d, const float* particles, m
   f->seed = d->seed;
   f->use_graph = d->use_graph != 0;
   f->max_graphs = d->max_graphs > 0 ? d->max_graphs : 8;
+  f->steps = d->first_step;
   f->status = st.status;
   const size_t P = (size_t)d->P, N = (size_t)d->max_points;
   const size_t nt = (size_t)resample_tiles((int)d->P);

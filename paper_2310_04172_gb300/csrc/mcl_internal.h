@@ -22,11 +22,19 @@ constexpr int kKindBrickGrid = 3;    // internal kind: brick map (linear layout)
 // Bits of the per-device status word that kernels set instead of faulting.
 enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
 
+// Debug builds (-DMCL_DEBUG_BOUNDS=1) check every brick slot a kernel is about
+// to read against the number of stored bricks; a bad one sets kDevErrIndex in
+// the status word (mcl_sync reports MCL_EINTERNAL) and reads nothing.
+#ifndef MCL_DEBUG_BOUNDS
+#define MCL_DEBUG_BOUNDS 0
+#endif
+
 // Device view of a TSDF map (Sec. III). Passed by value to the kernels.
 struct MapView {
   const void* values;   // dense grid or brick-major values
   const uint2* table;   // BRICK, hash index: open-addressing hash (key, slot), capacity 2^bits
   const uint32_t* grid; // BRICK, grid index: slot of each brick cell (kNoSlot if none)
+  uint32_t n_slots;     // BRICK: bricks stored (slots are below this)
   float ox, oy, oz;     // grid corner
   float inv;            // 1 / voxel as used by the index rule
   float fnx, fny, fnz;  // dims as FP32 for the inside test

@@ -381,6 +381,7 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   *out = nullptr;
   if (!d->map || !d->particles || d->P < 1 || d->P > kMaxCount || d->max_N < 1 || d->max_N > kMaxCount)
     return fail(MCL_EINVAL, "session_open: map, particles, P or max_N");
+  if (d->first_step < 0) return fail(MCL_EINVAL, "session_open: first_step < 0");
   for (int k = 0; k < 6; ++k)
     if (!(d->motion_sigma[k] >= 0.f && d->motion_sigma[k] < 1e30f)) return fail(MCL_EINVAL, "session_open: motion_sigma");
   mcl_sensor_params prm{sizeof(mcl_sensor_params), d->sigma_hit, d->mode, d->flags,
@@ -401,6 +402,7 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   ss->flags = d->flags;
   std::copy(d->motion_sigma, d->motion_sigma + 6, ss->msig);
   ss->seed = d->seed;
+  ss->step = d->first_step;
   if (mcl_status rc = make_plan(d->map, d->P, d->max_N, &prm, &ss->pl)) {
     delete ss;
     return rc;
@@ -510,6 +512,23 @@ mcl_status mcl_wait(mcl_server_t S, mcl_ticket_t t, int32_t timeout_ms, mcl_resu
   out->estimate = it->second.est;
   S->tickets.erase(it);
   if (!S->sched_error.empty()) return fail(MCL_ECUDA, "server step failed: %s", S->sched_error.c_str());
+  return MCL_OK;
+}
+
+mcl_status mcl_session_get_info(mcl_session_t ss, mcl_session_info* out, int32_t timeout_ms) {
+  if (!ss || !out || out->struct_size < sizeof(mcl_session_info))
+    return fail(MCL_EINVAL, "session_get_info: bad argument");
+  mcl_server_s* S = ss->srv;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto idle = [&] { return !ss->pending && !ss->in_flight; };
+  if (timeout_ms < 0) S->cv_done.wait(lk, idle);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle))
+    return fail(MCL_ETIMEDOUT, "session_get_info: session busy after %d ms", timeout_ms);
+  out->P = ss->P;
+  out->max_N = ss->max_N;
+  out->step = ss->step;
+  out->seed = ss->seed;
+  out->device_bytes = ss->bytes;
   return MCL_OK;
 }
 

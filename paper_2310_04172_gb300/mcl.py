@@ -102,7 +102,13 @@ class mcl_server_desc(ctypes.Structure):
 class mcl_session_desc(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("P", _i64), ("max_N", _i64),
                 ("particles", _c_void_p), ("sigma_hit", ctypes.c_float), ("mode", _i32),
-                ("flags", _u32), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64)]
+                ("flags", _u32), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64),
+                ("first_step", _i64)]
+
+
+class mcl_session_info(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("P", _i64), ("max_N", _i64), ("step", _i64), ("seed", _u64),
+                ("device_bytes", _i64)]
 
 
 
@@ -135,7 +141,7 @@ class mcl_result(ctypes.Structure):
 class mcl_filter_desc(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("P", _i64), ("max_points", _i64),
                 ("sensor", mcl_sensor_params), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64),
-                ("use_graph", _i32), ("max_graphs", _i32)]
+                ("use_graph", _i32), ("max_graphs", _i32), ("first_step", _i64)]
 
 
 class mcl_filter_state(ctypes.Structure):
@@ -198,6 +204,7 @@ SIGNATURES = {
     "mcl_submit_scan": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p, ctypes.POINTER(_u64)]),
     "mcl_wait": (_i32, [_c_void_p, _u64, _i32, ctypes.POINTER(mcl_result)]),
     "mcl_session_read": (_i32, [_c_void_p, _c_void_p, _c_void_p, _i32]),
+    "mcl_session_get_info": (_i32, [_c_void_p, ctypes.POINTER(mcl_session_info), _i32]),
     "mcl_session_close": (_i32, [_c_void_p]),
     "mcl_server_get_stats": (_i32, [_c_void_p, _i32, ctypes.POINTER(mcl_server_stats)]),
     "mcl_server_pause": (_i32, [_c_void_p, _i32]),
@@ -602,12 +609,13 @@ class Filter:
 
     def __init__(self, m: Map, particles, max_points: int, params: mcl_sensor_params = None,
                  motion_sigma=(0.0,) * 6, seed: int = 0, use_graph: bool = True,
-                 max_graphs: int = 0):
+                 max_graphs: int = 0, first_step: int = 0):
         import torch
         d = mcl_filter_desc(struct_size=ctypes.sizeof(mcl_filter_desc), map=m.handle,
                             P=particles.shape[0], max_points=int(max_points),
                             sensor=params if params is not None else sensor_params(),
-                            seed=int(seed), use_graph=int(bool(use_graph)), max_graphs=max_graphs)
+                            seed=int(seed), use_graph=int(bool(use_graph)), max_graphs=max_graphs,
+                            first_step=int(first_step))
         for k in range(6):
             d.motion_sigma[k] = float(motion_sigma[k])
         h = ctypes.c_void_p()
@@ -706,11 +714,13 @@ class Server:
         self.handle = h
 
     def open(self, m: Map, particles: np.ndarray, max_N: int, sigma_hit: float = 0.1,
-             mode: int = MCL_LOGPROD, flags: int = 0, motion_sigma=(0,) * 6, seed: int = 0):
+             mode: int = MCL_LOGPROD, flags: int = 0, motion_sigma=(0,) * 6, seed: int = 0,
+             first_step: int = 0):
         parts = np.ascontiguousarray(particles, np.float32).reshape(-1, 6)
         d = mcl_session_desc(struct_size=ctypes.sizeof(mcl_session_desc), map=m.handle, P=len(parts),
                              max_N=int(max_N), particles=parts.ctypes.data_as(ctypes.c_void_p),
-                             sigma_hit=sigma_hit, mode=mode, flags=flags, seed=int(seed))
+                             sigma_hit=sigma_hit, mode=mode, flags=flags, seed=int(seed),
+                             first_step=int(first_step))
         d.motion_sigma[:] = [float(x) for x in motion_sigma]
         h = ctypes.c_void_p()
         _check(lib().mcl_session_open(self.handle, ctypes.byref(d), ctypes.byref(h)))
@@ -757,6 +767,11 @@ class Session:
                                      ctypes.byref(t)))
         return t.value
 
+    def info(self, timeout_ms: int = -1) -> dict:
+        st = mcl_session_info(struct_size=ctypes.sizeof(mcl_session_info))
+        _check(lib().mcl_session_get_info(self.handle, ctypes.byref(st), int(timeout_ms)))
+        return {k: getattr(st, k) for k, _ in mcl_session_info._fields_ if k != "struct_size"}
+
     def read(self, timeout_ms: int = -1):
         parts = np.empty((self.P, 6), np.float32)
         w = np.empty(self.P, np.float32)
@@ -788,6 +803,10 @@ def mcl_wait(server: Server, ticket: int, timeout_ms: int = -1) -> dict:
 
 def mcl_session_read(session: Session, timeout_ms: int = -1):
     return session.read(timeout_ms)
+
+
+def mcl_session_get_info(session: Session, timeout_ms: int = -1) -> dict:
+    return session.info(timeout_ms)
 
 
 def mcl_session_close(session: Session):

@@ -89,3 +89,19 @@ def test_product_path_does_not_reach_the_oracle():
             text = open(f).read()
             assert "import oracle" not in text and "from oracle" not in text, f
             assert "_oracle.so" not in text and "oracle.c" not in text, f
+
+
+def test_debug_bounds_build_compiles(tmp_path):
+    """The debug variant (slot bounds checks that set the status word instead
+    of reading) builds for sm_103a."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", "k_sensor_i16_grid.cu")
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                        "-DMCL_DEBUG_BOUNDS=1", "-I", os.path.join(ROOT, "include"),
+                        "-I", os.path.dirname(src), "-c", src, "-o", str(tmp_path / "k.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

@@ -140,3 +140,44 @@ def test_filter_graph_cache_and_errors(env):
         mcl.Filter(m, torch.from_numpy(parts0).cuda(), max_points=10, motion_sigma=[-1, 0, 0, 0, 0, 0])
     assert f.state()["steps"] == 5                           # failed calls enqueue nothing
     f.close()
+
+
+def test_filter_and_session_resume_from_a_checkpoint(env):
+    """Particles and step counter of step k are a checkpoint: a filter (or a
+    serving session) created from them with first_step = k continues the same
+    sequence bit for bit."""
+    torch, mcl, (wl, poses, deltas, scans, parts0), m = env
+    prm = mcl.sensor_params(sigma_hit=wl.sigma_hit)
+    kw = dict(max_points=1024, params=prm, motion_sigma=MOTION_SIGMA, seed=SEED)
+    a = mcl.Filter(m, torch.from_numpy(parts0).cuda(), **kw)
+    for k in range(3):
+        a.step(torch.from_numpy(scans[k]).cuda(), deltas[k])
+    mcl.mcl_sync()
+    ckpt = a.tensors()["particles"].clone()
+    steps = a.state()["steps"]
+    b = mcl.Filter(m, ckpt, first_step=steps, **kw)
+    for k in range(3, 6):
+        a.step(torch.from_numpy(scans[k]).cuda(), deltas[k])
+        b.step(torch.from_numpy(scans[k]).cuda(), deltas[k])
+    mcl.mcl_sync()
+    assert torch.equal(a.tensors()["particles"], b.tensors()["particles"])
+    a.close()
+    b.close()
+    srv = mcl.Server(hbm_budget_bytes=1 << 30, max_sessions=2)
+    s1 = srv.open(m, parts0, max_N=1024, sigma_hit=wl.sigma_hit, motion_sigma=MOTION_SIGMA, seed=SEED)
+    for k in range(2):
+        assert srv.wait(s1.submit(scans[k], deltas[k]), 60_000)["status"] == 0
+    cp, _ = s1.read(60_000)
+    info = s1.info(60_000)
+    assert info["step"] == 2 and info["seed"] == SEED
+    s2 = srv.open(m, cp, max_N=1024, sigma_hit=wl.sigma_hit, motion_sigma=MOTION_SIGMA, seed=SEED,
+                  first_step=info["step"])
+    for k in range(2, 4):
+        for s in (s1, s2):
+            assert srv.wait(s.submit(scans[k], deltas[k]), 60_000)["status"] == 0
+    p1, w1 = s1.read(60_000)
+    p2, w2 = s2.read(60_000)
+    assert np.array_equal(p1, p2) and np.array_equal(w1, w2)
+    s1.close()
+    s2.close()
+    srv.close()
