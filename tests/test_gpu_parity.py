@@ -433,3 +433,29 @@ def test_profile_counts_phases(torch_cuda, mcl, room):
     assert prof["sensor"]["launches"] == 1 and prof["sensor"]["ms"] > 0
     assert prof["pose"]["launches"] == 1 and prof["normalise"]["launches"] == 1
     m.close()
+
+
+@pytest.mark.parametrize("index", [1, 2])
+def test_empty_brick_map_and_non_finite_scan_points(torch_cuda, mcl, room, index):
+    """A brick map with no brick reads +tau everywhere (both indexes); scan
+    points that are NaN or infinite fall outside the grid."""
+    torch = torch_cuda
+    empty = scenes.BrickMap((0.0, 0.0, 0.0), 0.05, (128, 128, 64), 0.3, scenes.I16,
+                            np.zeros((0, 3), np.int32), np.zeros((0, 16, 16, 16), np.int16))
+    m = mcl.map_from_scene(empty, 0, index)
+    assert m.info()["n_bricks"] == 0
+    scan = room.scan.copy()
+    scan[::97] = np.float32([np.nan, 0.0, 1.0])
+    scan[5::101] = np.float32([np.inf, -np.inf, 0.0])
+    for flags in (0, mcl.MCL_TRILINEAR):
+        Lg, wg = run_sensor(torch, mcl, m, room.particles, scan, 0.1, 0, flags)
+        Lo = oracle.sensor_update(oracle.Map.from_scene_map(empty), room.particles, scan, 0.1,
+                                  trilinear=bool(flags))
+        check_logw(Lg, Lo)
+        assert np.allclose(wg, 1.0 / len(wg), rtol=1e-6)     # every particle scores the same
+    m.close()
+    # the room with the same bad points
+    m = mcl.map_from_scene(room.map)
+    Lg, _ = run_sensor(torch, mcl, m, room.particles, scan, 0.1)
+    check_logw(Lg, oracle.sensor_update(oracle.Map.from_scene_map(room.map), room.particles, scan, 0.1))
+    m.close()
