@@ -591,6 +591,23 @@ __device__ __forceinline__ void init_barrier(uint32_t bar_s) {
   __syncthreads();
 }
 
+// Item -> (chunk c, particle block blk). Items are numbered sweep by sweep:
+// a sweep is `sweep` consecutive particle blocks (fewer in the last) times
+// all K chunks, chunk-major within the sweep. sweep = nblk numbers all items
+// chunk-major; a small sweep keeps the particles that resident CTAs work on
+// at the same time few and (in spatial order) close together. Every item
+// writes only its own partial sums, so the order changes no result.
+__device__ __forceinline__ void item_coords(long long item, int nblk, int K, int sweep, int& c,
+                                            int& blk) {
+  const long long per = (long long)sweep * K;
+  const long long s = item / per;
+  const int b0 = (int)s * sweep;
+  const int bs = min(sweep, nblk - b0);
+  const long long r = item - s * per;
+  c = (int)(r / bs);
+  blk = b0 + (int)(r % bs);
+}
+
 // One session: items (chunk c, particle block) strided over a persistent grid.
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_sensor(const SensorArgs a) {
@@ -602,8 +619,9 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
   int loaded = -1;
   uint32_t parity = 0;
   for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    const int c = (int)(item / a.nblk);
-    const int p0 = (int)(item % a.nblk) * a.ppi;
+    int c, blk;
+    item_coords(item, a.nblk, a.K, a.sweep, c, blk);
+    const int p0 = blk * a.ppi;
     const int pn = min(a.ppi, a.P - p0);
     const int cnt = min(a.chunk, a.N - c * a.chunk);
     if (c != loaded) {  // uniform over the CTA: every thread walks the same items
@@ -637,8 +655,9 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
     }
     const BatchSession S = b.sessions[lo];
     const long long local = item - __ldg(b.item_begin + lo);
-    const int c = (int)(local / S.nblk);
-    const int p0 = (int)(local % S.nblk) * a.ppi;
+    int c, blk;
+    item_coords(local, S.nblk, S.K, S.sweep, c, blk);
+    const int p0 = blk * a.ppi;
     const int pn = min(a.ppi, S.P - p0);
     const int cnt = min(a.chunk, S.N - c * a.chunk);
     const long long key = ((long long)lo << 32) | (unsigned)c;

@@ -163,7 +163,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     sp.u = u;
     sp.prm = mcl_sensor_params{sizeof(mcl_sensor_params), u.sigma_hit, u.mode, u.flags,
                                bp->points_per_chunk, bp->lanes_per_particle, bp->particles_per_item,
-                               bp->unroll, bp->pipeline, bp->particle_order};
+                               bp->unroll, bp->pipeline, bp->particle_order, bp->item_order};
     if (mcl_status rc = check_params(&sp.prm)) return bail(rc);
     if (mcl_status rc = make_plan(u.map, u.P, u.N, &sp.prm, &sp.pl)) return bail(rc);
     const int nt = resample_tiles((int)u.P);
@@ -223,7 +223,8 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       const SessionPlan& sp = b->s[i];
       char* ws = b->ws + sp.base;
       tab.push_back(BatchSession{(const float4*)(ws + sp.pl.off_mats), (const float4*)(ws + sp.pl.off_scan),
-                                 (float*)(ws + sp.pl.off_partial), (int)sp.u.P, (int)sp.u.N, sp.pl.nblk});
+                                 (float*)(ws + sp.pl.off_partial), (int)sp.u.P, (int)sp.u.N, sp.pl.nblk,
+                                 sp.pl.K, sp.pl.sweep});
       beg.push_back(beg.back() + sp.pl.n_items);
     }
     e = cudaMemcpy(b->ws + off_tab[k], tab.data(), tab.size() * sizeof(BatchSession), cudaMemcpyHostToDevice);

@@ -168,6 +168,7 @@ struct SensorArgs {
   float* partial;      // K x P chunk partial sums (chunk-major)
   unsigned* status;
   int P, N, chunk, K, ppi, nblk;
+  int sweep;           // particle blocks per sweep (nblk: chunk-major order)
   long long n_items;
   int mode, neglect;
   float vout;          // value read where nothing is stored, in storage units (tau, or 32767 for I16)
@@ -181,7 +182,7 @@ struct BatchSession {
   const float4* mats;  // P x 3 rows
   const float4* scan;  // N packed points
   float* partial;      // K x P chunk sums
-  int P, N, nblk;
+  int P, N, nblk, K, sweep;
 };
 
 struct BatchArgs {

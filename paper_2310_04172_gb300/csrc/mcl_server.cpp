@@ -198,7 +198,8 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       const int K = (int)((N + sh.chunk - 1) / sh.chunk);
       tab[q] = BatchSession{(const float4*)(ss->d_ws + ss->pl.off_mats),
                             (const float4*)(ss->d_ws + ss->pl.off_scan),
-                            (float*)(ss->d_ws + ss->pl.off_partial), (int)ss->P, (int)N, ss->pl.nblk};
+                            (float*)(ss->d_ws + ss->pl.off_partial), (int)ss->P, (int)N, ss->pl.nblk,
+                            K, ss->pl.sweep};
       beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
     }
     int bps = 0;
@@ -387,7 +388,7 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   mcl_sensor_params prm{sizeof(mcl_sensor_params), d->sigma_hit, d->mode, d->flags,
                         S->desc.shape.points_per_chunk, S->desc.shape.lanes_per_particle,
                         S->desc.shape.particles_per_item, S->desc.shape.unroll, S->desc.shape.pipeline,
-                        S->desc.shape.particle_order};
+                        S->desc.shape.particle_order, S->desc.shape.item_order};
   if (mcl_status rc = check_params(&prm)) return rc;
   int dev = 0;
   MCL_CUDA(cudaGetDevice(&dev));

@@ -3,7 +3,7 @@
 // Times candidate shapes with CUDA events on the caller's particles and scan
 // (a leading subset of the particles), by coordinate descent over the knobs:
 // particles per work item, look-ups in flight per lane, pipelining, particle
-// order, and, if allowed, points per chunk and lanes per particle (these two
+// order, work-item order, and, if allowed, points per chunk and lanes per particle (these two
 // fix the FP32 summation order, so a tuned pair must stay fixed for a
 // session). Winners are cached per (GPU, map kind, layout, storage type, score
 // mode, P bucket, N bucket) in a JSON-lines file.
@@ -25,7 +25,7 @@ namespace {
 std::mutex g_tune_mu;
 
 struct Knobs {
-  int chunk, lanes, ppi, unroll, pipeline, order;
+  int chunk, lanes, ppi, unroll, pipeline, order, items;
 };
 
 int log2_bucket(int64_t v) {
@@ -58,8 +58,8 @@ bool cache_lookup(const char* path, const std::string& key, Knobs* k, double* ms
     if (sscanf(line,
                "{\"key\": \"%511[^\"]\", \"points_per_chunk\": %d, \"lanes_per_particle\": %d, "
                "\"particles_per_item\": %d, \"unroll\": %d, \"pipeline\": %d, \"particle_order\": %d, "
-               "\"ms\": %lf}",
-               kbuf, &t.chunk, &t.lanes, &t.ppi, &t.unroll, &t.pipeline, &t.order, &tms) == 8 &&
+               "\"item_order\": %d, \"ms\": %lf}",
+               kbuf, &t.chunk, &t.lanes, &t.ppi, &t.unroll, &t.pipeline, &t.order, &t.items, &tms) == 9 &&
         key == kbuf) {
       *k = t;  // the last entry for a key wins
       *ms = tms;
@@ -76,8 +76,8 @@ void cache_store(const char* path, const std::string& key, const Knobs& k, doubl
   fprintf(f,
           "{\"key\": \"%s\", \"points_per_chunk\": %d, \"lanes_per_particle\": %d, "
           "\"particles_per_item\": %d, \"unroll\": %d, \"pipeline\": %d, \"particle_order\": %d, "
-          "\"ms\": %.6f}\n",
-          key.c_str(), k.chunk, k.lanes, k.ppi, k.unroll, k.pipeline, k.order, ms);
+          "\"item_order\": %d, \"ms\": %.6f}\n",
+          key.c_str(), k.chunk, k.lanes, k.ppi, k.unroll, k.pipeline, k.order, k.items, ms);
   fclose(f);
 }
 
@@ -89,6 +89,7 @@ mcl_sensor_params to_params(const mcl_sensor_params& base, const Knobs& k) {
   p.unroll = k.unroll;
   p.pipeline = k.pipeline;
   p.particle_order = k.order;
+  p.item_order = k.items;
   return p;
 }
 
@@ -116,8 +117,9 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
 
   Knobs best{base->points_per_chunk ? base->points_per_chunk : 2048,
              base->lanes_per_particle ? base->lanes_per_particle : 32,
-             base->particles_per_item ? base->particles_per_item : 128, base->unroll ? base->unroll : 4,
-             base->pipeline ? base->pipeline : 1, base->particle_order ? base->particle_order : 2};
+             base->particles_per_item, base->unroll ? base->unroll : 4,
+             base->pipeline ? base->pipeline : 1, base->particle_order ? base->particle_order : 2,
+             base->item_order};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     double ms = 0;
@@ -161,7 +163,7 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
   default_ms = best_ms;
   // coordinate descent: each knob in turn over its candidate values, twice
   const std::vector<int> chunks = {1024, 2048, 4096}, lanes = {32, 16}, ppis = {64, 128, 256},
-                         unrolls = {2, 4, 8}, pipes = {1, 2}, orders = {1, 2};
+                         unrolls = {2, 4, 8}, pipes = {1, 2}, orders = {1, 2}, items = {1, 2};
   for (int round = 0; round < 2 && rc == MCL_OK; ++round) {
     auto sweep = [&](int Knobs::*field, const std::vector<int>& vals) {
       for (int v : vals) {
@@ -186,6 +188,7 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
     sweep(&Knobs::pipeline, pipes);
     sweep(&Knobs::ppi, ppis);
     sweep(&Knobs::order, orders);
+    sweep(&Knobs::items, items);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

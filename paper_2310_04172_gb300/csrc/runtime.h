@@ -49,6 +49,7 @@ class PhaseScope {
 struct Plan {
   SensorShape sh;
   int K, nblk, blocks_per_sm, sms;
+  int sweep;  // particle blocks per sweep of the item order (nblk: chunk-major)
   bool spatial;
   long long n_items;
   size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, off_est, off_key,

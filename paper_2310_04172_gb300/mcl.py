@@ -50,7 +50,7 @@ class mcl_sensor_params(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("sigma_hit", ctypes.c_float), ("mode", _i32),
                 ("flags", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
                 ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
-                ("particle_order", _i32)]
+                ("particle_order", _i32), ("item_order", _i32)]
 
 
 class mcl_sensor_plan(ctypes.Structure):
@@ -58,7 +58,7 @@ class mcl_sensor_plan(ctypes.Structure):
                 ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
                 ("particle_order", _i32), ("threads", _i32), ("grid", _i32),
                 ("blocks_per_sm", _i32), ("num_sms", _i32), ("n_items", _i64),
-                ("workspace_bytes", _i64)]
+                ("workspace_bytes", _i64), ("item_order", _i32), ("blocks_per_sweep", _i32)]
 
 
 class mcl_profile(ctypes.Structure):
@@ -85,7 +85,7 @@ class mcl_session_update(ctypes.Structure):
 class mcl_batch_params(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
                 ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
-                ("particle_order", _i32), ("use_graph", _i32)]
+                ("particle_order", _i32), ("use_graph", _i32), ("item_order", _i32)]
 
 
 class mcl_batch_info(ctypes.Structure):
@@ -363,12 +363,14 @@ def mcl_map_lookup(m: Map, points, out_index=None, out_value=None, stream=None):
 def sensor_params(sigma_hit: float = 0.1, mode: int = MCL_LOGPROD, flags: int = 0,
                   points_per_chunk: int = 0, lanes_per_particle: int = 0,
                   particles_per_item: int = 0, unroll: int = 0,
-                  pipeline: int = 0, particle_order: int = 0) -> mcl_sensor_params:
+                  pipeline: int = 0, particle_order: int = 0,
+                  item_order: int = 0) -> mcl_sensor_params:
     return mcl_sensor_params(struct_size=ctypes.sizeof(mcl_sensor_params), sigma_hit=sigma_hit,
                              mode=mode, flags=flags, points_per_chunk=points_per_chunk,
                              lanes_per_particle=lanes_per_particle,
                              particles_per_item=particles_per_item, unroll=unroll,
-                             pipeline=pipeline, particle_order=particle_order)
+                             pipeline=pipeline, particle_order=particle_order,
+                             item_order=item_order)
 
 
 def mcl_sensor_update(m: Map, particles, scan, params: mcl_sensor_params, logw=None, w=None,
@@ -510,7 +512,7 @@ def mcl_autotune(m: Map, particles, scan, base: mcl_sensor_params, max_particles
             "from_cache": bool(res.from_cache),
             "shape": {k: getattr(res.best, k) for k in ("points_per_chunk", "lanes_per_particle",
                                                          "particles_per_item", "unroll", "pipeline",
-                                                         "particle_order")}}
+                                                         "particle_order", "item_order")}}
     return best, info
 
 
@@ -521,7 +523,7 @@ class Batch:
     estimate_buffer()); the CUDA tensors stay referenced."""
 
     def __init__(self, sessions, points_per_chunk=0, lanes_per_particle=0, particles_per_item=0,
-                 unroll=0, pipeline=0, particle_order=0, use_graph=False):
+                 unroll=0, pipeline=0, particle_order=0, use_graph=False, item_order=0):
         import torch
         arr = (mcl_session_update * len(sessions))()
         self._keep = []
@@ -545,7 +547,8 @@ class Batch:
         bp = mcl_batch_params(struct_size=ctypes.sizeof(mcl_batch_params),
                               points_per_chunk=points_per_chunk, lanes_per_particle=lanes_per_particle,
                               particles_per_item=particles_per_item, unroll=unroll, pipeline=pipeline,
-                              particle_order=particle_order, use_graph=int(bool(use_graph)))
+                              particle_order=particle_order, use_graph=int(bool(use_graph)),
+                              item_order=item_order)
         h = ctypes.c_void_p()
         _check(lib().mcl_batch_create(arr, len(sessions), ctypes.byref(bp), ctypes.byref(h)))
         self.handle = h

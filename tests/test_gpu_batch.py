@@ -88,14 +88,15 @@ def batch_outputs(s):
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
-@pytest.mark.parametrize("chunk,lanes", [(2048, 32), (1024, 16)])
-def test_batch_matches_single_sessions(env, use_graph, chunk, lanes):
+@pytest.mark.parametrize("chunk,lanes,item_order", [(2048, 32, 0), (1024, 16, 0), (2048, 32, 1)])
+def test_batch_matches_single_sessions(env, use_graph, chunk, lanes, item_order):
     torch, mcl, room, hall, bld, maps = env
     rng = np.random.default_rng(11)
     sessions = make_sessions(torch, room, hall, bld, maps, rng)
     for k in (0, 3, 4):  # pose estimates fused into the batched normalisation
         sessions[k]["estimate"] = mcl.estimate_buffer()
-    b = mcl.Batch(sessions, points_per_chunk=chunk, lanes_per_particle=lanes, use_graph=use_graph)
+    b = mcl.Batch(sessions, points_per_chunk=chunk, lanes_per_particle=lanes, use_graph=use_graph,
+                  item_order=item_order)
     info = b.info()
     assert info["n_sessions"] == 6 and info["n_groups"] == 5  # two sessions share the room group
     for run in range(2):
