@@ -391,6 +391,66 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
       v[c] = in ? load_raw_l1<DTYPE, MODE>(m.values, lin) : a.vout;
       stored |= in;
     }
+  } else if constexpr (KIND == kKindBrickGrid || KIND == MCL_MAP_BRICK) {
+    // Linear bricks. Along each axis the two corners share a brick unless
+    // the lower one sits on the brick's last voxel (s = 1; always so for
+    // i0 = -1). Corner c therefore lies in brick b0 + (c_x s_x, c_y s_y,
+    // c_z s_z): at most 2^(s_x + s_y + s_z) distinct bricks, one for 82 % of
+    // the points of the building scan. A brick is looked up only if a corner
+    // inside the grid lies in it; a corner outside the grid maps to a brick
+    // that was not looked up, so its slot is empty. Brick keys are formed in
+    // 32-bit arithmetic, which wraps consistently for i0 = -1.
+    const uint32_t sx = (x0 & 15) == 15, sy = (y0 & 15) == 15, sz = (z0 & 15) == 15;
+    const uint32_t nbx = m.nbx, nbxy = m.nbx * m.nby;
+    const uint32_t k0 = ((uint32_t)(z0 >> 4) * m.nby + (uint32_t)(y0 >> 4)) * nbx + (uint32_t)(x0 >> 4);
+    const bool ux[2] = {inx[0], (sx != 0) & inx[1]};
+    const bool uy[2] = {iny[0], (sy != 0) & iny[1]};
+    const bool uz[2] = {inz[0], (sz != 0) & inz[1]};
+    uint32_t b[8];  // slot of brick b0 + (q & 1, (q >> 1) & 1, q >> 2)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+      const bool need = ux[qx] & uy[qy] & uz[qz];
+      const uint32_t key = k0 + (uint32_t)qx + (uint32_t)qy * nbx + (uint32_t)qz * nbxy;
+      if constexpr (KIND == kKindBrickGrid) {
+        b[q] = need ? __ldg(m.grid + key) : kNoSlot;
+      } else {
+        b[q] = kNoSlot;
+        if (need) {
+          const uint32_t h = brick_hash(key, m.hash_shift);
+          const uint2 e = __ldg(m.table + h);
+          b[q] = e.x == key ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key, h));
+        }
+      }
+    }
+    uint32_t slot[8];
+    slot[0] = b[0];
+    slot[1] = sx ? b[1] : b[0];
+    slot[2] = sy ? b[2] : b[0];
+    slot[3] = sx ? (sy ? b[3] : b[1]) : slot[2];
+    slot[4] = sz ? b[4] : b[0];
+    slot[5] = sz ? (sx ? b[5] : b[4]) : slot[1];
+    slot[6] = sz ? (sy ? b[6] : b[4]) : slot[2];
+    slot[7] = sz ? (sx ? (sy ? b[7] : b[5]) : (sy ? b[6] : b[4])) : slot[3];
+    // in-brick offsets: one step up along an axis is +1 / +16 / +256, or back
+    // to 0 on that axis when the corner crosses into the next brick
+    const int base = (((z0 & 15) << 8) | ((y0 & 15) << 4) | (x0 & 15));
+    const int ox = sx ? -15 : 1, oy = sy ? -240 : 16, oz = sz ? -3840 : 256;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+#if MCL_DEBUG_BOUNDS
+      if (slot[c] != kNoSlot && slot[c] >= m.n_slots) {
+        atomicOr(a.status, kDevErrIndex);
+        slot[c] = kNoSlot;
+      }
+#endif
+      const bool st = slot[c] != kNoSlot;
+      const int off = base + (cx ? ox : 0) + (cy ? oy : 0) + (cz ? oz : 0);
+      v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, (size_t)slot[c] * kBrickVoxels + (uint32_t)off)
+                : a.vout;
+      stored |= st;
+    }
   } else {
     uint32_t key[8], slot[8];
 #pragma unroll
