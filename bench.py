@@ -706,7 +706,7 @@ def run_precision(args):
     per = P // S
     sess_parts = [parts[k * per:(k + 1) * per].contiguous() for k in range(S)]
     outs = [(torch.empty(per, device="cuda"), torch.empty(per, device="cuda")) for _ in range(S)]
-    plain = mcl.sensor_params(wl.sigma_hit, particle_order=1)
+    plain = mcl.sensor_params(wl.sigma_hit, particle_order=1, item_order=1)
 
     def plain_step():
         for k in range(S):
