@@ -1,8 +1,9 @@
 // Spatial processing order of the particles (a GB300 locality device; the
 // paper evaluates particles in the order given, Sec. V-B).
 //
-// Particles are bucketed by position into a 64 x 64 x 64 grid over the map's
-// extent, buckets ordered along a Morton (Z-order) curve, and each particle
+// Particles are bucketed by position into cubic cells, 64 along the longest
+// axis of the map's extent (fewer along the others), buckets ordered along a
+// Morton (Z-order) curve, and each particle
 // gets a slot rank[p] in that order (counting sort: histogram, exclusive
 // scan of the bucket counts in tiles of 1024 plus a scan of the tile totals,
 // scatter). The sensor kernel then works on the particles slot
@@ -114,7 +115,10 @@ cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, u
   const float cells = (float)(1 << kOrderBits);
   const float ex = m.fnx / m.inv, ey = m.fny / m.inv, ez = m.fnz / m.inv;  // extent in metres
   const float3 o = make_float3(m.ox, m.oy, m.oz);
-  const float3 sc = make_float3(cells / ex, cells / ey, cells / ez);
+  // cubic cells, 64 along the longest axis: a run of buckets on the curve
+  // then covers a compact block of space rather than a flat slab
+  const float emax = fmaxf(ex, fmaxf(ey, ez));
+  const float3 sc = make_float3(cells / emax, cells / emax, cells / emax);
   const int g = (P + 255) / 256;
   k_order_keys<<<g, 256, 0, s>>>(poses, P, o, sc, key, hist);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
