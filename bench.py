@@ -201,7 +201,7 @@ def algorithmic_bytes(P: int, N: int, elem: int, index_entry: int) -> int:
 
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16_grid.cu", "mcl_internal.h"):
+    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16_grid.cu", "mcl_internal.h", "k_order.cu"):
         with open(os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
