@@ -134,28 +134,59 @@ __device__ __forceinline__ void est_add(EstAcc& a, const float* __restrict__ par
   est_best(a, w, p);
 }
 
-__device__ __forceinline__ void est_warp_reduce(EstAcc& a) {
+__device__ __forceinline__ void est_best_warp(EstAcc& a) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int i = 0; i < kEstSums; ++i) a.v[i] += __shfl_xor_sync(0xffffffffu, a.v[i], off);
     const float ow = __shfl_xor_sync(0xffffffffu, a.bw, off);
     const int op = __shfl_xor_sync(0xffffffffu, a.bp, off);
     est_best(a, ow, op);
   }
 }
 
-// Fixed tree over the block; the result is thread 0's.
-__device__ void est_block_reduce(EstAcc& a, EstAcc* sh) {
-  est_warp_reduce(a);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Block reduction of the estimate terms (blockDim.x == kT; the result is
+// thread 0's). Every thread's sums go to shared memory; thread k + 18 g
+// (g < 8 warps) adds term k of warp g's 32 threads in thread order, then
+// thread k adds the 8 warp totals in warp order. A fixed order, and far fewer
+// FP64 warp instructions than a shuffle tree over all 18 terms in every lane
+// (FP64 issue is slow on this part: this reduction dominated the estimate
+// for small particle sets). The best weight is reduced with shuffles.
+struct EstShared {
+  double v[kT][kEstSums];
+  double warp[kT / 32][kEstSums];
+  float bw[kT / 32];
+  int bp[kT / 32];
+};
+
+__device__ void est_block_reduce(EstAcc& a, EstShared& sh) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  __syncthreads();  // sh may still be read by a previous use
+#pragma unroll
+  for (int k = 0; k < kEstSums; ++k) sh.v[t][k] = a.v[k];
+  est_best_warp(a);
+  if (lane == 0) {
+    sh.bw[warp] = a.bw;
+    sh.bp[warp] = a.bp;
+  }
   __syncthreads();
-  if (lane == 0) sh[warp] = a;
+  if (t < kEstSums * (kT / 32)) {
+    const int k = t % kEstSums, g = t / kEstSums;
+    double s = 0.0;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) s += sh.v[g * 32 + i][k];
+    sh.warp[g][k] = s;
+  }
   __syncthreads();
-  if (warp == 0) {
-    if (lane < (int)(blockDim.x >> 5)) a = sh[lane];
-    else est_init(a);
-    est_warp_reduce(a);
+  if (t < kEstSums) {
+    double s = 0.0;
+#pragma unroll
+    for (int g = 0; g < kT / 32; ++g) s += sh.warp[g][t];
+    sh.v[0][t] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < kEstSums; ++k) a.v[k] = sh.v[0][k];
+    for (int g = 0; g < kT / 32; ++g) est_best(a, sh.bw[g], sh.bp[g]);
   }
 }
 
@@ -198,8 +229,8 @@ __global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw
     out_stats[0] = M;
     out_stats[1] = degenerate ? 0.f : S;
   }
-  if (EST) {
-    __shared__ EstAcc esh[kT / 32];
+  if constexpr (EST) {
+    __shared__ EstShared esh;
     est_block_reduce(acc, esh);
     if (threadIdx.x == 0) est_store(acc, part + blockIdx.x);
   }
@@ -209,7 +240,7 @@ __global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw
 __global__ void __launch_bounds__(kT) k_estimate_blocks(const float* __restrict__ particles,
                                                         const float* __restrict__ w, int P,
                                                         int range, EstPartial* __restrict__ part) {
-  __shared__ EstAcc esh[kT / 32];
+  __shared__ EstShared esh;
   EstAcc acc;
   est_init(acc);
   const int start = blockIdx.x * range, end = min(P, start + range);
@@ -269,15 +300,15 @@ __device__ void jacobi4f(float A[4][4], float V[4][4]) {
   }
 }
 
-// One block of kTF threads: partials are combined in a fixed order (thread
-// i takes i, i + kTF, ..., then the block tree), then thread 0 solves the
+// One block of kT threads: partials are combined in a fixed order (thread
+// i takes i, i + kT, ..., then the block reduction), then thread 0 solves the
 // 4 x 4 eigenproblem.
-constexpr int kTF = 256;
+constexpr int kTF = kT;
 
 __global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __restrict__ part, int nb,
                                                         const float* __restrict__ particles,
                                                         mcl_estimate* __restrict__ out) {
-  __shared__ EstAcc esh[kTF / 32];
+  __shared__ EstShared esh;
   EstAcc acc;
   est_init(acc);
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
