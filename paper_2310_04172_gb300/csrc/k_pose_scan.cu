@@ -96,7 +96,11 @@ __global__ void k_score_values(const void* __restrict__ src, long long n, double
 
 cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
                                   cudaStream_t s) {
-  k_pose_to_matrix<<<blocks_for(P, 256), 256, 0, s>>>(poses, P, mats, rank);
+  // FP64 trigonometry per particle: small sets use small blocks so that they
+  // spread over many SMs instead of loading a few (FP64 issue per SM is slow)
+  int threads = 256;
+  while (threads > 32 && (P + threads - 1) / threads < 2 * 152) threads >>= 1;
+  k_pose_to_matrix<<<blocks_for(P, threads), threads, 0, s>>>(poses, P, mats, rank);
   return cudaGetLastError();
 }
 

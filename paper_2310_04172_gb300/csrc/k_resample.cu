@@ -8,6 +8,7 @@
 // one block scans the tile totals, and each output j finds
 // min{p : C_p > t_j}, t_j = ((j + r) / P) S, by a binary search over tile ends
 // and then inside the tile. Sets of at most one tile take one fused launch.
+#include <algorithm>
 #include <mutex>
 
 #include "mcl_internal.h"
@@ -165,9 +166,13 @@ __global__ void k_systematic(const double* __restrict__ cum, const double* __res
   }
 }
 
-// Sets of at most one tile in one block: the same quantised weights, the
+// Sets of at most one tile in one launch: the same quantised weights, the
 // same exact prefix (kept in shared memory), the same targets and search, so
-// the same indices as the three-launch path, in one launch.
+// the same indices as the three-launch path. Every block forms the whole
+// prefix (exact, so the same bits in every block and for any block size) and
+// then serves its own contiguous slice of the targets: the FP64 division and
+// search of each target run on several SMs instead of one (FP64 issue per SM
+// is slow on this part).
 __global__ void __launch_bounds__(kRT) k_systematic_small(const float* __restrict__ w, int P,
                                                           double r, const double* __restrict__ r_dev,
                                                           int32_t* __restrict__ idx,
@@ -199,7 +204,9 @@ __global__ void __launch_bounds__(kRT) k_systematic_small(const float* __restric
   last = block_max_ll(last, shl);
   __syncthreads();
   if (r_dev) r = *r_dev;
-  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+  const int slice = (P + gridDim.x - 1) / gridDim.x;
+  const int j_end = min(P, (int)(blockIdx.x + 1) * slice);
+  for (int j = blockIdx.x * slice + threadIdx.x; j < j_end; j += blockDim.x) {
     int res;
     if (!(S > 0.0)) {
       res = j;  // all weights zero: identity
@@ -277,7 +284,10 @@ cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,
                             double* tile_total, long long* tile_last, cudaStream_t s,
                             const double* r_dev) {
   if (P <= kTile) {
-    k_systematic_small<<<1, kRT, 0, s>>>(w, P, r, r_dev, idx, particles_in, particles_out);
+    // threads: kRI weights each, whole warps; blocks: about 128 targets each
+    const int threads = std::min(kRT, ((P + kRI - 1) / kRI + 31) / 32 * 32);
+    const int blocks = std::min(32, (P + 127) / 128);
+    k_systematic_small<<<blocks, threads, 0, s>>>(w, P, r, r_dev, idx, particles_in, particles_out);
     return cudaGetLastError();
   }
   const int ntiles = resample_tiles(P);
