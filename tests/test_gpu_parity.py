@@ -404,6 +404,21 @@ def test_motion_update_parity(torch_cuda, mcl):
     assert pos_err.max() <= 2e-6
     ang = np.abs(np.angle(np.exp(1j * (got[:, 3:] - ref[:, 3:]))))
     assert ang.max() <= 2e-6
+    # Small sets run a kernel that splits each particle's FP64 work over six
+    # warps: same bits as the one-thread-per-particle kernel (the noise of
+    # particle i depends only on i), for set sizes around the switch.
+    for n in (1, 31, 1000, 5120, 5121):
+        ts = dev(torch, poses[:n])
+        mcl.mcl_motion_update(ts, delta, sigma, seed=0x1234_5678_9ABC, step=42)
+        mcl.mcl_sync()
+        assert np.array_equal(ts.cpu().numpy(), got[:n].astype(np.float32)), n
+    ts = dev(torch, poses[:1000])
+    mcl.mcl_motion_update(ts, np.zeros(6, np.float32), sigma, seed=3, step=1)  # noise only
+    mcl.mcl_sync()
+    ref = oracle.motion_update(poses[:1000], np.zeros(6, np.float32), sigma, 3, 1).astype(np.float64)
+    got1 = ts.cpu().numpy().astype(np.float64)
+    assert (np.abs(got1[:, :3] - ref[:, :3]) / np.maximum(1.0, np.abs(ref[:, :3]))).max() <= 2e-6
+    assert np.abs(np.angle(np.exp(1j * (got1[:, 3:] - ref[:, 3:])))).max() <= 2e-6
 
 
 # ----------------------------------------------------------------- determinism, errors, profiling
