@@ -201,6 +201,9 @@ def algorithmic_bytes(P: int, N: int, elem: int, index_entry: int) -> int:
     return P * N * (elem + index_entry) + P * 48 + N * 16 + P * 4
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
     for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16_grid.cu", "mcl_internal.h", "k_order.cu"):
@@ -419,7 +422,15 @@ def run_ours(args):
             sensor_gbs = traffic / (sensor_ms / 1e3) / 1e9
             gather_gbs = gather["map_footprint"]["gathers_per_s"] * per_gather / 1e9
             gather.update({"dram_bytes_per_gather": per_gather, "gather_dram_gbs": gather_gbs,
-                           "sensor_dram_gbs": sensor_gbs, "frac_dram": sensor_gbs / gather_gbs})
+                           "sensor_dram_gbs": sensor_gbs, "frac_dram": sensor_gbs / gather_gbs,
+                           # the sensor kernel's DRAM rate against the copy peak and
+                           # against the part's nominal 7.9 TB/s
+                           "sensor_dram_frac_of_copy_peak": sensor_gbs / peak,
+                           "sensor_dram_frac_of_nominal": sensor_gbs / NOMINAL_HBM_GBS})
+        # the absolute bound: every evaluation moving only its element bytes at
+        # the copy peak
+        gather["elem_bytes_bound_evals_per_s"] = peak * 1e9 / elem
+        gather["frac_of_elem_bytes_bound"] = value / (peak * 1e9 / elem)
 
     # end to end through the C ABI with host buffers (pinned), copies in the region
     e2e = None
