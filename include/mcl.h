@@ -102,7 +102,9 @@ enum { MCL_INDEX_AUTO = 0, MCL_INDEX_HASH = 1, MCL_INDEX_GRID = 2 };
  * neighbours in memory), MCL_INDEX_HASH an open-addressing hash table of
  * 8-byte entries, at least 4 per brick (for sparse maps of a huge extent).
  * MCL_INDEX_AUTO takes the grid for the linear layout when it needs at most
- * 512 MB, else the hash. The grid is only built with MCL_LAYOUT_LINEAR.
+ * 512 MB and the map has at most 2^20 bricks, else the hash. The grid is
+ * only built with MCL_LAYOUT_LINEAR and for at most 2^20 bricks (its kernels
+ * address values with 32-bit indices); MCL_INDEX_GRID beyond that is EINVAL.
  * Results do not depend on the index. */
 typedef struct mcl_map_desc {
   uint32_t struct_size; /* sizeof(mcl_map_desc) */

@@ -170,6 +170,14 @@ __device__ __forceinline__ typename Raw<DTYPE, MODE>::value outside_value(const 
   return a.vout;
 }
 
+// Index of a brick value: 32-bit arithmetic for the cell-grid kind (at most
+// kGridMaxBricks bricks, so it cannot wrap), 64-bit otherwise.
+template <int KIND>
+__device__ __forceinline__ size_t value_index(uint32_t slot, uint32_t local) {
+  if constexpr (KIND == kKindBrickGrid) return (size_t)(slot * (uint32_t)kBrickVoxels + local);
+  else return (size_t)slot * kBrickVoxels + local;
+}
+
 // In-brick offset: linear x-fastest, or 4x4x4 blocks (block-major, each block
 // z-major) so that a 32-byte sector of int16 values is a 4 x 4 patch in x, y.
 template <int KIND>
@@ -281,7 +289,7 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
       }
 #endif
       const bool st = slot != kNoSlot;
-      dv[u] = st ? load_raw<DTYPE, MODE>(m.values, (size_t)slot * kBrickVoxels + s.loc[u])
+      dv[u] = st ? load_raw<DTYPE, MODE>(m.values, value_index<KIND>(slot, s.loc[u]))
                  : outside_value<DTYPE, MODE>(a);
       use[u] = s.v[u] && (st || !a.neglect);
     }
@@ -447,7 +455,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
 #endif
       const bool st = slot[c] != kNoSlot;
       const int off = base + (cx ? ox : 0) + (cy ? oy : 0) + (cz ? oz : 0);
-      v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, (size_t)slot[c] * kBrickVoxels + (uint32_t)off)
+      v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, value_index<KIND>(slot[c], (uint32_t)off))
                 : a.vout;
       stored |= st;
     }

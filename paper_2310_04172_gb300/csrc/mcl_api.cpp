@@ -209,6 +209,9 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     return fail(MCL_EINVAL, "map_create: index %d", d->index);
   if (d->kind == MCL_MAP_BRICK && d->index == MCL_INDEX_GRID && d->device_layout != MCL_LAYOUT_LINEAR)
     return fail(MCL_EINVAL, "map_create: the grid index is built for the linear layout only");
+  if (d->kind == MCL_MAP_BRICK && d->index == MCL_INDEX_GRID && d->n_bricks > kGridMaxBricks)
+    return fail(MCL_EINVAL, "map_create: the grid index addresses at most 2^20 bricks (%lld given)",
+                (long long)d->n_bricks);
   float inv = d->inv_voxel == 0.f ? (float)(1.0 / (double)d->voxel) : d->inv_voxel;
   if (!finite_pos(inv)) return fail(MCL_EINVAL, "map_create: inv_voxel must be finite and > 0");
   const size_t es = d->dtype == MCL_F32 ? 4 : 2;
@@ -312,7 +315,7 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     const uint64_t cells = nbx * nby * nbz;
     const bool grid = d->index == MCL_INDEX_GRID ||
                       (d->index == MCL_INDEX_AUTO && v.layout == MCL_LAYOUT_LINEAR &&
-                       cells * sizeof(uint32_t) <= (512ull << 20));
+                       cells * sizeof(uint32_t) <= (512ull << 20) && nb <= kGridMaxBricks);
     v.nbx = (uint32_t)nbx;
     v.nby = (uint32_t)nby;
     v.n_slots = (uint32_t)nb;

@@ -13,6 +13,11 @@ namespace mcl {
 
 constexpr int kBrick = 16;
 constexpr int kBrickVoxels = kBrick * kBrick * kBrick;
+// Bricks the cell-grid index addresses: the grid kernels form value indices
+// slot * 4096 + offset in 32 bits (one instruction fewer per value read than
+// 64-bit indices: 177.1 -> 175.7 ms for the 1M x 65,536 building, 676 -> 594
+// ms for its trilinear read), so slot * 4096 must stay below 2^32.
+constexpr int64_t kGridMaxBricks = int64_t(1) << 20;
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr int kKindBrickBlock4 = 2;  // internal kind: brick map stored in 4x4x4 blocks
