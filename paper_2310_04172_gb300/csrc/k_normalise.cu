@@ -318,19 +318,30 @@ __global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __rest
     est_best(acc, e.best_w, e.best_p);
   }
   est_block_reduce(acc, esh);
+  // The 16 quotients sum / W (6 mean pose terms, 10 second moments) on 16
+  // lanes at once: an FP64 division is a dozen FP64 instructions, and one
+  // thread doing all of them in turn dominated this kernel.
+  __shared__ double quot[kEstSums - 2];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < kEstSums; ++k) esh.v[0][k] = acc.v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kEstSums - 2) quot[threadIdx.x] = esh.v[0][2 + threadIdx.x] / esh.v[0][0];
+  __syncthreads();
   if (threadIdx.x != 0) return;
   const double W = acc.v[0], W2 = acc.v[1];
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   out->weight_sum = W;
   out->n_eff = W2 > 0.0 ? W * W / W2 : 0.0;
-  for (int k = 0; k < 6; ++k) out->mean_pose[k] = acc.v[2 + k] / W;
+  for (int k = 0; k < 6; ++k) out->mean_pose[k] = quot[k];
   double A[4][4];
   bool finite = W != 0.0;
   {
-    int o = 8;
+    int o = 6;
     for (int i = 0; i < 4; ++i)
       for (int j = i; j < 4; ++j) {
-        const double qij = acc.v[o++] / W;
+        const double qij = quot[o++];
         finite = finite && isfinite(qij);
         A[i][j] = qij;
         A[j][i] = qij;
