@@ -684,7 +684,7 @@ mcl_status mcl_workspace_release(mcl_stream_t stream);
  * resample, motion, other) whether profiling is on or not. */
 enum {
   MCL_PHASE_POSE = 0,     /* pose -> [R | t] */
-  MCL_PHASE_PACK = 1,     /* scan packing */
+  MCL_PHASE_PACK = 1,     /* scan packing (now done by the pose phase's kernel: no launches) */
   MCL_PHASE_SENSOR = 2,   /* transform, look-up, score, per-chunk sums */
   MCL_PHASE_REDUCE = 3,   /* chunk sums -> log-weights, block statistics */
   MCL_PHASE_NORMALISE = 4,

@@ -14,10 +14,8 @@ namespace {
 //   [ cy*cp   a*sr - sy*cr   a*cr + sy*sr ]
 //   [ sy*cp   b*sr + cy*cr   b*cr - cy*sr ]
 //   [ -sp     cp*sr          cp*cr        ]
-__global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4* __restrict__ mats,
-                                 const int* __restrict__ rank) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+__device__ __forceinline__ void pose_to_matrix(const float* __restrict__ poses, int p,
+                                               float4* __restrict__ mats, const int* __restrict__ rank) {
   const float* s = poses + 6 * (size_t)p;
   const float x = s[0], y = s[1], z = s[2];
   const double roll = (double)s[3], pitch = (double)s[4], yaw = (double)s[5];
@@ -43,11 +41,32 @@ __global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4*
 
 // N x 3 scan rows -> N float4 (x, y, z, 0): 16-byte records that a bulk copy
 // can move and a lane can read with one 128-bit shared-memory load.
-__global__ void k_scan_pack(const float* __restrict__ scan, int N, float4* __restrict__ packed) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
+__device__ __forceinline__ void scan_pack(const float* __restrict__ scan, int j,
+                                          float4* __restrict__ packed) {
   const float* q = scan + 3 * (size_t)j;
   packed[j] = make_float4(q[0], q[1], q[2], 0.f);
+}
+
+__global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4* __restrict__ mats,
+                                 const int* __restrict__ rank) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) pose_to_matrix(poses, p, mats, rank);
+}
+
+// Pose matrices and scan packing of one sensor update in one launch: blocks
+// [0, pose_blocks) take particles, the rest take scan points (the two are
+// independent; one launch instead of two matters for small updates, where
+// each launch costs about as much as its work).
+__global__ void k_pose_and_pack(const float* __restrict__ poses, int P, float4* __restrict__ mats,
+                                const int* __restrict__ rank, int pose_blocks,
+                                const float* __restrict__ scan, int N, float4* __restrict__ packed) {
+  if ((int)blockIdx.x < pose_blocks) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) pose_to_matrix(poses, p, mats, rank);
+  } else {
+    const int j = (blockIdx.x - pose_blocks) * blockDim.x + threadIdx.x;
+    if (j < N) scan_pack(scan, j, packed);
+  }
 }
 
 template <int KIND, int DTYPE>
@@ -94,18 +113,26 @@ __global__ void k_score_values(const void* __restrict__ src, long long n, double
 
 }  // namespace
 
-cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
-                                  cudaStream_t s) {
-  // FP64 trigonometry per particle: small sets use small blocks so that they
-  // spread over many SMs instead of loading a few (FP64 issue per SM is slow)
+// FP64 trigonometry per particle: small sets use small blocks so that they
+// spread over many SMs instead of loading a few (FP64 issue per SM is slow)
+inline int pose_threads(int P) {
   int threads = 256;
   while (threads > 32 && (P + threads - 1) / threads < 2 * 152) threads >>= 1;
+  return threads;
+}
+
+cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const int* rank,
+                                  cudaStream_t s) {
+  const int threads = pose_threads(P);
   k_pose_to_matrix<<<blocks_for(P, threads), threads, 0, s>>>(poses, P, mats, rank);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_pack(const float* scan, int N, float4* packed, cudaStream_t s) {
-  k_scan_pack<<<blocks_for(N, 256), 256, 0, s>>>(scan, N, packed);
+cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const int* rank,
+                                 const float* scan, int N, float4* packed, cudaStream_t s) {
+  const int threads = pose_threads(P);
+  const int pb = blocks_for(P, threads), sb = blocks_for(N, threads);
+  k_pose_and_pack<<<pb + sb, threads, 0, s>>>(poses, P, mats, rank, pb, scan, N, packed);
   return cudaGetLastError();
 }
 

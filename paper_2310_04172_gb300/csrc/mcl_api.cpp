@@ -669,15 +669,12 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   float* ostats = (float*)(ws + pl.off_ostats);
   int* rank = pl.spatial ? (int*)(ws + pl.off_rank) : nullptr;
   {
+    // the pose phase also packs the scan (one launch for both)
     PhaseScope ps(MCL_PHASE_POSE, s, pl.spatial ? 5 : 1);
     if (pl.spatial)
       MCL_CUDA(launch_particle_order(particles, (int)P, m->view, (uint32_t*)(ws + pl.off_key),
                                      (uint32_t*)(ws + pl.off_hist), rank, s));
-    MCL_CUDA(launch_pose_to_matrix(particles, (int)P, mats, rank, s));
-  }
-  {
-    PhaseScope ps(MCL_PHASE_PACK, s);
-    MCL_CUDA(launch_scan_pack(scan, (int)N, packed, s));
+    MCL_CUDA(launch_pose_and_pack(particles, (int)P, mats, rank, scan, (int)N, packed, s));
   }
   const double sig = (double)p->sigma_hit;
   SensorArgs a;

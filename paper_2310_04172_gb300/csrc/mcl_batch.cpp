@@ -78,8 +78,8 @@ mcl_status enqueue(mcl_batch_s* b, cudaStream_t st, bool profile) {
       MCL_CUDA(launch_particle_order(sp.u.particles, (int)sp.u.P, sp.u.map->view,
                                      (uint32_t*)(ws + pl.off_key), (uint32_t*)(ws + pl.off_hist),
                                      rank, st));
-    MCL_CUDA(launch_pose_to_matrix(sp.u.particles, (int)sp.u.P, (float4*)(ws + pl.off_mats), rank, st));
-    MCL_CUDA(launch_scan_pack(sp.u.scan, (int)sp.u.N, (float4*)(ws + pl.off_scan), st));
+    MCL_CUDA(launch_pose_and_pack(sp.u.particles, (int)sp.u.P, (float4*)(ws + pl.off_mats), rank,
+                                  sp.u.scan, (int)sp.u.N, (float4*)(ws + pl.off_scan), st));
   }
   for (auto& g : b->g) {
     if (profile) {
@@ -253,7 +253,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
   }
   int kern = (int)b->g.size();
   for (auto& sp : b->s)
-    kern += (sp.pl.spatial ? 4 : 0) + 2 + 1 + (sp.u.w ? 1 : 0) + (sp.u.estimate ? 1 : 0) +
+    kern += (sp.pl.spatial ? 4 : 0) + 1 + 1 + (sp.u.w ? 1 : 0) + (sp.u.estimate ? 1 : 0) +
             (sp.u.resample_idx ? resample_kernels((int)sp.u.P) : 0);
   b->kernels_per_run = kern;
   *out = b;

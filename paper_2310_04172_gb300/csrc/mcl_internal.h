@@ -210,7 +210,10 @@ cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const
 size_t order_hist_bytes();
 cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, uint32_t* key,
                                   uint32_t* hist, int* rank, cudaStream_t s);
-cudaError_t launch_scan_pack(const float* scan, int N, float4* packed, cudaStream_t s);
+// Pose matrices (as launch_pose_to_matrix) and scan packing (N x 3 -> N float4)
+// in one launch.
+cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const int* rank,
+                                 const float* scan, int N, float4* packed, cudaStream_t s);
 cudaError_t launch_sensor(int kind, int layout, int dtype, const SensorArgs& a,
                           const SensorShape& sh, cudaStream_t s);
 int sensor_smem_bytes(const SensorShape& sh);

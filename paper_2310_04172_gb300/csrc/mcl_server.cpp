@@ -153,8 +153,8 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     if (pl.spatial)
       MCL_CUDA(launch_particle_order(part, (int)ss->P, ss->map->view, (uint32_t*)(ss->d_ws + pl.off_key),
                                      (uint32_t*)(ss->d_ws + pl.off_hist), rank, st));
-    MCL_CUDA(launch_pose_to_matrix(part, (int)ss->P, (float4*)(ss->d_ws + pl.off_mats), rank, st));
-    MCL_CUDA(launch_scan_pack(ss->d_scan, (int)Ns[i], (float4*)(ss->d_ws + pl.off_scan), st));
+    MCL_CUDA(launch_pose_and_pack(part, (int)ss->P, (float4*)(ss->d_ws + pl.off_mats), rank, ss->d_scan,
+                                  (int)Ns[i], (float4*)(ss->d_ws + pl.off_scan), st));
   }
   // group the slot's sessions by map and score constants; tables go to the slot buffer
   struct G {

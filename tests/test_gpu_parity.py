@@ -484,6 +484,7 @@ def test_profile_counts_phases(torch_cuda, mcl, room):
     prof = mcl.mcl_profile_end()
     assert prof["sensor"]["launches"] == 1 and prof["sensor"]["ms"] > 0
     assert prof["pose"]["launches"] == 1 and prof["normalise"]["launches"] == 1
+    assert prof["pack"]["launches"] == 0        # the pose phase's kernel packs the scan
     m.close()
 
 
