@@ -800,12 +800,20 @@ def run_vlp16(args):
     reps = max(args.steps, 20)
     ms_plain = timed(plain, reps)
     ms_batch = timed(batch.run, reps)
+    # the same hall stored as FP16 (64 MB, the half-size form of this workload)
+    wl16 = scenes.vlp16_multiroom(P=50_000, dtype=scenes.F16)
+    m16 = mcl.map_from_scene(wl16.map)
+    ms_f16 = timed(lambda: (mcl.mcl_sensor_update(m16, parts, scan, prm, logw, w),
+                            mcl.mcl_resample(w, 0.5, idx, parts, nxt)), reps)
+    m16.close()
     line = {"mode": "vlp16", "metric": "particle×point evals/s (50,000×28,800, FP32 dense TSDF)",
             "value": P * N / (ms_batch / 1e3), "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
             "data": "synthetic", "dtype": "f32", "config": {"workload": wl.name},
             "plain": {"ms_per_step": ms_plain, "evals_per_s": P * N / (ms_plain / 1e3)},
             "batched_graph": {"ms_per_step": ms_batch, "evals_per_s": P * N / (ms_batch / 1e3),
-                              "kernels_per_step": batch.info()["kernels_per_run"]}}
+                              "kernels_per_step": batch.info()["kernels_per_run"]},
+            "plain_f16_map": {"ms_per_step": ms_f16, "evals_per_s": P * N / (ms_f16 / 1e3),
+                              "map_bytes": int(wl16.map.values.nbytes)}}
     print(json.dumps(line), flush=True)
     batch.close()
     m.close()
