@@ -341,7 +341,7 @@ def test_building_full_size_sampled(torch_cuda, mcl, building_i16):
 
 
 # ----------------------------------------------------------------- a9: systematic resampling
-@pytest.mark.parametrize("P", [1, 2, 3, 4095, 4096, 4097, 65537, 1_000_000])
+@pytest.mark.parametrize("P", [1, 2, 3, 33, 128, 129, 1000, 2049, 4095, 4096, 4097, 65537, 1_000_000])
 def test_resample_bit_exact(torch_cuda, mcl, P):
     torch = torch_cuda
     rng = np.random.default_rng(P)
