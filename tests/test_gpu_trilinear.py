@@ -86,6 +86,22 @@ def test_trilinear_ragged_tails_and_hints(torch_cuda, mcl, room, chunk, ppi):
     m.close()
 
 
+def test_trilinear_building_full_size_sampled(torch_cuda, mcl):
+    """1M particles x 65,536 points in the bench's launch configuration of the
+    trilinear variant; the oracle recomputes a seeded sample one by one."""
+    torch = torch_cuda
+    wl = scenes.os064_building(P=1_000_000, dtype=scenes.I16)
+    m = mcl.map_from_scene(wl.map)
+    Lg, wg = run_tri(torch, mcl, m, wl.particles, wl.scan, wl.sigma_hit)
+    rng = np.random.default_rng(11)
+    sample = np.concatenate([rng.choice(len(Lg), 200, replace=False), [int(np.argmax(Lg))]])
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), wl.particles[sample], wl.scan,
+                              wl.sigma_hit, parity=True, trilinear=True)
+    check_logw(Lg[sample], Lo)
+    assert abs(wg.astype(np.float64).sum() - 1.0) <= 1e-5
+    m.close()
+
+
 def test_trilinear_building_subset(torch_cuda, mcl):
     torch = torch_cuda
     wl = scenes.os064_building(P=1500, dtype=scenes.I16)
