@@ -21,6 +21,10 @@
 // use the stored integer q (d = q * scale): LOGPROD accumulates q^2 and the
 // chunk sum is multiplied by scale^2 once; SUM folds scale^2 into the exponent
 // constant. A point without a stored value reads +tau (q = 32767 for int16).
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "mcl_internal.h"
 
 namespace mcl {
@@ -52,11 +56,57 @@ void* pick(int kind, int layout, int dtype, int mode, const SensorShape& sh, boo
   return nullptr;
 }
 
-cudaError_t prepare(void* f, int smem) {
+// Shared memory / L1 split of the SM's unified array. The kernel needs `smem`
+// bytes per CTA; whatever the carveout leaves is L1, which holds the brick
+// index and (trilinear read) the corner values. The carveout is sized for the
+// resident CTAs, at most kL1Blocks of them, instead of the largest shared
+// configuration: 176.9 -> 134.0 ms for the 1M x 65,536 building (nearest),
+// 599 -> 559 ms (trilinear), 2.36 -> 2.07 ms for the dense hall (which gives
+// up two of its six CTAs for it). The hash-index kernels keep all the CTAs
+// their registers allow (6: 4 CTAs and a larger L1 measured 259 against
+// 211 ms): their probe loop needs the warps more than the L1. Chosen once
+// per (kernel, shape).
+#ifndef MCL_L1_BLOCKS
+#define MCL_L1_BLOCKS 4
+#endif
+constexpr int kL1Blocks = MCL_L1_BLOCKS;
+
+int l1_blocks(int kind) { return kind == MCL_MAP_BRICK ? 1 << 30 : kL1Blocks; }
+
+struct CarveKey {
+  void* f;
+  int smem, threads;
+  bool operator<(const CarveKey& o) const {
+    return f != o.f ? f < o.f : smem != o.smem ? smem < o.smem : threads < o.threads;
+  }
+};
+std::mutex g_carve_mu;
+std::map<CarveKey, int> g_carve;  // kernel -> carveout percent
+
+cudaError_t prepare(void* f, int smem, int threads, int max_blocks) {
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              cudaSharedmemCarveoutMaxShared);
+  int pct = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_carve_mu);
+    auto it = g_carve.find(CarveKey{f, smem, threads});
+    if (it != g_carve.end()) pct = it->second;
+  }
+  if (pct < 0) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    int bps = 0, dev = 0, per_sm = 0, reserved = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess) return e;
+    const long long need = (long long)std::min(bps, max_blocks) * (smem + reserved);
+    pct = per_sm > 0 && bps > 0 ? (int)std::min<long long>(100, (100 * need + per_sm - 1) / per_sm) : 100;
+    std::lock_guard<std::mutex> lk(g_carve_mu);
+    g_carve[CarveKey{f, smem, threads}] = pct;
+  }
+  return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
 }  // namespace
@@ -71,7 +121,7 @@ cudaError_t sensor_occupancy(int kind, int layout, int dtype, int mode, const Se
   void* f = pick(kind, layout, dtype, mode, sh);
   if (!f) return cudaErrorInvalidValue;
   const int smem = sensor_smem_bytes(sh);
-  cudaError_t e = prepare(f, smem);
+  cudaError_t e = prepare(f, smem, sh.threads, l1_blocks(kind));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, sh.threads, smem);
 }
@@ -81,7 +131,7 @@ cudaError_t launch_sensor(int kind, int layout, int dtype, const SensorArgs& a,
   void* f = pick(kind, layout, dtype, a.mode, sh);
   if (!f) return cudaErrorInvalidValue;
   const int smem = sensor_smem_bytes(sh);
-  cudaError_t e = prepare(f, smem);
+  cudaError_t e = prepare(f, smem, sh.threads, l1_blocks(kind));
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<SensorArgs*>(&a)};
   return cudaLaunchKernel(f, dim3(sh.grid), dim3(sh.threads), args, (size_t)smem, s);
@@ -92,7 +142,7 @@ cudaError_t sensor_batch_occupancy(int kind, int layout, int dtype, int mode, co
   void* f = pick(kind, layout, dtype, mode, sh, true);
   if (!f) return cudaErrorInvalidValue;
   const int smem = sensor_smem_bytes(sh);
-  cudaError_t e = prepare(f, smem);
+  cudaError_t e = prepare(f, smem, sh.threads, l1_blocks(kind));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, sh.threads, smem);
 }
@@ -102,7 +152,7 @@ cudaError_t launch_sensor_batch(int kind, int layout, int dtype, const BatchArgs
   void* f = pick(kind, layout, dtype, b.base.mode, sh, true);
   if (!f) return cudaErrorInvalidValue;
   const int smem = sensor_smem_bytes(sh);
-  cudaError_t e = prepare(f, smem);
+  cudaError_t e = prepare(f, smem, sh.threads, l1_blocks(kind));
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<BatchArgs*>(&b)};
   return cudaLaunchKernel(f, dim3(sh.grid), dim3(sh.threads), args, (size_t)smem, s);
