@@ -556,10 +556,12 @@ mcl_status mcl_filter_destroy(mcl_filter_t f);
  * sessions that are not already on the GPU into one batched step as soon as
  * one of max_in_flight slots (each with its own stream) is free, so scans
  * that arrive while others run are admitted and their work overlaps on the
- * device (continuous batching). Each session keeps at most one queued scan:
- * a newer scan supersedes a queued, unstarted one (its ticket completes as
- * MCL_RESULT_SUPERSEDED). Latency is measured from submission to the host
- * seeing the step complete. */
+ * device (continuous batching); the sessions that have waited longest go
+ * first, up to max_batch per step. Each session keeps at most one queued
+ * scan: a newer scan supersedes a queued, unstarted one (its ticket completes
+ * as MCL_RESULT_SUPERSEDED) and its odometry increment is composed with the
+ * newer scan's (body frame, FP64), so the motion is not lost. Latency is
+ * measured from submission to the host seeing the step complete. */
 typedef struct mcl_server_s* mcl_server_t;
 typedef struct mcl_session_s* mcl_session_t;
 typedef uint64_t mcl_ticket_t;

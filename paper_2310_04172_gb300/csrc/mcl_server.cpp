@@ -38,6 +38,31 @@ struct Ticket {
 
 struct Slot;
 
+// Body-frame increment a followed by b (each relative to the body at its
+// start), in FP64: t = t_a + R_a t_b, R = R_a R_b, angles read back as in the
+// motion update (R = Rz(yaw) Ry(pitch) Rx(roll), yaw in [-pi, pi)).
+void compose_increment(const float a[6], const float b[6], float out[6]) {
+  auto rot = [](double r, double p, double y, double R[9]) {
+    const double cr = std::cos(r), sr = std::sin(r), cp = std::cos(p), sp = std::sin(p),
+                 cy = std::cos(y), sy = std::sin(y);
+    R[0] = cy * cp; R[1] = cy * sp * sr - sy * cr; R[2] = cy * sp * cr + sy * sr;
+    R[3] = sy * cp; R[4] = sy * sp * sr + cy * cr; R[5] = sy * sp * cr - cy * sr;
+    R[6] = -sp;     R[7] = cp * sr;                R[8] = cp * cr;
+  };
+  double A[9], B[9], C[9];
+  rot(a[3], a[4], a[5], A);
+  rot(b[3], b[4], b[5], B);
+  for (int r = 0; r < 3; ++r) {
+    out[r] = (float)((double)a[r] + A[3 * r] * b[0] + A[3 * r + 1] * b[1] + A[3 * r + 2] * b[2]);
+    for (int c = 0; c < 3; ++c) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+  }
+  out[3] = (float)std::atan2(C[7], C[8]);
+  out[4] = (float)std::asin(std::fmin(1.0, std::fmax(-1.0, -C[6])));
+  double yaw = std::atan2(C[3], C[0]);
+  if (yaw >= 3.141592653589793) yaw = -3.141592653589793;
+  out[5] = (float)yaw;
+}
+
 }  // namespace
 
 struct mcl_session_s {
@@ -67,6 +92,7 @@ struct mcl_session_s {
   bool pending_delta = false;
   float delta[6] = {0, 0, 0, 0, 0, 0};
   mcl_ticket_t pending_ticket = 0;
+  double pending_since = 0;  // when the session last became pending (kept on supersede)
   // running step
   bool in_flight = false;
   bool closing = false;
@@ -295,9 +321,15 @@ void scheduler(mcl_server_s* S) {
       if (!sl->busy) free_slot = sl;
     std::vector<mcl_session_s*> take;
     if (!S->stop && !S->paused && free_slot) {
+      // the sessions that have waited longest first (since their first queued
+      // scan, whatever superseded it), up to max_batch of them
       const int cap = S->desc.max_batch > 0 ? S->desc.max_batch : S->desc.max_sessions;
+      std::vector<std::pair<double, mcl_session_s*>> ready;
       for (mcl_session_s* ss : S->sessions)
-        if (ss->pending && !ss->in_flight && !ss->closing && (int)take.size() < cap) take.push_back(ss);
+        if (ss->pending && !ss->in_flight && !ss->closing) ready.emplace_back(ss->pending_since, ss);
+      std::stable_sort(ready.begin(), ready.end(),
+                       [](const auto& a, const auto& b) { return a.first < b.first; });
+      for (size_t i = 0; i < ready.size() && (int)take.size() < cap; ++i) take.push_back(ready[i].second);
     }
     if (take.empty()) {
       S->cv.wait_for(lk, std::chrono::milliseconds(2));
@@ -468,22 +500,34 @@ mcl_status mcl_submit_scan(mcl_session_t ss, const float* scan, int64_t N, const
   mcl_server_s* S = ss->srv;
   std::lock_guard<std::mutex> lk(S->mu);
   if (ss->closing) return fail(MCL_EINVAL, "submit_scan: session is closing");
+  const double now = now_s();
   if (ss->pending) {  // latest scan wins: the queued, unstarted one is superseded
     auto it = S->tickets.find(ss->pending_ticket);
     if (it != S->tickets.end()) it->second.status = MCL_RESULT_SUPERSEDED;
     ++S->superseded;
+    // the robot still moved: the superseded scan's increment is kept, composed
+    // with the new one
+    if (ss->pending_delta && delta) {
+      float c[6];
+      compose_increment(ss->delta, delta, c);
+      std::copy(c, c + 6, ss->delta);
+    } else if (delta) {
+      std::copy(delta, delta + 6, ss->delta);
+    }
+    ss->pending_delta = ss->pending_delta || delta != nullptr;
   } else {
     ss->stage_next = 1 - ss->stage_next;  // the other buffer may be in use by the running step
+    ss->pending_since = now;
+    ss->pending_delta = delta != nullptr;
+    if (delta) std::copy(delta, delta + 6, ss->delta);
   }
   // the queued scan lives in h_stage[1 - stage_next]
   std::memcpy(ss->h_stage[1 - ss->stage_next], scan, (size_t)N * 12);
   ss->pending = true;
   ss->pending_N = N;
-  ss->pending_delta = delta != nullptr;
-  if (delta) std::copy(delta, delta + 6, ss->delta);
   const mcl_ticket_t t = S->next_ticket++;
   Ticket tk;
-  tk.t_submit = now_s();
+  tk.t_submit = now;
   S->tickets[t] = tk;
   ss->pending_ticket = t;
   *out = t;

@@ -163,6 +163,57 @@ def test_admission_supersede_timeout_and_close(env):
     srv.close()
 
 
+def _compose(a, b):
+    """Body-frame increment a then b, FP64 (t = t_a + R_a t_b, R = R_a R_b)."""
+    def rot(r, p, y):
+        cr, sr, cp, sp, cy, sy = np.cos(r), np.sin(r), np.cos(p), np.sin(p), np.cos(y), np.sin(y)
+        return np.array([[cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr],
+                         [sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr],
+                         [-sp, cp * sr, cp * cr]])
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    A, B = rot(*a[3:]), rot(*b[3:])
+    C = A @ B
+    t = a[:3] + A @ b[:3]
+    ang = [np.arctan2(C[2, 1], C[2, 2]), np.arcsin(np.clip(-C[2, 0], -1, 1)), np.arctan2(C[1, 0], C[0, 0])]
+    return np.concatenate([t, ang]).astype(np.float32)
+
+
+def test_superseded_odometry_is_composed(env):
+    """A superseded scan's odometry increment is not lost: the step that runs
+    moves the particles by both increments, composed."""
+    import torch
+    mcl, room, hall, bld, maps = env
+    sig = [0.01, 0.01, 0.005, 0.002, 0.002, 0.005]
+    d1 = np.float32([0.1, 0.0, 0.0, 0.0, 0.0, 0.3])
+    d2 = np.float32([0.05, 0.02, 0.0, 0.0, 0.0, 0.1])
+    srv = mcl.Server(1 << 30, 2, max_in_flight=2)
+    ss = srv.open(maps["room"], room.particles, 2048, sigma_hit=room.sigma_hit, motion_sigma=sig, seed=9)
+    srv.pause(True)
+    t1 = ss.submit(room.scan, d1)
+    t2 = ss.submit(room.scan, d2)                        # supersedes t1
+    srv.pause(False)
+    assert srv.wait(t1, 10_000)["status"] == mcl.MCL_RESULT_SUPERSEDED
+    r = srv.wait(t2, 10_000)
+    assert r["status"] == mcl.MCL_RESULT_DONE
+    scan = torch.from_numpy(room.scan).cuda()
+    prm = mcl.sensor_params(room.sigma_hit)
+    got = r["estimate"]["mean_pose"]
+    for delta, same in ((_compose(d1, d2), True), (d2, False)):
+        f = mcl.Filter(maps["room"], torch.from_numpy(room.particles).cuda(), max_points=2048, params=prm,
+                       motion_sigma=sig, seed=9, use_graph=False)
+        est = mcl.estimate_buffer()
+        f.step(scan, delta, est)
+        mcl.mcl_sync()
+        ref = mcl.estimate_to_dict(est)["mean_pose"]
+        if same:
+            np.testing.assert_allclose(got, ref, rtol=0, atol=1e-5)
+        else:
+            assert np.abs(np.asarray(got[:3]) - np.asarray(ref[:3])).max() > 0.05
+        f.close()
+    ss.close()
+    srv.close()
+
+
 def test_score_map_and_trilinear_sessions_match_single_calls(env):
     """Sessions on a score map (SUM) and with the trilinear read, served in one
     batch beside a plain session: each session's weights equal the single
