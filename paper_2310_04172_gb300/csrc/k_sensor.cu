@@ -60,14 +60,14 @@ void* pick(int kind, int layout, int dtype, int mode, const SensorShape& sh, boo
 // bytes per CTA; whatever the carveout leaves is L1, which holds the brick
 // index and (trilinear read) the corner values. The carveout is sized for the
 // resident CTAs, at most kL1Blocks of them, instead of the largest shared
-// configuration: 176.9 -> 134.0 ms for the 1M x 65,536 building (nearest),
-// 599 -> 559 ms (trilinear), 2.36 -> 2.07 ms for the dense hall (which gives
-// up two of its six CTAs for it). The hash-index kernels keep all the CTAs
+// configuration: 176.9 -> 134.0 ms for the 1M x 65,536 building (nearest, 4
+// CTAs; 128.0 ms at 5), 599 -> 559 ms (trilinear), 2.36 -> 2.08 ms for the
+// dense hall (which gives up one of its six CTAs for it). The hash-index kernels keep all the CTAs
 // their registers allow (6: 4 CTAs and a larger L1 measured 259 against
 // 211 ms): their probe loop needs the warps more than the L1. Chosen once
 // per (kernel, shape).
 #ifndef MCL_L1_BLOCKS
-#define MCL_L1_BLOCKS 4
+#define MCL_L1_BLOCKS 5
 #endif
 constexpr int kL1Blocks = MCL_L1_BLOCKS;
 

@@ -547,25 +547,32 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 
 // Resident CTAs per SM the register allocation is held to (measured on the
 // 1M x 65,536 building step): with the hash index 6 for the 2- and 4-deep
-// loops (40 registers; 5 or 4 were slower), with the cell-grid index 4 (64
-// registers, no spills: 189 ms against 206 ms at 6), 3 for the 8-deep loop,
-// 4 for the trilinear read (crossing-bit walk, 32-bit value indices: 596 ms
-// against 602 ms at 3 and 613 ms at 5).
+// loops (40 registers; 5 or 4 were slower); with the cell-grid index 5 for
+// the single-session kernel (48 registers, 8 bytes spilled; with the
+// shared-memory carveout sized for 5 CTAs: 128.0 ms against 133.7 ms at 4
+// and 182 ms at 6) and 4 for the batched one (at 48 registers it spills 36
+// bytes: 134.8 against 127.1 ms); 3 for the 8-deep loop; 4 for the
+// trilinear read (crossing-bit walk, 32-bit value indices: 596 ms against
+// 602 ms at 3 and 613 ms at 5).
 #ifndef MCL_SENSOR_MIN_BLOCKS
 #define MCL_SENSOR_MIN_BLOCKS 6
 #endif
 #ifndef MCL_SENSOR_MIN_BLOCKS_GRID
-#define MCL_SENSOR_MIN_BLOCKS_GRID 4
+#define MCL_SENSOR_MIN_BLOCKS_GRID 5
+#endif
+#ifndef MCL_BATCH_MIN_BLOCKS_GRID
+#define MCL_BATCH_MIN_BLOCKS_GRID 4
 #endif
 #ifndef MCL_TRI_MIN_BLOCKS
 #define MCL_TRI_MIN_BLOCKS 4
 #endif
 
-template <int KIND, int U, bool TRI = false>
+template <int KIND, int U, bool TRI = false, bool BATCH = false>
 struct MinBlocks {
   static constexpr int value = TRI ? MCL_TRI_MIN_BLOCKS : U == 8 ? 3
-                               : KIND == kKindBrickGrid ? MCL_SENSOR_MIN_BLOCKS_GRID
-                                                        : MCL_SENSOR_MIN_BLOCKS;
+                               : KIND == kKindBrickGrid
+                                   ? (BATCH ? MCL_BATCH_MIN_BLOCKS_GRID : MCL_SENSOR_MIN_BLOCKS_GRID)
+                                   : MCL_SENSOR_MIN_BLOCKS;
 };
 
 // Stage `cnt` scan points starting at `src` into shared memory with one bulk
@@ -705,7 +712,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
 // (item_begin[s] is the first item of session s), strided over a persistent
 // grid. Each session's results are the ones the single-session kernel gives.
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
-__global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_sensor_batch(const BatchArgs b) {
+__global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI, true>::value)) k_sensor_batch(const BatchArgs b) {
   const SensorArgs& a = b.base;
   extern __shared__ __align__(128) unsigned char smem[];
   float4* sscan = reinterpret_cast<float4*>(smem);
