@@ -808,6 +808,8 @@ mcl_status mcl_resample_noalloc(const float* w, int64_t P, double r, int32_t* id
   if (pin && pin == pout) return fail(MCL_EINVAL, "resample_noalloc: particles_in and particles_out alias");
   if (!aligned(w, 4) || !aligned(idx, 4) || !aligned(pin, 4) || !aligned(pout, 4))
     return fail(MCL_EINVAL, "resample_noalloc: misaligned pointer");
+  // the scope records pooled events only; it allocates no device memory
+  PhaseScope ps(MCL_PHASE_RESAMPLE, (cudaStream_t)stream, resample_kernels((int)P));
   MCL_CUDA(launch_resample_static(w, (int)P, r, idx, pin, pout, (cudaStream_t)stream));
   return MCL_OK;
 }

@@ -5,9 +5,10 @@ allocation after start-up (cudaMalloc and cudaFree can block, and cudaFree
 synchronises the device), or a plug-in whose host application owns every
 device allocation. For them the library keeps the resampling scratch in a
 static device array (at most 2^20 particles). This test calls the entry point
-through the C ABI and checks it against mcl_resample, bit for bit, on two
-calls in a row; it runs last so that a failure here leaves every other test
-already run.
+through the C ABI and checks it against mcl_resample, bit for bit, on calls
+in a row, the last at the array's limit of 2^20 particles (every tile entry
+of the scratch in use); it runs last so that a failure here leaves every
+other test already run.
 """
 import ctypes
 
@@ -35,7 +36,7 @@ def test_resample_noalloc_matches_resample_twice():
     torch.cuda.set_device(0)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rng = np.random.default_rng(2024)
-    for call, (P, r) in enumerate([(1_000_000, 0.37), (4097, 0.81)]):
+    for call, (P, r) in enumerate([(1_000_000, 0.37), (4097, 0.81), (1 << 20, 0.52)]):
         w, parts = _inputs(rng, P)
         idx_ref = torch.empty(P, dtype=torch.int32, device="cuda")
         out_ref = torch.empty_like(parts)
