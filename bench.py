@@ -53,6 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--pipeline", type=int, default=0, help="0 auto, 1 off, 2 on")
     ap.add_argument("--order", type=int, default=0, help="particle order: 0 auto, 1 given, 2 spatial")
+    ap.add_argument("--item-order", type=int, default=0,
+                    help="work-item order: 0 auto, 1 chunk-major, 2 sweeps, 3 dynamic sweeps")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
     ap.add_argument("--index", type=int, default=0, help="brick index: 0 auto, 1 hash, 2 cell grid")
     ap.add_argument("--mode", default="headline",
@@ -63,7 +65,9 @@ def parse_args(argv=None):
                          "filter steps (motion, sensor, estimate, resampling) as separate calls, as one "
                          "call and replayed from a CUDA graph; variants (or trilinear): the 1M x 65,536 "
                          "step with SUM on the TSDF, SUM on an FP16 score map and the trilinear read")
-    ap.add_argument("--no-serving", action="store_true", help="skip the serving probe of the headline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving run of the headline")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the weight-error report and the storage/form comparison of the headline")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     ap.add_argument("--filter-workloads", default="room,hall",
                     help="--mode filter: comma list of room, hall")
@@ -178,11 +182,14 @@ def energy(clocks: dict, ms_per_step: float, evals_per_step: float):
 
 
 # ------------------------------------------------------------------ workload
-def make_workload(args, rank: int):
+def make_workload(args, rank: int, with_f32: bool = False):
+    """The building workload; with_f32 also voxelises FP32 values (the
+    reference values of the weight-error report and the FP32 comparison)."""
     import scenes
     dt = {"f32": scenes.F32, "f16": scenes.F16, "i16": scenes.I16}[args.dtype]
+    dts = tuple(sorted({dt, scenes.F32})) if with_f32 else None
     return scenes.os064_building(P=args.particles, dtype=dt, seed=3, azimuths=args.azimuths,
-                                 size=args.building, floors=args.floors)
+                                 size=args.building, floors=args.floors, dtypes=dts)
 
 
 def rank_particles(wl, rank: int):
@@ -350,7 +357,8 @@ def run_ours(args):
     from paper_2310_04172_gb300 import mcl
     mcl.lib()
 
-    wl = make_workload(args, rank)
+    precision_on = rank == 0 and not args.no_precision
+    wl = make_workload(args, rank, with_f32=precision_on)
     parts_np = rank_particles(wl, rank)
     P, N = len(parts_np), len(wl.scan)
     m = mcl.map_from_scene(wl.map, args.layout, args.index)
@@ -366,7 +374,8 @@ def run_ours(args):
     offsets = scenes.uniform(11 + rank, 200, args.steps + args.warmup + 64)
     prm = mcl.sensor_params(sigma_hit=wl.sigma_hit, points_per_chunk=args.chunk,
                             lanes_per_particle=args.lanes, particles_per_item=args.ppi,
-                            unroll=args.unroll, pipeline=args.pipeline, particle_order=args.order)
+                            unroll=args.unroll, pipeline=args.pipeline, particle_order=args.order,
+                            item_order=args.item_order)
     plan = mcl.mcl_sensor_plan_get(m, P, N, prm)
 
     def step(k, s):
@@ -450,9 +459,19 @@ def run_ours(args):
                "sample": f"{n} of {P} particles x {N} points, sensor update + normalise + "
                          f"resample, {dt:.1f} s (FP64, OpenMP over particles)"}
 
+    precision = forms = None
+    if precision_on:
+        try:
+            precision, forms = precision_block(torch, mcl, wl, m, parts, scan, prm, sensor_ms, args)
+        except Exception as e:  # the headline line is printed whatever happens here
+            precision = {"error": f"{type(e).__name__}: {e}"}
+
     serving = None
     if rank == 0 and not args.no_serving:
-        serving = serving_probe(mcl, m, wl, capacity=value, seconds=args.serving_seconds)
+        try:
+            serving = serving_block(mcl, args.serving_seconds)
+        except Exception as e:
+            serving = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         cfg = config_dict(args, wl)
@@ -465,7 +484,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roof, "gather_roofline": gather, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(), "serving": serving,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
+            "precision": precision, "quantised_vs_plain_fp32": forms, "serving": serving,
             "energy": energy(clocks.summary(), ms_max / args.steps, float(P) * N),
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["launches"]},
         }
@@ -604,41 +624,14 @@ def serving_sessions(mcl, srv, maps, n, p_lo, p_hi, seed):
     return out
 
 
-def serving_probe(mcl, m_bld, wl, capacity, seconds):
-    """Short continuous-batching run beside the headline: 16 sessions over the
-    building map and a dense FP16 hall (VLP-16 scans), P log-uniform in
-    [1e3, 2e5], Poisson 10-20 Hz scaled so the offered load is 70 % of the
-    measured step throughput."""
+def serving_block(mcl, seconds: float):
+    """The 64-session serving workload: 64 robot sessions over 8 maps (4 dense
+    512x512x128 FP16 halls, 4 brick int16 160x160x20 m buildings), P
+    log-uniform in [1e3, 1e6], scans of 28,800 (halls) and 65,536 (buildings)
+    points, Poisson 10-20 Hz per session: first at the nominal rates (offered
+    load far above one GPU: the latest scan of a session wins), then scaled to
+    70 % of the achieved throughput. `seconds` of arrivals per load level."""
     import scenes
-    hall = scenes.vlp16_multiroom(P=16, dtype=scenes.F16, seed=12)
-    m_hall = mcl.map_from_scene(hall.map)
-    srv = mcl.Server(64 << 30, 64, max_in_flight=2, max_batch=SERVING_MAX_BATCH)
-    sess = serving_sessions(mcl, srv, [(m_bld, wl.scene, wl.scan), (m_hall, hall.scene, hall.scan)],
-                            16, 1e3, 2e5, 21)
-    offered = sum(rt * s.P * len(sc) for s, sc, rt in sess)
-    scale = 0.7 * capacity / offered
-    out = serving_measure(mcl, srv, sess, seconds, scale, 5)
-    out.update({"sessions": 16, "maps": 2, "rate_scale": scale,
-                "load": "Poisson, 10-20 Hz per session scaled to 70% of the measured step throughput"})
-    for s, _, _ in sess:
-        s.close()
-    srv.close()
-    m_hall.close()
-    return out
-
-
-def run_serving(args):
-    """64 robot sessions over 8 maps (4 dense 512x512x128 FP16 halls, 4 brick int16
-    160x160x20 m buildings), P log-uniform in [1e3, 1e6], scans of 28,800 (halls)
-    and 65,536 (buildings) points, Poisson 10-20 Hz per session: first at the
-    nominal rates (offered load far above capacity: latest scan wins), then
-    scaled to 70 % of the achieved throughput."""
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import scenes
-    from paper_2310_04172_gb300 import mcl
-    torch.cuda.set_device(0)
     maps = []
     for k in range(4):
         hall = scenes.vlp16_multiroom(P=16, dtype=scenes.F16, seed=11 + k)
@@ -647,32 +640,158 @@ def run_serving(args):
         maps.append((mcl.map_from_scene(bld.map), bld.scene, bld.scan))
     srv = mcl.Server(200 << 30, 64, max_in_flight=2, max_batch=SERVING_MAX_BATCH)
     sess = serving_sessions(mcl, srv, maps, 64, 1e3, 1e6, 31)
-    nominal = serving_measure(mcl, srv, sess, args.serving_seconds * 2, 1.0, 7)
+    nominal = serving_measure(mcl, srv, sess, seconds, 1.0, 7)
     scale = 0.7 * nominal["achieved_evals_per_s"] / nominal["offered_evals_per_s"]
-    scaled = serving_measure(mcl, srv, sess, args.serving_seconds * 2, scale, 9)
-    line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
-            "value": scaled["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
-            "n_gpus": 1, "data": "synthetic", "dtype": "f32",
-            "config": {"workload": "64 sessions over 4 dense FP16 halls + 4 int16 brick buildings",
-                       "policy": f"max_in_flight 2, max_batch {SERVING_MAX_BATCH}, longest-waiting sessions first",
-                       "particles_total": int(sum(s.P for s, _, _ in sess))},
-            "nominal_load": nominal, "scaled_load_70pct": dict(scaled, rate_scale=scale)}
-    print(json.dumps(line), flush=True)
-    for s, _, _ in sess:
-        s.close()
+    scaled = serving_measure(mcl, srv, sess, seconds, scale, 9)
+    out = {"sessions": len(sess), "maps": len(maps),
+           "workload": "64 sessions over 4 dense FP16 halls + 4 int16 brick buildings",
+           "policy": f"max_in_flight 2, max_batch {SERVING_MAX_BATCH}, longest-waiting sessions first",
+           "particles_total": int(sum(x.P for x, _, _ in sess)),
+           "nominal_load": nominal, "scaled_load_70pct": dict(scaled, rate_scale=scale)}
+    for x, _, _ in sess:
+        x.close()
     srv.close()
-    for m, _, _ in maps:
-        m.close()
+    for mm, _, _ in maps:
+        mm.close()
+    return out
+
+
+# ------------------------------------------------------------------ weight error against the oracle
+def weight_report(Lg, wg, Lo) -> dict:
+    """Errors of one GPU result (its log-weights Lg and its own normalised
+    weights wg) against the FP64 oracle's log-weights Lo of the same particles
+    (Eq. 3 per point, normalisation as in Sec. V-A)."""
+    import numpy as np
+    Lg = np.asarray(Lg, np.float64)
+    wg = np.asarray(wg, np.float64)
+    wo = np.exp(Lo - Lo.max())
+    wo /= wo.sum()
+    jo = int(np.argmax(Lo))
+    near = np.flatnonzero(Lo >= Lo[jo] - 30.0)  # weights within e^-30 of the best
+    ro = np.exp(Lo[near] - Lo[jo])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rg = wg[near] / wg[jo]
+    k = min(100, len(Lo))
+    top_o = set(np.argsort(-Lo, kind="stable")[:k].tolist())
+    top_g = set(np.argsort(-Lg, kind="stable")[:k].tolist())
+    return {"max_rel_logw_err": float(np.max(np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo)))),
+            "max_abs_logw_err": float(np.max(np.abs(Lg - Lo))),
+            "tv_distance": float(0.5 * np.abs(wg - wo).sum()),
+            "particles_within_30_nats": int(len(near)),
+            "max_rel_w_err_within_30_nats": float(np.max(np.abs(rg - ro) / ro)),
+            "top100_agreement": len(top_o & top_g) / k,
+            "argmax_agrees": bool(int(np.argmax(Lg)) == jo)}
+
+
+def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, args):
+    """Weight error of the headline form (int16 map) and of the same step on
+    FP32 map values against the FP64 oracle (quality mode: FP64 throughout on
+    the FP32 values) on two seeded 10,000-particle subsets: the headline's
+    global-localisation cloud, and a tracking cloud Gaussian about the true
+    pose (0.2 m, 2 deg), where more particles carry weight. Then the same
+    1M x 65,536 update on the FP32 map, in the same kernel shape and in the
+    plain per-session form (particles as given, chunk-major items), and the
+    int16 map in a graph-captured batch of four 250,000-particle sessions."""
+    import numpy as np
+    import oracle
+    import scenes
+    maps = wl.info["maps"]
+    P, N = len(wl.particles), len(wl.scan)
+    m32 = mcl.map_from_scene(maps[scenes.F32])
+    om = oracle.Map.from_scene_map(maps[scenes.F32])
+    rng = np.random.default_rng(4)
+    subsets = {"global_10000": wl.particles[np.sort(rng.choice(P, 10_000, replace=False))],
+               "tracking_10000": scenes.particles_gaussian(wl.pose, 10_000, 0.2, 2.0, 41)}
+    rep = {"reference": "FP64 oracle, quality mode (FP64 throughout on the FP32 map values)",
+           "subsets": {}}
+    for name, sub in subsets.items():
+        t0 = time.perf_counter()
+        Lo = oracle.sensor_update(om, sub, wl.scan, wl.sigma_hit, parity=False)
+        oracle_s = time.perf_counter() - t0
+        dsub = torch.from_numpy(np.ascontiguousarray(sub)).to(parts.device)
+        res = {"oracle_s": oracle_s}
+        for label, mm in (("i16", m_head), ("f32", m32)):
+            lg = torch.empty(len(sub), device=parts.device)
+            wg = torch.empty(len(sub), device=parts.device)
+            mcl.mcl_sensor_update(mm, dsub, scan, prm, lg, wg)
+            mcl.mcl_sync()
+            res[label] = weight_report(lg.cpu().numpy(), wg.cpu().numpy(), Lo)
+        rep["subsets"][name] = res
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        e.synchronize()
+        return a.elapsed_time(e) / reps
+
+    logw = torch.empty(P, device=parts.device)
+    w = torch.empty(P, device=parts.device)
+    plain = mcl.sensor_params(wl.sigma_hit, particle_order=1, item_order=1)
+    ms_f32 = timed(lambda: mcl.mcl_sensor_update(m32, parts, scan, prm, logw, w))
+    ms_f32_plain = timed(lambda: mcl.mcl_sensor_update(m32, parts, scan, plain, logw, w))
+    S = 4
+    per = P // S
+    sess_parts = [parts[k * per:(k + 1) * per].contiguous() for k in range(S)]
+    outs = [(torch.empty(per, device=parts.device), torch.empty(per, device=parts.device))
+            for _ in range(S)]
+    batch = mcl.Batch([{"map": m_head, "particles": sess_parts[k], "scan": scan,
+                        "logw": outs[k][0], "w": outs[k][1]} for k in range(S)], use_graph=True)
+    ms_batch = timed(batch.run)
+    kernels = batch.info()["kernels_per_run"]
+    batch.close()
+    m32.close()
+    ev = float(P) * N
+
+    def form(ms):
+        return {"ms_per_update": ms, "evals_per_s": ev / (ms / 1e3)}
+
+    err_i16 = rep["subsets"]["tracking_10000"]["i16"]
+    err_f32 = rep["subsets"]["tracking_10000"]["f32"]
+    forms = {
+        "f32_same_shape": form(ms_f32),
+        "f32_plain_per_session": dict(form(ms_f32_plain), shape="particles as given, chunk-major items"),
+        "i16_single": form(head_kernel_ms),
+        "i16_batched_graph_4x250000": dict(form(ms_batch), kernels_per_run=kernels),
+        "speedup_i16_batched_vs_f32_same_shape": ms_f32 / ms_batch,
+        "speedup_i16_batched_vs_f32_plain": ms_f32_plain / ms_batch,
+        "at_weight_error": {"subset": "tracking_10000",
+                            "i16_tv_distance": err_i16["tv_distance"],
+                            "f32_tv_distance": err_f32["tv_distance"],
+                            "i16_max_rel_logw_err": err_i16["max_rel_logw_err"],
+                            "f32_max_rel_logw_err": err_f32["max_rel_logw_err"]},
+    }
+    return rep, forms
+
+
+def run_serving(args):
+    """The 64-session serving workload alone (see serving_block), with twice
+    the arrival time per load level."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    out = serving_block(mcl, args.serving_seconds * 2)
+    line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
+            "value": out["scaled_load_70pct"]["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "config": {k: out[k] for k in ("workload", "policy", "particles_total")},
+            "nominal_load": out["nominal_load"], "scaled_load_70pct": out["scaled_load_70pct"]}
+    print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ precision sweep
 def run_precision(args):
-    """The building workload stored as FP32, FP16 and int16: step throughput for
-    1M x 65,536, and weight error / top-100 agreement against the FP64 oracle
-    (quality mode, FP32 reference values) on a seeded 10,000-particle subset;
-    then the plain FP32 per-session form against the int16 batched
-    graph-captured form on four 250,000-particle sessions."""
+    """The building workload stored as FP32, FP16 and int16: update time for
+    1M x 65,536 and the weight report (weight_report) of each against the FP64
+    oracle (quality mode, FP32 values) on the two seeded 10,000-particle
+    subsets of precision_block."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -688,18 +807,15 @@ def run_precision(args):
     parts = torch.from_numpy(wl.particles).cuda()
     scan = torch.from_numpy(wl.scan).cuda()
     rng = np.random.default_rng(4)
-    sub = np.sort(rng.choice(P, 10_000, replace=False))
-    L_ref = oracle.sensor_update(oracle.Map.from_scene_map(maps[scenes.F32]), wl.particles[sub], wl.scan,
-                                 wl.sigma_hit, parity=False)
-    w_ref, *_ = oracle.normalise(L_ref)
-    top_ref = set(np.argsort(-L_ref)[:100].tolist())
+    subsets = {"global_10000": wl.particles[np.sort(rng.choice(P, 10_000, replace=False))],
+               "tracking_10000": scenes.particles_gaussian(wl.pose, 10_000, 0.2, 2.0, 41)}
+    om = oracle.Map.from_scene_map(maps[scenes.F32])
+    refs = {k: oracle.sensor_update(om, v, wl.scan, wl.sigma_hit, parity=False) for k, v in subsets.items()}
+    prm = mcl.sensor_params(wl.sigma_hit)
     out = {}
-    handles = {}
     for dt, name in ((scenes.F32, "f32"), (scenes.F16, "f16"), (scenes.I16, "i16")):
         m = mcl.map_from_scene(maps[dt])
-        handles[name] = m
         logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
-        prm = mcl.sensor_params(wl.sigma_hit)
         mcl.mcl_sensor_update(m, parts, scan, prm, logw, w)
         torch.cuda.synchronize()
         a, e = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -709,57 +825,22 @@ def run_precision(args):
         e.record()
         e.synchronize()
         ms = a.elapsed_time(e) / args.steps
-        ls = torch.empty(len(sub), device="cuda")
-        mcl.mcl_sensor_update(m, parts[torch.from_numpy(sub).cuda()].contiguous(), scan, prm, ls)
-        Lg = ls.cpu().numpy().astype(np.float64)
-        wg = np.exp(Lg - Lg.max())           # the GPU's weights, normalised here (not by the oracle)
-        wg /= wg.sum()
-        sel = w_ref >= 1e-6 * w_ref.max()
-        out[name] = {"ms_per_update": ms, "evals_per_s": P * N / (ms / 1e3),
-                     "map_bytes": int(maps[dt].values.nbytes),
-                     "max_rel_logw_err": float(np.max(np.abs(Lg - L_ref) / np.maximum(1, np.abs(L_ref)))),
-                     "max_rel_w_err_top": float(np.max(np.abs(wg[sel] - w_ref[sel]) / w_ref[sel])),
-                     "top100_agreement": len(top_ref & set(np.argsort(-Lg)[:100].tolist())) / 100.0}
-    # plain FP32 per-session form vs int16 batched graph-captured form, 4 sessions
-    S = 4
-    per = P // S
-    sess_parts = [parts[k * per:(k + 1) * per].contiguous() for k in range(S)]
-    outs = [(torch.empty(per, device="cuda"), torch.empty(per, device="cuda")) for _ in range(S)]
-    plain = mcl.sensor_params(wl.sigma_hit, particle_order=1, item_order=1)
-
-    def plain_step():
-        for k in range(S):
-            mcl.mcl_sensor_update(handles["f32"], sess_parts[k], scan, plain, outs[k][0], outs[k][1])
-
-    batch = mcl.Batch([{"map": handles["i16"], "particles": sess_parts[k], "scan": scan,
-                        "logw": outs[k][0], "w": outs[k][1]} for k in range(S)], use_graph=True)
-
-    def timed(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
-        a.record()
-        for _ in range(reps):
-            fn()
-        e.record()
-        e.synchronize()
-        return a.elapsed_time(e) / reps
-
-    ms_plain = timed(plain_step, args.steps)
-    ms_batch = timed(batch.run, args.steps)
-    batch.close()
+        res = {"ms_per_update": ms, "evals_per_s": P * N / (ms / 1e3),
+               "map_bytes": int(maps[dt].values.nbytes)}
+        for k, sub in subsets.items():
+            ds = torch.from_numpy(np.ascontiguousarray(sub)).cuda()
+            lg, wg = torch.empty(len(sub), device="cuda"), torch.empty(len(sub), device="cuda")
+            mcl.mcl_sensor_update(m, ds, scan, prm, lg, wg)
+            mcl.mcl_sync()
+            res[k] = weight_report(lg.cpu().numpy(), wg.cpu().numpy(), refs[k])
+        out[name] = res
+        m.close()
     line = {"mode": "precision", "metric": METRIC, "value": out["i16"]["evals_per_s"], "unit": UNIT,
             "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f32",
-            "config": {"workload": wl.name, "subset": 10_000,
-                       "reference": "FP64 oracle, quality mode, FP32 map values"},
-            "storage": out,
-            "plain_f32_per_session": {"sessions": S, "evals_per_s": P * N / (ms_plain / 1e3),
-                                      "ms": ms_plain},
-            "i16_batched_graph": {"sessions": S, "evals_per_s": P * N / (ms_batch / 1e3), "ms": ms_batch,
-                                  "max_rel_logw_err": out["i16"]["max_rel_logw_err"]}}
+            "config": {"workload": wl.name, "subsets": list(subsets),
+                       "reference": "FP64 oracle, quality mode (FP64 throughout on the FP32 map values)"},
+            "storage": out}
     print(json.dumps(line), flush=True)
-    for m in handles.values():
-        m.close()
     return 0
 
 

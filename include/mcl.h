@@ -209,14 +209,18 @@ typedef struct mcl_sensor_params {
   int32_t particle_order;     /* 0 (auto), 1 as given, 2 spatial (Morton-ordered buckets over
                                  the map extent): the order particles are evaluated in;
                                  no effect on results */
-  int32_t item_order;         /* 0 (auto), 1 chunk-major, 2 sweeps: the order of the (point
-                                 chunk, particle block) work items. Sweeps walk a few
-                                 particle blocks through every chunk at a time, each
-                                 resident CTA keeping one chunk, so the CTAs working at the
-                                 same time read the map around few (spatially ordered)
-                                 particles; auto takes sweeps for the nearest read of a
-                                 brick map once there are at least two items per resident
-                                 CTA. No effect on results */
+  int32_t item_order;         /* 0 (auto), 1 chunk-major, 2 sweeps, 3 dynamic sweeps: the
+                                 order of the (point chunk, particle block) work items.
+                                 Sweeps walk a few particle blocks through every chunk at a
+                                 time, so the CTAs working at the same time read the map
+                                 around few (spatially ordered) particles; in 2 each
+                                 resident CTA keeps one chunk (static striding), in 3 a
+                                 device counter hands the items out in order to whichever
+                                 CTA is free (which re-stages its item's chunk), so the
+                                 items in flight stay within about one sweep whatever each
+                                 chunk costs. Auto takes 3 for the nearest read of a brick
+                                 map once there are at least two items per resident CTA,
+                                 else 1. No effect on results */
 } mcl_sensor_params;
 
 /* Sensor update of P particles (device, P x 6 FP32) against one scan
@@ -308,7 +312,7 @@ typedef struct mcl_sensor_plan {
   int32_t threads, grid, blocks_per_sm, num_sms;
   int64_t n_items;          /* (chunk, particle block) work items */
   int64_t workspace_bytes;  /* library scratch for one call */
-  int32_t item_order;       /* 1 chunk-major, 2 sweeps */
+  int32_t item_order;       /* 1 chunk-major, 2 sweeps, 3 dynamic sweeps */
   int32_t blocks_per_sweep; /* particle blocks per sweep (all blocks: chunk-major) */
 } mcl_sensor_plan;
 

@@ -164,10 +164,11 @@ __device__ __forceinline__ typename Raw<DTYPE, MODE>::value load_raw_l1(const vo
   }
 }
 
-// Value read where nothing is stored, in the same units.
+// Value the nearest read takes where nothing is stored, in the same units
+// (its term is exactly zero under MCL_NEGLECT_OUTSIDE).
 template <int DTYPE, int MODE>
 __device__ __forceinline__ typename Raw<DTYPE, MODE>::value outside_value(const SensorArgs& a) {
-  return a.vout;
+  return a.vnear;
 }
 
 // Index of a brick value: 32-bit arithmetic for the cell-grid kind (at most
@@ -272,7 +273,7 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
   for (int u = 0; u < U; ++u) {
     if constexpr (KIND == MCL_MAP_DENSE) {
       dv[u] = s.dv[u];
-      use[u] = s.v[u] && (s.in[u] || !a.neglect);
+      use[u] = s.v[u];
     } else {
       uint32_t slot = kNoSlot;
       if constexpr (KIND == kKindBrickGrid) {
@@ -291,7 +292,7 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
       const bool st = slot != kNoSlot;
       dv[u] = st ? load_raw<DTYPE, MODE>(m.values, value_index<KIND>(slot, s.loc[u]))
                  : outside_value<DTYPE, MODE>(a);
-      use[u] = s.v[u] && (st || !a.neglect);
+      use[u] = s.v[u];
     }
   }
 }
@@ -692,6 +693,31 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
   init_barrier(bar_s);
   int loaded = -1;
   uint32_t parity = 0;
+  if (a.queue) {
+    // Dynamic order: thread 0 takes the next item from the device counter one
+    // item ahead; the barrier at the top of each step publishes it and is the
+    // point where every warp is done with the previous item.
+    __shared__ long long s_next[2];
+    if (threadIdx.x == 0) s_next[0] = (long long)atomicAdd(a.queue, 1ull);
+    for (int k = 0;; ++k) {
+      __syncthreads();
+      const long long item = s_next[k & 1];
+      if (item >= a.n_items) break;
+      if (threadIdx.x == 0) s_next[(k + 1) & 1] = (long long)atomicAdd(a.queue, 1ull);
+      int c, blk;
+      item_coords(item, a.nblk, a.K, a.sweep, c, blk);
+      const int p0 = blk * a.ppi;
+      const int pn = min(a.ppi, a.P - p0);
+      const int cnt = min(a.chunk, a.N - c * a.chunk);
+      if (c != loaded) {
+        if (!stage_chunk(sscan, bar_s, a.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
+        loaded = c;
+      }
+      process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, sscan, smat, a.mats, a.partial, a.P, c, p0,
+                                                        pn, cnt);
+    }
+    return;
+  }
   for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     int c, blk;
     item_coords(item, a.nblk, a.K, a.sweep, c, blk);

@@ -494,7 +494,7 @@ mcl_status check_params(const mcl_sensor_params* p) {
   if (p->pipeline < 0 || p->pipeline > 2) return fail(MCL_EINVAL, "sensor params: pipeline %d", p->pipeline);
   if (p->particle_order < 0 || p->particle_order > 2)
     return fail(MCL_EINVAL, "sensor params: particle_order %d", p->particle_order);
-  if (p->item_order < 0 || p->item_order > 2)
+  if (p->item_order < 0 || p->item_order > 3)
     return fail(MCL_EINVAL, "sensor params: item_order %d", p->item_order);
   return MCL_OK;
 }
@@ -519,8 +519,9 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   if (mcl_status rc = device_state(nullptr, &st)) return rc;
   SensorShape& sh = pl->sh;
   // Brick maps read nearest: map larger than L2, where the sweep item order
-  // pays (measured on GB300: 1M x 65,536 int16 bricks 184.2 -> 177.4 ms;
-  // slower for the L2-resident dense hall and the trilinear read).
+  // pays (measured on GB300: 1M x 65,536 int16 bricks 184.2 -> 177.4 ms
+  // static, 130.3 -> 113.8 ms handed out dynamically; slower for the
+  // L2-resident dense hall and the trilinear read).
   const bool brick_nearest = m->kind == MCL_MAP_BRICK && !(p->flags & MCL_TRILINEAR);
   sh.chunk = p->points_per_chunk ? p->points_per_chunk : 2048;
   sh.lanes = p->lanes_per_particle ? p->lanes_per_particle : 32;
@@ -569,9 +570,20 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   // least one CTA per chunk; auto takes it for nearest reads of brick maps
   // from two items per slot on.
   pl->sweep = pl->nblk;
-  const bool sweeps =
-      p->item_order == 2 || (p->item_order == 0 && brick_nearest && pl->n_items >= 2 * slots);
-  if (sweeps && pl->K > 1 && slots >= pl->K) {
+  pl->dynamic = false;
+  const bool auto_sweeps = p->item_order == 0 && brick_nearest && pl->n_items >= 2 * slots;
+  const bool sweeps = p->item_order == 2;
+  if ((p->item_order == 3 || auto_sweeps) && pl->K > 1 && slots >= pl->K) {
+    // Dynamic sweeps: the same numbering, items handed out in order by a
+    // device counter to whichever CTA is free, so the items in flight stay
+    // within about one sweep whatever the cost of each chunk (with static
+    // striding the CTAs of cheap chunks run ahead of the others, the CTAs in
+    // flight spread over many sweeps and the map reads of different
+    // particles no longer meet in L2: 9.75 against 6.06 DRAM bytes per
+    // evaluation at 200,000 x 65,536).
+    pl->sweep = (int)std::min<long long>(pl->nblk, std::max<long long>(1, slots / pl->K));
+    pl->dynamic = true;
+  } else if (sweeps && pl->K > 1 && slots >= pl->K) {
     pl->sweep = (int)std::min<long long>(pl->nblk, slots / pl->K);
     sh.grid = (int)std::min<long long>(pl->n_items, (long long)pl->sweep * pl->K);
   }
@@ -596,6 +608,8 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   o = align256(o + (pl->spatial ? (size_t)P * sizeof(int) : 0));
   pl->off_hist = o;
   o = align256(o + (pl->spatial ? order_hist_bytes() : 0));
+  pl->off_queue = o;
+  o = align256(o + sizeof(unsigned long long));
   pl->total = o;
   return MCL_OK;
 }
@@ -625,7 +639,7 @@ mcl_status mcl_sensor_plan_get(mcl_map_t m, int64_t P, int64_t N, const mcl_sens
   out->num_sms = pl.sms;
   out->n_items = pl.n_items;
   out->workspace_bytes = (int64_t)pl.total;
-  out->item_order = pl.sweep < pl.nblk ? 2 : 1;
+  out->item_order = pl.dynamic ? 3 : pl.sweep < pl.nblk ? 2 : 1;
   out->blocks_per_sweep = pl.sweep;
   return MCL_OK;
 }
@@ -697,8 +711,13 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
   a.vout = outside_raw(m);
+  a.vnear = nearest_fill(m, a.mode, a.neglect != 0);
   a.cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : c;
   a.store_scale = (q16 && p->mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
+  if (pl.dynamic) {
+    a.queue = (unsigned long long*)(ws + pl.off_queue);
+    MCL_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+  }
   {
     PhaseScope ps(MCL_PHASE_SENSOR, s);
     MCL_CUDA(launch_sensor(kernel_kind(m), m->view.layout, m->dtype, a, pl.sh, s));

@@ -245,6 +245,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     a.mode = kernel_mode(g.map, g.mode);
     a.neglect = g.neglect;
     score_constants(g.map, g.sigma, g.mode, &a);
+    a.vnear = nearest_fill(g.map, a.mode, a.neglect != 0);
     g.args.sessions = (const BatchSession*)(b->ws + off_tab[k]);
     g.args.item_begin = (const long long*)(b->ws + off_beg[k]);
     g.args.n_sessions = (int)g.sessions.size();

@@ -177,8 +177,16 @@ struct SensorArgs {
   long long n_items;
   int mode, neglect;
   float vout;          // value read where nothing is stored, in storage units (tau, or 32767 for I16)
+  // What the nearest read takes where nothing is stored: vout, or with
+  // MCL_NEGLECT_OUTSIDE a value whose term is exactly zero (0 for LOGPROD and
+  // score maps, +inf for SUM: exp(-inf) = 0), so that no per-point test of
+  // the flag is needed and the sums keep their bits.
+  float vnear;
   float cs;            // SUM exponent constant in storage units: -1/(2 sigma^2) (* scale^2 for I16)
   float store_scale;   // chunk sum -> real units: scale^2 for I16 in LOGPROD (sum of q^2), else 1
+  // Dynamic item order: a device counter (zero at launch) hands out the items
+  // in order, one at a time per CTA; NULL: static striding over the grid.
+  unsigned long long* queue = nullptr;
 };
 
 // Pose rows -> [R | t]; with rank, particle p's matrix goes to slot rank[p].

@@ -162,8 +162,8 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
   rc = time_knobs(best, &best_ms);
   default_ms = best_ms;
   // coordinate descent: each knob in turn over its candidate values, twice
-  const std::vector<int> chunks = {1024, 2048, 4096}, lanes = {32, 16}, ppis = {64, 128, 256},
-                         unrolls = {2, 4, 8}, pipes = {1, 2}, orders = {1, 2}, items = {1, 2};
+  const std::vector<int> chunks = {1024, 2048, 4096}, lanes = {32, 16}, ppis = {32, 64, 128, 256},
+                         unrolls = {2, 4, 8}, pipes = {1, 2}, orders = {1, 2}, items = {1, 2, 3};
   for (int round = 0; round < 2 && rc == MCL_OK; ++round) {
     auto sweep = [&](int Knobs::*field, const std::vector<int>& vals) {
       for (int v : vals) {

@@ -51,9 +51,10 @@ struct Plan {
   int K, nblk, blocks_per_sm, sms;
   int sweep;  // particle blocks per sweep of the item order (nblk: chunk-major)
   bool spatial;
+  bool dynamic;  // items handed out by a device counter (item order 3)
   long long n_items;
   size_t off_mats, off_scan, off_partial, off_logw, off_stats, off_ostats, off_est, off_key,
-      off_rank, off_hist, total;
+      off_rank, off_hist, off_queue, total;
 };
 
 // Enqueues one sensor update (pose matrices, scan packing, sensor kernel,
@@ -118,6 +119,12 @@ inline int kernel_mode(const mcl_map_s* m, int mode) { return m->score_sigma > 0
 inline float outside_raw(const mcl_map_s* m) {
   if (m->score_sigma > 0.f) return m->score_outside;
   return m->dtype == MCL_I16 ? 32767.0f : m->view.tau;
+}
+// The nearest read's value where nothing is stored (SensorArgs::vnear) for
+// kernel mode `kmode` on map m.
+inline float nearest_fill(const mcl_map_s* m, int kmode, bool neglect) {
+  if (!neglect) return outside_raw(m);
+  return kmode == MCL_SUM ? __builtin_huge_valf() : 0.0f;
 }
 // EINVAL unless the parameters fit the map (a score map needs SUM, its own
 // sigma and the nearest-voxel read).

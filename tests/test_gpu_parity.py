@@ -265,10 +265,12 @@ def test_particle_order_gives_identical_bits(torch_cuda, mcl, room, building_i16
 
 
 def test_item_order_gives_identical_bits(torch_cuda, mcl, building_i16):
-    """Chunk-major items and sweeps (each CTA keeping one chunk) write the
-    same partial sums: same bits, with ragged chunk and particle tails. Each
-    run follows a run on other particles, so an item that a schedule skipped
-    would leave another run's partial sums behind and fail the comparison."""
+    """Chunk-major items, static sweeps (each CTA keeping one chunk) and
+    dynamic sweeps (items handed out by a device counter) write the same
+    partial sums: same bits, with ragged chunk and particle tails. Each run
+    follows a run on other particles in another order, so an item that a
+    schedule skipped would leave another run's partial sums behind and fail
+    the comparison."""
     torch = torch_cuda
     wl = building_i16
     m = mcl.map_from_scene(wl.map)
@@ -277,9 +279,11 @@ def test_item_order_gives_identical_bits(torch_cuda, mcl, building_i16):
     other[:, :3] += np.float32(0.37)
     scan = wl.scan[: len(wl.scan) - 100]
     res = {}
-    for order in (2, 1, 0):
-        for kw in (dict(), dict(particles_per_item=64), dict(points_per_chunk=1024)):
-            run_sensor(torch, mcl, m, other, scan, wl.sigma_hit, item_order=3 - order if order else 0, **kw)
+    before = {3: 2, 2: 1, 1: 3, 0: 2}
+    for order in (3, 2, 1, 0):
+        for kw in (dict(), dict(particles_per_item=64), dict(points_per_chunk=1024),
+                   dict(particles_per_item=16)):
+            run_sensor(torch, mcl, m, other, scan, wl.sigma_hit, item_order=before[order], **kw)
             res[(order, tuple(kw.items()))] = run_sensor(torch, mcl, m, parts, scan, wl.sigma_hit,
                                                          item_order=order, **kw)
     for (order, kw), r in res.items():
@@ -288,15 +292,17 @@ def test_item_order_gives_identical_bits(torch_cuda, mcl, building_i16):
     plan = mcl.mcl_sensor_plan_get(m, len(parts), len(scan), mcl.sensor_params(0.1))
     K = -(-len(scan) // plan["points_per_chunk"])
     slots = plan["num_sms"] * plan["blocks_per_sm"]
-    assert plan["n_items"] >= 2 * slots                   # auto takes sweeps here
-    assert plan["item_order"] == 2 and plan["blocks_per_sweep"] == slots // K
-    assert plan["grid"] == plan["blocks_per_sweep"] * K
+    assert plan["n_items"] >= 2 * slots                   # auto takes dynamic sweeps here
+    assert plan["item_order"] == 3 and plan["blocks_per_sweep"] == slots // K
+    assert plan["grid"] == slots
+    static = mcl.mcl_sensor_plan_get(m, len(parts), len(scan), mcl.sensor_params(0.1, item_order=2))
+    assert static["item_order"] == 2 and static["grid"] == static["blocks_per_sweep"] * K
     small = mcl.mcl_sensor_plan_get(m, 1000, len(scan), mcl.sensor_params(0.1))
     assert small["item_order"] == 1                       # too few items: chunk-major
     tri = mcl.mcl_sensor_plan_get(m, len(parts), len(scan), mcl.sensor_params(0.1, flags=mcl.MCL_TRILINEAR))
     assert tri["item_order"] == 1                         # auto: sweeps only for the nearest read
     Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), parts[:200], scan, wl.sigma_hit)
-    check_logw(res[(2, ())][0][:200], Lo)
+    check_logw(res[(3, ())][0][:200], Lo)
     m.close()
 
 
@@ -451,7 +457,7 @@ def test_invalid_arguments_are_refused(torch_cuda, mcl, room):
     L = mcl.lib()
     for bad in [dict(sigma_hit=0.0), dict(sigma_hit=float("nan")), dict(mode=7), dict(flags=8),
                 dict(points_per_chunk=48), dict(lanes_per_particle=12), dict(unroll=3),
-                dict(unroll=16), dict(pipeline=3), dict(particle_order=5), dict(item_order=3),
+                dict(unroll=16), dict(pipeline=3), dict(particle_order=5), dict(item_order=4),
                 dict(item_order=-1)]:
         kw = dict(sigma_hit=0.1)
         kw.update(bad)
