@@ -79,7 +79,9 @@ enum { MCL_INDEX_AUTO = 0, MCL_INDEX_HASH = 1, MCL_INDEX_GRID = 2 };
  *
  * Voxel (ix, iy, iz) covers [o + i r, o + (i + 1) r) on each axis. A point x
  * falls in voxel i_k = floor(u_k) with u_k = (x_k - o_k) * inv_voxel in two
- * FP32 roundings; it is inside iff 0 <= u_k < dims_k on every axis.
+ * FP32 roundings; it is inside iff 0 <= u_k < dims_k on every axis. dims_k
+ * lie in [1, 2^23] (the kernels take floor(u) from the bits of a round-down
+ * u + 2^23, exact below 2^23); larger dims are EINVAL.
  * Values are the signed distance at the voxel centre, clamped to
  * [-truncation, truncation], stored as FP32, FP16 or scaled int16
  * (q stands for q * truncation / 32767).

@@ -53,19 +53,53 @@ __global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4*
   if (p < P) pose_to_matrix(poses, p, mats, rank);
 }
 
+// Pair t of the pair layout (ScanLayout): chunk c = t / full_pairs, pair
+// (s, l) = divmod(t % full_pairs, G) of points s 2G + l and s 2G + G + l of
+// the chunk (zeros past its end).
+__device__ __forceinline__ void scan_pack_pair(const float* __restrict__ scan, int N,
+                                               const ScanLayout L, int t,
+                                               unsigned char* __restrict__ packed) {
+  const int fp = L.full_pairs();
+  const int c = t / fp, pi = t - c * fp;
+  const int cnt = min(L.chunk, N - c * L.chunk);
+  const int np = L.pairs(cnt);
+  if (pi >= np) return;  // beyond this (last) chunk's pairs
+  const int G = L.pair_g;
+  const int s = pi / G, l = pi - s * G;
+  const int i0 = s * 2 * G + l, i1 = i0 + G;
+  float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
+  if (i0 < cnt) {
+    const float* q = scan + 3 * ((size_t)c * L.chunk + i0);
+    a[0] = q[0]; a[1] = q[1]; a[2] = q[2];
+  }
+  if (i1 < cnt) {
+    const float* q = scan + 3 * ((size_t)c * L.chunk + i1);
+    b[0] = q[0]; b[1] = q[1]; b[2] = q[2];
+  }
+  unsigned char* base = packed + L.chunk_offset(c);
+  reinterpret_cast<float4*>(base)[pi] = make_float4(a[0], b[0], a[1], b[1]);
+  reinterpret_cast<float2*>(base + (size_t)np * 16)[pi] = make_float2(a[2], b[2]);
+}
+
 // Pose matrices and scan packing of one sensor update in one launch: blocks
-// [0, pose_blocks) take particles, the rest take scan points (the two are
-// independent; one launch instead of two matters for small updates, where
-// each launch costs about as much as its work).
+// [0, pose_blocks) take particles, the rest take scan points or pairs (the
+// two are independent; one launch instead of two matters for small updates,
+// where each launch costs about as much as its work).
 __global__ void k_pose_and_pack(const float* __restrict__ poses, int P, float4* __restrict__ mats,
                                 const int* __restrict__ rank, int pose_blocks,
-                                const float* __restrict__ scan, int N, float4* __restrict__ packed) {
+                                const float* __restrict__ scan, int N, const ScanLayout L,
+                                void* __restrict__ packed) {
   if ((int)blockIdx.x < pose_blocks) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < P) pose_to_matrix(poses, p, mats, rank);
   } else {
     const int j = (blockIdx.x - pose_blocks) * blockDim.x + threadIdx.x;
-    if (j < N) scan_pack(scan, j, packed);
+    if (L.pair_g == 0) {
+      if (j < N) scan_pack(scan, j, static_cast<float4*>(packed));
+    } else {
+      const int K = (N + L.chunk - 1) / L.chunk;
+      if (j < K * L.full_pairs()) scan_pack_pair(scan, N, L, j, static_cast<unsigned char*>(packed));
+    }
   }
 }
 
@@ -129,10 +163,13 @@ cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const
 }
 
 cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const int* rank,
-                                 const float* scan, int N, float4* packed, cudaStream_t s) {
+                                 const float* scan, int N, const ScanLayout& layout, void* packed,
+                                 cudaStream_t s) {
   const int threads = pose_threads(P);
-  const int pb = blocks_for(P, threads), sb = blocks_for(N, threads);
-  k_pose_and_pack<<<pb + sb, threads, 0, s>>>(poses, P, mats, rank, pb, scan, N, packed);
+  const long long K = (N + layout.chunk - 1) / layout.chunk;
+  const long long units = layout.pair_g ? K * layout.full_pairs() : (long long)N;
+  const int pb = blocks_for(P, threads), sb = blocks_for(units, threads);
+  k_pose_and_pack<<<pb + sb, threads, 0, s>>>(poses, P, mats, rank, pb, scan, N, layout, packed);
   return cudaGetLastError();
 }
 

@@ -111,9 +111,10 @@ cudaError_t prepare(void* f, int smem, int threads, int max_blocks) {
 
 }  // namespace
 
-// scan chunk | mbarrier (16 B) | per-group pose rows (up to 32 groups x 3 float4)
+// staged scan chunk | mbarrier (16 B) | per-group pose rows (up to 32 groups
+// x 6 float4)
 int sensor_smem_bytes(const SensorShape& sh) {
-  return sh.chunk * (int)sizeof(float4) + 16 + 32 * 3 * (int)sizeof(float4);
+  return scan_layout(sh).smem_bytes() + 16 + 32 * 6 * (int)sizeof(float4);
 }
 
 cudaError_t sensor_occupancy(int kind, int layout, int dtype, int mode, const SensorShape& sh,

@@ -205,14 +205,11 @@ struct Pending {
   bool in[U], v[U];
 };
 
-// The particle's [R | t] rows live in shared memory (one slot per lane group)
-// and are re-read every step, so they do not hold 12 registers across the
-// gathers; with the register cap below this gives 6 resident CTAs per SM
-// instead of 5 (measured 239 ms against 243 ms for 1M x 65,536).
-#ifndef MCL_MATRIX_IN_SMEM
-#define MCL_MATRIX_IN_SMEM 1
-#endif
-
+// The particle's [R | t] rows live in shared memory (one slot per lane group,
+// each entry duplicated into both halves of a pair for the packed
+// instructions) and are re-read every step, so they do not hold registers
+// across the gathers (with the pose rows in registers the kernel needed 5
+// resident CTAs per SM instead of 6: 243 against 239 ms for 1M x 65,536).
 __device__ __forceinline__ float4 lds_volatile(const float4* p) {
   float4 v;
   asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -221,32 +218,66 @@ __device__ __forceinline__ float4 lds_volatile(const float4* p) {
   return v;
 }
 
+// Stage A on the pair layout (ScanLayout): the lane's points j and j + G of a
+// step come as one XY float4 and one Z float2, so each coordinate of the two
+// sits in one register pair and the transform and the first index steps run
+// as packed FP32x2 instructions (IEEE per element: the same bits as the
+// scalar fmaf / __fsub_rn / __fmul_rn chain). The floor comes from a
+// round-down add of 2^23: for 0 <= u < 2^23 the sum's bits are 0x4B000000 +
+// floor(u) exactly, and every other u (negative, >= 2^23, +-inf, NaN) leaves
+// bits - 0x4B000000 >= 2^23 as an unsigned number, so one unsigned compare
+// with n (at most 2^23) is the rule 0 <= u < n, NaN outside. rows: the
+// group's six float4 of duplicated pose entries (pair_rows).
+constexpr uint32_t kFloorBits = 0x4B000000u;  // bits of 2^23
+
 template <int KIND, int DTYPE, int MODE, int G, int U, bool FULL>
-__device__ __forceinline__ void stage_a(const SensorArgs& a, const float4* __restrict__ sscan,
-                                        int base, int glane, int cnt, bool gvalid,
-                                        const float4& r0_, const float4& r1_, const float4& r2_,
-                                        Pending<KIND, DTYPE, MODE, U>& s) {
+__device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4* __restrict__ sxy,
+                                              const float2* __restrict__ sz, int base, int glane,
+                                              int cnt, bool gvalid, const float4* rows,
+                                              Pending<KIND, DTYPE, MODE, U>& s) {
+  static_assert(U % 2 == 0, "points come in pairs");
   const MapView& m = a.map;
-#if MCL_MATRIX_IN_SMEM
-  // r0_ points at the group's three rows in shared memory
-  const float4 r0 = lds_volatile(&r0_), r1 = lds_volatile(&r0_ + 1), r2 = lds_volatile(&r0_ + 2);
-#else
-  const float4 &r0 = r0_, &r1 = r1_, &r2 = r2_;
-#endif
+  const float4 q0 = lds_volatile(rows), q1 = lds_volatile(rows + 1), q2 = lds_volatile(rows + 2),
+               q3 = lds_volatile(rows + 3), q4 = lds_volatile(rows + 4), q5 = lds_volatile(rows + 5);
+  const float2 no_x = make_float2(-m.ox, -m.ox), no_y = make_float2(-m.oy, -m.oy),
+               no_z = make_float2(-m.oz, -m.oz), inv = make_float2(m.inv, m.inv),
+               two23 = make_float2(8388608.f, 8388608.f);
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int j = base + u * G + glane;
-    s.v[u] = FULL || (gvalid && j < cnt);
-    const float4 z = sscan[FULL ? j : (s.v[u] ? j : 0)];
-    float x, y, w;
-    transform_point(r0, r1, r2, z, x, y, w);
-    int ix, iy, iz;
-    s.in[u] = s.v[u] && voxel_of(m, x, y, w, ix, iy, iz);
-    if constexpr (KIND == MCL_MAP_DENSE) {
-      s.key[u] = ((uint32_t)iz * (uint32_t)m.ny + (uint32_t)iy) * (uint32_t)m.nx + (uint32_t)ix;
-    } else {
-      s.key[u] = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
-      s.loc[u] = brick_local<KIND>(ix, iy, iz);
+  for (int k = 0; k < U / 2; ++k) {
+    const int j0 = base + 2 * k * G + glane;
+    s.v[2 * k] = FULL || (gvalid && j0 < cnt);
+    s.v[2 * k + 1] = FULL || (gvalid && j0 + G < cnt);
+    const int pi = (base / (2 * G) + k) * G + glane;
+    const float4 xy = sxy[pi];
+    const float2 zz = sz[pi];
+    const float2 zx = make_float2(xy.x, xy.y), zy = make_float2(xy.z, xy.w);
+    // x_i = fma(R_i0, z0, fma(R_i1, z1, fma(R_i2, z2, t_i))) for both points
+    const float2 X = __ffma2_rn(make_float2(q0.x, q0.y), zx,
+                                __ffma2_rn(make_float2(q0.z, q0.w), zy,
+                                           __ffma2_rn(make_float2(q1.x, q1.y), zz, make_float2(q1.z, q1.w))));
+    const float2 Y = __ffma2_rn(make_float2(q2.x, q2.y), zx,
+                                __ffma2_rn(make_float2(q2.z, q2.w), zy,
+                                           __ffma2_rn(make_float2(q3.x, q3.y), zz, make_float2(q3.z, q3.w))));
+    const float2 W = __ffma2_rn(make_float2(q4.x, q4.y), zx,
+                                __ffma2_rn(make_float2(q4.z, q4.w), zy,
+                                           __ffma2_rn(make_float2(q5.x, q5.y), zz, make_float2(q5.z, q5.w))));
+    // u = (x - o) * inv, then floor via the round-down add of 2^23
+    const float2 fx = __fadd2_rd(__fmul2_rn(__fadd2_rn(X, no_x), inv), two23);
+    const float2 fy = __fadd2_rd(__fmul2_rn(__fadd2_rn(Y, no_y), inv), two23);
+    const float2 fz = __fadd2_rd(__fmul2_rn(__fadd2_rn(W, no_z), inv), two23);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = 2 * k + h;
+      const uint32_t ix = __float_as_uint(h ? fx.y : fx.x) - kFloorBits;
+      const uint32_t iy = __float_as_uint(h ? fy.y : fy.x) - kFloorBits;
+      const uint32_t iz = __float_as_uint(h ? fz.y : fz.x) - kFloorBits;
+      s.in[u] = s.v[u] && (ix < (uint32_t)m.nx) && (iy < (uint32_t)m.ny) && (iz < (uint32_t)m.nz);
+      if constexpr (KIND == MCL_MAP_DENSE) {
+        s.key[u] = (iz * (uint32_t)m.ny + iy) * (uint32_t)m.nx + ix;
+      } else {
+        s.key[u] = ((iz >> 4) * m.nby + (iy >> 4)) * m.nbx + (ix >> 4);
+        s.loc[u] = brick_local<KIND>((int)ix, (int)iy, (int)iz);
+      }
     }
   }
 #pragma unroll
@@ -321,28 +352,28 @@ __device__ __forceinline__ void accumulate(const SensorArgs& a,
 // step i are consumed, so the index look-ups of the next step overlap the
 // value gathers of this one (the per-point order of the sum is unchanged).
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE>
-__device__ __forceinline__ void eval_full(const SensorArgs& a, const float4* __restrict__ sscan,
-                                          int end, int glane, const float4& r0, const float4& r1,
-                                          const float4& r2, typename Raw<DTYPE, MODE>::acc& acc) {
+__device__ __forceinline__ void eval_full(const SensorArgs& a, const float4* __restrict__ sxy,
+                                          const float2* __restrict__ sz, int end, int glane,
+                                          const float4* rows, typename Raw<DTYPE, MODE>::acc& acc) {
   constexpr int STEP = G * U;
   using V = typename Raw<DTYPE, MODE>::value;
   if (end <= 0) return;
   Pending<KIND, DTYPE, MODE, U> s;
   if constexpr (PIPE) {
-    stage_a<KIND, DTYPE, MODE, G, U, true>(a, sscan, 0, glane, end, true, r0, r1, r2, s);
+    stage_a_pairs<KIND, DTYPE, MODE, G, U, true>(a, sxy, sz, 0, glane, end, true, rows, s);
     for (int base = 0; base < end; base += STEP) {
       V dv[U];
       bool use[U];
       stage_b<KIND, DTYPE, MODE, U>(a, s, dv, use);
       if (base + STEP < end)
-        stage_a<KIND, DTYPE, MODE, G, U, true>(a, sscan, base + STEP, glane, end, true, r0, r1, r2, s);
+        stage_a_pairs<KIND, DTYPE, MODE, G, U, true>(a, sxy, sz, base + STEP, glane, end, true, rows, s);
       accumulate<DTYPE, MODE, U>(a, dv, use, acc);
     }
   } else {
     for (int base = 0; base < end; base += STEP) {
       V dv[U];
       bool use[U];
-      stage_a<KIND, DTYPE, MODE, G, U, true>(a, sscan, base, glane, end, true, r0, r1, r2, s);
+      stage_a_pairs<KIND, DTYPE, MODE, G, U, true>(a, sxy, sz, base, glane, end, true, rows, s);
       stage_b<KIND, DTYPE, MODE, U>(a, s, dv, use);
       accumulate<DTYPE, MODE, U>(a, dv, use, acc);
     }
@@ -351,14 +382,14 @@ __device__ __forceinline__ void eval_full(const SensorArgs& a, const float4* __r
 
 // One bounds-checked step (chunk tails, partly valid groups).
 template <int KIND, int DTYPE, int MODE, int G, int U>
-__device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* __restrict__ sscan,
-                                             int base, int glane, int cnt, bool gvalid,
-                                             const float4& r0, const float4& r1, const float4& r2,
+__device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* __restrict__ sxy,
+                                             const float2* __restrict__ sz, int base, int glane,
+                                             int cnt, bool gvalid, const float4* rows,
                                              typename Raw<DTYPE, MODE>::acc& acc) {
   Pending<KIND, DTYPE, MODE, U> s;
   typename Raw<DTYPE, MODE>::value dv[U];
   bool use[U];
-  stage_a<KIND, DTYPE, MODE, G, U, false>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, s);
+  stage_a_pairs<KIND, DTYPE, MODE, G, U, false>(a, sxy, sz, base, glane, cnt, gvalid, rows, s);
   stage_b<KIND, DTYPE, MODE, U>(a, s, dv, use);
   accumulate<DTYPE, MODE, U>(a, dv, use, acc);
 }
@@ -576,17 +607,17 @@ struct MinBlocks {
                                    : MCL_SENSOR_MIN_BLOCKS;
 };
 
-// Stage `cnt` scan points starting at `src` into shared memory with one bulk
-// copy; every thread of the CTA calls this. Returns false (after recording the
-// error and letting an in-flight copy land) if the bounded wait ran out.
-__device__ __forceinline__ bool stage_chunk(float4* sscan, uint32_t bar_s, const float4* src,
-                                            int cnt, uint32_t& parity, unsigned* status) {
+// Stage one chunk of the packed scan (`bytes` from `src`) into shared memory
+// with one bulk copy; every thread of the CTA calls this. Returns false (after
+// recording the error and letting an in-flight copy land) if the bounded wait
+// ran out.
+__device__ __forceinline__ bool stage_chunk(void* sdst, uint32_t bar_s, const void* src,
+                                            uint32_t bytes, uint32_t& parity, unsigned* status) {
   __syncthreads();  // every group is done with the previous chunk
   if (threadIdx.x == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(float4);
     mbar_expect_tx(bar_s, bytes);
-    bulk_copy_g2s(smem_addr(sscan), src, bytes, bar_s);
+    bulk_copy_g2s(smem_addr(sdst), src, bytes, bar_s);
   }
   const bool ok = mbar_wait_bounded(bar_s, parity);
   parity ^= 1u;
@@ -601,10 +632,14 @@ __device__ __forceinline__ bool stage_chunk(float4* sscan, uint32_t bar_s, const
 }
 
 // Particles [p0, p0 + pn) of one session against the staged chunk c (cnt
-// points): each lane group takes a particle, sums its chunk terms and writes
-// the chunk sum to partial[c * P + p].
+// points at sscan, in the layout of a.layout): each lane group takes a
+// particle, sums its chunk terms and writes the chunk sum to
+// partial[c * P + p]. The group's slot of smat holds its particle's pose
+// rows: six float4 of duplicated entries (R_i0, R_i0, R_i1, R_i1), (R_i2,
+// R_i2, t_i, t_i) per row i for the packed nearest read, the three rows as
+// they are for the trilinear read.
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
-__device__ __forceinline__ void process_block(const SensorArgs& a, const float4* __restrict__ sscan,
+__device__ __forceinline__ void process_block(const SensorArgs& a, const unsigned char* sscan,
                                               float4* smat, const float4* __restrict__ mats,
                                               float* __restrict__ partial, int P, int c, int p0,
                                               int pn, int cnt) {
@@ -614,48 +649,43 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const float4*
   const int gid = lane / G, glane = lane % G;
   const int ngroups = (blockDim.x >> 5) * GPW;
   const int full_end = (cnt / STEP) * STEP;
+  const float4* sxy = reinterpret_cast<const float4*>(sscan);
+  const float2* sz = nullptr;
+  if constexpr (!TRI) sz = reinterpret_cast<const float2*>(sscan + (size_t)a.layout.pairs(cnt) * 16);
   for (int i0 = warp * GPW; i0 < pn; i0 += ngroups) {
     const int i = i0 + gid;
     const bool gvalid = i < pn;
     if (G == 32 && !gvalid) continue;  // warp-uniform for whole-warp groups
     const size_t p = (size_t)p0 + (gvalid ? i : 0);
-#if MCL_MATRIX_IN_SMEM
-    float4* srow = smat + 3 * (warp * GPW + gid);
-    if (glane < 3) srow[glane] = __ldg(mats + 3 * p + glane);
+    float4* rows = smat + 6 * (warp * GPW + gid);
+    if constexpr (TRI) {
+      if (glane < 3) rows[glane] = __ldg(mats + 3 * p + glane);
+    } else if (glane < 6) {
+      const float4 r = __ldg(mats + 3 * p + (glane >> 1));
+      rows[glane] = (glane & 1) ? make_float4(r.z, r.z, r.w, r.w) : make_float4(r.x, r.x, r.y, r.y);
+    }
     __syncwarp();
-    const float4& r0 = srow[0];
-    const float4& r1 = srow[0];
-    const float4& r2 = srow[0];
-#else
-    const float4 r0 = __ldg(mats + 3 * p), r1 = __ldg(mats + 3 * p + 1), r2 = __ldg(mats + 3 * p + 2);
-#endif
     typename Raw<DTYPE, MODE>::acc acc = 0;
     if constexpr (TRI) {
       static_assert(G == 32, "the trilinear read uses whole-warp groups");
-#if MCL_MATRIX_IN_SMEM
-      const float4 q0 = lds_volatile(&r0), q1 = lds_volatile(&r0 + 1), q2 = lds_volatile(&r0 + 2);
-#else
-      const float4 q0 = r0, q1 = r1, q2 = r2;
-#endif
-      eval_tri<KIND, DTYPE, MODE, G>(a, sscan, glane, cnt, q0, q1, q2, acc);
+      const float4 q0 = lds_volatile(rows), q1 = lds_volatile(rows + 1), q2 = lds_volatile(rows + 2);
+      eval_tri<KIND, DTYPE, MODE, G>(a, reinterpret_cast<const float4*>(sscan), glane, cnt, q0, q1,
+                                     q2, acc);
     } else {
       int base = 0;
       if (G == 32 || __all_sync(0xffffffffu, gvalid)) {
-        eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sscan, full_end, glane, r0, r1, r2, acc);
+        eval_full<KIND, DTYPE, MODE, G, U, PIPE>(a, sxy, sz, full_end, glane, rows, acc);
         base = full_end;
       }
       for (; base < cnt; base += STEP)
-        eval_checked<KIND, DTYPE, MODE, G, U>(a, sscan, base, glane, cnt, gvalid, r0, r1, r2, acc);
+        eval_checked<KIND, DTYPE, MODE, G, U>(a, sxy, sz, base, glane, cnt, gvalid, rows, acc);
     }
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1)
       acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
     if (glane == 0 && gvalid) partial[(size_t)c * P + p] = __fmul_rn(acc, a.store_scale);
-#if MCL_MATRIX_IN_SMEM
     __syncwarp();  // every lane read the rows before the next particle's are written
-#endif
   }
-  (void)smat;
 }
 
 __device__ __forceinline__ void init_barrier(uint32_t bar_s) {
@@ -687,9 +717,9 @@ __device__ __forceinline__ void item_coords(long long item, int nblk, int K, int
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_sensor(const SensorArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float4* sscan = reinterpret_cast<float4*>(smem);
-  const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
-  float4* smat = reinterpret_cast<float4*>(smem + (size_t)a.chunk * sizeof(float4) + 16);
+  const int sbytes = a.layout.smem_bytes();
+  const uint32_t bar_s = smem_addr(smem + sbytes);
+  float4* smat = reinterpret_cast<float4*>(smem + sbytes + 16);
   init_barrier(bar_s);
   int loaded = -1;
   uint32_t parity = 0;
@@ -710,10 +740,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
       const int pn = min(a.ppi, a.P - p0);
       const int cnt = min(a.chunk, a.N - c * a.chunk);
       if (c != loaded) {
-        if (!stage_chunk(sscan, bar_s, a.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
+        if (!stage_chunk(smem, bar_s, reinterpret_cast<const unsigned char*>(a.scan) +
+                                          a.layout.chunk_offset(c),
+                         a.layout.chunk_bytes(cnt), parity, a.status))
+          return;
         loaded = c;
       }
-      process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, sscan, smat, a.mats, a.partial, a.P, c, p0,
+      process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, smem, smat, a.mats, a.partial, a.P, c, p0,
                                                         pn, cnt);
     }
     return;
@@ -725,10 +758,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
     const int pn = min(a.ppi, a.P - p0);
     const int cnt = min(a.chunk, a.N - c * a.chunk);
     if (c != loaded) {  // uniform over the CTA: every thread walks the same items
-      if (!stage_chunk(sscan, bar_s, a.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
+      if (!stage_chunk(smem, bar_s, reinterpret_cast<const unsigned char*>(a.scan) +
+                                        a.layout.chunk_offset(c),
+                       a.layout.chunk_bytes(cnt), parity, a.status))
+        return;
       loaded = c;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, sscan, smat, a.mats, a.partial, a.P, c, p0,
+    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, smem, smat, a.mats, a.partial, a.P, c, p0,
                                                       pn, cnt);
   }
 }
@@ -741,9 +777,9 @@ template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI, true>::value)) k_sensor_batch(const BatchArgs b) {
   const SensorArgs& a = b.base;
   extern __shared__ __align__(128) unsigned char smem[];
-  float4* sscan = reinterpret_cast<float4*>(smem);
-  const uint32_t bar_s = smem_addr(smem + (size_t)a.chunk * sizeof(float4));
-  float4* smat = reinterpret_cast<float4*>(smem + (size_t)a.chunk * sizeof(float4) + 16);
+  const int sbytes = a.layout.smem_bytes();
+  const uint32_t bar_s = smem_addr(smem + sbytes);
+  float4* smat = reinterpret_cast<float4*>(smem + sbytes + 16);
   init_barrier(bar_s);
   long long loaded = -1;
   uint32_t parity = 0;
@@ -757,15 +793,18 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI, true>::value)) k
     const long long local = item - __ldg(b.item_begin + lo);
     int c, blk;
     item_coords(local, S.nblk, S.K, S.sweep, c, blk);
-    const int p0 = blk * a.ppi;
-    const int pn = min(a.ppi, S.P - p0);
+    const int p0 = blk * S.ppi;
+    const int pn = min(S.ppi, S.P - p0);
     const int cnt = min(a.chunk, S.N - c * a.chunk);
     const long long key = ((long long)lo << 32) | (unsigned)c;
     if (key != loaded) {
-      if (!stage_chunk(sscan, bar_s, S.scan + (size_t)c * a.chunk, cnt, parity, a.status)) return;
+      if (!stage_chunk(smem, bar_s, reinterpret_cast<const unsigned char*>(S.scan) +
+                                        a.layout.chunk_offset(c),
+                       a.layout.chunk_bytes(cnt), parity, a.status))
+        return;
       loaded = key;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, sscan, smat, S.mats, S.partial, S.P, c, p0,
+    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, smem, smat, S.mats, S.partial, S.P, c, p0,
                                                       pn, cnt);
   }
 }

@@ -197,8 +197,8 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     return fail(MCL_EINVAL, "map_create: voxel and truncation must be finite and > 0");
   for (int k = 0; k < 3; ++k) {
     if (!std::isfinite(d->origin[k])) return fail(MCL_EINVAL, "map_create: origin not finite");
-    if (d->dims[k] <= 0 || d->dims[k] > (1 << 24))
-      return fail(MCL_EINVAL, "map_create: dims[%d] = %lld outside [1, 2^24]", k, (long long)d->dims[k]);
+    if (d->dims[k] <= 0 || d->dims[k] > (1 << 23))
+      return fail(MCL_EINVAL, "map_create: dims[%d] = %lld outside [1, 2^23]", k, (long long)d->dims[k]);
   }
   if (d->kind == MCL_MAP_BRICK && d->device_layout != MCL_LAYOUT_LINEAR &&
       d->device_layout != MCL_LAYOUT_BLOCK4)
@@ -591,7 +591,7 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   pl->off_mats = o;
   o = align256(o + (size_t)P * 3 * sizeof(float4));
   pl->off_scan = o;
-  o = align256(o + (size_t)N * sizeof(float4));
+  o = align256(o + scan_layout(sh).total_bytes((int)N));
   pl->off_partial = o;
   o = align256(o + (size_t)pl->K * (size_t)P * sizeof(float));
   pl->off_logw = o;
@@ -676,7 +676,7 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
                           mcl_estimate* est, const Plan& pl, char* ws, unsigned* status,
                           cudaStream_t s) {
   float4* mats = (float4*)(ws + pl.off_mats);
-  float4* packed = (float4*)(ws + pl.off_scan);
+  void* packed = ws + pl.off_scan;
   float* partial = (float*)(ws + pl.off_partial);
   float* L = logw ? logw : (float*)(ws + pl.off_logw);
   float2* bstats = (float2*)(ws + pl.off_stats);
@@ -688,13 +688,15 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
     if (pl.spatial)
       MCL_CUDA(launch_particle_order(particles, (int)P, m->view, (uint32_t*)(ws + pl.off_key),
                                      (uint32_t*)(ws + pl.off_hist), rank, s));
-    MCL_CUDA(launch_pose_and_pack(particles, (int)P, mats, rank, scan, (int)N, packed, s));
+    MCL_CUDA(launch_pose_and_pack(particles, (int)P, mats, rank, scan, (int)N, scan_layout(pl.sh),
+                                  packed, s));
   }
   const double sig = (double)p->sigma_hit;
   SensorArgs a;
   a.map = m->view;
   a.mats = mats;
-  a.scan = packed;
+  a.scan = (const float4*)packed;
+  a.layout = scan_layout(pl.sh);
   a.partial = partial;
   a.status = status;
   a.P = (int)P;

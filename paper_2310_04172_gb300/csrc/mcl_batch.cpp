@@ -79,7 +79,7 @@ mcl_status enqueue(mcl_batch_s* b, cudaStream_t st, bool profile) {
                                      (uint32_t*)(ws + pl.off_key), (uint32_t*)(ws + pl.off_hist),
                                      rank, st));
     MCL_CUDA(launch_pose_and_pack(sp.u.particles, (int)sp.u.P, (float4*)(ws + pl.off_mats), rank,
-                                  sp.u.scan, (int)sp.u.N, (float4*)(ws + pl.off_scan), st));
+                                  sp.u.scan, (int)sp.u.N, scan_layout(pl.sh), ws + pl.off_scan, st));
   }
   for (auto& g : b->g) {
     if (profile) {
@@ -224,7 +224,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       char* ws = b->ws + sp.base;
       tab.push_back(BatchSession{(const float4*)(ws + sp.pl.off_mats), (const float4*)(ws + sp.pl.off_scan),
                                  (float*)(ws + sp.pl.off_partial), (int)sp.u.P, (int)sp.u.N, sp.pl.nblk,
-                                 sp.pl.K, sp.pl.sweep});
+                                 sp.pl.K, sp.pl.sweep, sp.pl.sh.ppi});
       beg.push_back(beg.back() + sp.pl.n_items);
     }
     e = cudaMemcpy(b->ws + off_tab[k], tab.data(), tab.size() * sizeof(BatchSession), cudaMemcpyHostToDevice);
@@ -242,6 +242,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     a.status = st.status;
     a.chunk = g.sh.chunk;
     a.ppi = g.sh.ppi;
+    a.layout = scan_layout(g.sh);
     a.mode = kernel_mode(g.map, g.mode);
     a.neglect = g.neglect;
     score_constants(g.map, g.sigma, g.mode, &a);

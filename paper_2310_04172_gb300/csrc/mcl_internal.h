@@ -155,6 +155,34 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
 #endif  // __CUDACC__
 
 // ---------------------------------------------------------------- launchers
+// Packed scan of one sensor update, chunk by chunk (a1). Nearest reads use
+// pairs: a lane group of G lanes takes points l, l + G, l + 2G, ... of a
+// chunk, two per step of its loop, so pair (s, l) of a chunk holds points
+// s 2G + l and s 2G + G + l as XY = (x0, x1, y0, y1) (one float4) in a first
+// array and Z = (z0, z1) (one float2) in a second right after it: the lane
+// reads its two points with two shared loads and has each coordinate of the
+// two in one register pair for the packed FP32x2 instructions. A chunk of cnt
+// points holds pairs(cnt) = ceil(cnt / 2G) G pairs (24 bytes each; points past
+// cnt are zero) and starts at byte c * full_pairs() * 24. The trilinear read
+// keeps one float4 (x, y, z, 0) per point (pair_g = 0).
+struct ScanLayout {
+  int chunk;   // points per chunk
+  int pair_g;  // G of the pair layout, 0: one float4 per point
+  __host__ __device__ int pairs(int cnt) const { return (cnt + 2 * pair_g - 1) / (2 * pair_g) * pair_g; }
+  __host__ __device__ int full_pairs() const { return pairs(chunk); }
+  __host__ __device__ size_t chunk_offset(int c) const {
+    return pair_g ? (size_t)c * (size_t)full_pairs() * 24 : (size_t)c * (size_t)chunk * 16;
+  }
+  __host__ __device__ uint32_t chunk_bytes(int cnt) const {
+    return pair_g ? (uint32_t)pairs(cnt) * 24u : (uint32_t)cnt * 16u;
+  }
+  __host__ __device__ int smem_bytes() const { return pair_g ? full_pairs() * 24 : chunk * 16; }
+  __host__ __device__ size_t total_bytes(int N) const {
+    const size_t K = ((size_t)N + chunk - 1) / chunk;
+    return pair_g ? K * (size_t)full_pairs() * 24 : (size_t)N * 16;
+  }
+};
+
 struct SensorShape {
   int chunk;      // points per chunk (fixes the summation order)
   int lanes;      // lanes per particle (fixes the summation order)
@@ -166,10 +194,15 @@ struct SensorShape {
   int grid;       // CTAs (persistent)
 };
 
+// Scan layout of a launch shape: pairs for the nearest read, one float4 per
+// point for the trilinear read.
+inline ScanLayout scan_layout(const SensorShape& sh) { return ScanLayout{sh.chunk, sh.interp ? 0 : sh.lanes}; }
+
 struct SensorArgs {
   MapView map;
   const float4* mats;  // P x 3 rows [R_i0 R_i1 R_i2 t_i]
-  const float4* scan;  // N packed (x, y, z, 0)
+  const float4* scan;  // packed scan (layout)
+  ScanLayout layout;
   float* partial;      // K x P chunk partial sums (chunk-major)
   unsigned* status;
   int P, N, chunk, K, ppi, nblk;
@@ -193,9 +226,10 @@ struct SensorArgs {
 // Batched sensor update: sessions sharing one map and score constants.
 struct BatchSession {
   const float4* mats;  // P x 3 rows
-  const float4* scan;  // N packed points
+  const float4* scan;  // packed scan (the group's layout)
   float* partial;      // K x P chunk sums
   int P, N, nblk, K, sweep;
+  int ppi;             // particles per block of this session (its plan may shrink it)
 };
 
 struct BatchArgs {
@@ -218,10 +252,11 @@ cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const
 size_t order_hist_bytes();
 cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, uint32_t* key,
                                   uint32_t* hist, int* rank, cudaStream_t s);
-// Pose matrices (as launch_pose_to_matrix) and scan packing (N x 3 -> N float4)
-// in one launch.
+// Pose matrices (as launch_pose_to_matrix) and scan packing (N x 3 -> the
+// layout) in one launch.
 cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const int* rank,
-                                 const float* scan, int N, float4* packed, cudaStream_t s);
+                                 const float* scan, int N, const ScanLayout& layout, void* packed,
+                                 cudaStream_t s);
 cudaError_t launch_sensor(int kind, int layout, int dtype, const SensorArgs& a,
                           const SensorShape& sh, cudaStream_t s);
 int sensor_smem_bytes(const SensorShape& sh);

@@ -180,7 +180,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       MCL_CUDA(launch_particle_order(part, (int)ss->P, ss->map->view, (uint32_t*)(ss->d_ws + pl.off_key),
                                      (uint32_t*)(ss->d_ws + pl.off_hist), rank, st));
     MCL_CUDA(launch_pose_and_pack(part, (int)ss->P, (float4*)(ss->d_ws + pl.off_mats), rank, ss->d_scan,
-                                  (int)Ns[i], (float4*)(ss->d_ws + pl.off_scan), st));
+                                  (int)Ns[i], scan_layout(pl.sh), ss->d_ws + pl.off_scan, st));
   }
   // group the slot's sessions by map and score constants; tables go to the slot buffer
   struct G {
@@ -225,7 +225,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       tab[q] = BatchSession{(const float4*)(ss->d_ws + ss->pl.off_mats),
                             (const float4*)(ss->d_ws + ss->pl.off_scan),
                             (float*)(ss->d_ws + ss->pl.off_partial), (int)ss->P, (int)N, ss->pl.nblk,
-                            K, ss->pl.sweep};
+                            K, ss->pl.sweep, ss->pl.sh.ppi};
       beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
     }
     int bps = 0;
@@ -240,6 +240,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     a.status = S->dev.status;
     a.chunk = sh.chunk;
     a.ppi = sh.ppi;
+    a.layout = scan_layout(sh);
     a.mode = kernel_mode(g.map, g.mode);
     a.neglect = g.neglect;
     const double sig = (double)g.sigma, scale = (double)g.map->view.scale;
