@@ -712,8 +712,7 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   const float c = (float)(-0.5 / (sig * sig));
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
-  a.vout = outside_raw(m);
-  a.vnear = nearest_fill(m, a.mode, a.neglect != 0);
+  set_fills(m, &a);
   a.cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : c;
   a.store_scale = (q16 && p->mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
   if (pl.dynamic) {

@@ -44,7 +44,6 @@ void score_constants(const mcl_map_s* m, float sigma, int mode, SensorArgs* a) {
   const double sig = (double)sigma;
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
-  a->vout = outside_raw(m);
   a->cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : sensor_c(sigma);
   a->store_scale = (q16 && mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
 }
@@ -246,7 +245,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     a.mode = kernel_mode(g.map, g.mode);
     a.neglect = g.neglect;
     score_constants(g.map, g.sigma, g.mode, &a);
-    a.vnear = nearest_fill(g.map, a.mode, a.neglect != 0);
+    set_fills(g.map, &a);
     g.args.sessions = (const BatchSession*)(b->ws + off_tab[k]);
     g.args.item_begin = (const long long*)(b->ws + off_beg[k]);
     g.args.n_sessions = (int)g.sessions.size();

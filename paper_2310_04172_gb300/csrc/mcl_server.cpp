@@ -245,8 +245,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     a.neglect = g.neglect;
     const double sig = (double)g.sigma, scale = (double)g.map->view.scale;
     const bool q16 = g.map->dtype == MCL_I16;
-    a.vout = outside_raw(g.map);
-    a.vnear = nearest_fill(g.map, a.mode, a.neglect != 0);
+    set_fills(g.map, &a);
     a.cs = (float)(-0.5 / (sig * sig) * (q16 ? scale * scale : 1.0));
     a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
     b.sessions = (const BatchSession*)(sl->d_tab + off_tab);

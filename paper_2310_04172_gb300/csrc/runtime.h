@@ -120,11 +120,12 @@ inline float outside_raw(const mcl_map_s* m) {
   if (m->score_sigma > 0.f) return m->score_outside;
   return m->dtype == MCL_I16 ? 32767.0f : m->view.tau;
 }
-// The nearest read's value where nothing is stored (SensorArgs::vnear) for
-// kernel mode `kmode` on map m.
-inline float nearest_fill(const mcl_map_s* m, int kmode, bool neglect) {
-  if (!neglect) return outside_raw(m);
-  return kmode == MCL_SUM ? __builtin_huge_valf() : 0.0f;
+// The values a read takes where nothing is stored (SensorArgs::vout, vnear)
+// for the kernel mode a->mode and neglect flag a->neglect on map m.
+inline void set_fills(const mcl_map_s* m, SensorArgs* a) {
+  a->vout = outside_raw(m);
+  if (!a->neglect) a->vnear = a->vout;
+  else a->vnear = a->mode == MCL_SUM ? __builtin_huge_valf() : 0.0f;
 }
 // EINVAL unless the parameters fit the map (a score map needs SUM, its own
 // sigma and the nearest-voxel read).
