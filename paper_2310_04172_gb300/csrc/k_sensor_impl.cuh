@@ -582,11 +582,11 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 // Resident CTAs per SM the register allocation is held to (measured on the
 // 1M x 65,536 building step): with the hash index 6 for the 2- and 4-deep
 // loops (40 registers; 5 or 4 were slower); with the cell-grid index 5 for
-// the single-session kernel (48 registers, 8 bytes spilled; with the
-// shared-memory carveout sized for 5 CTAs: 128.0 ms against 133.7 ms at 4
-// and 182 ms at 6) and 4 for the batched one (at 48 registers it spills 36
-// bytes: 134.8 against 127.1 ms); 3 for the 8-deep loop; 4 for the
-// trilinear read (crossing-bit walk, 32-bit value indices: 596 ms against
+// the 4-deep loop of the single-session kernel (48 registers; packed pair
+// stage, dynamic sweeps: 102.6 ms against 105.9 at 4 and 108.1 at 6) and 4
+// for the batched one; 4 for the 8-deep loop (64 registers: 97.0 ms, the
+// default of the cell-grid kernel, against 103.7 at 5 and 106.9 at 3); 4 for
+// the trilinear read (crossing-bit walk, 32-bit value indices: 596 ms against
 // 602 ms at 3 and 613 ms at 5).
 #ifndef MCL_SENSOR_MIN_BLOCKS
 #define MCL_SENSOR_MIN_BLOCKS 6
@@ -600,10 +600,13 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 #ifndef MCL_TRI_MIN_BLOCKS
 #define MCL_TRI_MIN_BLOCKS 4
 #endif
+#ifndef MCL_U8_MIN_BLOCKS
+#define MCL_U8_MIN_BLOCKS 4
+#endif
 
 template <int KIND, int U, bool TRI = false, bool BATCH = false>
 struct MinBlocks {
-  static constexpr int value = TRI ? MCL_TRI_MIN_BLOCKS : U == 8 ? 3
+  static constexpr int value = TRI ? MCL_TRI_MIN_BLOCKS : U == 8 ? MCL_U8_MIN_BLOCKS
                                : KIND == kKindBrickGrid
                                    ? (BATCH ? MCL_BATCH_MIN_BLOCKS_GRID : MCL_SENSOR_MIN_BLOCKS_GRID)
                                    : MCL_SENSOR_MIN_BLOCKS;
