@@ -647,7 +647,7 @@ template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
 __device__ __forceinline__ void process_block(const SensorArgs& a, const unsigned char* sscan,
                                               float4* smat, const float4* __restrict__ mats,
                                               float* __restrict__ partial, int P, int c, int p0,
-                                              int pn, int cnt) {
+                                              int pn, int cnt, int* pnext = nullptr) {
   constexpr int GPW = 32 / G;  // groups per warp
   constexpr int STEP = G * U;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -657,10 +657,18 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const unsigne
   const float4* sxy = reinterpret_cast<const float4*>(sscan);
   const float2* sz = nullptr;
   if constexpr (!TRI) sz = reinterpret_cast<const float2*>(sscan + (size_t)a.layout.pairs(cnt) * 16);
-  for (int i0 = warp * GPW; i0 < pn; i0 += ngroups) {
+  // pnext (shared, zero at the item's start): the warps take the item's
+  // particles from this counter, GPW at a time, so a warp that drew cheap
+  // particles takes more and the item's closing barrier waits less; NULL:
+  // warp w takes particles w GPW, w GPW + ngroups, ...
+  int i0 = warp * GPW;
+  if (pnext) {
+    if (lane == 0) i0 = atomicAdd(pnext, GPW);
+    i0 = __shfl_sync(0xffffffffu, i0, 0);
+  }
+  for (; i0 < pn;) {
     const int i = i0 + gid;
-    const bool gvalid = i < pn;
-    if (G == 32 && !gvalid) continue;  // warp-uniform for whole-warp groups
+    const bool gvalid = i < pn;  // (whole-warp groups: always, as i0 < pn)
     const size_t p = (size_t)p0 + (gvalid ? i : 0);
     float4* rows = smat + 6 * (warp * GPW + gid);
     if constexpr (TRI) {
@@ -690,6 +698,12 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const unsigne
       acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
     if (glane == 0 && gvalid) partial[(size_t)c * P + p] = __fmul_rn(acc, a.store_scale);
     __syncwarp();  // every lane read the rows before the next particle's are written
+    if (pnext) {
+      if (lane == 0) i0 = atomicAdd(pnext, GPW);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+    } else {
+      i0 += ngroups;
+    }
   }
 }
 
@@ -732,13 +746,23 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
     // Dynamic order: thread 0 takes the next item from the device counter one
     // item ahead; the barrier at the top of each step publishes it and is the
     // point where every warp is done with the previous item.
+    // The item's particles go to the warps through a shared counter, one per
+    // item parity: counter (k + 1) & 1 is reset during item k, when no warp
+    // uses it any more (all passed the barrier that closed item k - 1).
     __shared__ long long s_next[2];
-    if (threadIdx.x == 0) s_next[0] = (long long)atomicAdd(a.queue, 1ull);
+    __shared__ int s_pnext[2];
+    if (threadIdx.x == 0) {
+      s_next[0] = (long long)atomicAdd(a.queue, 1ull);
+      s_pnext[0] = 0;
+    }
     for (int k = 0;; ++k) {
       __syncthreads();
       const long long item = s_next[k & 1];
       if (item >= a.n_items) break;
-      if (threadIdx.x == 0) s_next[(k + 1) & 1] = (long long)atomicAdd(a.queue, 1ull);
+      if (threadIdx.x == 0) {
+        s_next[(k + 1) & 1] = (long long)atomicAdd(a.queue, 1ull);
+        s_pnext[(k + 1) & 1] = 0;
+      }
       int c, blk;
       item_coords(item, a.nblk, a.K, a.sweep, c, blk);
       const int p0 = blk * a.ppi;
@@ -752,7 +776,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
         loaded = c;
       }
       process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, smem, smat, a.mats, a.partial, a.P, c, p0,
-                                                        pn, cnt);
+                                                        pn, cnt, &s_pnext[k & 1]);
     }
     return;
   }
