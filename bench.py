@@ -218,7 +218,8 @@ SERVING_MAX_BATCH = 2
 
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16_grid.cu", "mcl_internal.h", "k_order.cu"):
+    for f in ("k_sensor.cu", "k_sensor_impl.cuh", "k_sensor_i16_grid.cu", "mcl_internal.h", "k_order.cu",
+              "k_pose_scan.cu", "mcl_api.cpp"):
         with open(os.path.join(ROOT, "paper_2310_04172_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -674,11 +675,14 @@ def weight_report(Lg, wg, Lo) -> dict:
     k = min(100, len(Lo))
     top_o = set(np.argsort(-Lo, kind="stable")[:k].tolist())
     top_g = set(np.argsort(-Lg, kind="stable")[:k].tolist())
+    big = wo >= 1e-6 * wo.max()  # weights within 1e-6 of the largest
     return {"max_rel_logw_err": float(np.max(np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo)))),
             "max_abs_logw_err": float(np.max(np.abs(Lg - Lo))),
             "tv_distance": float(0.5 * np.abs(wg - wo).sum()),
             "particles_within_30_nats": int(len(near)),
             "max_rel_w_err_within_30_nats": float(np.max(np.abs(rg - ro) / ro)),
+            "particles_w_above_1e-6_max": int(big.sum()),
+            "max_rel_w_err_above_1e-6_max": float(np.max(np.abs(wg[big] - wo[big]) / wo[big])),
             "top100_agreement": len(top_o & top_g) / k,
             "argmax_agrees": bool(int(np.argmax(Lg)) == jo)}
 
@@ -703,19 +707,26 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     subsets = {"global_10000": wl.particles[np.sort(rng.choice(P, 10_000, replace=False))],
                "tracking_10000": scenes.particles_gaussian(wl.pose, 10_000, 0.2, 2.0, 41)}
     rep = {"reference": "FP64 oracle, quality mode (FP64 throughout on the FP32 map values)",
+           "note": "LOGPROD: the weights of a 65,536-point scan concentrate on one particle "
+                   "(the log-weights of neighbouring poses differ by thousands of nats), so "
+                   "the weight error there is the argmax, top-100 and log-weight agreement; "
+                   "SUM (Eq. 3 summed over points) spreads the weight over many particles "
+                   "and gives a relative weight error",
            "subsets": {}}
+    prm_sum = mcl.sensor_params(wl.sigma_hit, mode=mcl.MCL_SUM)
     for name, sub in subsets.items():
-        t0 = time.perf_counter()
-        Lo = oracle.sensor_update(om, sub, wl.scan, wl.sigma_hit, parity=False)
-        oracle_s = time.perf_counter() - t0
         dsub = torch.from_numpy(np.ascontiguousarray(sub)).to(parts.device)
-        res = {"oracle_s": oracle_s}
-        for label, mm in (("i16", m_head), ("f32", m32)):
-            lg = torch.empty(len(sub), device=parts.device)
-            wg = torch.empty(len(sub), device=parts.device)
-            mcl.mcl_sensor_update(mm, dsub, scan, prm, lg, wg)
-            mcl.mcl_sync()
-            res[label] = weight_report(lg.cpu().numpy(), wg.cpu().numpy(), Lo)
+        res = {}
+        for mode, mprm, key in ((oracle.LOGPROD, prm, "logprod"), (oracle.SUM, prm_sum, "sum")):
+            t0 = time.perf_counter()
+            Lo = oracle.sensor_update(om, sub, wl.scan, wl.sigma_hit, mode=mode, parity=False)
+            res[f"oracle_s_{key}"] = time.perf_counter() - t0
+            for label, mm in (("i16", m_head), ("f32", m32)):
+                lg = torch.empty(len(sub), device=parts.device)
+                wg = torch.empty(len(sub), device=parts.device)
+                mcl.mcl_sensor_update(mm, dsub, scan, mprm, lg, wg)
+                mcl.mcl_sync()
+                res[f"{label}_{key}"] = weight_report(lg.cpu().numpy(), wg.cpu().numpy(), Lo)
         rep["subsets"][name] = res
 
     def timed(fn, reps=3):
@@ -750,8 +761,10 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     def form(ms):
         return {"ms_per_update": ms, "evals_per_s": ev / (ms / 1e3)}
 
-    err_i16 = rep["subsets"]["tracking_10000"]["i16"]
-    err_f32 = rep["subsets"]["tracking_10000"]["f32"]
+    err_i16 = rep["subsets"]["tracking_10000"]["i16_logprod"]
+    err_f32 = rep["subsets"]["tracking_10000"]["f32_logprod"]
+    sum_i16 = rep["subsets"]["tracking_10000"]["i16_sum"]
+    sum_f32 = rep["subsets"]["tracking_10000"]["f32_sum"]
     forms = {
         "f32_same_shape": form(ms_f32),
         "f32_plain_per_session": dict(form(ms_f32_plain), shape="particles as given, chunk-major items"),
@@ -763,7 +776,13 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
                             "i16_tv_distance": err_i16["tv_distance"],
                             "f32_tv_distance": err_f32["tv_distance"],
                             "i16_max_rel_logw_err": err_i16["max_rel_logw_err"],
-                            "f32_max_rel_logw_err": err_f32["max_rel_logw_err"]},
+                            "f32_max_rel_logw_err": err_f32["max_rel_logw_err"],
+                            "i16_top100_agreement": err_i16["top100_agreement"],
+                            "f32_top100_agreement": err_f32["top100_agreement"],
+                            "sum_mode_i16_max_rel_w_err": sum_i16["max_rel_w_err_above_1e-6_max"],
+                            "sum_mode_f32_max_rel_w_err": sum_f32["max_rel_w_err_above_1e-6_max"],
+                            "sum_mode_i16_tv_distance": sum_i16["tv_distance"],
+                            "sum_mode_f32_tv_distance": sum_f32["tv_distance"]},
     }
     return rep, forms
 
@@ -810,7 +829,10 @@ def run_precision(args):
     subsets = {"global_10000": wl.particles[np.sort(rng.choice(P, 10_000, replace=False))],
                "tracking_10000": scenes.particles_gaussian(wl.pose, 10_000, 0.2, 2.0, 41)}
     om = oracle.Map.from_scene_map(maps[scenes.F32])
-    refs = {k: oracle.sensor_update(om, v, wl.scan, wl.sigma_hit, parity=False) for k, v in subsets.items()}
+    modes = {"logprod": (oracle.LOGPROD, mcl.sensor_params(wl.sigma_hit)),
+             "sum": (oracle.SUM, mcl.sensor_params(wl.sigma_hit, mode=mcl.MCL_SUM))}
+    refs = {(k, mk): oracle.sensor_update(om, v, wl.scan, wl.sigma_hit, mode=mo, parity=False)
+            for k, v in subsets.items() for mk, (mo, _) in modes.items()}
     prm = mcl.sensor_params(wl.sigma_hit)
     out = {}
     for dt, name in ((scenes.F32, "f32"), (scenes.F16, "f16"), (scenes.I16, "i16")):
@@ -829,10 +851,11 @@ def run_precision(args):
                "map_bytes": int(maps[dt].values.nbytes)}
         for k, sub in subsets.items():
             ds = torch.from_numpy(np.ascontiguousarray(sub)).cuda()
-            lg, wg = torch.empty(len(sub), device="cuda"), torch.empty(len(sub), device="cuda")
-            mcl.mcl_sensor_update(m, ds, scan, prm, lg, wg)
-            mcl.mcl_sync()
-            res[k] = weight_report(lg.cpu().numpy(), wg.cpu().numpy(), refs[k])
+            for mk, (_, mprm) in modes.items():
+                lg, wg = torch.empty(len(sub), device="cuda"), torch.empty(len(sub), device="cuda")
+                mcl.mcl_sensor_update(m, ds, scan, mprm, lg, wg)
+                mcl.mcl_sync()
+                res[f"{k}_{mk}"] = weight_report(lg.cpu().numpy(), wg.cpu().numpy(), refs[(k, mk)])
         out[name] = res
         m.close()
     line = {"mode": "precision", "metric": METRIC, "value": out["i16"]["evals_per_s"], "unit": UNIT,
