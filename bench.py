@@ -69,6 +69,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the weight-error report and the storage/form comparison of the headline")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
+    ap.add_argument("--serving-batch", type=int, default=0,
+                    help="sessions per batched serving step (0: the default policy)")
     ap.add_argument("--filter-workloads", default="room,hall",
                     help="--mode filter: comma list of room, hall")
     return ap.parse_args(argv)
@@ -625,7 +627,7 @@ def serving_sessions(mcl, srv, maps, n, p_lo, p_hi, seed):
     return out
 
 
-def serving_block(mcl, seconds: float):
+def serving_block(mcl, seconds: float, max_batch: int = 0):
     """The 64-session serving workload: 64 robot sessions over 8 maps (4 dense
     512x512x128 FP16 halls, 4 brick int16 160x160x20 m buildings), P
     log-uniform in [1e3, 1e6], scans of 28,800 (halls) and 65,536 (buildings)
@@ -639,14 +641,15 @@ def serving_block(mcl, seconds: float):
         maps.append((mcl.map_from_scene(hall.map), hall.scene, hall.scan))
         bld = scenes.os064_building(P=16, dtype=scenes.I16, seed=15 + k)
         maps.append((mcl.map_from_scene(bld.map), bld.scene, bld.scan))
-    srv = mcl.Server(200 << 30, 64, max_in_flight=2, max_batch=SERVING_MAX_BATCH)
+    max_batch = max_batch or SERVING_MAX_BATCH
+    srv = mcl.Server(200 << 30, 64, max_in_flight=2, max_batch=max_batch)
     sess = serving_sessions(mcl, srv, maps, 64, 1e3, 1e6, 31)
     nominal = serving_measure(mcl, srv, sess, seconds, 1.0, 7)
     scale = 0.7 * nominal["achieved_evals_per_s"] / nominal["offered_evals_per_s"]
     scaled = serving_measure(mcl, srv, sess, seconds, scale, 9)
     out = {"sessions": len(sess), "maps": len(maps),
            "workload": "64 sessions over 4 dense FP16 halls + 4 int16 brick buildings",
-           "policy": f"max_in_flight 2, max_batch {SERVING_MAX_BATCH}, longest-waiting sessions first",
+           "policy": f"max_in_flight 2, max_batch {max_batch}, longest-waiting sessions first",
            "particles_total": int(sum(x.P for x, _, _ in sess)),
            "nominal_load": nominal, "scaled_load_70pct": dict(scaled, rate_scale=scale)}
     for x, _, _ in sess:
@@ -795,7 +798,7 @@ def run_serving(args):
     __graft_entry__.build()
     from paper_2310_04172_gb300 import mcl
     torch.cuda.set_device(0)
-    out = serving_block(mcl, args.serving_seconds * 2)
+    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch)
     line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
             "value": out["scaled_load_70pct"]["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32",

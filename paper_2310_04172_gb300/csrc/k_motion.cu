@@ -101,16 +101,9 @@ __device__ __forceinline__ double euler_angle(const double Rn[9], int k) {
 }
 
 // One thread per particle.
-__global__ void k_motion(float* __restrict__ poses, int P, MotionArgs a, uint64_t seed,
-                         uint64_t step, const StepIn* __restrict__ in) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  if (in) {
-    if (!in->motion) return;
-    step = in->step;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) a.delta[k] = in->delta[k];
-  }
+// Motion update of particle i (one thread).
+__device__ __forceinline__ void motion_one(float* __restrict__ poses, int i, const MotionArgs& a,
+                                           uint64_t seed, uint64_t step) {
   double n[6];
 #pragma unroll
   for (uint32_t b = 0; b < 3; ++b) normal_pair(b, i, step, seed, n[2 * b], n[2 * b + 1]);
@@ -134,6 +127,35 @@ __global__ void k_motion(float* __restrict__ poses, int P, MotionArgs a, uint64_
   for (int k = 0; k < 3; ++k) s[k] = (float)t[k];
 #pragma unroll
   for (int k = 0; k < 3; ++k) s[3 + k] = (float)ang[k];
+}
+
+__global__ void k_motion(float* __restrict__ poses, int P, MotionArgs a, uint64_t seed,
+                         uint64_t step, const StepIn* __restrict__ in) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  if (in) {
+    if (!in->motion) return;
+    step = in->step;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.delta[k] = in->delta[k];
+  }
+  motion_one(poses, i, a, seed, step);
+}
+
+// Batched form: every session with a motion update (SideSeg::mpart), one
+// thread per particle, the same arithmetic as k_motion.
+__global__ void __launch_bounds__(kSideThreads) k_motion_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  const int i = (blockIdx.x - __ldg(b.first + s)) * kSideThreads + threadIdx.x;
+  if (i >= g.P) return;
+  MotionArgs a;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    a.delta[k] = g.mdelta[k];
+    a.sigma[k] = g.msig[k];
+  }
+  motion_one(g.mpart, i, a, g.mseed, g.mstep);
 }
 
 // Small sets: FP64 issue is slow on this part (a warp instruction holds its
@@ -221,6 +243,14 @@ cudaError_t launch_motion(float* particles, int P, const float delta[6], const f
   int threads = 256;
   while (threads > 32 && (P + threads - 1) / threads < 2 * 152) threads >>= 1;
   k_motion<<<(P + threads - 1) / threads, threads, 0, s>>>(particles, P, a, seed, step, in);
+  return cudaGetLastError();
+}
+
+int side_blocks_motion(const SideSeg& g) { return g.mpart ? (g.P + kSideThreads - 1) / kSideThreads : 0; }
+
+cudaError_t launch_side_motion(const SideSeg* segs, const SegBlocks& b, cudaStream_t s) {
+  if (b.blocks == 0) return cudaSuccess;
+  k_motion_b<<<b.blocks, kSideThreads, 0, s>>>(segs, b);
   return cudaGetLastError();
 }
 

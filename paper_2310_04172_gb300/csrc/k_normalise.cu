@@ -50,13 +50,12 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
 // One block per contiguous particle range. With `partial`, L_p is first
 // assembled from the K chunk sums in chunk order: LOGPROD L = c * sum(d^2),
 // SUM L = log(k * sum exp(c d^2)).
-__global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ partial,
-                                                    const int* __restrict__ rank, int P, int K,
-                                                    int mode, float c, float k,
-                                                    float* __restrict__ logw,
-                                                    float2* __restrict__ stats, int range) {
+__device__ __forceinline__ void block_stats(const float* __restrict__ partial,
+                                            const int* __restrict__ rank, int P, int K, int mode,
+                                            float c, float k, float* __restrict__ logw,
+                                            float2* __restrict__ stats, int range, int blk) {
   __shared__ float sh[32];
-  const int start = blockIdx.x * range, end = min(P, start + range);
+  const int start = blk * range, end = min(P, start + range);
   float m = -INFINITY;
   for (int p = start + threadIdx.x; p < end; p += blockDim.x) {
     float L;
@@ -76,7 +75,15 @@ __global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ pa
   if (m > -INFINITY)
     for (int p = start + threadIdx.x; p < end; p += blockDim.x) s = __fadd_rn(s, expf(__fsub_rn(logw[p], m)));
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) stats[blockIdx.x] = make_float2(m, m > -INFINITY ? s : 0.f);
+  if (threadIdx.x == 0) stats[blk] = make_float2(m, m > -INFINITY ? s : 0.f);
+}
+
+__global__ void __launch_bounds__(kT) k_block_stats(const float* __restrict__ partial,
+                                                    const int* __restrict__ rank, int P, int K,
+                                                    int mode, float c, float k,
+                                                    float* __restrict__ logw,
+                                                    float2* __restrict__ stats, int range) {
+  block_stats(partial, rank, P, K, mode, c, k, logw, stats, range, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- pose estimate
@@ -198,12 +205,12 @@ __device__ __forceinline__ void est_store(const EstAcc& a, EstPartial* out) {
 }
 
 template <bool EST>
-__global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw, int P,
-                                                  float* __restrict__ w,
-                                                  const float2* __restrict__ stats, int nb,
-                                                  int range, float* __restrict__ out_stats,
-                                                  const float* __restrict__ particles,
-                                                  EstPartial* __restrict__ part) {
+__device__ __forceinline__ void normalise_block(const float* __restrict__ logw, int P,
+                                                float* __restrict__ w,
+                                                const float2* __restrict__ stats, int nb, int range,
+                                                float* __restrict__ out_stats,
+                                                const float* __restrict__ particles,
+                                                EstPartial* __restrict__ part, int blk) {
   __shared__ float sh[32];
   float m = -INFINITY;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmaxf(m, stats[i].x);
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw
       if (st.x > -INFINITY) s = __fadd_rn(s, __fmul_rn(st.y, expf(__fsub_rn(st.x, M))));
     }
   const float S = block_sum(s, sh);
-  const int start = blockIdx.x * range, end = min(P, start + range);
+  const int start = blk * range, end = min(P, start + range);
   const float uni = 1.0f / (float)P;
   EstAcc acc;
   if (EST) est_init(acc);
@@ -225,15 +232,25 @@ __global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw
     w[p] = wp;
     if (EST) est_add(acc, particles, wp, p);
   }
-  if (out_stats && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (out_stats && blk == 0 && threadIdx.x == 0) {
     out_stats[0] = M;
     out_stats[1] = degenerate ? 0.f : S;
   }
   if constexpr (EST) {
     __shared__ EstShared esh;
     est_block_reduce(acc, esh);
-    if (threadIdx.x == 0) est_store(acc, part + blockIdx.x);
+    if (threadIdx.x == 0) est_store(acc, part + blk);
   }
+}
+
+template <bool EST>
+__global__ void __launch_bounds__(kT) k_normalise(const float* __restrict__ logw, int P,
+                                                  float* __restrict__ w,
+                                                  const float2* __restrict__ stats, int nb,
+                                                  int range, float* __restrict__ out_stats,
+                                                  const float* __restrict__ particles,
+                                                  EstPartial* __restrict__ part) {
+  normalise_block<EST>(logw, P, w, stats, nb, range, out_stats, particles, part, blockIdx.x);
 }
 
 // The same per-block terms from weights in memory (same ranges, same order).
@@ -305,9 +322,9 @@ __device__ void jacobi4f(float A[4][4], float V[4][4]) {
 // 4 x 4 eigenproblem.
 constexpr int kTF = kT;
 
-__global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __restrict__ part, int nb,
-                                                        const float* __restrict__ particles,
-                                                        mcl_estimate* __restrict__ out) {
+__device__ __forceinline__ void estimate_final(const EstPartial* __restrict__ part, int nb,
+                                               const float* __restrict__ particles,
+                                               mcl_estimate* __restrict__ out) {
   __shared__ EstShared esh;
   EstAcc acc;
   est_init(acc);
@@ -400,9 +417,64 @@ __global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __rest
   out->reserved = 0;
 }
 
-inline int range_of(int P, int nb) { return (P + nb - 1) / nb; }
+__global__ void __launch_bounds__(kTF) k_estimate_final(const EstPartial* __restrict__ part, int nb,
+                                                        const float* __restrict__ particles,
+                                                        mcl_estimate* __restrict__ out) {
+  estimate_final(part, nb, particles, out);
+}
+
+inline __host__ __device__ int range_of(int P, int nb) { return (P + nb - 1) / nb; }
+
+// ---------------------------------------------------------------- batched forms
+// One launch of each pass for every session (segments of blocks, SegBlocks):
+// the same blocks, ranges and order as the single-session launches, so the
+// same bits.
+__global__ void __launch_bounds__(kT) k_block_stats_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  block_stats(g.partial, g.rank, g.P, g.K, g.mode, g.c, g.k, g.logw, g.stats, range_of(g.P, g.nb),
+              blockIdx.x - __ldg(b.first + s));
+}
+
+__global__ void __launch_bounds__(kT) k_normalise_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  const int j = blockIdx.x - __ldg(b.first + s);
+  if (g.est_part)
+    normalise_block<true>(g.logw, g.P, g.w, g.stats, g.nb, range_of(g.P, g.nb), g.ostats,
+                          g.particles, g.est_part, j);
+  else
+    normalise_block<false>(g.logw, g.P, g.w, g.stats, g.nb, range_of(g.P, g.nb), g.ostats, nullptr,
+                           nullptr, j);
+}
+
+__global__ void __launch_bounds__(kTF) k_estimate_final_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  estimate_final(g.est_part, g.nb, g.particles, g.est);
+}
 
 }  // namespace
+
+int side_blocks_normalise(int kind, const SideSeg& g) {
+  switch (kind) {
+    case kSideStats: return g.nb;
+    case kSideNormalise: return g.w ? g.nb : 0;
+    case kSideEstimate: return g.w && g.est_part ? 1 : 0;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_side_normalise(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s) {
+  if (b.blocks == 0) return cudaSuccess;
+  switch (kind) {
+    case kSideStats: k_block_stats_b<<<b.blocks, kT, 0, s>>>(segs, b); break;
+    case kSideNormalise: k_normalise_b<<<b.blocks, kT, 0, s>>>(segs, b); break;
+    case kSideEstimate: k_estimate_final_b<<<b.blocks, kTF, 0, s>>>(segs, b); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 int normalise_blocks(int P) {
   const int b = (P + kT - 1) / kT;

@@ -103,6 +103,30 @@ __global__ void k_pose_and_pack(const float* __restrict__ poses, int P, float4* 
   }
 }
 
+// Scan units of the packing: pairs of the pair layout, else points.
+__host__ __device__ inline long long pack_units(int N, const ScanLayout& L) {
+  return L.pair_g ? (long long)((N + L.chunk - 1) / L.chunk) * L.full_pairs() : (long long)N;
+}
+
+// Batched form: per session, pose blocks then packing blocks of kSideThreads.
+__global__ void __launch_bounds__(kSideThreads) k_pose_and_pack_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  const int j = blockIdx.x - __ldg(b.first + s);
+  const int pb = (g.P + kSideThreads - 1) / kSideThreads;
+  if (j < pb) {
+    const int p = j * kSideThreads + threadIdx.x;
+    if (p < g.P) pose_to_matrix(g.particles, p, g.mats, g.rank);
+  } else {
+    const int t = (j - pb) * kSideThreads + threadIdx.x;
+    const ScanLayout L = g.layout;
+    if (t < pack_units(g.N, L)) {
+      if (L.pair_g == 0) scan_pack(g.scan, t, static_cast<float4*>(g.packed));
+      else scan_pack_pair(g.scan, g.N, L, t, static_cast<unsigned char*>(g.packed));
+    }
+  }
+}
+
 template <int KIND, int DTYPE>
 __global__ void k_map_lookup(const MapView m, const float* __restrict__ pts, int N,
                              long long* __restrict__ out_index, float* __restrict__ out_value) {
@@ -166,10 +190,19 @@ cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const 
                                  const float* scan, int N, const ScanLayout& layout, void* packed,
                                  cudaStream_t s) {
   const int threads = pose_threads(P);
-  const long long K = (N + layout.chunk - 1) / layout.chunk;
-  const long long units = layout.pair_g ? K * layout.full_pairs() : (long long)N;
+  const long long units = pack_units(N, layout);
   const int pb = blocks_for(P, threads), sb = blocks_for(units, threads);
   k_pose_and_pack<<<pb + sb, threads, 0, s>>>(poses, P, mats, rank, pb, scan, N, layout, packed);
+  return cudaGetLastError();
+}
+
+int side_blocks_pose(const SideSeg& g) {
+  return blocks_for(g.P, kSideThreads) + blocks_for(pack_units(g.N, g.layout), kSideThreads);
+}
+
+cudaError_t launch_side_pose(const SideSeg* segs, const SegBlocks& b, cudaStream_t s) {
+  if (b.blocks == 0) return cudaSuccess;
+  k_pose_and_pack_b<<<b.blocks, kSideThreads, 0, s>>>(segs, b);
   return cudaGetLastError();
 }
 

@@ -67,13 +67,12 @@ __device__ __forceinline__ long long block_max_ll(long long v, long long* sh) {
   return v;
 }
 
-__global__ void __launch_bounds__(kRT) k_tile_scan(const float* __restrict__ w, int P,
-                                                   double* __restrict__ cum,
-                                                   double* __restrict__ tile_total,
-                                                   long long* __restrict__ tile_last) {
+__device__ __forceinline__ void tile_scan(const float* __restrict__ w, int P, double* __restrict__ cum,
+                                          double* __restrict__ tile_total,
+                                          long long* __restrict__ tile_last, int blk) {
   __shared__ double sh[32];
   __shared__ long long shl[32];
-  const long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kRI;
+  const long long base = (long long)blk * kTile + (long long)threadIdx.x * kRI;
   double run = 0.0, q[kRI];
   long long last = -1;
 #pragma unroll
@@ -95,16 +94,22 @@ __global__ void __launch_bounds__(kRT) k_tile_scan(const float* __restrict__ w, 
     if (base + i < P) cum[base + i] = __dadd_rn(excl, q[i]);
   last = block_max_ll(last, shl);
   if (threadIdx.x == 0) {
-    tile_total[blockIdx.x] = total;
-    tile_last[blockIdx.x] = last;
+    tile_total[blk] = total;
+    tile_last[blk] = last;
   }
+}
+
+__global__ void __launch_bounds__(kRT) k_tile_scan(const float* __restrict__ w, int P,
+                                                   double* __restrict__ cum,
+                                                   double* __restrict__ tile_total,
+                                                   long long* __restrict__ tile_last) {
+  tile_scan(w, P, cum, tile_total, tile_last, blockIdx.x);
 }
 
 // One block: tile totals -> exclusive tile offsets (in place); entry ntiles
 // receives the grand total S and the last index with a positive weight.
-__global__ void __launch_bounds__(kRT) k_tile_offsets(double* __restrict__ tile_total,
-                                                      long long* __restrict__ tile_last,
-                                                      int ntiles) {
+__device__ __forceinline__ void tile_offsets(double* __restrict__ tile_total,
+                                             long long* __restrict__ tile_last, int ntiles) {
   __shared__ double sh[32];
   __shared__ long long shl[32];
   double carry = 0.0;
@@ -127,13 +132,20 @@ __global__ void __launch_bounds__(kRT) k_tile_offsets(double* __restrict__ tile_
   }
 }
 
-__global__ void k_systematic(const double* __restrict__ cum, const double* __restrict__ tile_off,
-                             const long long* __restrict__ tile_last, int P, int ntiles, double r,
-                             const double* __restrict__ r_dev, int32_t* __restrict__ idx,
-                             const float* __restrict__ pin, float* __restrict__ pout) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= P) return;
-  if (r_dev) r = *r_dev;
+__global__ void __launch_bounds__(kRT) k_tile_offsets(double* __restrict__ tile_total,
+                                                      long long* __restrict__ tile_last,
+                                                      int ntiles) {
+  tile_offsets(tile_total, tile_last, ntiles);
+}
+
+// Draw j of the systematic scheme (target t_j, search over the tile ends,
+// then inside the tile) and the gather of its particle.
+__device__ __forceinline__ void systematic_one(const double* __restrict__ cum,
+                                               const double* __restrict__ tile_off,
+                                               const long long* __restrict__ tile_last, int P,
+                                               int ntiles, double r, int32_t* __restrict__ idx,
+                                               const float* __restrict__ pin,
+                                               float* __restrict__ pout, int j) {
   const double S = tile_off[ntiles];
   int res;
   if (!(S > 0.0)) {
@@ -164,6 +176,42 @@ __global__ void k_systematic(const double* __restrict__ cum, const double* __res
 #pragma unroll
     for (int k = 0; k < 6; ++k) dst[k] = src[k];
   }
+}
+
+__global__ void k_systematic(const double* __restrict__ cum, const double* __restrict__ tile_off,
+                             const long long* __restrict__ tile_last, int P, int ntiles, double r,
+                             const double* __restrict__ r_dev, int32_t* __restrict__ idx,
+                             const float* __restrict__ pin, float* __restrict__ pout) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  if (r_dev) r = *r_dev;
+  systematic_one(cum, tile_off, tile_last, P, ntiles, r, idx, pin, pout, j);
+}
+
+// ---------------------------------------------------------------- batched forms
+// The three-launch path for every session at once (segments of blocks,
+// SegBlocks); for a set of at most one tile it draws the same indices as the
+// fused small-set kernel (same quantised weights, exact prefix, targets and
+// search).
+__global__ void __launch_bounds__(kRT) k_tile_scan_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  tile_scan(g.w, g.P, g.cum, g.tile_total, g.tile_last, blockIdx.x - __ldg(b.first + s));
+}
+
+__global__ void __launch_bounds__(kRT) k_tile_offsets_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  tile_offsets(g.tile_total, g.tile_last, (g.P + kTile - 1) / kTile);
+}
+
+__global__ void __launch_bounds__(256) k_systematic_b(const SideSeg* __restrict__ segs, SegBlocks b) {
+  const int s = seg_of(b.first, b.n, blockIdx.x);
+  const SideSeg& g = segs[s];
+  const int j = (blockIdx.x - __ldg(b.first + s)) * 256 + threadIdx.x;
+  if (j >= g.P) return;
+  systematic_one(g.cum, g.tile_total, g.tile_last, g.P, (g.P + kTile - 1) / kTile, *g.r, g.idx,
+                 g.pin, g.pout, j);
 }
 
 // Sets of at most one tile in one launch: the same quantised weights, the
@@ -277,6 +325,27 @@ cudaError_t launch_resample_static(const float* w, int P, double r, int32_t* idx
   double* tile_total = cum + kStaticMaxParticles;
   long long* tile_last = reinterpret_cast<long long*>(tile_total + (kStaticTiles + 1));
   return launch_resample(w, P, r, idx, particles_in, particles_out, cum, tile_total, tile_last, s);
+}
+
+int side_blocks_resample(int kind, const SideSeg& g) {
+  if (!g.idx) return 0;
+  switch (kind) {
+    case kSideTileScan: return (g.P + kTile - 1) / kTile;
+    case kSideTileOffsets: return 1;
+    case kSideSystematic: return (g.P + 255) / 256;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_side_resample(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s) {
+  if (b.blocks == 0) return cudaSuccess;
+  switch (kind) {
+    case kSideTileScan: k_tile_scan_b<<<b.blocks, kRT, 0, s>>>(segs, b); break;
+    case kSideTileOffsets: k_tile_offsets_b<<<b.blocks, kRT, 0, s>>>(segs, b); break;
+    case kSideSystematic: k_systematic_b<<<b.blocks, 256, 0, s>>>(segs, b); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resample(const float* w, int P, double r, int32_t* idx,

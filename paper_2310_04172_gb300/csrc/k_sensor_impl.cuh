@@ -798,10 +798,53 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
   }
 }
 
-// Many sessions on one map with one set of score constants: items (session,
-// chunk, particle block) of uneven sizes, numbered session by session
-// (item_begin[s] is the first item of session s), strided over a persistent
-// grid. Each session's results are the ones the single-session kernel gives.
+// Many sessions whose maps share kind, storage type, geometry and score
+// constants: items (session, chunk, particle block) of uneven sizes, numbered
+// session by session (item_begin[s] is the first item of session s, each
+// session's items in its own sweep order). A device counter hands them out in
+// order when b.base.queue is set (as in k_sensor), else they are strided over
+// the grid. Each session reads its own map (values and brick index from its
+// table entry; the rest of the view is the group's) and gets the results the
+// single-session kernel gives.
+template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
+__device__ __forceinline__ bool batch_item(const BatchArgs& b, long long item, unsigned char* smem,
+                                           uint32_t bar_s, float4* smat, long long& loaded,
+                                           uint32_t& parity, int* pnext) {
+  const SensorArgs& a = b.base;
+  int lo = 0, hi = b.n_sessions - 1;  // session whose item range holds `item`
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(b.item_begin + mid) <= item) lo = mid; else hi = mid - 1;
+  }
+  const BatchSession& S = b.sessions[lo];
+  const long long local = item - __ldg(b.item_begin + lo);
+  int c, blk;
+  item_coords(local, S.nblk, S.K, S.sweep, c, blk);
+  const int ppi = S.ppi, P = S.P;
+  const int p0 = blk * ppi;
+  const int pn = min(ppi, P - p0);
+  const int cnt = min(a.chunk, S.N - c * a.chunk);
+  const long long key = ((long long)lo << 32) | (unsigned)c;
+  if (key != loaded) {
+    if (!stage_chunk(smem, bar_s, reinterpret_cast<const unsigned char*>(S.scan) +
+                                      a.layout.chunk_offset(c),
+                     a.layout.chunk_bytes(cnt), parity, a.status))
+      return false;
+    loaded = key;
+  }
+  SensorArgs as = a;  // the group's arguments with this session's map
+  as.map.values = S.values;
+  as.map.grid = S.grid;
+  as.map.table = S.table;
+  as.map.n_slots = S.n_slots;
+  as.map.hash_mask = S.hash_mask;
+  as.map.hash_shift = S.hash_shift;
+  as.map.max_probe = S.max_probe;
+  process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(as, smem, smat, S.mats, S.partial, P, c, p0, pn,
+                                                    cnt, pnext);
+  return true;
+}
+
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI>
 __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI, true>::value)) k_sensor_batch(const BatchArgs b) {
   const SensorArgs& a = b.base;
@@ -812,30 +855,31 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI, true>::value)) k
   init_barrier(bar_s);
   long long loaded = -1;
   uint32_t parity = 0;
-  for (long long item = blockIdx.x; item < b.n_items; item += gridDim.x) {
-    int lo = 0, hi = b.n_sessions - 1;  // session whose item range holds `item`
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(b.item_begin + mid) <= item) lo = mid; else hi = mid - 1;
+  if (a.queue) {  // dynamic order, as in k_sensor
+    __shared__ long long s_next[2];
+    __shared__ int s_pnext[2];
+    if (threadIdx.x == 0) {
+      s_next[0] = (long long)atomicAdd(a.queue, 1ull);
+      s_pnext[0] = 0;
     }
-    const BatchSession S = b.sessions[lo];
-    const long long local = item - __ldg(b.item_begin + lo);
-    int c, blk;
-    item_coords(local, S.nblk, S.K, S.sweep, c, blk);
-    const int p0 = blk * S.ppi;
-    const int pn = min(S.ppi, S.P - p0);
-    const int cnt = min(a.chunk, S.N - c * a.chunk);
-    const long long key = ((long long)lo << 32) | (unsigned)c;
-    if (key != loaded) {
-      if (!stage_chunk(smem, bar_s, reinterpret_cast<const unsigned char*>(S.scan) +
-                                        a.layout.chunk_offset(c),
-                       a.layout.chunk_bytes(cnt), parity, a.status))
+    for (int k = 0;; ++k) {
+      __syncthreads();
+      const long long item = s_next[k & 1];
+      if (item >= b.n_items) break;
+      if (threadIdx.x == 0) {
+        s_next[(k + 1) & 1] = (long long)atomicAdd(a.queue, 1ull);
+        s_pnext[(k + 1) & 1] = 0;
+      }
+      if (!batch_item<KIND, DTYPE, MODE, G, U, PIPE, TRI>(b, item, smem, bar_s, smat, loaded, parity,
+                                                          &s_pnext[k & 1]))
         return;
-      loaded = key;
     }
-    process_block<KIND, DTYPE, MODE, G, U, PIPE, TRI>(a, smem, smat, S.mats, S.partial, S.P, c, p0,
-                                                      pn, cnt);
+    return;
   }
+  for (long long item = blockIdx.x; item < b.n_items; item += gridDim.x)
+    if (!batch_item<KIND, DTYPE, MODE, G, U, PIPE, TRI>(b, item, smem, bar_s, smat, loaded, parity,
+                                                        nullptr))
+      return;
 }
 
 template <int KIND, int DTYPE, int MODE, int G, int U, bool PIPE, bool TRI = false>

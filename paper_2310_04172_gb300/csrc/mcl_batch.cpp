@@ -1,12 +1,17 @@
 // Batched sensor update over many robot sessions (C ABI in include/mcl.h).
 //
-// A plan fixes the sessions' device buffers, groups the sessions by map and
-// score constants, and lays out one device workspace for the whole step. A
-// run enqueues, per session, the spatial order, pose matrices and scan
-// packing; per group, one persistent sensor kernel over the (session, point
-// chunk, particle block) work items of all its sessions; per session, the
-// log-weights, normalisation and (optionally) systematic resampling. With
-// use_graph the step is captured once into a CUDA graph and replayed.
+// A plan fixes the sessions' device buffers, groups the sessions whose maps
+// share kernel kind, storage type, geometry and score constants (each
+// session keeps its own map values and brick index, read from the group's
+// device table), and lays out one device workspace for the whole step. A run
+// enqueues one launch per side step for all sessions at once (spatial order,
+// pose rows and scan packing; log-weights, normalisation with the optional
+// estimate, systematic resampling; see SideSeg) and one persistent sensor
+// kernel per group over the (session, point chunk, particle block) items of
+// its sessions, handed out in order by a device counter for brick maps read
+// nearest. The number of launches does not grow with the number of
+// sessions. With use_graph the step is captured once into a CUDA graph and
+// replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -28,10 +33,11 @@ struct SessionPlan {
 };
 
 struct Group {
-  mcl_map_t map;
+  mcl_map_t map;  // the first session's map: geometry and score constants
   int mode, neglect;
   uint32_t flags;
   float sigma;
+  bool dynamic;
   std::vector<int> sessions;
   SensorShape sh;
   BatchArgs args;
@@ -50,6 +56,34 @@ void score_constants(const mcl_map_s* m, float sigma, int mode, SensorArgs* a) {
 
 }  // namespace
 
+namespace mcl {
+
+// Maps whose sessions can share a batched sensor launch: the same kernel kind,
+// brick layout, storage type, grid geometry, truncation and int16 scale, and
+// the same kind of values (TSDF, or scores of one sigma). Values and brick
+// index may differ.
+bool same_geometry(const mcl_map_s* a, const mcl_map_s* b) {
+  const MapView &x = a->view, &y = b->view;
+  return kernel_kind(a) == kernel_kind(b) && a->dtype == b->dtype && x.layout == y.layout &&
+         x.ox == y.ox && x.oy == y.oy && x.oz == y.oz && x.inv == y.inv && x.nx == y.nx &&
+         x.ny == y.ny && x.nz == y.nz && x.nbx == y.nbx && x.nby == y.nby && x.tau == y.tau &&
+         x.scale == y.scale && a->score_sigma == b->score_sigma &&
+         a->score_outside == b->score_outside;
+}
+
+// The per-session fields of BatchSession that name its map.
+void session_map(const mcl_map_s* m, BatchSession* t) {
+  t->values = m->view.values;
+  t->table = m->view.table;
+  t->grid = m->view.grid;
+  t->n_slots = m->view.n_slots;
+  t->hash_mask = m->view.hash_mask;
+  t->hash_shift = m->view.hash_shift;
+  t->max_probe = m->view.max_probe;
+}
+
+}  // namespace mcl
+
 struct mcl_batch_s {
   int device = 0;
   std::vector<SessionPlan> s;
@@ -57,7 +91,9 @@ struct mcl_batch_s {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   double* d_r = nullptr;
+  unsigned long long* d_queue = nullptr;  // one item counter per group
   unsigned* status = nullptr;
+  SideTables side;
   bool use_graph = false;
   cudaStream_t cap = nullptr;  // plan-owned stream the step is captured on
   cudaGraph_t graph = nullptr;
@@ -69,49 +105,41 @@ struct mcl_batch_s {
 namespace {
 
 mcl_status enqueue(mcl_batch_s* b, cudaStream_t st, bool profile) {
-  for (auto& sp : b->s) {
-    const Plan& pl = sp.pl;
-    char* ws = b->ws + sp.base;
-    int* rank = pl.spatial ? (int*)(ws + pl.off_rank) : nullptr;
-    if (pl.spatial)
-      MCL_CUDA(launch_particle_order(sp.u.particles, (int)sp.u.P, sp.u.map->view,
-                                     (uint32_t*)(ws + pl.off_key), (uint32_t*)(ws + pl.off_hist),
-                                     rank, st));
-    MCL_CUDA(launch_pose_and_pack(sp.u.particles, (int)sp.u.P, (float4*)(ws + pl.off_mats), rank,
-                                  sp.u.scan, (int)sp.u.N, scan_layout(pl.sh), ws + pl.off_scan, st));
+  auto side = [&](std::initializer_list<int> kinds) -> mcl_status {
+    for (int k : kinds)
+      if (mcl_status rc = enqueue_side(b->side, k, st)) return rc;
+    return MCL_OK;
+  };
+  auto count = [&](std::initializer_list<int> kinds) {
+    int n = 0;
+    for (int k : kinds) n += b->side.b[k].blocks > 0 ? 1 : 0;
+    return n;
+  };
+  const auto pre = {(int)kSideOrderZero, (int)kSideOrderKeys, (int)kSideOrderTiles,
+                    (int)kSideOrderTotals, (int)kSideOrderScatter, (int)kSidePosePack};
+  const auto norm = {(int)kSideNormalise, (int)kSideEstimate};
+  const auto res = {(int)kSideTileScan, (int)kSideTileOffsets, (int)kSideSystematic};
+  {
+    PhaseScope ps(MCL_PHASE_POSE, st, profile ? count(pre) : 0);
+    if (mcl_status rc = side(pre)) return rc;
   }
-  for (auto& g : b->g) {
-    if (profile) {
-      PhaseScope ps(MCL_PHASE_SENSOR, st);
+  {
+    PhaseScope ps(MCL_PHASE_SENSOR, st, profile ? (int)b->g.size() : 0);
+    if (b->d_queue) MCL_CUDA(cudaMemsetAsync(b->d_queue, 0, b->g.size() * sizeof(unsigned long long), st));
+    for (auto& g : b->g)
       MCL_CUDA(launch_sensor_batch(kernel_kind(g.map), g.map->view.layout, g.map->dtype, g.args, g.sh, st));
-    } else {
-      MCL_CUDA(launch_sensor_batch(kernel_kind(g.map), g.map->view.layout, g.map->dtype, g.args, g.sh, st));
-    }
   }
-  for (size_t i = 0; i < b->s.size(); ++i) {
-    auto& sp = b->s[i];
-    const Plan& pl = sp.pl;
-    char* ws = b->ws + sp.base;
-    const int P = (int)sp.u.P;
-    int* rank = pl.spatial ? (int*)(ws + pl.off_rank) : nullptr;
-    float* L = sp.u.logw ? sp.u.logw : (float*)(ws + pl.off_logw);
-    const double sig = (double)sp.u.sigma_hit;
-    const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
-    const int nb = normalise_blocks(P);
-    MCL_CUDA(launch_finish_and_normalise((float*)(ws + pl.off_partial), rank, P, pl.K, sp.u.mode,
-                                         sensor_c(sp.u.sigma_hit), k, L,
-                                         sp.u.estimate ? nullptr : sp.u.w,
-                                         (float2*)(ws + pl.off_stats), nb, (float*)(ws + pl.off_ostats),
-                                         st));
-    if (sp.u.estimate)
-      MCL_CUDA(launch_normalise_from_stats(L, P, sp.u.w, (float2*)(ws + pl.off_stats), nb,
-                                           (float*)(ws + pl.off_ostats), sp.u.particles,
-                                           (EstPartial*)(ws + pl.off_est), sp.u.estimate, st));
-    if (sp.u.resample_idx)
-      MCL_CUDA(launch_resample(sp.u.w, P, 0.0, sp.u.resample_idx,
-                               sp.u.particles_out ? sp.u.particles : nullptr, sp.u.particles_out,
-                               (double*)(ws + sp.off_cum), (double*)(ws + sp.off_tot),
-                               (long long*)(ws + sp.off_last), st, b->d_r + i));
+  {
+    PhaseScope ps(MCL_PHASE_REDUCE, st, profile ? count({(int)kSideStats}) : 0);
+    if (mcl_status rc = side({(int)kSideStats})) return rc;
+  }
+  {
+    PhaseScope ps(MCL_PHASE_NORMALISE, st, profile ? count(norm) : 0);
+    if (mcl_status rc = side(norm)) return rc;
+  }
+  {
+    PhaseScope ps(MCL_PHASE_RESAMPLE, st, profile ? count(res) : 0);
+    if (mcl_status rc = side(res)) return rc;
   }
   return MCL_OK;
 }
@@ -175,11 +203,11 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     sp.off_last = o;
     o = align256(o + (u.resample_idx ? (size_t)(nt + 1) * 8 : 0));
     off = align256(off + o);
-    // group by map, score constants and read rule
+    // group by map geometry, score constants and read rule
     const int neglect = (u.flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
     int gi = -1;
     for (size_t k = 0; k < b->g.size(); ++k)
-      if (b->g[k].map == u.map && b->g[k].mode == u.mode && b->g[k].flags == u.flags &&
+      if (same_geometry(b->g[k].map, u.map) && b->g[k].mode == u.mode && b->g[k].flags == u.flags &&
           b->g[k].sigma == u.sigma_hit)
         gi = (int)k;
     if (gi < 0) {
@@ -190,6 +218,10 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       g.flags = u.flags;
       g.sigma = u.sigma_hit;
       g.sh = sp.pl.sh;
+      // items handed out by a counter for nearest reads of brick maps (as
+      // the single-session update does for large sets)
+      g.dynamic = u.map->kind == MCL_MAP_BRICK && !(u.flags & MCL_TRILINEAR) &&
+                  (bp->item_order == 0 || bp->item_order == 3);
       b->g.push_back(g);
       gi = (int)b->g.size() - 1;
     }
@@ -198,7 +230,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     b->s.push_back(sp);
     b->total_evals += u.P * u.N;
   }
-  // group tables and offsets follow the session blocks
+  // group tables, item counters, offsets and the side tables follow the session blocks
   std::vector<size_t> off_tab(b->g.size()), off_beg(b->g.size());
   for (size_t k = 0; k < b->g.size(); ++k) {
     off_tab[k] = off;
@@ -206,14 +238,19 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     off_beg[k] = off;
     off = align256(off + (b->g[k].sessions.size() + 1) * sizeof(long long));
   }
+  const size_t off_queue = off;
+  off = align256(off + b->g.size() * sizeof(unsigned long long));
   const size_t off_r = off;
   off = align256(off + (size_t)n * sizeof(double));
+  const size_t off_side = off;
+  off = align256(off + side_table_bytes(n));
   b->ws_bytes = off;
   cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
   if (e != cudaSuccess) return bail(cuda_fail(e, "batch_create workspace"));
   b->d_r = (double*)(b->ws + off_r);
   e = cudaMemset(b->d_r, 0, (size_t)n * sizeof(double));
   if (e != cudaSuccess) return bail(cuda_fail(e, "batch_create offsets"));
+  bool any_dynamic = false;
   for (size_t k = 0; k < b->g.size(); ++k) {
     Group& g = b->g[k];
     std::vector<BatchSession> tab;
@@ -221,9 +258,18 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     for (int i : g.sessions) {
       const SessionPlan& sp = b->s[i];
       char* ws = b->ws + sp.base;
-      tab.push_back(BatchSession{(const float4*)(ws + sp.pl.off_mats), (const float4*)(ws + sp.pl.off_scan),
-                                 (float*)(ws + sp.pl.off_partial), (int)sp.u.P, (int)sp.u.N, sp.pl.nblk,
-                                 sp.pl.K, sp.pl.sweep, sp.pl.sh.ppi});
+      BatchSession t{};
+      t.mats = (const float4*)(ws + sp.pl.off_mats);
+      t.scan = (const float4*)(ws + sp.pl.off_scan);
+      t.partial = (float*)(ws + sp.pl.off_partial);
+      t.P = (int)sp.u.P;
+      t.N = (int)sp.u.N;
+      t.nblk = sp.pl.nblk;
+      t.K = sp.pl.K;
+      t.sweep = sp.pl.sweep;
+      t.ppi = sp.pl.sh.ppi;
+      session_map(sp.u.map, &t);
+      tab.push_back(t);
       beg.push_back(beg.back() + sp.pl.n_items);
     }
     e = cudaMemcpy(b->ws + off_tab[k], tab.data(), tab.size() * sizeof(BatchSession), cudaMemcpyHostToDevice);
@@ -246,17 +292,68 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     a.neglect = g.neglect;
     score_constants(g.map, g.sigma, g.mode, &a);
     set_fills(g.map, &a);
+    if (g.dynamic) {
+      a.queue = (unsigned long long*)(b->ws + off_queue) + k;
+      any_dynamic = true;
+    }
     g.args.sessions = (const BatchSession*)(b->ws + off_tab[k]);
     g.args.item_begin = (const long long*)(b->ws + off_beg[k]);
     g.args.n_sessions = (int)g.sessions.size();
     g.args.n_items = beg.back();
     b->n_items += beg.back();
   }
-  int kern = (int)b->g.size();
-  for (auto& sp : b->s)
-    kern += (sp.pl.spatial ? 4 : 0) + 1 + 1 + (sp.u.w ? 1 : 0) + (sp.u.estimate ? 1 : 0) +
-            (sp.u.resample_idx ? resample_kernels((int)sp.u.P) : 0);
-  b->kernels_per_run = kern;
+  if (any_dynamic) b->d_queue = (unsigned long long*)(b->ws + off_queue);
+  // side tables of all sessions
+  std::vector<SideSeg> segs(n);
+  for (int i = 0; i < n; ++i) {
+    const SessionPlan& sp = b->s[i];
+    const Plan& pl = sp.pl;
+    char* ws = b->ws + sp.base;
+    SideSeg& q = segs[i];
+    q = SideSeg{};
+    q.particles = sp.u.particles;
+    q.scan = sp.u.scan;
+    q.P = (int)sp.u.P;
+    q.N = (int)sp.u.N;
+    if (pl.spatial) {
+      q.key = (uint32_t*)(ws + pl.off_key);
+      q.hist = (uint32_t*)(ws + pl.off_hist);
+      q.rank = (int*)(ws + pl.off_rank);
+      order_grid(sp.u.map->view, &q.order_o, &q.order_s);
+    }
+    q.mats = (float4*)(ws + pl.off_mats);
+    q.packed = ws + pl.off_scan;
+    q.layout = scan_layout(pl.sh);
+    q.partial = (const float*)(ws + pl.off_partial);
+    q.K = pl.K;
+    q.mode = sp.u.mode;
+    const double sig = (double)sp.u.sigma_hit;
+    q.c = sensor_c(sp.u.sigma_hit);
+    q.k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
+    q.logw = sp.u.logw ? sp.u.logw : (float*)(ws + pl.off_logw);
+    q.w = sp.u.w;
+    q.stats = (float2*)(ws + pl.off_stats);
+    q.nb = normalise_blocks(q.P);
+    q.ostats = (float*)(ws + pl.off_ostats);
+    if (sp.u.estimate) {
+      q.est_part = (EstPartial*)(ws + pl.off_est);
+      q.est = sp.u.estimate;
+    }
+    if (sp.u.resample_idx) {
+      q.idx = sp.u.resample_idx;
+      q.pin = sp.u.particles_out ? sp.u.particles : nullptr;
+      q.pout = sp.u.particles_out;
+      q.cum = (double*)(ws + sp.off_cum);
+      q.tile_total = (double*)(ws + sp.off_tot);
+      q.tile_last = (long long*)(ws + sp.off_last);
+      q.r = b->d_r + i;
+    }
+  }
+  std::vector<char> h(side_table_bytes(n));
+  side_tables(segs, h.data(), b->ws + off_side, &b->side);
+  e = cudaMemcpy(b->ws + off_side, h.data(), h.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "batch_create side tables"));
+  b->kernels_per_run = (int)b->g.size() + side_launch_count(b->side);
   *out = b;
   return MCL_OK;
 }
@@ -282,7 +379,11 @@ mcl_status mcl_batch_run(mcl_batch_t b, mcl_stream_t stream) {
     // stream, which cannot be captured); the graph then runs on the caller's
     if (!b->cap) MCL_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     MCL_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    mcl_status rc = enqueue(b, b->cap, false);
+    mcl_status rc;
+    {
+      NoProfileScope np;  // no profiling events inside the graph
+      rc = enqueue(b, b->cap, false);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &g);
     if (rc != MCL_OK) {

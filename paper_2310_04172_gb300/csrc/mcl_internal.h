@@ -230,7 +230,108 @@ struct BatchSession {
   float* partial;      // K x P chunk sums
   int P, N, nblk, K, sweep;
   int ppi;             // particles per block of this session (its plan may shrink it)
+  // this session's map: values and brick index (geometry and score constants
+  // are the group's, in BatchArgs::base.map)
+  const void* values;
+  const uint2* table;
+  const uint32_t* grid;
+  uint32_t n_slots, hash_mask;
+  int hash_shift, max_probe;
 };
+
+// ---------------------------------------------------------------- batched side kernels
+struct EstPartial;
+// One session of a batched step as the side kernels read it (a device table):
+// the spatial order, pose rows and scan packing, log-weights, normalisation
+// with the optional estimate, and systematic resampling of every session run
+// as one launch each, whatever the number of sessions.
+struct SideSeg {
+  float* mpart;            // motion update of these P x 6 poses first (NULL: none)
+  float mdelta[6], msig[6];
+  unsigned long long mseed, mstep;
+  const float* particles;  // P x 6
+  const float* scan;       // N x 3
+  int P, N;
+  uint32_t* key;           // spatial order: key, histogram (then cursors), rank; rank NULL: none
+  uint32_t* hist;
+  int* rank;
+  float3 order_o, order_s; // cell-grid origin and scale of the spatial order
+  float4* mats;            // P x 3 pose rows
+  void* packed;            // packed scan
+  ScanLayout layout;
+  const float* partial;    // K x P chunk sums
+  int K, mode;             // kernel mode as the user gave it (MCL_LOGPROD or MCL_SUM)
+  float c, k;              // score constants of the log-weights
+  float* logw;
+  float* w;                // NULL: log-weights only
+  float2* stats;           // normalisation blocks
+  int nb;
+  float* ostats;           // (M, S)
+  EstPartial* est_part;    // NULL: no estimate
+  mcl_estimate* est;
+  int32_t* idx;            // NULL: no resampling
+  const float* pin;        // particles gathered by the draw (NULL: indices only)
+  float* pout;
+  double* cum;
+  double* tile_total;
+  long long* tile_last;
+  const double* r;         // resampling offset, read when the kernel runs
+};
+
+// Blocks of one batched launch: segment s owns blocks [first[s], first[s + 1]).
+struct SegBlocks {
+  const int* first;  // device, n + 1 entries
+  int n;
+  int blocks;        // first[n]
+};
+
+// Kinds of batched side launch (one block layout each).
+enum SideLaunch : int {
+  kSideMotion = 0,     // motion update
+  kSideOrderZero,      // zero the spatial-order histograms
+  kSideOrderKeys,      // bucket keys and counts
+  kSideOrderTiles,     // exclusive scan of the counts, tile by tile
+  kSideOrderTotals,    // exclusive scan of the tile totals
+  kSideOrderScatter,   // ranks
+  kSidePosePack,       // pose rows and packed scan
+  kSideStats,          // log-weights and block statistics
+  kSideNormalise,      // weights (and estimate partials)
+  kSideEstimate,       // estimate of each session
+  kSideTileScan,       // resampling: prefix tiles
+  kSideTileOffsets,    // resampling: tile offsets
+  kSideSystematic,     // resampling: the draw
+  kSideLaunches
+};
+
+// Segment of block b: the last s with first[s] <= b (empty segments skipped).
+#ifdef __CUDACC__
+__device__ __forceinline__ int seg_of(const int* __restrict__ first, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(first + mid) <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+// The spatial order's cell grid of a map: origin and scale (cells per metre).
+void order_grid(const MapView& m, float3* o, float3* s);
+// Per-file parts of the batched side launches.
+int side_blocks_order(int kind, const SideSeg& g);
+cudaError_t launch_side_order(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
+int side_blocks_pose(const SideSeg& g);
+cudaError_t launch_side_pose(const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
+int side_blocks_normalise(int kind, const SideSeg& g);
+cudaError_t launch_side_normalise(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
+int side_blocks_resample(int kind, const SideSeg& g);
+cudaError_t launch_side_resample(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
+int side_blocks_motion(const SideSeg& g);
+cudaError_t launch_side_motion(const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
+
+// Blocks session `g` needs in side launch `kind` (threads per block fixed per kind).
+int side_blocks(int kind, const SideSeg& g);
+constexpr int kSideThreads = 256;  // of the per-particle side launches
+cudaError_t launch_side(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
 
 struct BatchArgs {
   SensorArgs base;                 // map, score constants, chunk, ppi, status

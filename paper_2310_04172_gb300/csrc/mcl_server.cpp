@@ -80,8 +80,6 @@ struct mcl_session_s {
   float *d_scan = nullptr, *d_logw = nullptr, *d_w = nullptr;
   int32_t* d_idx = nullptr;
   char* d_ws = nullptr;
-  mcl_estimate* d_est = nullptr;  // the running step's estimate
-  mcl_estimate* h_est = nullptr;  // pinned copy, read when the step completed
   Plan pl{};
   size_t off_cum = 0, off_tot = 0, off_last = 0;
   float* h_stage[2] = {nullptr, nullptr};  // pinned scan staging: queued / running
@@ -103,9 +101,11 @@ namespace {
 
 struct Slot {
   cudaStream_t st = nullptr;
-  char* d_tab = nullptr;  // device session tables and item offsets of the step
+  char* d_tab = nullptr;  // device tables of the step (side launches, groups, counters, offsets)
   char* h_tab = nullptr;  // pinned staging of the same
   size_t tab_bytes = 0;
+  mcl_estimate* d_est = nullptr;  // the step's estimates, one per session
+  mcl_estimate* h_est = nullptr;  // pinned copy, read when the step completed
   bool busy = false;
   std::atomic<bool> done{false};
   mcl_server_s* srv = nullptr;
@@ -154,14 +154,24 @@ void free_session(mcl_session_s* ss) {
   cudaFree(ss->d_w);
   cudaFree(ss->d_idx);
   cudaFree(ss->d_ws);
-  cudaFree(ss->d_est);
-  cudaFreeHost(ss->h_est);
   cudaFreeHost(ss->h_stage[0]);
   cudaFreeHost(ss->h_stage[1]);
   delete ss;
 }
 
-// Enqueues one batched filter step for the slot's sessions on its stream.
+// Bytes of a slot's step tables for up to cap sessions (and as many groups).
+size_t slot_table_bytes(int cap) {
+  return side_table_bytes(cap) + (size_t)cap * (align256(sizeof(BatchSession)) + 256 + 256) +
+         3 * align256((size_t)cap * 8) + 4096;
+}
+
+// Enqueues one batched filter step for the slot's sessions on its stream:
+// per session the host-to-device copy of its scan, then one launch per step
+// for all sessions (motion, spatial order, pose rows and scan packing), one
+// sensor kernel per group of sessions whose maps share geometry, one launch
+// per step again (log-weights, normalisation with the estimate, resampling)
+// and one copy of all estimates back. The number of launches does not grow
+// with the number of sessions.
 mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& Ns,
                         const std::vector<int>& stages, const std::vector<bool>& deltas,
                         const std::vector<std::array<float, 6>>& dvals) {
@@ -171,18 +181,70 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     mcl_session_s* ss = sl->sessions[i];
     MCL_CUDA(cudaMemcpyAsync(ss->d_scan, ss->h_stage[stages[i]], (size_t)Ns[i] * 3 * sizeof(float),
                              cudaMemcpyHostToDevice, st));
-    float* part = ss->d_part[ss->cur];
-    if (deltas[i])
-      MCL_CUDA(launch_motion(part, (int)ss->P, dvals[i].data(), ss->msig, ss->seed, (uint64_t)ss->step, st));
-    const Plan& pl = ss->pl;
-    int* rank = pl.spatial ? (int*)(ss->d_ws + pl.off_rank) : nullptr;
-    if (pl.spatial)
-      MCL_CUDA(launch_particle_order(part, (int)ss->P, ss->map->view, (uint32_t*)(ss->d_ws + pl.off_key),
-                                     (uint32_t*)(ss->d_ws + pl.off_hist), rank, st));
-    MCL_CUDA(launch_pose_and_pack(part, (int)ss->P, (float4*)(ss->d_ws + pl.off_mats), rank, ss->d_scan,
-                                  (int)Ns[i], scan_layout(pl.sh), ss->d_ws + pl.off_scan, st));
   }
-  // group the slot's sessions by map and score constants; tables go to the slot buffer
+  // slot buffer: side tables | resampling offsets | item counters | group tables
+  size_t off = side_table_bytes((int)n);
+  const size_t off_r = off;
+  off = align256(off + n * sizeof(double));
+  const size_t off_queue = off;
+  off = align256(off + n * sizeof(unsigned long long));
+  double* h_r = (double*)(sl->h_tab + off_r);
+  std::memset(sl->h_tab + off_queue, 0, n * sizeof(unsigned long long));  // counters start at 0
+  std::vector<SideSeg> segs(n);
+  for (size_t i = 0; i < n; ++i) {
+    mcl_session_s* ss = sl->sessions[i];
+    const Plan& pl = ss->pl;
+    char* ws = ss->d_ws;
+    float* part = ss->d_part[ss->cur];
+    SideSeg& q = segs[i];
+    q = SideSeg{};
+    if (deltas[i]) {
+      q.mpart = part;
+      for (int k = 0; k < 6; ++k) {
+        q.mdelta[k] = dvals[i][k];
+        q.msig[k] = ss->msig[k];
+      }
+      q.mseed = ss->seed;
+      q.mstep = (unsigned long long)ss->step;
+    }
+    q.particles = part;
+    q.scan = ss->d_scan;
+    q.P = (int)ss->P;
+    q.N = (int)Ns[i];
+    if (pl.spatial) {
+      q.key = (uint32_t*)(ws + pl.off_key);
+      q.hist = (uint32_t*)(ws + pl.off_hist);
+      q.rank = (int*)(ws + pl.off_rank);
+      order_grid(ss->map->view, &q.order_o, &q.order_s);
+    }
+    q.mats = (float4*)(ws + pl.off_mats);
+    q.packed = ws + pl.off_scan;
+    q.layout = scan_layout(pl.sh);
+    q.partial = (const float*)(ws + pl.off_partial);
+    q.K = (int)((Ns[i] + pl.sh.chunk - 1) / pl.sh.chunk);
+    q.mode = ss->mode;
+    const double sig = (double)ss->sigma;
+    q.c = (float)(-0.5 / (sig * sig));
+    q.k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
+    q.logw = ss->d_logw;
+    q.w = ss->d_w;
+    q.stats = (float2*)(ws + pl.off_stats);
+    q.nb = normalise_blocks(q.P);
+    q.ostats = (float*)(ws + pl.off_ostats);
+    q.est_part = (EstPartial*)(ws + pl.off_est);
+    q.est = sl->d_est + i;
+    q.idx = ss->d_idx;
+    q.pin = part;
+    q.pout = ss->d_part[1 - ss->cur];
+    q.cum = (double*)(ws + ss->off_cum);
+    q.tile_total = (double*)(ws + ss->off_tot);
+    q.tile_last = (long long*)(ws + ss->off_last);
+    q.r = (const double*)(sl->d_tab + off_r) + i;
+    h_r[i] = resample_offset(ss->seed, (uint64_t)ss->step);
+  }
+  SideTables side;
+  side_tables(segs, sl->h_tab, sl->d_tab, &side);
+  // group the slot's sessions by map geometry and score constants
   struct G {
     mcl_map_t map;
     int mode, neglect;
@@ -196,14 +258,14 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     const int neglect = (ss->flags & MCL_NEGLECT_OUTSIDE) ? 1 : 0;
     G* g = nullptr;
     for (auto& x : groups)
-      if (x.map == ss->map && x.mode == ss->mode && x.flags == ss->flags && x.sigma == ss->sigma) g = &x;
+      if (same_geometry(x.map, ss->map) && x.mode == ss->mode && x.flags == ss->flags && x.sigma == ss->sigma)
+        g = &x;
     if (!g) {
       groups.push_back(G{ss->map, ss->mode, neglect, ss->flags, ss->sigma, {}});
       g = &groups.back();
     }
     g->idx.push_back(i);
   }
-  size_t off = 0;
   std::vector<BatchArgs> args(groups.size());
   std::vector<SensorShape> shapes(groups.size());
   for (size_t k = 0; k < groups.size(); ++k) {
@@ -222,10 +284,18 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       const int64_t N = Ns[g.idx[q]];
       sh = ss->pl.sh;
       const int K = (int)((N + sh.chunk - 1) / sh.chunk);
-      tab[q] = BatchSession{(const float4*)(ss->d_ws + ss->pl.off_mats),
-                            (const float4*)(ss->d_ws + ss->pl.off_scan),
-                            (float*)(ss->d_ws + ss->pl.off_partial), (int)ss->P, (int)N, ss->pl.nblk,
-                            K, ss->pl.sweep, ss->pl.sh.ppi};
+      BatchSession t{};
+      t.mats = (const float4*)(ss->d_ws + ss->pl.off_mats);
+      t.scan = (const float4*)(ss->d_ws + ss->pl.off_scan);
+      t.partial = (float*)(ss->d_ws + ss->pl.off_partial);
+      t.P = (int)ss->P;
+      t.N = (int)N;
+      t.nblk = ss->pl.nblk;
+      t.K = K;
+      t.sweep = ss->pl.sweep;
+      t.ppi = ss->pl.sh.ppi;
+      session_map(ss->map, &t);
+      tab[q] = t;
       beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
     }
     int bps = 0;
@@ -248,36 +318,27 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     set_fills(g.map, &a);
     a.cs = (float)(-0.5 / (sig * sig) * (q16 ? scale * scale : 1.0));
     a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
+    // nearest reads of brick maps: items handed out in order by a counter
+    if (g.map->kind == MCL_MAP_BRICK && !(g.flags & MCL_TRILINEAR) &&
+        (S->desc.shape.item_order == 0 || S->desc.shape.item_order == 3))
+      a.queue = (unsigned long long*)(sl->d_tab + off_queue) + k;
     b.sessions = (const BatchSession*)(sl->d_tab + off_tab);
     b.item_begin = (const long long*)(sl->d_tab + off_beg);
     b.n_sessions = (int)g.idx.size();
     b.n_items = beg[g.idx.size()];
   }
   MCL_CUDA(cudaMemcpyAsync(sl->d_tab, sl->h_tab, off, cudaMemcpyHostToDevice, st));
+  for (int k : {(int)kSideMotion, (int)kSideOrderZero, (int)kSideOrderKeys, (int)kSideOrderTiles,
+                (int)kSideOrderTotals, (int)kSideOrderScatter, (int)kSidePosePack})
+    if (mcl_status rc = enqueue_side(side, k, st)) return rc;
   for (size_t k = 0; k < groups.size(); ++k)
     MCL_CUDA(launch_sensor_batch(kernel_kind(groups[k].map), groups[k].map->view.layout, groups[k].map->dtype,
                                  args[k], shapes[k], st));
-  for (size_t i = 0; i < n; ++i) {
-    mcl_session_s* ss = sl->sessions[i];
-    const Plan& pl = ss->pl;
-    const int P = (int)ss->P;
-    const int K = (int)((Ns[i] + pl.sh.chunk - 1) / pl.sh.chunk);
-    int* rank = pl.spatial ? (int*)(ss->d_ws + pl.off_rank) : nullptr;
-    const double sig = (double)ss->sigma;
-    const float c = (float)(-0.5 / (sig * sig));
-    const float k = (float)(1.0 / std::sqrt(2.0 * 3.141592653589793 * sig * sig));
-    MCL_CUDA(launch_finish_and_normalise((float*)(ss->d_ws + pl.off_partial), rank, P, K, ss->mode, c, k,
-                                         ss->d_logw, nullptr, (float2*)(ss->d_ws + pl.off_stats),
-                                         normalise_blocks(P), nullptr, st));
-    MCL_CUDA(launch_normalise_from_stats(ss->d_logw, P, ss->d_w, (float2*)(ss->d_ws + pl.off_stats),
-                                         normalise_blocks(P), (float*)(ss->d_ws + pl.off_ostats),
-                                         ss->d_part[ss->cur], (EstPartial*)(ss->d_ws + pl.off_est),
-                                         ss->d_est, st));
-    MCL_CUDA(cudaMemcpyAsync(ss->h_est, ss->d_est, sizeof(mcl_estimate), cudaMemcpyDeviceToHost, st));
-    MCL_CUDA(launch_resample(ss->d_w, P, resample_offset(ss->seed, (uint64_t)ss->step), ss->d_idx,
-                             ss->d_part[ss->cur], ss->d_part[1 - ss->cur], (double*)(ss->d_ws + ss->off_cum),
-                             (double*)(ss->d_ws + ss->off_tot), (long long*)(ss->d_ws + ss->off_last), st));
-  }
+  for (int k : {(int)kSideStats, (int)kSideNormalise, (int)kSideEstimate})
+    if (mcl_status rc = enqueue_side(side, k, st)) return rc;
+  MCL_CUDA(cudaMemcpyAsync(sl->h_est, sl->d_est, n * sizeof(mcl_estimate), cudaMemcpyDeviceToHost, st));
+  for (int k : {(int)kSideTileScan, (int)kSideTileOffsets, (int)kSideSystematic})
+    if (mcl_status rc = enqueue_side(side, k, st)) return rc;
   MCL_CUDA(cudaLaunchHostFunc(st, on_slot_done, sl));
   return MCL_OK;
 }
@@ -291,7 +352,7 @@ void finalize(mcl_server_s* S, Slot* sl) {
     auto it = S->tickets.find(sl->tickets[i]);
     if (it != S->tickets.end()) {
       it->second.status = MCL_RESULT_DONE;
-      it->second.est = *ss->h_est;  // the slot's stream has completed
+      it->second.est = sl->h_est[i];  // the slot's stream has completed
       it->second.latency_ms = 1e3 * (t - it->second.t_submit);
       S->lat.push_back(it->second.latency_ms);
       S->evals += it->second.evals;
@@ -393,11 +454,12 @@ mcl_status mcl_server_create(const mcl_server_desc* d, mcl_server_t* out) {
   for (int i = 0; i < d->max_in_flight; ++i) {
     Slot* sl = new Slot();
     sl->srv = S;
-    // per group: align256(n * sizeof(BatchSession)) + align256((n + 1) * 8) <= 48 n + 526
-    sl->tab_bytes = (size_t)cap * (48 + 528) + 4096;
+    sl->tab_bytes = slot_table_bytes(cap);
     cudaError_t e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&sl->d_tab, sl->tab_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(&sl->h_tab, sl->tab_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sl->d_est, (size_t)cap * sizeof(mcl_estimate));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl->h_est, (size_t)cap * sizeof(mcl_estimate));
     S->slots.push_back(sl);
     if (e != cudaSuccess) {
       mcl_server_destroy(S);
@@ -472,8 +534,6 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   if (e == cudaSuccess) e = cudaMalloc(&ss->d_w, (size_t)P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ss->d_idx, (size_t)P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ss->d_ws, o);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&ss->d_est, sizeof(mcl_estimate));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&ss->h_est, sizeof(mcl_estimate));
   if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stage[0], (size_t)d->max_N * 12);
   if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stage[1], (size_t)d->max_N * 12);
   if (e == cudaSuccess) e = cudaMemcpy(ss->d_part[0], d->particles, (size_t)P * 24, cudaMemcpyHostToDevice);
@@ -672,6 +732,8 @@ mcl_status mcl_server_destroy(mcl_server_t S) {
     if (sl->st) cudaStreamDestroy(sl->st);
     cudaFree(sl->d_tab);
     cudaFreeHost(sl->h_tab);
+    cudaFree(sl->d_est);
+    cudaFreeHost(sl->h_est);
     delete sl;
   }
   delete S;

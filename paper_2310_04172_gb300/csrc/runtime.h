@@ -5,6 +5,7 @@
 
 #include <cstdarg>
 #include <cstdint>
+#include <vector>
 
 #include "mcl_internal.h"
 
@@ -32,6 +33,24 @@ mcl_status workspace(cudaStream_t s, size_t bytes, void** out);
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 inline bool finite_pos(float v) { return v == v && v > 0.f && v < 3.4e38f; }
+
+// Maps whose sessions can share one batched sensor launch (same kernel kind,
+// layout, storage type, geometry and kind of values), and the per-session
+// map fields of a batch table entry (mcl_batch.cpp).
+bool same_geometry(const mcl_map_s* a, const mcl_map_s* b);
+void session_map(const mcl_map_s* m, BatchSession* t);
+
+// Batched side launches (mcl_side.cpp): the session table and the block
+// prefix of every launch kind, written into one host buffer of
+// side_table_bytes(n) bytes whose device copy lives at d.
+struct SideTables {
+  const SideSeg* segs = nullptr;  // device
+  SegBlocks b[kSideLaunches];
+};
+size_t side_table_bytes(int n);
+void side_tables(const std::vector<SideSeg>& segs, char* h, char* d, SideTables* out);
+mcl_status enqueue_side(const SideTables& t, int kind, cudaStream_t s);
+int side_launch_count(const SideTables& t);  // launch kinds with work
 
 // Brackets the work enqueued in its scope with CUDA events while profiling is on.
 class PhaseScope {

@@ -1,8 +1,10 @@
-"""Batched step (one persistent kernel per map over (session, chunk, particle
-block) items of uneven size): every session's log-weights, weights and
-resampled indices (and pose estimates) are identical, bit for bit, to the single-session calls with
-the same chunk and lane split — alone or in the mix, plain or replayed from a
-CUDA graph."""
+"""Batched step (one persistent sensor kernel per group of sessions whose maps
+share geometry, over (session, chunk, particle block) items of uneven size;
+one launch per side step for all sessions): every session's log-weights,
+weights and resampled indices (and pose estimates) are identical, bit for bit,
+to the single-session calls with the same chunk and lane split — alone or in
+the mix, plain or replayed from a CUDA graph — and the launches of a step do
+not grow with the number of sessions."""
 import numpy as np
 import pytest
 
@@ -88,7 +90,8 @@ def batch_outputs(s):
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
-@pytest.mark.parametrize("chunk,lanes,item_order", [(2048, 32, 0), (1024, 16, 0), (2048, 32, 1)])
+@pytest.mark.parametrize("chunk,lanes,item_order", [(2048, 32, 0), (1024, 16, 0), (2048, 32, 1),
+                                                     (2048, 32, 3)])
 def test_batch_matches_single_sessions(env, use_graph, chunk, lanes, item_order):
     torch, mcl, room, hall, bld, maps = env
     rng = np.random.default_rng(11)
@@ -114,6 +117,49 @@ def test_batch_matches_single_sessions(env, use_graph, chunk, lanes, item_order)
                 assert np.array_equal(g, e), f"session {k} run {run}"
     assert b.info()["graph_captured"] == int(use_graph)
     b.close()
+
+
+def test_batch_shares_launches_across_maps(env):
+    """Sessions on two different building maps of one geometry (different
+    seeds) form one group: one sensor launch reads each session's own map.
+    The step's launches are the same for 1, 2, 4 and 8 sessions, and every
+    session equals its single call bit for bit."""
+    torch, mcl, room, hall, bld, maps = env
+    b1 = scenes.os064_building(P=3000, dtype=scenes.I16, seed=21, size=80.0, floors=2)
+    b2 = scenes.os064_building(P=3000, dtype=scenes.I16, seed=22, size=80.0, floors=2)
+    m1, m2 = mcl.map_from_scene(b1.map), mcl.map_from_scene(b2.map)
+    rng = np.random.default_rng(5)
+    counts = []
+    for S in (1, 2, 4, 8):
+        sessions = []
+        for k in range(S):
+            m, wl = (m1, b1) if k % 2 == 0 else (m2, b2)
+            P = 500 + 300 * k
+            parts = torch.from_numpy(np.ascontiguousarray(wl.particles[:P])).cuda()
+            s = {"map": m, "particles": parts, "scan": torch.from_numpy(wl.scan).cuda(),
+                 "sigma_hit": 0.1, "mode": 0, "logw": torch.empty(P, device="cuda"),
+                 "w": torch.empty(P, device="cuda"),
+                 "resample_idx": torch.empty(P, dtype=torch.int32, device="cuda"),
+                 "particles_out": torch.empty((P, 6), device="cuda")}
+            if k % 3 == 0:
+                s["estimate"] = mcl.estimate_buffer()
+            sessions.append(s)
+        b = mcl.Batch(sessions, use_graph=(S % 4 == 0))
+        info = b.info()
+        assert info["n_groups"] == 1
+        counts.append(info["kernels_per_run"])
+        r = rng.uniform(0, 1, S)
+        b.set_offsets(r)
+        b.run()
+        mcl.mcl_sync()
+        for k, s in enumerate(sessions):
+            ref = single(torch, mcl, s, float(r[k]), 0, 0)
+            for g, e in zip(batch_outputs(s), ref):
+                assert np.array_equal(g, e), f"S={S} session {k}"
+        b.close()
+    assert len(set(counts)) == 1, counts
+    m1.close()
+    m2.close()
 
 
 def test_batch_against_oracle(env):
