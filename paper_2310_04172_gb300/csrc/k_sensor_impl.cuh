@@ -404,14 +404,14 @@ __device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* 
 // a = f - i0 and 1 - a. A corner outside the grid or in no brick reads the
 // same value as an unstored voxel. The point counts as stored if any corner
 // is. Interpolation in FP32: along x for the four (y, z) corner pairs, then
-// y, then z, each step fma(a, v1 - v0, v0).
+// y, then z, each step fma(a, v1 - v0, v0). (Skipping the look-ups of bricks
+// beyond the first that no lane of the warp needs, decided by warp votes,
+// needs the whole warp on this path for every point: 595 against 459 ms for
+// 1M x 65,536, the early return for points outside the grid matters more.)
 template <int KIND, int DTYPE, int MODE>
-__device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y, float z,
+__device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float fy, float fz,
                                           bool& stored) {
   const MapView& m = a.map;
-  const float fx = __fsub_rn(__fmul_rn(__fsub_rn(x, m.ox), m.inv), 0.5f);
-  const float fy = __fsub_rn(__fmul_rn(__fsub_rn(y, m.oy), m.inv), 0.5f);
-  const float fz = __fsub_rn(__fmul_rn(__fsub_rn(z, m.oz), m.inv), 0.5f);
   stored = false;
   // Some corner is inside iff -1 <= f < n on every axis (NaN fails).
   if (!((fx >= -1.f) & (fx < m.fnx) & (fy >= -1.f) & (fy < m.fny) & (fz >= -1.f) & (fz < m.fnz)))
@@ -445,9 +445,9 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
     const uint32_t sx = (x0 & 15) == 15, sy = (y0 & 15) == 15, sz = (z0 & 15) == 15;
     const uint32_t nbx = m.nbx, nbxy = m.nbx * m.nby;
     const uint32_t k0 = ((uint32_t)(z0 >> 4) * m.nby + (uint32_t)(y0 >> 4)) * nbx + (uint32_t)(x0 >> 4);
-    const bool ux[2] = {inx[0], (sx != 0) & inx[1]};
-    const bool uy[2] = {iny[0], (sy != 0) & iny[1]};
-    const bool uz[2] = {inz[0], (sz != 0) & inz[1]};
+    const bool ux[2] = {inx[0], (sx != 0) && inx[1]};
+    const bool uy[2] = {iny[0], (sy != 0) && iny[1]};
+    const bool uz[2] = {inz[0], (sz != 0) && inz[1]};
     uint32_t b[8];  // slot of brick b0 + (q & 1, (q >> 1) & 1, q >> 2)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -550,32 +550,50 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float x, float y,
 
 // One particle's points of the staged chunk with the trilinear read: lane
 // glane takes points glane, glane + G, ... in order (the summation order of
-// the nearest-voxel path), two per loop step.
+// the nearest-voxel path), one pair (j, j + G) of the pair layout per loop
+// step. The transform and f = u - 1/2 run as packed FP32x2 instructions (the
+// same bits as the scalar chain: x - o is x + (-o), f - 1/2 is f + (-1/2));
+// rows: the group's duplicated pose entries, as for the nearest read.
 template <int KIND, int DTYPE, int MODE, int G>
-__device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __restrict__ sscan,
-                                         int glane, int cnt, const float4& r0, const float4& r1,
-                                         const float4& r2, float& acc) {
-  int j = glane;
-  for (; j + G < cnt; j += 2 * G) {
+__device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __restrict__ sxy,
+                                         const float2* __restrict__ sz, int glane, int cnt,
+                                         const float4* rows, float& acc) {
+  const MapView& m = a.map;
+  const float2 no_x = make_float2(-m.ox, -m.ox), no_y = make_float2(-m.oy, -m.oy),
+               no_z = make_float2(-m.oz, -m.oz), inv = make_float2(m.inv, m.inv),
+               half = make_float2(-0.5f, -0.5f);
+  for (int j = glane; j < cnt; j += 2 * G) {
+    // the rows are re-read each step: they hold no registers across the corner reads
+    const float4 q0 = lds_volatile(rows), q1 = lds_volatile(rows + 1), q2 = lds_volatile(rows + 2),
+                 q3 = lds_volatile(rows + 3), q4 = lds_volatile(rows + 4), q5 = lds_volatile(rows + 5);
+    const int pi = (j - glane) / (2 * G) * G + glane;
+    const float4 xy = sxy[pi];
+    const float2 zz = sz[pi];
+    const float2 zx = make_float2(xy.x, xy.y), zy = make_float2(xy.z, xy.w);
+    const float2 X = __ffma2_rn(make_float2(q0.x, q0.y), zx,
+                                __ffma2_rn(make_float2(q0.z, q0.w), zy,
+                                           __ffma2_rn(make_float2(q1.x, q1.y), zz, make_float2(q1.z, q1.w))));
+    const float2 Y = __ffma2_rn(make_float2(q2.x, q2.y), zx,
+                                __ffma2_rn(make_float2(q2.z, q2.w), zy,
+                                           __ffma2_rn(make_float2(q3.x, q3.y), zz, make_float2(q3.z, q3.w))));
+    const float2 W = __ffma2_rn(make_float2(q4.x, q4.y), zx,
+                                __ffma2_rn(make_float2(q4.z, q4.w), zy,
+                                           __ffma2_rn(make_float2(q5.x, q5.y), zz, make_float2(q5.z, q5.w))));
+    const float2 fx = __fadd2_rn(__fmul2_rn(__fadd2_rn(X, no_x), inv), half);
+    const float2 fy = __fadd2_rn(__fmul2_rn(__fadd2_rn(Y, no_y), inv), half);
+    const float2 fz = __fadd2_rn(__fmul2_rn(__fadd2_rn(W, no_z), inv), half);
     float d[2];
-    bool use[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      float x, y, w;
-      transform_point(r0, r1, r2, sscan[j + u * G], x, y, w);
-      bool st;
-      d[u] = tri_read<KIND, DTYPE, MODE>(a, x, y, w, st);
-      use[u] = st || !a.neglect;
+    bool use[2], st;
+    d[0] = tri_read<KIND, DTYPE, MODE>(a, fx.x, fy.x, fz.x, st);
+    use[0] = st || !a.neglect;
+    if (j + G < cnt) {
+      d[1] = tri_read<KIND, DTYPE, MODE>(a, fx.y, fy.y, fz.y, st);
+      use[1] = st || !a.neglect;
+    } else {
+      d[1] = 0.f;
+      use[1] = false;
     }
     accumulate<DTYPE, MODE, 2>(a, d, use, acc);
-  }
-  if (j < cnt) {
-    float x, y, w;
-    transform_point(r0, r1, r2, sscan[j], x, y, w);
-    bool st;
-    float d = tri_read<KIND, DTYPE, MODE>(a, x, y, w, st);
-    bool use = st || !a.neglect;
-    accumulate<DTYPE, MODE, 1>(a, &d, &use, acc);
   }
 }
 
@@ -655,8 +673,7 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const unsigne
   const int ngroups = (blockDim.x >> 5) * GPW;
   const int full_end = (cnt / STEP) * STEP;
   const float4* sxy = reinterpret_cast<const float4*>(sscan);
-  const float2* sz = nullptr;
-  if constexpr (!TRI) sz = reinterpret_cast<const float2*>(sscan + (size_t)a.layout.pairs(cnt) * 16);
+  const float2* sz = reinterpret_cast<const float2*>(sscan + (size_t)a.layout.pairs(cnt) * 16);
   // pnext (shared, zero at the item's start): the warps take the item's
   // particles from this counter, GPW at a time, so a warp that drew cheap
   // particles takes more and the item's closing barrier waits less; NULL:
@@ -671,9 +688,7 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const unsigne
     const bool gvalid = i < pn;  // (whole-warp groups: always, as i0 < pn)
     const size_t p = (size_t)p0 + (gvalid ? i : 0);
     float4* rows = smat + 6 * (warp * GPW + gid);
-    if constexpr (TRI) {
-      if (glane < 3) rows[glane] = __ldg(mats + 3 * p + glane);
-    } else if (glane < 6) {
+    if (glane < 6) {
       const float4 r = __ldg(mats + 3 * p + (glane >> 1));
       rows[glane] = (glane & 1) ? make_float4(r.z, r.z, r.w, r.w) : make_float4(r.x, r.x, r.y, r.y);
     }
@@ -681,9 +696,7 @@ __device__ __forceinline__ void process_block(const SensorArgs& a, const unsigne
     typename Raw<DTYPE, MODE>::acc acc = 0;
     if constexpr (TRI) {
       static_assert(G == 32, "the trilinear read uses whole-warp groups");
-      const float4 q0 = lds_volatile(rows), q1 = lds_volatile(rows + 1), q2 = lds_volatile(rows + 2);
-      eval_tri<KIND, DTYPE, MODE, G>(a, reinterpret_cast<const float4*>(sscan), glane, cnt, q0, q1,
-                                     q2, acc);
+      eval_tri<KIND, DTYPE, MODE, G>(a, sxy, sz, glane, cnt, rows, acc);
     } else {
       int base = 0;
       if (G == 32 || __all_sync(0xffffffffu, gvalid)) {

@@ -518,10 +518,11 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   DeviceState st;
   if (mcl_status rc = device_state(nullptr, &st)) return rc;
   SensorShape& sh = pl->sh;
-  // Brick maps read nearest: map larger than L2, where the sweep item order
-  // pays (measured on GB300: 1M x 65,536 int16 bricks 184.2 -> 177.4 ms
-  // static, 130.3 -> 113.8 ms handed out dynamically; slower for the
-  // L2-resident dense hall and the trilinear read).
+  // Brick maps: map larger than L2, where the sweep item order pays
+  // (measured on GB300: 1M x 65,536 int16 bricks 184.2 -> 177.4 ms static,
+  // 130.3 -> 113.8 ms handed out dynamically; the trilinear read 545.0 ->
+  // 460.8 ms dynamically, 584.4 ms static; slower for the L2-resident dense
+  // hall).
   const bool brick_nearest = m->kind == MCL_MAP_BRICK && !(p->flags & MCL_TRILINEAR);
   sh.chunk = p->points_per_chunk ? p->points_per_chunk : 2048;
   sh.lanes = p->lanes_per_particle ? p->lanes_per_particle : 32;
@@ -576,7 +577,7 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   // from two items per slot on.
   pl->sweep = pl->nblk;
   pl->dynamic = false;
-  const bool auto_sweeps = p->item_order == 0 && brick_nearest && pl->n_items >= 2 * slots;
+  const bool auto_sweeps = p->item_order == 0 && m->kind == MCL_MAP_BRICK && pl->n_items >= 2 * slots;
   const bool sweeps = p->item_order == 2;
   if ((p->item_order == 3 || auto_sweeps) && pl->K > 1 && slots >= pl->K) {
     // Dynamic sweeps: the same numbering, items handed out in order by a

@@ -218,10 +218,9 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       g.flags = u.flags;
       g.sigma = u.sigma_hit;
       g.sh = sp.pl.sh;
-      // items handed out by a counter for nearest reads of brick maps (as
-      // the single-session update does for large sets)
-      g.dynamic = u.map->kind == MCL_MAP_BRICK && !(u.flags & MCL_TRILINEAR) &&
-                  (bp->item_order == 0 || bp->item_order == 3);
+      // items handed out by a counter for brick maps (as the
+      // single-session update does for large sets)
+      g.dynamic = u.map->kind == MCL_MAP_BRICK && (bp->item_order == 0 || bp->item_order == 3);
       b->g.push_back(g);
       gi = (int)b->g.size() - 1;
     }

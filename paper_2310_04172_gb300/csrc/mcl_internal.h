@@ -155,16 +155,16 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
 #endif  // __CUDACC__
 
 // ---------------------------------------------------------------- launchers
-// Packed scan of one sensor update, chunk by chunk (a1). Nearest reads use
-// pairs: a lane group of G lanes takes points l, l + G, l + 2G, ... of a
-// chunk, two per step of its loop, so pair (s, l) of a chunk holds points
+// Packed scan of one sensor update, chunk by chunk (a1), in pairs: a lane
+// group of G lanes takes points l, l + G, l + 2G, ... of a chunk, two per
+// step of its loop, so pair (s, l) of a chunk holds points
 // s 2G + l and s 2G + G + l as XY = (x0, x1, y0, y1) (one float4) in a first
 // array and Z = (z0, z1) (one float2) in a second right after it: the lane
 // reads its two points with two shared loads and has each coordinate of the
 // two in one register pair for the packed FP32x2 instructions. A chunk of cnt
 // points holds pairs(cnt) = ceil(cnt / 2G) G pairs (24 bytes each; points past
-// cnt are zero) and starts at byte c * full_pairs() * 24. The trilinear read
-// keeps one float4 (x, y, z, 0) per point (pair_g = 0).
+// cnt are zero) and starts at byte c * full_pairs() * 24. Both reads (nearest
+// and trilinear) use it; pair_g = 0 packs one float4 (x, y, z, 0) per point.
 struct ScanLayout {
   int chunk;   // points per chunk
   int pair_g;  // G of the pair layout, 0: one float4 per point
@@ -194,9 +194,9 @@ struct SensorShape {
   int grid;       // CTAs (persistent)
 };
 
-// Scan layout of a launch shape: pairs for the nearest read, one float4 per
-// point for the trilinear read.
-inline ScanLayout scan_layout(const SensorShape& sh) { return ScanLayout{sh.chunk, sh.interp ? 0 : sh.lanes}; }
+// Scan layout of a launch shape: pairs of the shape's lane groups (the
+// nearest and the trilinear read).
+inline ScanLayout scan_layout(const SensorShape& sh) { return ScanLayout{sh.chunk, sh.lanes}; }
 
 struct SensorArgs {
   MapView map;

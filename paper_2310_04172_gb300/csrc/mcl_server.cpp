@@ -318,9 +318,8 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     set_fills(g.map, &a);
     a.cs = (float)(-0.5 / (sig * sig) * (q16 ? scale * scale : 1.0));
     a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
-    // nearest reads of brick maps: items handed out in order by a counter
-    if (g.map->kind == MCL_MAP_BRICK && !(g.flags & MCL_TRILINEAR) &&
-        (S->desc.shape.item_order == 0 || S->desc.shape.item_order == 3))
+    // brick maps: items handed out in order by a counter
+    if (g.map->kind == MCL_MAP_BRICK && (S->desc.shape.item_order == 0 || S->desc.shape.item_order == 3))
       a.queue = (unsigned long long*)(sl->d_tab + off_queue) + k;
     b.sessions = (const BatchSession*)(sl->d_tab + off_tab);
     b.item_begin = (const long long*)(sl->d_tab + off_beg);

@@ -300,7 +300,7 @@ def test_item_order_gives_identical_bits(torch_cuda, mcl, building_i16):
     small = mcl.mcl_sensor_plan_get(m, 1000, len(scan), mcl.sensor_params(0.1))
     assert small["item_order"] == 1                       # too few items: chunk-major
     tri = mcl.mcl_sensor_plan_get(m, len(parts), len(scan), mcl.sensor_params(0.1, flags=mcl.MCL_TRILINEAR))
-    assert tri["item_order"] == 1                         # auto: sweeps only for the nearest read
+    assert tri["item_order"] == 3                         # auto: dynamic sweeps for the trilinear read too
     Lo = oracle.sensor_update(oracle.Map.from_scene_map(wl.map), parts[:200], scan, wl.sigma_hit)
     check_logw(res[(3, ())][0][:200], Lo)
     m.close()
