@@ -528,11 +528,13 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
   sh.lanes = p->lanes_per_particle ? p->lanes_per_particle : 32;
   sh.ppi = p->particles_per_item ? p->particles_per_item : (brick_nearest ? 64 : 128);
   // Eight look-ups in flight per lane (64 registers, 4 CTAs per SM) for the
-  // cell-grid brick map: the packed pair stage halves the pose-row reloads
-  // per point against four (1M x 65,536 int16 building: 97.0 against 102.6
-  // ms at 5 CTAs); four elsewhere.
-  const bool grid_nearest = brick_nearest && m->d_grid != nullptr;
-  sh.unroll = p->unroll ? p->unroll : (grid_nearest ? 8 : 4);
+  // nearest read of the cell-grid brick map and of dense maps: the packed
+  // pair stage re-reads the pose rows half as often as with four (1M x
+  // 65,536 int16 building: 97.0 against 102.6 ms at 5 CTAs; 50,000 x 28,800
+  // dense FP32 hall: 1.74 against 1.97 ms); four for the hash index.
+  const bool nearest = !(p->flags & MCL_TRILINEAR);
+  const bool deep = nearest && (m->kind == MCL_MAP_DENSE || m->d_grid != nullptr);
+  sh.unroll = p->unroll ? p->unroll : (deep ? 8 : 4);
   sh.pipeline = p->pipeline == 2 ? 1 : 0;
   // unroll and pipeline are hints: lane groups narrower than a warp run the
   // plain 4-deep loop, and the pipelined loop exists for 2 or 4 look-ups.
