@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--item-order", type=int, default=0,
                     help="work-item order: 0 auto, 1 chunk-major, 2 sweeps, 3 dynamic sweeps")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
+    ap.add_argument("--trilinear", action="store_true",
+                    help="the trilinear read (eight corners per evaluation) instead of the nearest voxel")
     ap.add_argument("--index", type=int, default=0, help="brick index: 0 auto, 1 hash, 2 cell grid")
     ap.add_argument("--mode", default="headline",
                     choices=["headline", "serving", "precision", "vlp16", "filter", "variants", "trilinear"],
@@ -68,6 +70,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run of the headline")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the weight-error report and the storage/form comparison of the headline")
+    ap.add_argument("--no-vlp16", action="store_true",
+                    help="skip the VLP-16 tracking workload (dense hall) of the headline")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     ap.add_argument("--serving-batch", type=int, default=0,
                     help="sessions per batched serving step (0: the default policy)")
@@ -189,7 +193,7 @@ def make_workload(args, rank: int, with_f32: bool = False):
     reference values of the weight-error report and the FP32 comparison)."""
     import scenes
     dt = {"f32": scenes.F32, "f16": scenes.F16, "i16": scenes.I16}[args.dtype]
-    dts = tuple(sorted({dt, scenes.F32})) if with_f32 else None
+    dts = tuple(sorted({dt, scenes.F32, scenes.F16})) if with_f32 else None
     return scenes.os064_building(P=args.particles, dtype=dt, seed=3, azimuths=args.azimuths,
                                  size=args.building, floors=args.floors, dtypes=dts)
 
@@ -339,6 +343,7 @@ def config_dict(args, wl):
                 "dims": list(m.dims), "bricks": int(len(m.coords)), "bytes": int(m.values.nbytes),
                 "truncation_m": 0.3},
         "sigma_hit": wl.sigma_hit, "mode": "logprod",
+        "read": "trilinear (8 corners)" if args.trilinear else "nearest voxel",
         "l2": "inputs larger than L2 (map %.2f GB, L2 129 MB)" % (m.values.nbytes / 1e9),
     }
 
@@ -378,7 +383,8 @@ def run_ours(args):
     prm = mcl.sensor_params(sigma_hit=wl.sigma_hit, points_per_chunk=args.chunk,
                             lanes_per_particle=args.lanes, particles_per_item=args.ppi,
                             unroll=args.unroll, pipeline=args.pipeline, particle_order=args.order,
-                            item_order=args.item_order)
+                            item_order=args.item_order,
+                            flags=mcl.MCL_TRILINEAR if args.trilinear else 0)
     plan = mcl.mcl_sensor_plan_get(m, P, N, prm)
 
     def step(k, s):
@@ -418,15 +424,16 @@ def run_ours(args):
     # roofline of the dominant kernel, timed live in the region above
     sensor_ms = prof["sensor"]["ms"] / max(1, prof["sensor"]["launches"])
     index_entry = {1: 8, 2: 4}.get(m.info()["index"], 0)
-    abytes = algorithmic_bytes(P, N, elem, index_entry)
+    corners = 8 if args.trilinear else 1
+    abytes = algorithmic_bytes(P, N, corners * elem, index_entry)
     achieved = abytes / (sensor_ms / 1e3) / 1e9
     peak, peak_src = peaks()
-    traffic = measured_traffic(P, N)
+    traffic = None if args.trilinear else measured_traffic(P, N)  # the record is the nearest read's
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
             "kernel": "k_sensor", "kernel_ms": sensor_ms,
             "algorithmic_bytes_per_launch": abytes,
-            "bytes_per_eval": elem + index_entry}
+            "bytes_per_eval": corners * elem + index_entry}
 
     # gather roofline: uniform-random element reads over a buffer of the map's size
     gather = None
@@ -469,6 +476,13 @@ def run_ours(args):
         except Exception as e:  # the headline line is printed whatever happens here
             precision = {"error": f"{type(e).__name__}: {e}"}
 
+    vlp16 = None
+    if rank == 0 and not args.no_vlp16:
+        try:
+            vlp16 = vlp16_block(torch, mcl, max(args.steps, 20))
+        except Exception as e:
+            vlp16 = {"error": f"{type(e).__name__}: {e}"}
+
     serving = None
     if rank == 0 and not args.no_serving:
         try:
@@ -488,7 +502,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roof, "gather_roofline": gather, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
-            "precision": precision, "quantised_vs_plain_fp32": forms, "serving": serving,
+            "precision": precision, "quantised_vs_plain_fp32": forms, "vlp16_tracking": vlp16,
+            "serving": serving,
             "energy": energy(clocks.summary(), ms_max / args.steps, float(P) * N),
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["launches"]},
         }
@@ -627,6 +642,58 @@ def serving_sessions(mcl, srv, maps, n, p_lo, p_hi, seed):
     return out
 
 
+def vlp16_block(torch, mcl, reps: int):
+    """The VLP-16 tracking workload: dense 512x512x128 FP32 hall (and the same
+    hall as FP16), 50,000 Gaussian particles x 28,800 points; one step =
+    sensor update + normalisation + resampling, plain calls against the
+    batched, graph-captured form."""
+    import scenes
+    wl = scenes.vlp16_multiroom(P=50_000, dtype=scenes.F32)
+    m = mcl.map_from_scene(wl.map)
+    parts = torch.from_numpy(wl.particles).cuda()
+    nxt = torch.empty_like(parts)
+    scan = torch.from_numpy(wl.scan).cuda()
+    P, N = parts.shape[0], scan.shape[0]
+    logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+    idx = torch.empty(P, dtype=torch.int32, device="cuda")
+    prm = mcl.sensor_params(wl.sigma_hit)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        e.synchronize()
+        return a.elapsed_time(e) / reps
+
+    def plain(mm):
+        mcl.mcl_sensor_update(mm, parts, scan, prm, logw, w)
+        mcl.mcl_resample(w, 0.5, idx, parts, nxt)
+
+    ms_plain = timed(lambda: plain(m))
+    batch = mcl.Batch([{"map": m, "particles": parts, "scan": scan, "logw": logw, "w": w,
+                        "resample_idx": idx, "particles_out": nxt}], use_graph=True)
+    batch.set_offsets([0.5])
+    ms_batch = timed(batch.run)
+    kernels = batch.info()["kernels_per_run"]
+    batch.close()
+    m.close()
+    wl16 = scenes.vlp16_multiroom(P=16, dtype=scenes.F16)
+    m16 = mcl.map_from_scene(wl16.map)
+    ms_f16 = timed(lambda: plain(m16))
+    m16.close()
+    ev = float(P) * N
+    return {"workload": wl.name, "particles": P, "points": N,
+            "plain": {"ms_per_step": ms_plain, "evals_per_s": ev / (ms_plain / 1e3)},
+            "batched_graph": {"ms_per_step": ms_batch, "evals_per_s": ev / (ms_batch / 1e3),
+                              "kernels_per_step": kernels},
+            "plain_f16_map": {"ms_per_step": ms_f16, "evals_per_s": ev / (ms_f16 / 1e3)}}
+
+
 def serving_block(mcl, seconds: float, max_batch: int = 0):
     """The 64-session serving workload: 64 robot sessions over 8 maps (4 dense
     512x512x128 FP16 halls, 4 brick int16 160x160x20 m buildings), P
@@ -748,6 +815,9 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     plain = mcl.sensor_params(wl.sigma_hit, particle_order=1, item_order=1)
     ms_f32 = timed(lambda: mcl.mcl_sensor_update(m32, parts, scan, prm, logw, w))
     ms_f32_plain = timed(lambda: mcl.mcl_sensor_update(m32, parts, scan, plain, logw, w))
+    m16 = mcl.map_from_scene(maps[scenes.F16])
+    ms_f16 = timed(lambda: mcl.mcl_sensor_update(m16, parts, scan, prm, logw, w))
+    m16.close()
     S = 4
     per = P // S
     sess_parts = [parts[k * per:(k + 1) * per].contiguous() for k in range(S)]
@@ -772,6 +842,7 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
         "f32_same_shape": form(ms_f32),
         "f32_plain_per_session": dict(form(ms_f32_plain), shape="particles as given, chunk-major items"),
         "i16_single": form(head_kernel_ms),
+        "f16_same_shape": form(ms_f16),
         "i16_batched_graph_4x250000": dict(form(ms_batch), kernels_per_run=kernels),
         "speedup_i16_batched_vs_f32_same_shape": ms_f32 / ms_batch,
         "speedup_i16_batched_vs_f32_plain": ms_f32_plain / ms_batch,
