@@ -1,0 +1,149 @@
+"""The sensor kernels' voxel rule at its edges, against the oracle's FP32 rule.
+
+The kernels take floor(u) from the bits of a round-down u + 2^23 and test
+0 <= u < n with one unsigned compare per axis (packed FP32x2 for two points
+at a time); the oracle compares u with 0 and n in FP32 and truncates (Sec.
+III look-up; readings r3 and r19). Here every particle sits at an adversarial
+position with identity rotation and the scan is one point at the sensor
+origin, so a particle's log-weight is the score of exactly the voxel its
+position falls in, or of +tau outside: voxel faces, -0, one ulp below 0,
+one ulp below n, n, 2^23 and beyond, 1e30, +-inf, NaN, on maps with negative
+and positive origins. Neighbouring voxels hold distinct values, so a wrong
+voxel shows as a wrong log-weight.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+TAU = 0.3
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2310_04172_gb300 import _build, mcl
+    _build.build()
+    mcl.lib()
+    torch.cuda.set_device(0)
+    return torch, mcl
+
+
+def values_f64(dims):
+    nx, ny, nz = dims
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return TAU * (((7 * ix + 13 * iy + 29 * iz) % 61) / 30.5 - 1.0)
+
+
+def quantise(v, dtype):
+    if dtype == scenes.F32:
+        return v.astype(np.float32)
+    if dtype == scenes.F16:
+        return v.astype(np.float16)
+    return np.rint(v / TAU * 32767.0).astype(np.int16)
+
+
+def dense_map(origin, dims, dtype):
+    v = quantise(values_f64(dims), dtype)
+    return scenes.DenseMap(tuple(origin), 0.05, tuple(dims), TAU, dtype, v)
+
+
+def brick_map(origin, dims, dtype):
+    """All bricks of the extent but one (which reads +tau)."""
+    full = quantise(values_f64(dims), dtype)  # (nz, ny, nx)
+    nb = [d // 16 for d in dims]
+    coords, vals = [], []
+    for bz in range(nb[2]):
+        for by in range(nb[1]):
+            for bx in range(nb[0]):
+                if (bx, by, bz) == (1, 0, 1):
+                    continue
+                coords.append((bx, by, bz))
+                vals.append(full[16 * bz:16 * bz + 16, 16 * by:16 * by + 16, 16 * bx:16 * bx + 16])
+    return scenes.BrickMap(tuple(origin), 0.05, tuple(dims), TAU, dtype,
+                           np.array(coords, np.int32), np.ascontiguousarray(np.stack(vals)))
+
+
+def edge_positions(origin, dims, voxel=0.05):
+    """Positions whose u = (x - o) / r sits at or next to the rule's edges on
+    one axis, the other two coordinates well inside."""
+    o = np.asarray(origin, np.float32)
+    mid = o + np.float32(voxel) * (np.asarray(dims, np.float32) / 2 + np.float32(0.3))
+    pts = []
+    for axis in range(3):
+        n = dims[axis]
+        cand = []
+        for u in (0.0, 1.0, 2.0, n - 1.0, float(n), n + 1.0, 0.5, n - 0.5, 2.0 ** 23, 2.0 ** 24):
+            x = np.float32(o[axis] + np.float64(u) * voxel)
+            cand += [x, np.nextafter(x, np.float32(-np.inf)), np.nextafter(x, np.float32(np.inf)),
+                     np.nextafter(np.nextafter(x, np.float32(-np.inf)), np.float32(-np.inf))]
+        cand += [o[axis], np.float32(-0.0), np.float32(0.0), np.float32(1e30), np.float32(-1e30),
+                 np.float32(np.inf), np.float32(-np.inf), np.float32(np.nan),
+                 np.nextafter(o[axis], np.float32(-np.inf))]
+        for c in cand:
+            p = mid.copy()
+            p[axis] = c
+            pts.append(p)
+    # face crossings in every axis at once
+    for k in range(0, 17):
+        pts.append(o + np.float32(0.05) * np.float32(k) + np.zeros(3, np.float32))
+    return np.array(pts, np.float32)
+
+
+def run_case(torch, mcl, smap, layout=0, index=0):
+    pos = edge_positions(smap.origin, smap.dims)
+    parts = np.zeros((len(pos), 6), np.float32)
+    parts[:, :3] = pos
+    scan = np.zeros((1, 3), np.float32)
+    m = mcl.map_from_scene(smap, layout, index) if smap.kind == "brick" else mcl.map_from_scene(smap)
+    P = len(parts)
+    logw = torch.empty(P, device="cuda")
+    results = []
+    for shape in (dict(), dict(lanes_per_particle=8), dict(unroll=4), dict(unroll=2)):
+        prm = mcl.sensor_params(0.1, **shape)
+        mcl.mcl_sensor_update(m, torch.from_numpy(parts).cuda(), torch.from_numpy(scan).cuda(), prm, logw)
+        mcl.mcl_sync()
+        results.append(logw.cpu().numpy().astype(np.float64))
+    m.close()
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(smap), parts, scan, 0.1)
+    for Lg in results:
+        assert np.array_equal(Lg, results[0])  # the same bits whatever the launch shape
+        err = np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo))
+        bad = np.flatnonzero(~(err <= 1e-5))
+        assert len(bad) == 0, f"positions {pos[bad[:5]]}: GPU {Lg[bad[:5]]} oracle {Lo[bad[:5]]}"
+    # the outside value is reached for the far positions, so both branches are exercised
+    outside = -(TAU * TAU) / (2 * 0.01)
+    assert np.any(np.isclose(Lo, outside, rtol=1e-6)) and np.any(~np.isclose(Lo, outside, rtol=1e-6))
+
+
+@pytest.mark.parametrize("origin", [(0.0, 0.0, 0.0), (-1.6, -0.8, -0.4), (3.15, -2.05, 0.6)])
+@pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16])
+def test_dense_index_edges(env, origin, dtype):
+    torch, mcl = env
+    run_case(torch, mcl, dense_map(origin, (48, 32, 32), dtype))
+
+
+@pytest.mark.parametrize("origin", [(0.0, 0.0, 0.0), (-1.6, -0.8, -0.4)])
+@pytest.mark.parametrize("layout,index", [(0, 2), (0, 1), (1, 1)])
+def test_brick_index_edges(env, origin, layout, index):
+    torch, mcl = env
+    run_case(torch, mcl, brick_map(origin, (48, 32, 32), scenes.I16), layout, index)
+
+
+def test_dims_beyond_the_index_rule_are_refused(env):
+    torch, mcl = env
+    empty = np.zeros((0, 16, 16, 16), np.int16)
+    with pytest.raises(mcl.MclError) as e:
+        mcl.mcl_map_create(mcl.MCL_MAP_BRICK, mcl.MCL_I16, (0.0, 0.0, 0.0), np.float32(0.05),
+                           np.float32(TAU), (2 ** 23 + 16, 16, 16), empty, np.zeros((0, 3), np.int32))
+    assert e.value.status == mcl.MCL_EINVAL
+    m = mcl.mcl_map_create(mcl.MCL_MAP_BRICK, mcl.MCL_I16, (0.0, 0.0, 0.0), np.float32(0.05),
+                           np.float32(TAU), (2 ** 23, 16, 16), empty, np.zeros((0, 3), np.int32),
+                           index=mcl.MCL_INDEX_HASH)
+    m.close()
