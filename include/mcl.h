@@ -445,10 +445,16 @@ typedef struct mcl_batch_params {
 typedef struct mcl_batch_s* mcl_batch_t;
 
 /* Plans a batched step over n sessions (Sec. V-B: every particle evaluated
- * in parallel, here across robots too): sessions are grouped by map and score
- * constants; each group runs as one persistent kernel over (session, point
- * chunk, particle block) work items of uneven size. Allocates the plan's
- * device scratch. EINVAL for any invalid session (as mcl_sensor_update). */
+ * in parallel, here across robots too). Sessions whose maps share kernel
+ * kind, storage type, geometry (origin, voxel, dims, truncation) and kind of
+ * values, and that share mode, flags and sigma, form a group; each group
+ * runs as one persistent kernel over the (session, point chunk, particle
+ * block) work items of its sessions, each session reading its own map. The
+ * side steps (spatial order, pose matrices and scan packing, log-weights,
+ * normalisation with the estimate, resampling) run as one launch each for
+ * all sessions, so a step's launches do not grow with n. Allocates the
+ * plan's device scratch. EINVAL for any invalid session (as
+ * mcl_sensor_update). */
 mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
                             const mcl_batch_params* params, mcl_batch_t* out);
 
@@ -456,12 +462,13 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
  * session order), copied to the device on `stream`. */
 mcl_status mcl_batch_set_offsets(mcl_batch_t b, const double* r, mcl_stream_t stream);
 
-/* Enqueues one step for every session on `stream`: pose matrices, scan
- * packing, the grouped sensor kernels, log-weights, normalisation and the
- * requested resampling. */
+/* Enqueues one step for every session on `stream`: spatial order, pose
+ * matrices, scan packing, the grouped sensor kernels, log-weights,
+ * normalisation (and estimates) and the requested resampling. */
 mcl_status mcl_batch_run(mcl_batch_t b, mcl_stream_t stream);
 
-/* Work items and launches of the plan (for reporting). */
+/* Work items and launches of the plan (for reporting): n_groups sensor
+ * kernels, kernels_per_run launches in all. */
 typedef struct mcl_batch_info {
   uint32_t struct_size;
   int32_t n_sessions, n_groups;
