@@ -232,6 +232,14 @@ __device__ __forceinline__ float4 lds_volatile(const float4* p) {
 // group's six float4 of duplicated pose entries (pair_rows).
 constexpr uint32_t kFloorBits = 0x4B000000u;  // bits of 2^23
 
+// Cell-grid kind: instead of the inside test, each index is clamped to n
+// (unsigned min), which sends every point outside the grid to a guard cell
+// of the padded cell grid that holds no brick, so it reads the outside value
+// exactly as the test would give, and the cell look-up needs no predicate.
+#ifndef MCL_GRID_CLAMP
+#define MCL_GRID_CLAMP 1
+#endif
+
 template <int KIND, int DTYPE, int MODE, int G, int U, bool FULL>
 __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4* __restrict__ sxy,
                                               const float2* __restrict__ sz, int base, int glane,
@@ -272,12 +280,22 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int u = 2 * k + h;
-      const uint32_t ix = __float_as_uint(h ? fx.y : fx.x) - kFloorBits;
-      const uint32_t iy = __float_as_uint(h ? fy.y : fy.x) - kFloorBits;
-      const uint32_t iz = __float_as_uint(h ? fz.y : fz.x) - kFloorBits;
-      s.in[u] = s.v[u] && (ix < (uint32_t)m.nx) && (iy < (uint32_t)m.ny) && (iz < (uint32_t)m.nz);
+      uint32_t ix = __float_as_uint(h ? fx.y : fx.x) - kFloorBits;
+      uint32_t iy = __float_as_uint(h ? fy.y : fy.x) - kFloorBits;
+      uint32_t iz = __float_as_uint(h ? fz.y : fz.x) - kFloorBits;
+      if constexpr (KIND == kKindBrickGrid && MCL_GRID_CLAMP) {
+        ix = min(ix, (uint32_t)m.nx);
+        iy = min(iy, (uint32_t)m.ny);
+        iz = min(iz, (uint32_t)m.nz);
+        s.in[u] = s.v[u];
+      } else {
+        s.in[u] = s.v[u] && (ix < (uint32_t)m.nx) && (iy < (uint32_t)m.ny) && (iz < (uint32_t)m.nz);
+      }
       if constexpr (KIND == MCL_MAP_DENSE) {
         s.key[u] = (iz * (uint32_t)m.ny + iy) * (uint32_t)m.nx + ix;
+      } else if constexpr (KIND == kKindBrickGrid) {
+        s.key[u] = (iz >> 4) * m.gsz + (iy >> 4) * m.gsy + (ix >> 4);
+        s.loc[u] = brick_local<KIND>((int)ix, (int)iy, (int)iz);
       } else {
         s.key[u] = ((iz >> 4) * m.nby + (iy >> 4)) * m.nbx + (ix >> 4);
         s.loc[u] = brick_local<KIND>((int)ix, (int)iy, (int)iz);
@@ -441,16 +459,22 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
     // the lower one sits on the brick's last voxel (s = 1; always so for
     // i0 = -1). Corner c therefore lies in brick b0 + (c_x s_x, c_y s_y,
     // c_z s_z): at most 2^(s_x + s_y + s_z) distinct bricks, one for 82 % of
-    // the points of the building scan. A brick is looked up only if a corner
-    // inside the grid lies in it; a corner outside the grid maps to a brick
-    // that was not looked up, so its slot is empty. Brick keys are formed in
-    // 32-bit arithmetic, which wraps consistently for i0 = -1.
+    // the points of the building scan. Hash index: a brick is looked up only
+    // if a corner inside the grid lies in it; a corner outside the grid maps
+    // to a brick that was not looked up, so its slot is empty. Cell grid: the
+    // cells at -1 and nb along each axis are guard cells that hold no brick,
+    // so every brick a corner lies in is looked up as it is. Brick keys are
+    // formed in 32-bit arithmetic, which wraps consistently for i0 = -1; a
+    // cell-grid key is then a signed offset from cell (0, 0, 0) (down to the
+    // first front guard cell) and is sign-extended before it meets the pointer.
     const uint32_t sx = (x0 & 15) == 15, sy = (y0 & 15) == 15, sz = (z0 & 15) == 15;
-    const uint32_t nbx = m.nbx, nbxy = m.nbx * m.nby;
-    const uint32_t k0 = ((uint32_t)(z0 >> 4) * m.nby + (uint32_t)(y0 >> 4)) * nbx + (uint32_t)(x0 >> 4);
-    const bool ux[2] = {inx[0], (sx != 0) && inx[1]};
-    const bool uy[2] = {iny[0], (sy != 0) && iny[1]};
-    const bool uz[2] = {inz[0], (sz != 0) && inz[1]};
+    constexpr bool kGuard = KIND == kKindBrickGrid && MCL_GRID_CLAMP;
+    const uint32_t nbx = KIND == kKindBrickGrid ? m.gsy : m.nbx,
+                   nbxy = KIND == kKindBrickGrid ? m.gsz : m.nbx * m.nby;
+    const uint32_t k0 = (uint32_t)(z0 >> 4) * nbxy + (uint32_t)(y0 >> 4) * nbx + (uint32_t)(x0 >> 4);
+    const bool ux[2] = {kGuard || inx[0], (sx != 0) && (kGuard || inx[1])};
+    const bool uy[2] = {kGuard || iny[0], (sy != 0) && (kGuard || iny[1])};
+    const bool uz[2] = {kGuard || inz[0], (sz != 0) && (kGuard || inz[1])};
     uint32_t b[8];  // slot of brick b0 + (q & 1, (q >> 1) & 1, q >> 2)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -458,7 +482,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
       const bool need = ux[qx] & uy[qy] & uz[qz];
       const uint32_t key = k0 + (uint32_t)qx + (uint32_t)qy * nbx + (uint32_t)qz * nbxy;
       if constexpr (KIND == kKindBrickGrid) {
-        b[q] = need ? __ldg(m.grid + key) : kNoSlot;
+        b[q] = need ? __ldg(m.grid + (int32_t)key) : kNoSlot;
       } else {
         b[q] = kNoSlot;
         if (need) {
@@ -518,9 +542,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
       else if (cz && (inx[cx] & iny[cy] & inz[0]) && key[c ^ 4] == key[c]) r = c ^ 4;
       if (r >= 0) {
         slot[c] = slot[r];
-      } else if constexpr (KIND == kKindBrickGrid) {
-        slot[c] = __ldg(m.grid + key[c]);
-      } else {
+      } else {  // 4x4x4-block bricks have the hash index only
         const uint32_t h = brick_hash(key[c], m.hash_shift);
         const uint2 e = __ldg(m.table + h);
         slot[c] = e.x == key[c] ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key[c], h));

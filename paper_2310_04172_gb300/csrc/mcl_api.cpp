@@ -312,12 +312,23 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
       cudaFree(stage);
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create block layout"));
     }
-    const uint64_t cells = nbx * nby * nbz;
+    // The cell grid with a guard layer: one more cell along each axis (cell
+    // nb) and gsz + gsy + 1 cells in front, all empty. Every cell coordinate
+    // in [-1, nb] then has its own cell (a guard one outside the map), so a
+    // voxel index clamped to n, or a trilinear corner at -1 or n, reads "no
+    // brick" without an inside test.
+    const uint64_t gsy = nbx + 1, gsz = (nbx + 1) * (nby + 1), front = gsz + gsy + 1;
+    const uint64_t cells = front + gsz * (nbz + 1);
+    if (d->index == MCL_INDEX_GRID && cells > 0x7FFFFFFFull)
+      return cleanup(fail(MCL_EINVAL, "map_create: %llu grid cells exceed signed 32-bit keys; use the hash index",
+                          (unsigned long long)cells));
     const bool grid = d->index == MCL_INDEX_GRID ||
                       (d->index == MCL_INDEX_AUTO && v.layout == MCL_LAYOUT_LINEAR &&
                        cells * sizeof(uint32_t) <= (512ull << 20) && nb <= kGridMaxBricks);
     v.nbx = (uint32_t)nbx;
     v.nby = (uint32_t)nby;
+    v.gsy = (uint32_t)gsy;
+    v.gsz = (uint32_t)gsz;
     v.n_slots = (uint32_t)nb;
     m->n_bricks = nb;
     if (grid) {
@@ -326,14 +337,15 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
       std::vector<uint32_t> cell_slot((size_t)cells, kNoSlot);
       for (int64_t b = 0; b < nb; ++b) {
         const int32_t* c = d->brick_coords + 3 * b;
-        cell_slot[((uint64_t)c[2] * nby + (uint64_t)c[1]) * nbx + (uint64_t)c[0]] = (uint32_t)b;
+        cell_slot[front + (uint64_t)c[2] * gsz + (uint64_t)c[1] * gsy + (uint64_t)c[0]] = (uint32_t)b;
       }
       e = cudaMalloc((void**)&m->d_grid, (size_t)cells * sizeof(uint32_t));
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create grid index"));
       e = cudaMemcpy(m->d_grid, cell_slot.data(), (size_t)cells * sizeof(uint32_t), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create grid upload"));
-      v.grid = m->d_grid;
+      v.grid = m->d_grid + front;
       m->grid_cells = (int64_t)cells;
+      m->grid_front = (int64_t)front;
       m->bytes = (int64_t)vbytes + (int64_t)cells * (int64_t)sizeof(uint32_t);
     } else {
       e = cudaMalloc(&m->d_table, (size_t)cap * sizeof(uint2));
@@ -401,7 +413,7 @@ mcl_status mcl_map_create_score(mcl_map_t src, float sigma, int32_t dtype, mcl_m
   m->score_sigma = sigma;
   m->view.values = m->d_values;
   m->view.table = m->d_table;
-  m->view.grid = m->d_grid;
+  m->view.grid = m->d_grid ? m->d_grid + m->grid_front : nullptr;
   m->view.tau = m->score_outside;  // what a look-up reads where nothing is stored
   m->bytes = (int64_t)n * (int64_t)es + (m->d_table ? m->capacity * (int64_t)sizeof(uint2) : 0) +
              (m->d_grid ? m->grid_cells * (int64_t)sizeof(uint32_t) : 0);

@@ -38,13 +38,16 @@ enum : unsigned { kDevErrTimeout = 1u, kDevErrIndex = 2u };
 struct MapView {
   const void* values;   // dense grid or brick-major values
   const uint2* table;   // BRICK, hash index: open-addressing hash (key, slot), capacity 2^bits
-  const uint32_t* grid; // BRICK, grid index: slot of each brick cell (kNoSlot if none)
+  const uint32_t* grid; // BRICK, grid index: slot of each brick cell (kNoSlot if none), cell
+                        // (cx, cy, cz) at cz * gsz + cy * gsy + cx for every cx in [-1, nbx],
+                        // cy in [-1, nby], cz in [-1, nbz] (guard cells outside the map)
   uint32_t n_slots;     // BRICK: bricks stored (slots are below this)
   float ox, oy, oz;     // grid corner
   float inv;            // 1 / voxel as used by the index rule
   float fnx, fny, fnz;  // dims as FP32 for the inside test
   int nx, ny, nz;
   uint32_t nbx, nby;    // BRICK: brick grid size (x, y)
+  uint32_t gsy, gsz;    // BRICK, grid index: cell strides nbx + 1 and (nbx + 1)(nby + 1)
   uint32_t hash_mask;   // capacity - 1
   int hash_shift;       // 32 - bits
   int max_probe;        // longest probe sequence of a stored key (>= 1)
@@ -104,10 +107,15 @@ __host__ __device__ inline uint32_t block4_local(uint32_t lx, uint32_t ly, uint3
          ((ly & 3u) << 2) | (lx & 3u);
 }
 
-// Brick-cell key and in-brick offset of a voxel.
+// Brick-cell key (hash index; GRID: the cell's place in the padded grid) and
+// in-brick offset of a voxel.
+template <bool GRID>
 __device__ __forceinline__ void brick_key(const MapView& m, int ix, int iy, int iz, uint32_t& key,
                                           uint32_t& local) {
-  key = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
+  if constexpr (GRID)
+    key = (uint32_t)(iz >> 4) * m.gsz + (uint32_t)(iy >> 4) * m.gsy + (uint32_t)(ix >> 4);
+  else
+    key = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
   const uint32_t lx = (uint32_t)ix & 15u, ly = (uint32_t)iy & 15u, lz = (uint32_t)iz & 15u;
   local = m.layout == MCL_LAYOUT_BLOCK4 ? block4_local(lx, ly, lz) : ((lz * kBrick + ly) * kBrick + lx);
 }
@@ -138,7 +146,7 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
     return true;
   } else {
     uint32_t key, local, slot;
-    brick_key(m, ix, iy, iz, key, local);
+    brick_key<KIND == kKindBrickGrid>(m, ix, iy, iz, key, local);
     if constexpr (KIND == kKindBrickGrid) {
       slot = __ldg(m.grid + key);
     } else {

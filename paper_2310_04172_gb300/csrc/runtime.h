@@ -118,8 +118,9 @@ struct mcl_map_s {
   mcl::MapView view{};
   void* d_values = nullptr;
   uint2* d_table = nullptr;     // hash index
-  uint32_t* d_grid = nullptr;   // grid index
-  int64_t grid_cells = 0;
+  uint32_t* d_grid = nullptr;   // grid index (allocation; view.grid = d_grid + grid_front)
+  int64_t grid_cells = 0;       // cells allocated, guard cells included
+  int64_t grid_front = 0;       // guard cells in front of cell (0, 0, 0)
   int64_t bytes = 0, n_bricks = 0, capacity = 0;
   int max_probe = 0;
   float score_sigma = 0.f;    // > 0: values are scores for this sigma

@@ -9,7 +9,10 @@ origin, so a particle's log-weight is the score of exactly the voxel its
 position falls in, or of +tau outside: voxel faces, -0, one ulp below 0,
 one ulp below n, n, 2^23 and beyond, 1e30, +-inf, NaN, on maps with negative
 and positive origins. Neighbouring voxels hold distinct values, so a wrong
-voxel shows as a wrong log-weight.
+voxel shows as a wrong log-weight. The trilinear read is taken at its own
+edges (f = u - 1/2 at and next to -1, 0, n - 1 and n, corners below the first
+and past the last brick cell on one axis or on all three at once), with the
+cell-grid and the hash index giving the same bits.
 """
 import math
 
@@ -134,6 +137,52 @@ def test_dense_index_edges(env, origin, dtype):
 def test_brick_index_edges(env, origin, layout, index):
     torch, mcl = env
     run_case(torch, mcl, brick_map(origin, (48, 32, 32), scenes.I16), layout, index)
+
+
+def tri_positions(origin, dims, voxel=0.05):
+    """Positions whose f = u - 1/2 sits at or next to the trilinear read's
+    edges: corners at -1 or n on one axis, or on all three at once."""
+    o = np.asarray(origin, np.float64)
+    mid = o + voxel * (np.asarray(dims, np.float64) / 2 + 0.3)
+    us = lambda n: (-0.5, -0.49, -0.25, 0.0, 0.25, 0.5, 0.75, 15.6, 16.4, n - 0.75, n - 0.5, n - 0.25,
+                    n, n + 0.25, n + 0.49, n + 0.5, n + 0.6)
+    pts = []
+    for axis in range(3):
+        for u in us(dims[axis]):
+            p = mid.copy()
+            p[axis] = o[axis] + u * voxel
+            pts.append(p)
+    for u in (-0.5, -0.3, 0.2, 0.5):   # all three axes at the low faces, then the high ones
+        pts.append(o + u * voxel)
+        pts.append(o + (np.asarray(dims, np.float64) - u) * voxel)
+    return np.array(pts, np.float32)
+
+
+@pytest.mark.parametrize("origin", [(0.0, 0.0, 0.0), (-1.6, -0.8, -0.4)])
+@pytest.mark.parametrize("neglect", [False, True])
+def test_trilinear_edges_both_indexes(env, origin, neglect):
+    torch, mcl = env
+    smap = brick_map(origin, (48, 32, 32), scenes.I16)
+    pos = tri_positions(smap.origin, smap.dims)
+    parts = np.zeros((len(pos), 6), np.float32)
+    parts[:, :3] = pos
+    scan = np.zeros((1, 3), np.float32)
+    flags = mcl.MCL_TRILINEAR | (mcl.MCL_NEGLECT_OUTSIDE if neglect else 0)
+    res = []
+    for index in (2, 1):
+        m = mcl.map_from_scene(smap, 0, index)
+        logw = torch.empty(len(parts), device="cuda")
+        mcl.mcl_sensor_update(m, torch.from_numpy(parts).cuda(), torch.from_numpy(scan).cuda(),
+                              mcl.sensor_params(0.1, flags=flags), logw)
+        mcl.mcl_sync()
+        res.append(logw.cpu().numpy().astype(np.float64))
+        m.close()
+    assert np.array_equal(res[0], res[1])
+    Lo = oracle.sensor_update(oracle.Map.from_scene_map(smap), parts, scan, 0.1, neglect=neglect,
+                              trilinear=True)
+    err = np.abs(res[0] - Lo) / np.maximum(1.0, np.abs(Lo))
+    bad = np.flatnonzero(~(err <= 1e-5))
+    assert len(bad) == 0, f"positions {pos[bad[:5]]}: GPU {res[0][bad[:5]]} oracle {Lo[bad[:5]]}"
 
 
 def test_dims_beyond_the_index_rule_are_refused(env):
