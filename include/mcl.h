@@ -77,11 +77,18 @@ enum { MCL_INDEX_AUTO = 0, MCL_INDEX_HASH = 1, MCL_INDEX_GRID = 2 };
  * blocks only where values lie within the truncation distance, every other
  * cell reads the truncation value).
  *
- * Voxel (ix, iy, iz) covers [o + i r, o + (i + 1) r) on each axis. A point x
- * falls in voxel i_k = floor(u_k) with u_k = (x_k - o_k) * inv_voxel in two
- * FP32 roundings; it is inside iff 0 <= u_k < dims_k on every axis. dims_k
- * lie in [1, 2^23] (the kernels take floor(u) from the bits of a round-down
- * u + 2^23, exact below 2^23); larger dims are EINVAL.
+ * Voxel (ix, iy, iz) covers [o + i r, o + (i + 1) r) on each axis. A point
+ * falls in voxel i_k = floor(u_k), inside iff 0 <= u_k < dims_k on every
+ * axis, with u_k its index coordinate in FP32:
+ *  - a world point x (mcl_map_lookup): u_k = (x_k - o_k) * inv_voxel in two
+ *    FP32 roundings;
+ *  - a scan point z seen from a particle (the sensor update): the pose rows
+ *    [R | t] are taken into the map's index frame, R'_kj = R_kj * inv_voxel
+ *    and t'_k = (t_k - o_k) * inv_voxel, each evaluated in FP64 (R from the
+ *    FP64 rotation of mcl_pose_to_matrix) and rounded to FP32 once, then
+ *    u_k = fma(R'_k0, z_0, fma(R'_k1, z_1, fma(R'_k2, z_2, t'_k))) in FP32.
+ * dims_k lie in [1, 2^23] (the kernels take floor(u) from the bits of a
+ * round-down u + 2^23, exact below 2^23); larger dims are EINVAL.
  * Values are the signed distance at the voxel centre, clamped to
  * [-truncation, truncation], stored as FP32, FP16 or scaled int16
  * (q stands for q * truncation / 32767).
@@ -166,7 +173,7 @@ mcl_status mcl_map_create_score(mcl_map_t src, float sigma_hit, int32_t dtype, m
  * int64) gets the linear voxel index (iz * dims[1] + iy) * dims[0] + ix or -1
  * outside the grid; out_value (device, N FP32) the value read there,
  * dequantised, +truncation outside the grid or in a voxel of no brick. Either
- * output may be NULL. Uses the index rule of the sensor update (Sec. III look-up). */
+ * output may be NULL. Uses the world-point index rule (Sec. III look-up). */
 mcl_status mcl_map_lookup(mcl_map_t map, const float* points, int64_t N, int64_t* out_index,
                           float* out_value, mcl_stream_t stream);
 
@@ -184,8 +191,9 @@ enum { MCL_LOGPROD = 0, MCL_SUM = 1 };
  * (Sec. III clamping), or with MCL_NEGLECT_OUTSIDE contributes nothing.
  * MCL_TRILINEAR (Sec. III: a pseudo-continuous value by interpolation)
  * replaces the containing voxel's value by the trilinear interpolation of the
- * eight voxel centres around the point: with u as in the index rule and
- * f = u - 1/2 (FP32), corners i0 + {0, 1} per axis, i0 = floor(f), weights
+ * eight voxel centres around the point: with f = u - 1/2, formed like u of
+ * the sensor update's index rule with t'_k = (t_k - o_k) * inv_voxel - 1/2
+ * (FP64, one FP32 rounding), corners i0 + {0, 1} per axis, i0 = floor(f), weights
  * a = f - i0 and 1 - a; a corner outside the grid or in no brick reads
  * +truncation, and the point counts as stored (for MCL_NEGLECT_OUTSIDE) if
  * any corner is. Interpolated in FP32 along x, then y, then z. Needs
@@ -300,7 +308,8 @@ mcl_status mcl_sensor_update_estimate(mcl_map_t map, const float* particles, int
  * R = Rz(yaw) Ry(pitch) Rx(roll) evaluated in FP64 in the fixed order
  * a = cy*sp, b = sy*sp, R = [[cy*cp, a*sr - sy*cr, a*cr + sy*sr],
  * [sy*cp, b*sr + cy*cr, b*cr - cy*sr], [-sp, cp*sr, cp*cr]], each entry
- * rounded to FP32. The sensor update uses exactly these matrices. */
+ * rounded to FP32. The sensor update takes its rows from the same FP64
+ * rotation, in the map's index frame (see the map description). */
 mcl_status mcl_pose_to_matrix(const float* particles, int64_t P, float* out_mat,
                               mcl_stream_t stream);
 

@@ -31,10 +31,11 @@
  *   - motion: body-frame increment plus per-component Gaussian noise drawn by
  *     Philox4x32-10 (Salmon et al., SC'11) and Box-Muller.
  *
- * Two modes. Parity mode rounds the pose matrix, the scan-point transform and
- * the voxel index to FP32 in a fixed operation order (this fixes which voxel
- * a point falls in exactly as an FP32 implementation sees it); from the map
- * value on everything is FP64. Quality mode is FP64 throughout.
+ * Two modes. Parity mode evaluates the scan point's index-rule coordinate in
+ * FP32 in a fixed operation order (the pose rows taken into the map's index
+ * frame, then one FP32 fma chain per axis; this fixes which voxel a point
+ * falls in exactly as an FP32 implementation sees it); from the map value on
+ * everything is FP64. Quality mode is FP64 throughout.
  *
  * Compile with -ffp-contract=off: no fused multiply-add is allowed anywhere
  * except the explicit fmaf calls of the parity-mode transform.
@@ -229,15 +230,15 @@ static int voxel_value(const ora_map* m, int64_t ix, int64_t iy, int64_t iz, dou
   return 1;
 }
 
-/* Trilinear read at world point x (Sec. III: a pseudo-continuous value by
- * interpolation). Voxel i's value is the SDF at its centre o + (i + 1/2) r, so
- * with f = u - 1/2 per axis (u the index-rule coordinate; parity mode: u and
- * f in FP32) the eight centres around x are i0 + c, c in {0, 1}^3,
- * i0 = floor(f), a = f - i0, and
+/* Trilinear read at the point whose coordinates, less 1/2, are f (Sec. III:
+ * a pseudo-continuous value by interpolation). Voxel i's value is the SDF at
+ * its centre o + (i + 1/2) r, so with f = u - 1/2 per axis (u the index-rule
+ * coordinate; parity mode: f in FP32) the eight centres around the point are
+ * i0 + c, c in {0, 1}^3, i0 = floor(f), a = f - i0, and
  *   d = sum_c prod_k (c_k ? a_k : 1 - a_k) * value(i0 + c)      (FP64)
  * with +tau for corners outside the grid or in no brick. Returns 1 if any
  * corner holds a stored value. idx3 gets i0 (or -1s if no corner is inside). */
-static int trilinear_read(const ora_map* m, const double x[3], int parity, double* d,
+static int trilinear_read(const ora_map* m, const double fc[3], int parity, double* d,
                           int64_t idx3[3]) {
   int64_t i0[3];
   double a[3];
@@ -245,14 +246,13 @@ static int trilinear_read(const ora_map* m, const double x[3], int parity, doubl
   *d = m->outside;
   for (int k = 0; k < 3; ++k) {
     if (parity) {
-      float u = ((float)x[k] - m->origin_f[k]) * m->inv_voxel_f;
-      float f = u - 0.5f;
+      float f = (float)fc[k];
       if (!(f >= -1.0f && f < (float)m->dims[k])) return 0;
       float fl = floorf(f);
       i0[k] = (int64_t)fl;
       a[k] = (double)(f - fl);
     } else {
-      double f = (x[k] - (double)m->origin_f[k]) / (double)m->voxel_f - 0.5;
+      double f = fc[k];
       if (!(f >= -1.0 && f < (double)m->dims[k])) return 0;
       double fl = floor(f);
       i0[k] = (int64_t)fl;
@@ -273,57 +273,73 @@ static int trilinear_read(const ora_map* m, const double x[3], int parity, doubl
   return any;
 }
 
-/* Scan point z seen from the pose [R | t]: world point x = R z + t.
- * Parity: x_i = fmaf(R_i0, z0, fmaf(R_i1, z1, fmaf(R_i2, z2, t_i))) in FP32.
- * Then the voxel containing x, the value stored there and whether it exists.
- * Returns 1 if a stored value was read (d set), 0 if outside the grid or in an
- * unallocated brick (d = +tau). idx3 gets the voxel index or -1s. */
+/* Scan point z seen from the pose [R | t] (FP64 rows M, Sec. III): the world
+ * point x = R z + t (FP64, returned in both modes) and its index-rule
+ * coordinates u = (x - o) / r per axis, less `shift` (0: the containing
+ * voxel; 1/2: f of the trilinear read).
+ * Quality mode: u = (x - o) / r - shift in FP64.
+ * Parity mode (the FP32 rule): the rows are first taken into the map's index
+ * frame, R'_ij = fl32(R_ij * inv) and t'_i = fl32((t_i - o_i) * inv - shift),
+ * each evaluated in FP64 in that order and rounded to FP32 once (inv = the
+ * map's FP32 1/r), then u_i = fmaf(R'_i0, z0, fmaf(R'_i1, z1, fmaf(R'_i2, z2,
+ * t'_i))) in FP32. */
+static void scan_coord(const ora_map* m, const double M[12], const float z[3], int parity,
+                       double shift, double u[3], double x[3]) {
+  for (int i = 0; i < 3; ++i)
+    x[i] = M[4 * i] * (double)z[0] + M[4 * i + 1] * (double)z[1] + M[4 * i + 2] * (double)z[2] +
+           M[4 * i + 3];
+  if (parity) {
+    const double inv = (double)m->inv_voxel_f;
+    for (int i = 0; i < 3; ++i) {
+      float r0 = (float)(M[4 * i] * inv), r1 = (float)(M[4 * i + 1] * inv),
+            r2 = (float)(M[4 * i + 2] * inv);
+      float t = (float)((M[4 * i + 3] - (double)m->origin_f[i]) * inv - shift);
+      u[i] = (double)fmaf(r0, z[0], fmaf(r1, z[1], fmaf(r2, z[2], t)));
+    }
+  } else {
+    for (int i = 0; i < 3; ++i) u[i] = (x[i] - (double)m->origin_f[i]) / (double)m->voxel_f - shift;
+  }
+}
+
+/* Value at voxel coordinates u (floor(u) per axis; inside iff 0 <= u < n,
+ * NaN fails; parity mode compares the FP32 u), whether it exists, and the
+ * voxel index (or -1s). */
+static int voxel_at(const ora_map* m, const double u[3], int parity, double* d, int64_t idx3[3]) {
+  int64_t ix[3];
+  idx3[0] = idx3[1] = idx3[2] = -1;
+  for (int k = 0; k < 3; ++k) {
+    if (parity) {
+      float uf = (float)u[k];
+      if (!(uf >= 0.0f && uf < (float)m->dims[k])) { *d = m->outside; return 0; }
+      ix[k] = (int64_t)floorf(uf);
+    } else {
+      double fl = floor(u[k]);
+      if (!(fl >= 0.0 && fl < (double)m->dims[k])) { *d = m->outside; return 0; }
+      ix[k] = (int64_t)fl;
+    }
+  }
+  for (int k = 0; k < 3; ++k) idx3[k] = ix[k];
+  return voxel_value(m, ix[0], ix[1], ix[2], d);
+}
+
+/* Scan point z seen from pose M: the voxel containing it (or the trilinear
+ * read around it), the value read and whether it is stored. Returns 1 if a
+ * stored value was read (d set), 0 if outside the grid or in an unallocated
+ * brick (d = +tau). x gets the FP64 world point, idx3 the voxel index (the
+ * trilinear read: i0) or -1s. An analytic map is read at x. */
 static int lookup_point(const ora_map* m, const double M[12], const float z[3], int parity,
                         int interp, double x[3], double* d, int64_t idx3[3]) {
+  double u[3];
   idx3[0] = idx3[1] = idx3[2] = -1;
-  if (parity) {
-    float xf[3];
-    for (int i = 0; i < 3; ++i)
-      xf[i] = fmaf((float)M[4 * i], z[0],
-                   fmaf((float)M[4 * i + 1], z[1], fmaf((float)M[4 * i + 2], z[2], (float)M[4 * i + 3])));
-    for (int i = 0; i < 3; ++i) x[i] = (double)xf[i];
-  } else {
-    for (int i = 0; i < 3; ++i)
-      x[i] = M[4 * i] * (double)z[0] + M[4 * i + 1] * (double)z[1] + M[4 * i + 2] * (double)z[2] +
-             M[4 * i + 3];
-  }
+  scan_coord(m, M, z, parity, interp ? 0.5 : 0.0, u, x);
   if (m->kind == ORA_ANALYTIC) {
     double v = analytic_sdf(m, x);
     double tau = (double)m->tau_f;
     *d = v > tau ? tau : (v < -tau ? -tau : v);
     return 1;
   }
-  if (interp) return trilinear_read(m, x, parity, d, idx3);
-  int64_t ix[3];
-  for (int k = 0; k < 3; ++k) {
-    if (parity) {
-      /* u = (x - o) * (1/r), two FP32 roundings; inside iff 0 <= u < n (NaN fails) */
-      float diff = (float)x[k] - m->origin_f[k];
-      float u = diff * m->inv_voxel_f;
-      if (!(u >= 0.0f && u < (float)m->dims[k])) { *d = m->outside; return 0; }
-      ix[k] = (int64_t)floorf(u);
-    } else {
-      double u = floor((x[k] - (double)m->origin_f[k]) / (double)m->voxel_f);
-      if (!(u >= 0.0 && u < (double)m->dims[k])) { *d = m->outside; return 0; }
-      ix[k] = (int64_t)u;
-    }
-  }
-  for (int k = 0; k < 3; ++k) idx3[k] = ix[k];
-  if (m->kind == ORA_DENSE) {
-    *d = stored_value(m, (ix[2] * m->dims[1] + ix[1]) * m->dims[0] + ix[0]);
-    return 1;
-  }
-  int64_t c = ((ix[2] / BRICK_EDGE) * m->nb[1] + ix[1] / BRICK_EDGE) * m->nb[0] + ix[0] / BRICK_EDGE;
-  int32_t slot = m->coarse[c];
-  if (slot < 0) { *d = m->outside; return 0; }
-  int64_t local = ((ix[2] % BRICK_EDGE) * BRICK_EDGE + ix[1] % BRICK_EDGE) * BRICK_EDGE + ix[0] % BRICK_EDGE;
-  *d = stored_value(m, (int64_t)slot * BRICK_EDGE * BRICK_EDGE * BRICK_EDGE + local);
-  return 1;
+  if (interp) return trilinear_read(m, u, parity, d, idx3);
+  return voxel_at(m, u, parity, d, idx3);
 }
 
 /* ------------------------------------------------------------------ sensor update */
@@ -366,20 +382,20 @@ void ora_sensor_update(const ora_map* m, const float* poses, int64_t P, const fl
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < P; ++p) {
     double M[12];
-    pose_matrix(poses + 6 * p, parity, M);
+    pose_matrix(poses + 6 * p, 0, M); /* FP64 rows; parity mode rounds in scan_coord */
     out_L[p] = particle_log_weight(m, M, scan, N, sigma, mode, flags, parity);
   }
 }
 
-/* Same with the poses given as FP64 [R | t] rows (12 per particle). Parity
- * mode rounds the given entries to FP32. */
+/* Same with the poses given as FP64 [R | t] rows (12 per particle), taken as
+ * they are (parity mode rounds in the index frame, as for poses). */
 void ora_sensor_update_mat(const ora_map* m, const double* mats, int64_t P, const float* scan,
                            int64_t N, double sigma, int mode, int flags, int parity,
                            double* out_L) {
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < P; ++p) {
     double M[12];
-    for (int k = 0; k < 12; ++k) M[k] = parity ? (double)(float)mats[12 * p + k] : mats[12 * p + k];
+    for (int k = 0; k < 12; ++k) M[k] = mats[12 * p + k];
     out_L[p] = particle_log_weight(m, M, scan, N, sigma, mode, flags, parity);
   }
 }
@@ -390,7 +406,7 @@ int64_t ora_eval_points(const ora_map* m, const float pose[6], const float* scan
                         int parity, int interp, double* out_x, double* out_d, int64_t* out_idx) {
   double M[12];
   int64_t n_stored = 0;
-  pose_matrix(pose, parity, M);
+  pose_matrix(pose, 0, M);
   for (int64_t j = 0; j < N; ++j) {
     double x[3], d;
     int64_t idx3[3];
@@ -404,14 +420,16 @@ int64_t ora_eval_points(const ora_map* m, const float pose[6], const float* scan
 
 /* Map query at FP32 world points: linear voxel index (iz*ny + iy)*nx + ix in
  * the whole grid (-1 outside) and the value read there (+tau outside the grid
- * or in an unallocated brick), with the parity-mode index rule. */
+ * or in an unallocated brick). The point's coordinates are
+ * u = fl32(fl32(x - o) * inv) per axis (two FP32 roundings), then the rule of
+ * voxel_at. */
 void ora_map_lookup(const ora_map* m, const float* pts, int64_t n, int64_t* out_index,
                     double* out_value) {
-  const double I[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
   for (int64_t j = 0; j < n; ++j) {
-    double x[3], d;
+    double u[3], d;
     int64_t idx3[3];
-    lookup_point(m, I, pts + 3 * j, 1, 0, x, &d, idx3);
+    for (int k = 0; k < 3; ++k) u[k] = (double)((pts[3 * j + k] - m->origin_f[k]) * m->inv_voxel_f);
+    voxel_at(m, u, 1, &d, idx3);
     out_index[j] = idx3[0] < 0 ? -1 : (idx3[2] * m->dims[1] + idx3[1]) * m->dims[0] + idx3[0];
     out_value[j] = d;
   }

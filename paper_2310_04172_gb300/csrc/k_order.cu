@@ -16,8 +16,16 @@
 namespace mcl {
 namespace {
 
-constexpr int kOrderBits = 6;                         // cells per axis = 64
-constexpr int kOrderBuckets = 1 << (3 * kOrderBits);  // 262144
+// MCL_ORDER_YAW_BITS: the low bits of a bucket number are the particle's
+// yaw bin (2^bits bins over the full turn) and the cells are coarser, so
+// that within a cell the particles facing the same way come together.
+#ifndef MCL_ORDER_YAW_BITS
+#define MCL_ORDER_YAW_BITS 0
+#endif
+constexpr int kYawBits = MCL_ORDER_YAW_BITS;
+static_assert(kYawBits % 3 == 0 && kYawBits < 18, "yaw bits replace whole Morton levels");
+constexpr int kOrderBits = 6 - kYawBits / 3;          // cells per axis = 2^kOrderBits
+constexpr int kOrderBuckets = 1 << 18;                // 262144
 constexpr int kScanTile = 1024;                          // buckets per scan block
 constexpr int kScanTiles = kOrderBuckets / kScanTile;  // 256
 
@@ -37,8 +45,14 @@ __device__ __forceinline__ uint32_t cell_of(float x, float o, float s) {
 __device__ __forceinline__ void order_key(const float* __restrict__ poses, int p, float3 o, float3 s,
                                           uint32_t* __restrict__ key, uint32_t* __restrict__ hist) {
   const float* q = poses + 6 * (size_t)p;
-  const uint32_t k = spread3(cell_of(q[0], o.x, s.x)) | (spread3(cell_of(q[1], o.y, s.y)) << 1) |
-                     (spread3(cell_of(q[2], o.z, s.z)) << 2);
+  uint32_t k = spread3(cell_of(q[0], o.x, s.x)) | (spread3(cell_of(q[1], o.y, s.y)) << 1) |
+               (spread3(cell_of(q[2], o.z, s.z)) << 2);
+  if constexpr (kYawBits > 0) {
+    const float t = q[5] * 0.15915494f;  // turns
+    const float f = t - floorf(t);       // [0, 1]; NaN and inf give NaN
+    const uint32_t yb = f >= 0.f ? min((uint32_t)(f * (float)(1 << kYawBits)), (1u << kYawBits) - 1u) : 0u;
+    k = (k << kYawBits) | yb;
+  }
   key[p] = k;
   atomicAdd(hist + k, 1u);
 }

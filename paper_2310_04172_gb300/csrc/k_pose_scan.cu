@@ -14,8 +14,16 @@ namespace {
 //   [ cy*cp   a*sr - sy*cr   a*cr + sy*sr ]
 //   [ sy*cp   b*sr + cy*cr   b*cr - cy*sr ]
 //   [ -sp     cp*sr          cp*cr        ]
+// In the frame f (RowFrame) each entry is then R_ij * inv and each
+// translation (t_i - o_i) * inv - shift, still in FP64, before the one
+// rounding; the identity frame changes no bit.
+__device__ __forceinline__ float frame_t(float t, float o, double inv, double shift) {
+  return __double2float_rn(__dsub_rn(__dmul_rn(__dsub_rn((double)t, (double)o), inv), shift));
+}
+
 __device__ __forceinline__ void pose_to_matrix(const float* __restrict__ poses, int p,
-                                               float4* __restrict__ mats, const int* __restrict__ rank) {
+                                               float4* __restrict__ mats, const int* __restrict__ rank,
+                                               const RowFrame& f) {
   const float* s = poses + 6 * (size_t)p;
   const float x = s[0], y = s[1], z = s[2];
   const double roll = (double)s[3], pitch = (double)s[4], yaw = (double)s[5];
@@ -33,10 +41,12 @@ __device__ __forceinline__ void pose_to_matrix(const float* __restrict__ poses, 
   const double r20 = -sp;
   const double r21 = __dmul_rn(cp, sr);
   const double r22 = __dmul_rn(cp, cr);
+  const double inv = (double)f.inv, sh = (double)f.shift;
+  auto e = [inv](double r) { return __double2float_rn(__dmul_rn(r, inv)); };
   float4* o = mats + 3 * (size_t)(rank ? rank[p] : p);
-  o[0] = make_float4(__double2float_rn(r00), __double2float_rn(r01), __double2float_rn(r02), x);
-  o[1] = make_float4(__double2float_rn(r10), __double2float_rn(r11), __double2float_rn(r12), y);
-  o[2] = make_float4(__double2float_rn(r20), __double2float_rn(r21), __double2float_rn(r22), z);
+  o[0] = make_float4(e(r00), e(r01), e(r02), frame_t(x, f.ox, inv, sh));
+  o[1] = make_float4(e(r10), e(r11), e(r12), frame_t(y, f.oy, inv, sh));
+  o[2] = make_float4(e(r20), e(r21), e(r22), frame_t(z, f.oz, inv, sh));
 }
 
 // N x 3 scan rows -> N float4 (x, y, z, 0): 16-byte records that a bulk copy
@@ -50,7 +60,7 @@ __device__ __forceinline__ void scan_pack(const float* __restrict__ scan, int j,
 __global__ void k_pose_to_matrix(const float* __restrict__ poses, int P, float4* __restrict__ mats,
                                  const int* __restrict__ rank) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < P) pose_to_matrix(poses, p, mats, rank);
+  if (p < P) pose_to_matrix(poses, p, mats, rank, identity_frame());
 }
 
 // Pair t of the pair layout (ScanLayout): chunk c = t / full_pairs, pair
@@ -86,12 +96,12 @@ __device__ __forceinline__ void scan_pack_pair(const float* __restrict__ scan, i
 // two are independent; one launch instead of two matters for small updates,
 // where each launch costs about as much as its work).
 __global__ void k_pose_and_pack(const float* __restrict__ poses, int P, float4* __restrict__ mats,
-                                const int* __restrict__ rank, int pose_blocks,
+                                const int* __restrict__ rank, const RowFrame f, int pose_blocks,
                                 const float* __restrict__ scan, int N, const ScanLayout L,
                                 void* __restrict__ packed) {
   if ((int)blockIdx.x < pose_blocks) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P) pose_to_matrix(poses, p, mats, rank);
+    if (p < P) pose_to_matrix(poses, p, mats, rank, f);
   } else {
     const int j = (blockIdx.x - pose_blocks) * blockDim.x + threadIdx.x;
     if (L.pair_g == 0) {
@@ -116,7 +126,7 @@ __global__ void __launch_bounds__(kSideThreads) k_pose_and_pack_b(const SideSeg*
   const int pb = (g.P + kSideThreads - 1) / kSideThreads;
   if (j < pb) {
     const int p = j * kSideThreads + threadIdx.x;
-    if (p < g.P) pose_to_matrix(g.particles, p, g.mats, g.rank);
+    if (p < g.P) pose_to_matrix(g.particles, p, g.mats, g.rank, g.frame);
   } else {
     const int t = (j - pb) * kSideThreads + threadIdx.x;
     const ScanLayout L = g.layout;
@@ -187,12 +197,12 @@ cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const
 }
 
 cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const int* rank,
-                                 const float* scan, int N, const ScanLayout& layout, void* packed,
-                                 cudaStream_t s) {
+                                 const RowFrame& f, const float* scan, int N,
+                                 const ScanLayout& layout, void* packed, cudaStream_t s) {
   const int threads = pose_threads(P);
   const long long units = pack_units(N, layout);
   const int pb = blocks_for(P, threads), sb = blocks_for(units, threads);
-  k_pose_and_pack<<<pb + sb, threads, 0, s>>>(poses, P, mats, rank, pb, scan, N, layout, packed);
+  k_pose_and_pack<<<pb + sb, threads, 0, s>>>(poses, P, mats, rank, f, pb, scan, N, layout, packed);
   return cudaGetLastError();
 }
 

@@ -222,9 +222,12 @@ __device__ __forceinline__ float4 lds_volatile(const float4* p) {
 
 // Stage A on the pair layout (ScanLayout): the lane's points j and j + G of a
 // step come as one XY float4 and one Z float2, so each coordinate of the two
-// sits in one register pair and the transform and the first index steps run
-// as packed FP32x2 instructions (IEEE per element: the same bits as the
-// scalar fmaf / __fsub_rn / __fmul_rn chain). The floor comes from a
+// sits in one register pair and the transform and the floor run as packed
+// FP32x2 instructions (IEEE per element: the same bits as the scalar fmaf
+// chain). The pose rows are in the map's index frame (RowFrame), so the fma
+// chain gives the index coordinate u itself: no origin or scale step per
+// point (the frame costs three FP32x2 operations per pair and axis less:
+// 93.5 against 87.0 ms for 1M x 65,536). The floor comes from a
 // round-down add of 2^23: for 0 <= u < 2^23 the sum's bits are 0x4B000000 +
 // floor(u) exactly, and every other u (negative, >= 2^23, +-inf, NaN) leaves
 // bits - 0x4B000000 >= 2^23 as an unsigned number, so one unsigned compare
@@ -251,9 +254,7 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
   // their 24 registers (no spills at 64) but measured 104.1 against 97.0 ms
   const float4 q0 = lds_volatile(rows), q1 = lds_volatile(rows + 1), q2 = lds_volatile(rows + 2),
                q3 = lds_volatile(rows + 3), q4 = lds_volatile(rows + 4), q5 = lds_volatile(rows + 5);
-  const float2 no_x = make_float2(-m.ox, -m.ox), no_y = make_float2(-m.oy, -m.oy),
-               no_z = make_float2(-m.oz, -m.oz), inv = make_float2(m.inv, m.inv),
-               two23 = make_float2(8388608.f, 8388608.f);
+  const float2 two23 = make_float2(8388608.f, 8388608.f);
 #pragma unroll
   for (int k = 0; k < U / 2; ++k) {
     const int j0 = base + 2 * k * G + glane;
@@ -263,7 +264,8 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
     const float4 xy = sxy[pi];
     const float2 zz = sz[pi];
     const float2 zx = make_float2(xy.x, xy.y), zy = make_float2(xy.z, xy.w);
-    // x_i = fma(R_i0, z0, fma(R_i1, z1, fma(R_i2, z2, t_i))) for both points
+    // u_i = fma(R'_i0, z0, fma(R'_i1, z1, fma(R'_i2, z2, t'_i))) for both points
+    // (rows in the map's index frame, RowFrame)
     const float2 X = __ffma2_rn(make_float2(q0.x, q0.y), zx,
                                 __ffma2_rn(make_float2(q0.z, q0.w), zy,
                                            __ffma2_rn(make_float2(q1.x, q1.y), zz, make_float2(q1.z, q1.w))));
@@ -273,10 +275,8 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
     const float2 W = __ffma2_rn(make_float2(q4.x, q4.y), zx,
                                 __ffma2_rn(make_float2(q4.z, q4.w), zy,
                                            __ffma2_rn(make_float2(q5.x, q5.y), zz, make_float2(q5.z, q5.w))));
-    // u = (x - o) * inv, then floor via the round-down add of 2^23
-    const float2 fx = __fadd2_rd(__fmul2_rn(__fadd2_rn(X, no_x), inv), two23);
-    const float2 fy = __fadd2_rd(__fmul2_rn(__fadd2_rn(Y, no_y), inv), two23);
-    const float2 fz = __fadd2_rd(__fmul2_rn(__fadd2_rn(W, no_z), inv), two23);
+    // floor via the round-down add of 2^23
+    const float2 fx = __fadd2_rd(X, two23), fy = __fadd2_rd(Y, two23), fz = __fadd2_rd(W, two23);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int u = 2 * k + h;
@@ -419,8 +419,9 @@ __device__ __forceinline__ void eval_checked(const SensorArgs& a, const float4* 
 // ---------------------------------------------------------------- trilinear read
 // MCL_TRILINEAR (Sec. III: a pseudo-continuous value by interpolation). The
 // stored value of voxel i is the SDF at its centre o + (i + 1/2) r, so with
-// u = (x - o) * inv as in the index rule and f = u - 1/2 (FP32), the eight
-// centres around x are i0 + {0, 1} per axis, i0 = floor(f), with weights
+// f = u - 1/2 (FP32; the pose rows in the index frame with shift 1/2,
+// RowFrame), the eight centres around the point are i0 + {0, 1} per axis,
+// i0 = floor(f), with weights
 // a = f - i0 and 1 - a. A corner outside the grid or in no brick reads the
 // same value as an unstored voxel. The point counts as stored if any corner
 // is. Interpolation in FP32: along x for the four (y, z) corner pairs, then
@@ -576,17 +577,14 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
 // One particle's points of the staged chunk with the trilinear read: lane
 // glane takes points glane, glane + G, ... in order (the summation order of
 // the nearest-voxel path), one pair (j, j + G) of the pair layout per loop
-// step. The transform and f = u - 1/2 run as packed FP32x2 instructions (the
-// same bits as the scalar chain: x - o is x + (-o), f - 1/2 is f + (-1/2));
-// rows: the group's duplicated pose entries, as for the nearest read.
+// step. The transform runs as packed FP32x2 instructions (the same bits as
+// the scalar fma chain); with the rows in the index frame with shift 1/2
+// (RowFrame) it gives f = u - 1/2 directly. rows: the group's duplicated
+// pose entries, as for the nearest read.
 template <int KIND, int DTYPE, int MODE, int G>
 __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __restrict__ sxy,
                                          const float2* __restrict__ sz, int glane, int cnt,
                                          const float4* rows, float& acc) {
-  const MapView& m = a.map;
-  const float2 no_x = make_float2(-m.ox, -m.ox), no_y = make_float2(-m.oy, -m.oy),
-               no_z = make_float2(-m.oz, -m.oz), inv = make_float2(m.inv, m.inv),
-               half = make_float2(-0.5f, -0.5f);
   for (int j = glane; j < cnt; j += 2 * G) {
     // the rows are re-read each step: they hold no registers across the corner reads
     const float4 q0 = lds_volatile(rows), q1 = lds_volatile(rows + 1), q2 = lds_volatile(rows + 2),
@@ -604,9 +602,7 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
     const float2 W = __ffma2_rn(make_float2(q4.x, q4.y), zx,
                                 __ffma2_rn(make_float2(q4.z, q4.w), zy,
                                            __ffma2_rn(make_float2(q5.x, q5.y), zz, make_float2(q5.z, q5.w))));
-    const float2 fx = __fadd2_rn(__fmul2_rn(__fadd2_rn(X, no_x), inv), half);
-    const float2 fy = __fadd2_rn(__fmul2_rn(__fadd2_rn(Y, no_y), inv), half);
-    const float2 fz = __fadd2_rn(__fmul2_rn(__fadd2_rn(W, no_z), inv), half);
+    const float2 fx = X, fy = Y, fz = W;  // rows in the frame of f = u - 1/2
     float d[2];
     bool use[2], st;
     d[0] = tri_read<KIND, DTYPE, MODE>(a, fx.x, fy.x, fz.x, st);

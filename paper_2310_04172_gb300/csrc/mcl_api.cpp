@@ -711,8 +711,8 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
     if (pl.spatial)
       MCL_CUDA(launch_particle_order(particles, (int)P, m->view, (uint32_t*)(ws + pl.off_key),
                                      (uint32_t*)(ws + pl.off_hist), rank, s));
-    MCL_CUDA(launch_pose_and_pack(particles, (int)P, mats, rank, scan, (int)N, scan_layout(pl.sh),
-                                  packed, s));
+    MCL_CUDA(launch_pose_and_pack(particles, (int)P, mats, rank, sensor_frame(m->view, pl.sh.interp != 0),
+                                  scan, (int)N, scan_layout(pl.sh), packed, s));
   }
   const double sig = (double)p->sigma_hit;
   SensorArgs a;

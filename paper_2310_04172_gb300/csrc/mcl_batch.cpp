@@ -321,6 +321,7 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       order_grid(sp.u.map->view, &q.order_o, &q.order_s);
     }
     q.mats = (float4*)(ws + pl.off_mats);
+    q.frame = sensor_frame(sp.u.map->view, pl.sh.interp != 0);
     q.packed = ws + pl.off_scan;
     q.layout = scan_layout(pl.sh);
     q.partial = (const float*)(ws + pl.off_partial);

@@ -63,18 +63,7 @@ __host__ __device__ inline uint32_t brick_hash(uint32_t key, int shift) {
 
 #ifdef __CUDACC__
 
-// Scan point z seen from pose rows [R | t]: x_i = fma(R_i0, z0, fma(R_i1, z1,
-// fma(R_i2, z2, t_i))), exactly this order (Sec. III: the point as seen from
-// the particle).
-__device__ __forceinline__ void transform_point(const float4& r0, const float4& r1,
-                                                const float4& r2, const float4& z, float& x,
-                                                float& y, float& w) {
-  x = fmaf(r0.x, z.x, fmaf(r0.y, z.y, fmaf(r0.z, z.z, r0.w)));
-  y = fmaf(r1.x, z.x, fmaf(r1.y, z.y, fmaf(r1.z, z.z, r1.w)));
-  w = fmaf(r2.x, z.x, fmaf(r2.y, z.y, fmaf(r2.z, z.z, r2.w)));
-}
-
-// Voxel containing a map-frame point: u = (x - o) * inv in two FP32
+// Voxel containing a world point (the map query): u = (x - o) * inv in two FP32
 // roundings per axis, inside iff 0 <= u < n on all axes (NaN is outside),
 // i = floor(u). Returns false outside the grid.
 __device__ __forceinline__ bool voxel_of(const MapView& m, float x, float y, float z, int& ix,
@@ -253,6 +242,21 @@ struct EstPartial;
 // the spatial order, pose rows and scan packing, log-weights, normalisation
 // with the optional estimate, and systematic resampling of every session run
 // as one launch each, whatever the number of sessions.
+// Frame of the sensor kernel's pose rows. Rows [R' | t'] with
+// R' = R inv and t' = (t - o) inv - shift, evaluated in FP64 in that order
+// (R from the FP64 pose rotation, t, o and inv as FP32 numbers) and rounded
+// to FP32 once per entry: R' z + t' is then the scan point's index-rule
+// coordinate u along each axis (shift 0: nearest voxel) or f = u - 1/2
+// (shift 1/2: trilinear read) directly, with three FP32 fma per axis. The
+// identity frame (o = 0, inv = 1, shift = 0) gives the plain [R | t].
+struct RowFrame {
+  float ox, oy, oz, inv, shift;
+};
+__host__ __device__ inline RowFrame identity_frame() { return RowFrame{0.f, 0.f, 0.f, 1.f, 0.f}; }
+inline RowFrame sensor_frame(const MapView& m, bool trilinear) {
+  return RowFrame{m.ox, m.oy, m.oz, m.inv, trilinear ? 0.5f : 0.f};
+}
+
 struct SideSeg {
   float* mpart;            // motion update of these P x 6 poses first (NULL: none)
   float mdelta[6], msig[6];
@@ -265,6 +269,7 @@ struct SideSeg {
   int* rank;
   float3 order_o, order_s; // cell-grid origin and scale of the spatial order
   float4* mats;            // P x 3 pose rows
+  RowFrame frame;          // their frame
   void* packed;            // packed scan
   ScanLayout layout;
   const float* partial;    // K x P chunk sums
@@ -361,11 +366,11 @@ cudaError_t launch_pose_to_matrix(const float* poses, int P, float4* mats, const
 size_t order_hist_bytes();
 cudaError_t launch_particle_order(const float* poses, int P, const MapView& m, uint32_t* key,
                                   uint32_t* hist, int* rank, cudaStream_t s);
-// Pose matrices (as launch_pose_to_matrix) and scan packing (N x 3 -> the
-// layout) in one launch.
+// Pose matrices in the frame f (as launch_pose_to_matrix for the identity
+// frame) and scan packing (N x 3 -> the layout) in one launch.
 cudaError_t launch_pose_and_pack(const float* poses, int P, float4* mats, const int* rank,
-                                 const float* scan, int N, const ScanLayout& layout, void* packed,
-                                 cudaStream_t s);
+                                 const RowFrame& f, const float* scan, int N,
+                                 const ScanLayout& layout, void* packed, cudaStream_t s);
 cudaError_t launch_sensor(int kind, int layout, int dtype, const SensorArgs& a,
                           const SensorShape& sh, cudaStream_t s);
 int sensor_smem_bytes(const SensorShape& sh);

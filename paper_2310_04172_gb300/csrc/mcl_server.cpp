@@ -218,6 +218,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       order_grid(ss->map->view, &q.order_o, &q.order_s);
     }
     q.mats = (float4*)(ws + pl.off_mats);
+    q.frame = sensor_frame(ss->map->view, pl.sh.interp != 0);
     q.packed = ws + pl.off_scan;
     q.layout = scan_layout(pl.sh);
     q.partial = (const float*)(ws + pl.off_partial);

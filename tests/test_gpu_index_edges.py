@@ -1,6 +1,8 @@
 """The sensor kernels' voxel rule at its edges, against the oracle's FP32 rule.
 
-The kernels take floor(u) from the bits of a round-down u + 2^23 and test
+Both sides form u per axis from the pose rows in the map's index frame
+(R inv and (t - o) inv, FP64 then one FP32 rounding) and one FP32 fma chain;
+the kernels take floor(u) from the bits of a round-down u + 2^23 and test
 0 <= u < n with one unsigned compare per axis (packed FP32x2 for two points
 at a time); the oracle compares u with 0 and n in FP32 and truncates (Sec.
 III look-up; readings r3 and r19). Here every particle sits at an adversarial
@@ -183,6 +185,39 @@ def test_trilinear_edges_both_indexes(env, origin, neglect):
     err = np.abs(res[0] - Lo) / np.maximum(1.0, np.abs(Lo))
     bad = np.flatnonzero(~(err <= 1e-5))
     assert len(bad) == 0, f"positions {pos[bad[:5]]}: GPU {res[0][bad[:5]]} oracle {Lo[bad[:5]]}"
+
+
+@pytest.mark.parametrize("kind", ["dense", "grid", "hash"])
+def test_rotated_poses_near_faces(env, kind):
+    """Rotated particles placed so that one scan point lands on or within a
+    few ulps of voxel faces: each particle's log-weight is the score of the
+    voxel the FP32 rule gives, on the GPU as in the oracle."""
+    torch, mcl = env
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(17)
+    origin, dims = (-1.6, -0.8, -0.4), (48, 32, 32)
+    smap = dense_map(origin, dims, scenes.F32) if kind == "dense" else brick_map(origin, dims, scenes.I16)
+    m = mcl.map_from_scene(smap) if kind == "dense" else mcl.map_from_scene(smap, 0, 2 if kind == "grid" else 1)
+    om = oracle.Map.from_scene_map(smap)
+    P = 3000
+    for z in ([0.7, -0.3, 0.4], [-0.05, 0.9, -0.6], [0.0, 0.0, 1.3]):
+        z = np.asarray(z, np.float32)
+        ang = rng.uniform(-math.pi, math.pi, (P, 3))
+        R = Rotation.from_euler("ZYX", ang[:, ::-1].astype(np.float32).astype(np.float64)).as_matrix()
+        u = rng.integers(0, dims, (P, 3)).astype(np.float64)
+        u += rng.choice([0.0, 1e-7, -1e-7, 3e-7, -3e-7, 0.5], (P, 3)) * np.maximum(u, 1.0)
+        x = np.asarray(origin, np.float64) + u * np.float64(np.float32(0.05))
+        parts = np.concatenate([x - R @ z.astype(np.float64), ang], 1).astype(np.float32)
+        logw = torch.empty(P, device="cuda")
+        mcl.mcl_sensor_update(m, torch.from_numpy(parts).cuda(), torch.from_numpy(z[None]).cuda(),
+                              mcl.sensor_params(0.1), logw)
+        mcl.mcl_sync()
+        Lg = logw.cpu().numpy().astype(np.float64)
+        Lo = oracle.sensor_update(om, parts, z[None], 0.1)
+        err = np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo))
+        bad = np.flatnonzero(~(err <= 1e-5))
+        assert len(bad) == 0, f"z {z}: particles {bad[:5]} GPU {Lg[bad[:5]]} oracle {Lo[bad[:5]]}"
+    m.close()
 
 
 def test_dims_beyond_the_index_rule_are_refused(env):

@@ -237,18 +237,29 @@ def np_stored_value(m, ix, iy, iz):
     return float(raw)
 
 
+def index_frame_rows(m, M, shift=0.0):
+    """FP32 rows [R' | t'] of the FP64 pose rows M in the map's index frame:
+    R' = fl32(R inv), t' = fl32((t - o) inv - shift), each in FP64 first."""
+    inv = np.float64(np.float32(m.inv_voxel))
+    o64 = np.asarray(m.origin, np.float32).astype(np.float64)
+    Rp = (np.asarray(M[:, :3], np.float64) * inv).astype(np.float32)
+    tp = (((np.asarray(M[:, 3], np.float64) - o64) * inv) - np.float64(shift)).astype(np.float32)
+    return Rp, tp
+
+
 def np_log_weight(m, M, scan, sigma, mode, neglect, parity):
+    """M: FP64 pose rows. Parity: the FP32 index rule (rows in the index
+    frame, then one exactly rounded fma chain per axis)."""
     sigma = float(np.float32(sigma))
     tau = float(np.float32(m.tau))
     o32 = np.asarray(m.origin, np.float32)
-    inv32 = np.float32(m.inv_voxel)
     r64 = float(np.float32(m.voxel))
+    Rp, tp = index_frame_rows(m, M)
     total = 0.0
     for z in scan:
         if parity:
-            x = [fmaf_exact(M[i, 0], z[0], fmaf_exact(M[i, 1], z[1], fmaf_exact(M[i, 2], z[2], M[i, 3])))
+            u = [fmaf_exact(Rp[i, 0], z[0], fmaf_exact(Rp[i, 1], z[1], fmaf_exact(Rp[i, 2], z[2], tp[i])))
                  for i in range(3)]
-            u = [np.float32(np.float32(x[k]) - o32[k]) * inv32 for k in range(3)]
             ok = all(0 <= u[k] < m.dims[k] for k in range(3))
             idx = [int(math.floor(u[k])) for k in range(3)] if ok else None
         else:
@@ -275,7 +286,7 @@ def test_brute_force_8_particles_16_points(rng, dtype, parity):
     dirs = rng.normal(size=(16, 3))
     scan = (dirs / np.linalg.norm(dirs, axis=1, keepdims=True) *
             rng.uniform(0.2, 1.2, (16, 1))).astype(np.float32)
-    mats = oracle.pose_to_matrix(poses, parity=parity)  # pinned to SciPy above
+    mats = oracle.pose_to_matrix(poses, parity=False)  # FP64 rows, pinned to SciPy above
     for m in (dense, brick):
         om = oracle.Map.from_scene_map(m)
         for mode in (oracle.LOGPROD, oracle.SUM):
@@ -283,6 +294,49 @@ def test_brute_force_8_particles_16_points(rng, dtype, parity):
                 got = oracle.sensor_update(om, poses, scan, 0.1, mode, neglect, parity)
                 ref = [np_log_weight(m, mats[p], scan, 0.1, mode, neglect, parity) for p in range(8)]
                 np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def near_face_scan(rng, m, pose, n):
+    """Sensor-frame points whose map coordinates sit on or within a few ulps
+    of voxel faces (FP64 solve, then FP32)."""
+    R = Rotation.from_euler("ZYX", pose[[5, 4, 3]].astype(np.float64)).as_matrix()
+    dims = np.asarray(m.dims)
+    u = rng.integers(0, dims, (n, 3)).astype(np.float64)
+    u += rng.choice([0.0, 1e-7, -1e-7, 3e-7, -3e-7, 0.5], (n, 3)) * np.maximum(u, 1.0)
+    x = np.asarray(m.origin, np.float64) + u * np.float64(np.float32(m.voxel))
+    return ((x - pose[:3].astype(np.float64)) @ R).astype(np.float32)
+
+
+def np_parity_index(m, M, z, shift=0.0, round_rows_first=False):
+    if round_rows_first:  # the plausible slip: rows rounded to FP32 before the frame
+        M = np.asarray(M, np.float32).astype(np.float64)
+    Rp, tp = index_frame_rows(m, M, shift)
+    u = [fmaf_exact(Rp[i, 0], z[0], fmaf_exact(Rp[i, 1], z[1], fmaf_exact(Rp[i, 2], z[2], tp[i])))
+         for i in range(3)]
+    if not all(0 <= u[k] < m.dims[k] for k in range(3)):
+        return [-1, -1, -1]
+    return [int(math.floor(u[k])) for k in range(3)]
+
+
+def test_parity_index_rule_per_point(rng):
+    """The parity-mode voxel of every scan point, for rotated poses and points
+    on or next to voxel faces, is the restated FP32 rule: rows in the map's
+    index frame (R inv, (t - o) inv, FP64 then one FP32 rounding), one exactly
+    rounded fma chain per axis, floor. Rounding the rows to FP32 before the
+    frame moves some of these points to a neighbouring voxel."""
+    dense, _ = brute_maps(rng, scenes.F32)
+    om = oracle.Map.from_scene_map(dense)
+    poses = np.concatenate([rng.uniform(0.2, 1.6, (6, 3)), rng.uniform(-math.pi, math.pi, (6, 3))],
+                           1).astype(np.float32)
+    mats = oracle.pose_to_matrix(poses, parity=False)
+    slipped = 0
+    for p in range(len(poses)):
+        z = near_face_scan(rng, dense, poses[p], 400)
+        _, _, idx, _ = oracle.eval_points(om, poses[p], z, parity=True)
+        for j in range(len(z)):
+            assert list(idx[j]) == np_parity_index(dense, mats[p], z[j]), (p, j)
+            slipped += np_parity_index(dense, mats[p], z[j], round_rows_first=True) != list(idx[j])
+    assert slipped > 0
 
 
 def test_map_lookup_matches_brute_force(rng):

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import scenes
-from test_oracle_pins import brute_maps, dense_map, np_stored_value
+from test_oracle_pins import brute_maps, dense_map, fmaf_exact, index_frame_rows, np_stored_value
 
 
 @pytest.fixture
@@ -76,14 +76,21 @@ def test_centres_read_the_stored_value(rng):
         np.testing.assert_array_equal(idx, np.stack([ix, iy, iz], -1).reshape(-1, 3))
 
 
+IDENTITY_ROWS = np.array([[1.0, 0, 0, 0], [0, 1.0, 0, 0], [0, 0, 1.0, 0]])
+
+
 def np_trilinear(m, x, parity):
-    """Plain restatement: FP64 (or FP32 index coordinates), 8 corners with
-    +tau for corners without a stored value."""
+    """Plain restatement at scan point x seen from the identity pose: FP64
+    (or the FP32 index rule: rows in the index frame with shift 1/2, one
+    exactly rounded fma chain per axis), 8 corners with +tau for corners
+    without a stored value."""
     tau = float(np.float32(m.tau))
     o32 = np.asarray(m.origin, np.float32)
     if parity:
-        f = [np.float32(np.float32(np.float32(x[k]) - o32[k]) * np.float32(m.inv_voxel)) - np.float32(0.5)
-             for k in range(3)]
+        Rp, tp = index_frame_rows(m, IDENTITY_ROWS, 0.5)
+        z = np.asarray(x, np.float32)
+        f = [fmaf_exact(Rp[i, 0], z[0], fmaf_exact(Rp[i, 1], z[1], fmaf_exact(Rp[i, 2], z[2], tp[i])))
+             for i in range(3)]
         if not all(-1.0 <= f[k] < m.dims[k] for k in range(3)):
             return tau, False
         i0 = [int(math.floor(f[k])) for k in range(3)]
