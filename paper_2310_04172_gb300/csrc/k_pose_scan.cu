@@ -159,6 +159,21 @@ __global__ void k_brick_to_block4(const T* __restrict__ src, T* __restrict__ dst
   dst[(b << 12) + block4_local(l & 15u, (l >> 4) & 15u, l >> 8)] = src[i];
 }
 
+// Value l of brick b (x-fastest) moves to skew_local of its voxel: local
+// (lx, ly, lz) plus 16 times the brick's cell coordinates.
+template <typename T>
+__global__ void k_brick_to_skew(const T* __restrict__ src, T* __restrict__ dst,
+                                const int32_t* __restrict__ coords, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long b = i >> 12;
+  const uint32_t l = (uint32_t)i & 4095u;
+  const uint32_t ix = (uint32_t)coords[3 * b] * 16u + (l & 15u);
+  const uint32_t iy = (uint32_t)coords[3 * b + 1] * 16u + ((l >> 4) & 15u);
+  const uint32_t iz = (uint32_t)coords[3 * b + 2] * 16u + (l >> 8);
+  dst[(b << 12) + skew_local(ix, iy, iz)] = src[i];
+}
+
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // Score map values (Sec. III: the exponential of Eq. 3 evaluated once per map
@@ -224,6 +239,17 @@ cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_brick
     k_brick_to_block4<<<blocks_for(n, 256), 256, 0, s>>>((const short*)src, (short*)dst, n);
   else
     k_brick_to_block4<<<blocks_for(n, 256), 256, 0, s>>>((const float*)src, (float*)dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_brick_to_skew(const void* src, void* dst, const int32_t* coords,
+                                 long long n_bricks, int elem_bytes, cudaStream_t s) {
+  const long long n = n_bricks * kBrickVoxels;
+  if (n <= 0) return cudaSuccess;
+  if (elem_bytes == 2)
+    k_brick_to_skew<<<blocks_for(n, 256), 256, 0, s>>>((const short*)src, (short*)dst, coords, n);
+  else
+    k_brick_to_skew<<<blocks_for(n, 256), 256, 0, s>>>((const float*)src, (float*)dst, coords, n);
   return cudaGetLastError();
 }
 

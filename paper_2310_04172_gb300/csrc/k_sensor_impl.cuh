@@ -173,12 +173,21 @@ __device__ __forceinline__ typename Raw<DTYPE, MODE>::value outside_value(const 
   return a.vnear;
 }
 
-// Index of a brick value: 32-bit arithmetic for the cell-grid kind (at most
-// kGridMaxBricks bricks, so it cannot wrap), 64-bit otherwise.
+// Index of a brick value. Cell-grid kind: `slot` is the grid entry, the
+// index of the brick's first value (slot * 4096, at most kGridMaxBricks
+// bricks, so 32 bits), and `local` the skewed offset (skew_local); 64-bit
+// slot * 4096 + local otherwise.
 template <int KIND>
 __device__ __forceinline__ size_t value_index(uint32_t slot, uint32_t local) {
-  if constexpr (KIND == kKindBrickGrid) return (size_t)(slot * (uint32_t)kBrickVoxels + local);
+  if constexpr (KIND == kKindBrickGrid) return (size_t)(slot | local);
   else return (size_t)slot * kBrickVoxels + local;
+}
+
+// Slot number of a slot as a kernel holds it (cell grid: the grid entry).
+template <int KIND>
+__device__ __forceinline__ uint32_t slot_number(uint32_t slot) {
+  if constexpr (KIND == kKindBrickGrid) return slot / (uint32_t)kBrickVoxels;
+  else return slot;
 }
 
 // In-brick offset: linear x-fastest, or 4x4x4 blocks (block-major, each block
@@ -295,7 +304,7 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
         s.key[u] = (iz * (uint32_t)m.ny + iy) * (uint32_t)m.nx + ix;
       } else if constexpr (KIND == kKindBrickGrid) {
         s.key[u] = (iz >> 4) * m.gsz + (iy >> 4) * m.gsy + (ix >> 4);
-        s.loc[u] = brick_local<KIND>((int)ix, (int)iy, (int)iz);
+        s.loc[u] = skew_local(ix, iy, iz);
       } else {
         s.key[u] = ((iz >> 4) * m.nby + (iy >> 4)) * m.nbx + (ix >> 4);
         s.loc[u] = brick_local<KIND>((int)ix, (int)iy, (int)iz);
@@ -337,7 +346,7 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
           slot = probe_rest(m, s.key[u], brick_hash(s.key[u], m.hash_shift));
       }
 #if MCL_DEBUG_BOUNDS
-      if (slot != kNoSlot && slot >= m.n_slots) {
+      if (slot != kNoSlot && slot_number<KIND>(slot) >= m.n_slots) {
         atomicOr(a.status, kDevErrIndex);
         slot = kNoSlot;
       }
@@ -502,21 +511,27 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
     slot[5] = sz ? (sx ? b[5] : b[4]) : slot[1];
     slot[6] = sz ? (sy ? b[6] : b[4]) : slot[2];
     slot[7] = sz ? (sx ? (sy ? b[7] : b[5]) : (sy ? b[6] : b[4])) : slot[3];
-    // in-brick offsets: one step up along an axis is +1 / +16 / +256, or back
-    // to 0 on that axis when the corner crosses into the next brick
-    const int base = (((z0 & 15) << 8) | ((y0 & 15) << 4) | (x0 & 15));
-    const int ox = sx ? -15 : 1, oy = sy ? -240 : 16, oz = sz ? -3840 : 256;
+    // in-brick offsets. Linear bricks: one step up along an axis is +1 / +16 /
+    // +256, or back to 0 on that axis when the corner crosses into the next
+    // brick. Cell grid (skewed bricks, skew_local): +1 / +16 / +256 mod 4096
+    // whether or not the corner crosses.
+    const int base = KIND == kKindBrickGrid
+                         ? (int)skew_local((uint32_t)x0, (uint32_t)y0, (uint32_t)z0)
+                         : (((z0 & 15) << 8) | ((y0 & 15) << 4) | (x0 & 15));
+    const int ox = KIND != kKindBrickGrid && sx ? -15 : 1, oy = KIND != kKindBrickGrid && sy ? -240 : 16,
+              oz = KIND != kKindBrickGrid && sz ? -3840 : 256;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
 #if MCL_DEBUG_BOUNDS
-      if (slot[c] != kNoSlot && slot[c] >= m.n_slots) {
+      if (slot[c] != kNoSlot && slot_number<KIND>(slot[c]) >= m.n_slots) {
         atomicOr(a.status, kDevErrIndex);
         slot[c] = kNoSlot;
       }
 #endif
       const bool st = slot[c] != kNoSlot;
-      const int off = base + (cx ? ox : 0) + (cy ? oy : 0) + (cz ? oz : 0);
+      int off = base + (cx ? ox : 0) + (cy ? oy : 0) + (cz ? oz : 0);
+      if constexpr (KIND == kKindBrickGrid) off &= kBrickVoxels - 1;
       v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, value_index<KIND>(slot[c], (uint32_t)off))
                 : a.vout;
       stored |= st;
@@ -553,7 +568,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
 #if MCL_DEBUG_BOUNDS
-      if (slot[c] != kNoSlot && slot[c] >= m.n_slots) {
+      if (slot[c] != kNoSlot && slot_number<KIND>(slot[c]) >= m.n_slots) {
         atomicOr(a.status, kDevErrIndex);
         slot[c] = kNoSlot;
       }

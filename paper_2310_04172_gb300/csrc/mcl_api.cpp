@@ -287,31 +287,6 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
       table[h] = make_uint2(key, (uint32_t)b);
       max_probe = std::max(max_probe, probe);
     }
-    const size_t vbytes = (size_t)nb * kBrickVoxels * es;
-    cudaError_t e = cudaMalloc(&m->d_values, std::max(vbytes, (size_t)256));
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
-    if (vbytes && v.layout == MCL_LAYOUT_LINEAR) {
-      e = cudaMemcpy(m->d_values, host_values, vbytes, cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
-    } else if (vbytes) {
-      // upload through a staging buffer and reorder each brick on the device
-      const int64_t per = std::min<int64_t>(nb, 1 << 16);
-      const size_t brick_bytes = (size_t)kBrickVoxels * es;
-      void* stage = nullptr;
-      e = cudaMalloc(&stage, (size_t)per * brick_bytes);
-      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create staging"));
-      for (int64_t b0 = 0; b0 < nb && e == cudaSuccess; b0 += per) {
-        const int64_t cnt = std::min(per, nb - b0);
-        e = cudaMemcpy(stage, (const char*)host_values + (size_t)b0 * brick_bytes,
-                       (size_t)cnt * brick_bytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-          e = launch_brick_to_block4(stage, (char*)m->d_values + (size_t)b0 * brick_bytes, cnt,
-                                     (int)es, nullptr);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-      }
-      cudaFree(stage);
-      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create block layout"));
-    }
     // The cell grid with a guard layer: one more cell along each axis (cell
     // nb) and gsz + gsy + 1 cells in front, all empty. Every cell coordinate
     // in [-1, nb] then has its own cell (a guard one outside the map), so a
@@ -325,6 +300,38 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     const bool grid = d->index == MCL_INDEX_GRID ||
                       (d->index == MCL_INDEX_AUTO && v.layout == MCL_LAYOUT_LINEAR &&
                        cells * sizeof(uint32_t) <= (512ull << 20) && nb <= kGridMaxBricks);
+    const size_t vbytes = (size_t)nb * kBrickVoxels * es;
+    cudaError_t e = cudaMalloc(&m->d_values, std::max(vbytes, (size_t)256));
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
+    if (vbytes && v.layout == MCL_LAYOUT_LINEAR && !grid) {
+      e = cudaMemcpy(m->d_values, host_values, vbytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
+    } else if (vbytes) {
+      // upload through a staging buffer and reorder each brick on the device:
+      // 4x4x4 blocks, or (cell grid) rotated by the brick's cell coordinates
+      const int64_t per = std::min<int64_t>(nb, 1 << 16);
+      const size_t brick_bytes = (size_t)kBrickVoxels * es;
+      void* stage = nullptr;
+      int32_t* dcoords = nullptr;
+      e = cudaMalloc(&stage, (size_t)per * brick_bytes);
+      if (e == cudaSuccess && grid) e = cudaMalloc((void**)&dcoords, (size_t)per * 3 * sizeof(int32_t));
+      for (int64_t b0 = 0; b0 < nb && e == cudaSuccess; b0 += per) {
+        const int64_t cnt = std::min(per, nb - b0);
+        e = cudaMemcpy(stage, (const char*)host_values + (size_t)b0 * brick_bytes,
+                       (size_t)cnt * brick_bytes, cudaMemcpyHostToDevice);
+        char* dst = (char*)m->d_values + (size_t)b0 * brick_bytes;
+        if (e == cudaSuccess && grid)
+          e = cudaMemcpy(dcoords, d->brick_coords + 3 * b0, (size_t)cnt * 3 * sizeof(int32_t),
+                         cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = grid ? launch_brick_to_skew(stage, dst, dcoords, cnt, (int)es, nullptr)
+                   : launch_brick_to_block4(stage, dst, cnt, (int)es, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      }
+      if (stage) cudaFree(stage);
+      if (dcoords) cudaFree(dcoords);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, grid ? "map_create skewed layout" : "map_create block layout"));
+    }
     v.nbx = (uint32_t)nbx;
     v.nby = (uint32_t)nby;
     v.gsy = (uint32_t)gsy;
@@ -332,12 +339,14 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     v.n_slots = (uint32_t)nb;
     m->n_bricks = nb;
     if (grid) {
-      // coarse level as a dense array: brick cell -> slot (the duplicates and
-      // ranges were checked while the hash was filled above)
+      // coarse level as a dense array: brick cell -> slot * 4096, the index of
+      // the brick's first value (the duplicates and ranges were checked while
+      // the hash was filled above; at most 2^20 bricks, so it fits)
       std::vector<uint32_t> cell_slot((size_t)cells, kNoSlot);
       for (int64_t b = 0; b < nb; ++b) {
         const int32_t* c = d->brick_coords + 3 * b;
-        cell_slot[front + (uint64_t)c[2] * gsz + (uint64_t)c[1] * gsy + (uint64_t)c[0]] = (uint32_t)b;
+        cell_slot[front + (uint64_t)c[2] * gsz + (uint64_t)c[1] * gsy + (uint64_t)c[0]] =
+            (uint32_t)b * (uint32_t)kBrickVoxels;
       }
       e = cudaMalloc((void**)&m->d_grid, (size_t)cells * sizeof(uint32_t));
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create grid index"));

@@ -96,8 +96,20 @@ __host__ __device__ inline uint32_t block4_local(uint32_t lx, uint32_t ly, uint3
          ((ly & 3u) << 2) | (lx & 3u);
 }
 
+// Cell-grid maps keep each brick's values rotated by the brick's cell
+// coordinates: voxel (ix, iy, iz) sits at skew_local(ix, iy, iz) =
+// (ix + 16 iy + 256 iz) mod 4096 of its brick, that is at lx + 16 ((ly + bx)
+// mod 16) + 256 ((lz + by + carry) mod 16), a bijection of the brick's 4096
+// places, and the grid holds slot * 4096 (or kNoSlot). The value index of a
+// voxel is then grid[cell] | skew_local: two shift-adds of the voxel index
+// and one OR whichever the brick, and a trilinear corner's offset is the
+// lower corner's plus cx + 16 cy + 256 cz, mod 4096, across brick faces too.
+__host__ __device__ inline uint32_t skew_local(uint32_t ix, uint32_t iy, uint32_t iz) {
+  return (ix + (iy << 4) + (iz << 8)) & (uint32_t)(kBrickVoxels - 1);
+}
+
 // Brick-cell key (hash index; GRID: the cell's place in the padded grid) and
-// in-brick offset of a voxel.
+// in-brick offset of a voxel (GRID: skew_local).
 template <bool GRID>
 __device__ __forceinline__ void brick_key(const MapView& m, int ix, int iy, int iz, uint32_t& key,
                                           uint32_t& local) {
@@ -106,7 +118,10 @@ __device__ __forceinline__ void brick_key(const MapView& m, int ix, int iy, int 
   else
     key = ((uint32_t)(iz >> 4) * m.nby + (uint32_t)(iy >> 4)) * m.nbx + (uint32_t)(ix >> 4);
   const uint32_t lx = (uint32_t)ix & 15u, ly = (uint32_t)iy & 15u, lz = (uint32_t)iz & 15u;
-  local = m.layout == MCL_LAYOUT_BLOCK4 ? block4_local(lx, ly, lz) : ((lz * kBrick + ly) * kBrick + lx);
+  if constexpr (GRID)
+    local = skew_local((uint32_t)ix, (uint32_t)iy, (uint32_t)iz);
+  else
+    local = m.layout == MCL_LAYOUT_BLOCK4 ? block4_local(lx, ly, lz) : ((lz * kBrick + ly) * kBrick + lx);
 }
 
 // Continue a probe sequence after a first entry that did not match. Bounded by
@@ -144,7 +159,10 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
       slot = e.x == key ? e.y : (e.x == kEmptyKey ? kNoSlot : probe_rest(m, key, h));
     }
     if (slot == kNoSlot) return false;
-    d = load_value<DTYPE>(m, (size_t)slot * kBrickVoxels + local);
+    if constexpr (KIND == kKindBrickGrid)
+      d = load_value<DTYPE>(m, (size_t)(slot | local));  // slot: index of the brick's first value
+    else
+      d = load_value<DTYPE>(m, (size_t)slot * kBrickVoxels + local);
     return true;
   }
 }
@@ -380,6 +398,10 @@ cudaError_t sensor_occupancy(int kind, int layout, int dtype, int mode, const Se
 // Map upload helper: x-fastest bricks (src) -> 4x4x4-block layout (dst).
 cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_bricks, int elem_bytes,
                                    cudaStream_t s);
+// Map upload helper: x-fastest bricks (src) at cell coordinates coords
+// (device, 3 int32 per brick) -> the cell grid's skewed layout (skew_local).
+cudaError_t launch_brick_to_skew(const void* src, void* dst, const int32_t* coords,
+                                 long long n_bricks, int elem_bytes, cudaStream_t s);
 
 // Score map values: s = exp(-d^2 / (2 sigma^2)) of n stored values (src of
 // src_dtype, int16 scaled by tau / 32767), FP64, rounded once to dst_dtype
