@@ -515,11 +515,10 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
     // +256, or back to 0 on that axis when the corner crosses into the next
     // brick. Cell grid (skewed bricks, skew_local): +1 / +16 / +256 mod 4096
     // whether or not the corner crosses.
-    const int base = KIND == kKindBrickGrid
-                         ? (int)skew_local((uint32_t)x0, (uint32_t)y0, (uint32_t)z0)
-                         : (((z0 & 15) << 8) | ((y0 & 15) << 4) | (x0 & 15));
-    const int ox = KIND != kKindBrickGrid && sx ? -15 : 1, oy = KIND != kKindBrickGrid && sy ? -240 : 16,
-              oz = KIND != kKindBrickGrid && sz ? -3840 : 256;
+    constexpr bool kSkew = KIND == kKindBrickGrid && MCL_GRID_SKEW;
+    const int base = kSkew ? (int)skew_local((uint32_t)x0, (uint32_t)y0, (uint32_t)z0)
+                           : (((z0 & 15) << 8) | ((y0 & 15) << 4) | (x0 & 15));
+    const int ox = !kSkew && sx ? -15 : 1, oy = !kSkew && sy ? -240 : 16, oz = !kSkew && sz ? -3840 : 256;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
@@ -531,7 +530,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
 #endif
       const bool st = slot[c] != kNoSlot;
       int off = base + (cx ? ox : 0) + (cy ? oy : 0) + (cz ? oz : 0);
-      if constexpr (KIND == kKindBrickGrid) off &= kBrickVoxels - 1;
+      if constexpr (kSkew) off &= kBrickVoxels - 1;
       v[c] = st ? load_raw_l1<DTYPE, MODE>(m.values, value_index<KIND>(slot[c], (uint32_t)off))
                 : a.vout;
       stored |= st;

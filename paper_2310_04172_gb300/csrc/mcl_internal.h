@@ -104,8 +104,15 @@ __host__ __device__ inline uint32_t block4_local(uint32_t lx, uint32_t ly, uint3
 // voxel is then grid[cell] | skew_local: two shift-adds of the voxel index
 // and one OR whichever the brick, and a trilinear corner's offset is the
 // lower corner's plus cx + 16 cy + 256 cz, mod 4096, across brick faces too.
+#ifndef MCL_GRID_SKEW
+#define MCL_GRID_SKEW 1
+#endif
 __host__ __device__ inline uint32_t skew_local(uint32_t ix, uint32_t iy, uint32_t iz) {
+#if MCL_GRID_SKEW
   return (ix + (iy << 4) + (iz << 8)) & (uint32_t)(kBrickVoxels - 1);
+#else
+  return ((iz & 15u) << 8) | ((iy & 15u) << 4) | (ix & 15u);
+#endif
 }
 
 // Brick-cell key (hash index; GRID: the cell's place in the padded grid) and
