@@ -495,6 +495,8 @@ def run_ours(args):
         info = m.info()
         cfg["launch"] = dict(plan, brick_index={1: "hash", 2: "cell grid"}.get(info["index"], "none"),
                              brick_index_bytes=info["index_bytes"])
+        if info["index"] == 2:  # cell-grid maps keep each brick rotated by its cell coordinates
+            cfg["map"]["device_layout"] = "skewed per brick (value of voxel i at (ix + 16 iy + 256 iz) mod 4096)"
         cfg["parallelism"] = f"replicas{world}" if world > 1 else "single"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -174,6 +174,19 @@ __global__ void k_brick_to_skew(const T* __restrict__ src, T* __restrict__ dst,
   dst[(b << 12) + skew_local(ix, iy, iz)] = src[i];
 }
 
+// Voxel i of layers [z0, z0 + nzs) (x-fastest in src) to dense_index.
+template <typename T>
+__global__ void k_dense_to_tiles(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny,
+                                 int z0, long long n, uint32_t ntx, uint32_t nty) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long layer = (long long)nx * ny;
+  const uint32_t iz = (uint32_t)(z0 + i / layer);
+  const uint32_t r = (uint32_t)(i % layer);
+  const uint32_t iy = r / (uint32_t)nx, ix = r - iy * (uint32_t)nx;
+  dst[dense_index<true>(ix, iy, iz, (uint32_t)nx, (uint32_t)ny, ntx, nty)] = src[i];
+}
+
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // Score map values (Sec. III: the exponential of Eq. 3 evaluated once per map
@@ -242,6 +255,19 @@ cudaError_t launch_brick_to_block4(const void* src, void* dst, long long n_brick
   return cudaGetLastError();
 }
 
+cudaError_t launch_dense_to_tiles(const void* src, void* dst, int nx, int ny, int z0, int nzs,
+                                  uint32_t ntx, uint32_t nty, int elem_bytes, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nzs;
+  if (n <= 0) return cudaSuccess;
+  if (elem_bytes == 2)
+    k_dense_to_tiles<<<blocks_for(n, 256), 256, 0, s>>>((const short*)src, (short*)dst, nx, ny, z0, n,
+                                                         ntx, nty);
+  else
+    k_dense_to_tiles<<<blocks_for(n, 256), 256, 0, s>>>((const float*)src, (float*)dst, nx, ny, z0, n,
+                                                         ntx, nty);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_brick_to_skew(const void* src, void* dst, const int32_t* coords,
                                  long long n_bricks, int elem_bytes, cudaStream_t s) {
   const long long n = n_bricks * kBrickVoxels;
@@ -272,6 +298,8 @@ cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float
   MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_F32)
   MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_F16)
   MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_I16)
+  MCL_LOOKUP_CASE(kKindDenseTiles, MCL_F32)
+  MCL_LOOKUP_CASE(kKindDenseTiles, MCL_F16)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F32)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F16)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_I16)

@@ -30,8 +30,9 @@
 namespace mcl {
 
 #define MCL_SENSOR_UNIT(d, k) void* sensor_kernel_##d##_##k(int mode, const SensorShape& sh, bool batch);
-#define MCL_SENSOR_UNITS(d) \
-  MCL_SENSOR_UNIT(d, dense) MCL_SENSOR_UNIT(d, hash) MCL_SENSOR_UNIT(d, block4) MCL_SENSOR_UNIT(d, grid)
+#define MCL_SENSOR_UNITS(d)                                                                   \
+  MCL_SENSOR_UNIT(d, dense) MCL_SENSOR_UNIT(d, hash) MCL_SENSOR_UNIT(d, block4) MCL_SENSOR_UNIT(d, grid) \
+  MCL_SENSOR_UNIT(d, tiles)
 MCL_SENSOR_UNITS(f32)
 MCL_SENSOR_UNITS(f16)
 MCL_SENSOR_UNITS(i16)
@@ -44,6 +45,7 @@ namespace {
 void* pick(int kind, int layout, int dtype, int mode, const SensorShape& sh, bool batch = false) {
 #define MCL_PICK(d)                                                                     \
   if (kind == MCL_MAP_DENSE) return sensor_kernel_##d##_dense(mode, sh, batch);         \
+  if (kind == kKindDenseTiles) return sensor_kernel_##d##_tiles(mode, sh, batch);       \
   if (kind == kKindBrickGrid) return sensor_kernel_##d##_grid(mode, sh, batch);         \
   if (kind == MCL_MAP_BRICK && layout == MCL_LAYOUT_BLOCK4)                             \
     return sensor_kernel_##d##_block4(mode, sh, batch);                                 \

@@ -300,8 +300,8 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
       } else {
         s.in[u] = s.v[u] && (ix < (uint32_t)m.nx) && (iy < (uint32_t)m.ny) && (iz < (uint32_t)m.nz);
       }
-      if constexpr (KIND == MCL_MAP_DENSE) {
-        s.key[u] = (iz * (uint32_t)m.ny + iy) * (uint32_t)m.nx + ix;
+      if constexpr (is_dense(KIND)) {
+        s.key[u] = dense_index<KIND == kKindDenseTiles>(ix, iy, iz, (uint32_t)m.nx, (uint32_t)m.ny, m.ntx, m.nty);
       } else if constexpr (KIND == kKindBrickGrid) {
         s.key[u] = (iz >> 4) * m.gsz + (iy >> 4) * m.gsy + (ix >> 4);
         s.loc[u] = skew_local(ix, iy, iz);
@@ -313,7 +313,7 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
   }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    if constexpr (KIND == MCL_MAP_DENSE) {
+    if constexpr (is_dense(KIND)) {
       s.dv[u] = s.in[u] ? load_raw<DTYPE, MODE>(m.values, s.key[u]) : outside_value<DTYPE, MODE>(a);
     } else if constexpr (KIND == kKindBrickGrid) {
       s.e[u].y = s.in[u] ? __ldg(m.grid + s.key[u]) : kNoSlot;
@@ -333,7 +333,7 @@ __device__ __forceinline__ void stage_b(const SensorArgs& a, const Pending<KIND,
   const MapView& m = a.map;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    if constexpr (KIND == MCL_MAP_DENSE) {
+    if constexpr (is_dense(KIND)) {
       dv[u] = s.dv[u];
       use[u] = s.v[u];
     } else {
@@ -454,13 +454,14 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
   const bool iny[2] = {y0 >= 0, y0 + 1 < m.ny};
   const bool inz[2] = {z0 >= 0, z0 + 1 < m.nz};
   float v[8];
-  if constexpr (KIND == MCL_MAP_DENSE) {
+  if constexpr (is_dense(KIND)) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
       const bool in = inx[cx] & iny[cy] & inz[cz];
-      const size_t lin = ((size_t)(z0 + cz) * (size_t)m.ny + (size_t)(y0 + cy)) * (size_t)m.nx +
-                         (size_t)(x0 + cx);
+      const uint32_t lin = dense_index<KIND == kKindDenseTiles>(
+          (uint32_t)(x0 + cx), (uint32_t)(y0 + cy), (uint32_t)(z0 + cz), (uint32_t)m.nx, (uint32_t)m.ny,
+          m.ntx, m.nty);
       v[c] = in ? load_raw_l1<DTYPE, MODE>(m.values, lin) : a.vout;
       stored |= in;
     }

@@ -246,14 +246,44 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
   };
 
   if (d->kind == MCL_MAP_DENSE) {
-    const int64_t total = d->dims[0] * d->dims[1] * d->dims[2];
-    if (total > kMaxCount) return cleanup(fail(MCL_EINVAL, "map_create: dense grid above 2^31 - 1 voxels"));
+    const int64_t nx = d->dims[0], ny = d->dims[1], nz = d->dims[2];
+    // FP32 grids in 8 x 4 tiles: 1.835 -> 1.807 ms for the VLP-16 hall step
+    // (FP16 grids, whose lines already hold 64 voxels of a row, measured
+    // slower in tiles: 1.86 -> 1.91 ms)
+    m->dense_tiles = d->dtype == MCL_F32 && MCL_DENSE_TILES;
+    if (nx * ny * nz > kMaxCount) return cleanup(fail(MCL_EINVAL, "map_create: dense grid above 2^31 - 1 voxels"));
+    const int64_t stored = dense_stored(nx, ny, nz, m->dense_tiles);  // with the tiles' padding
+    if (stored > kMaxCount)
+      return cleanup(fail(MCL_EINVAL, "map_create: dense grid above 2^31 - 1 values after padding to 8 x 4 tiles"));
     if (!host_values) return cleanup(fail(MCL_EINVAL, "map_create: NULL values"));
-    cudaError_t e = cudaMalloc(&m->d_values, (size_t)total * es);
+    v.ntx = (uint32_t)((nx + 7) / 8);
+    v.nty = (uint32_t)((ny + 3) / 4);
+    cudaError_t e = cudaMalloc(&m->d_values, (size_t)stored * es);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
-    e = cudaMemcpy(m->d_values, host_values, (size_t)total * es, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
-    m->bytes = total * (int64_t)es;
+    if (!m->dense_tiles) {
+      e = cudaMemcpy(m->d_values, host_values, (size_t)stored * es, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
+    } else {
+      e = cudaMemset(m->d_values, 0, (size_t)stored * es);
+      // upload through a staging buffer of whole z layers (about 64 MB) and move
+      // each voxel to its place in the tiles on the device
+      const int64_t layer = nx * ny;
+      const int64_t per = std::max<int64_t>(1, std::min<int64_t>(nz, (64ll << 20) / std::max<int64_t>(1, layer * (int64_t)es)));
+      void* stage = nullptr;
+      if (e == cudaSuccess) e = cudaMalloc(&stage, (size_t)(per * layer) * es);
+      for (int64_t z0 = 0; z0 < nz && e == cudaSuccess; z0 += per) {
+        const int64_t cnt = std::min(per, nz - z0);
+        e = cudaMemcpy(stage, (const char*)host_values + (size_t)(z0 * layer) * es, (size_t)(cnt * layer) * es,
+                       cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = launch_dense_to_tiles(stage, m->d_values, (int)nx, (int)ny, (int)z0, (int)cnt, v.ntx, v.nty,
+                                    (int)es, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      }
+      if (stage) cudaFree(stage);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create upload"));
+    }
+    m->bytes = stored * (int64_t)es;
   } else {
     for (int k = 0; k < 3; ++k)
       if (d->dims[k] % kBrick) return cleanup(fail(MCL_EINVAL, "map_create: dims must be multiples of 16"));
@@ -383,7 +413,7 @@ mcl_status mcl_map_create_score(mcl_map_t src, float sigma, int32_t dtype, mcl_m
   if (src->score_sigma > 0.f) return fail(MCL_EINVAL, "map_create_score: the source is a score map");
   if (mcl_status rc = check_device(src)) return rc;
   const int64_t n = src->kind == MCL_MAP_DENSE
-                        ? (int64_t)src->view.nx * src->view.ny * src->view.nz
+                        ? dense_stored(src->view.nx, src->view.ny, src->view.nz, src->dense_tiles)
                         : src->n_bricks * (int64_t)kBrickVoxels;
   const size_t es = dtype == MCL_F32 ? 4 : 2;
   mcl_map_s* m = new mcl_map_s(*src);

@@ -121,6 +121,7 @@ struct mcl_map_s {
   uint32_t* d_grid = nullptr;   // grid index (allocation; view.grid = d_grid + grid_front)
   int64_t grid_cells = 0;       // cells allocated, guard cells included
   int64_t grid_front = 0;       // guard cells in front of cell (0, 0, 0)
+  bool dense_tiles = false;     // DENSE: values in 8 x 4 tiles (kKindDenseTiles)
   int64_t bytes = 0, n_bricks = 0, capacity = 0;
   int max_probe = 0;
   float score_sigma = 0.f;    // > 0: values are scores for this sigma
@@ -129,9 +130,12 @@ struct mcl_map_s {
 
 namespace mcl {
 
-// Kernel kind of a map: dense, brick with the hash index (layout chosen at
-// run time) or brick with the grid index.
-inline int kernel_kind(const mcl_map_s* m) { return m->d_grid ? kKindBrickGrid : m->kind; }
+// Kernel kind of a map: dense (linear or in tiles), brick with the hash
+// index (layout chosen at run time) or brick with the grid index.
+inline int kernel_kind(const mcl_map_s* m) {
+  if (m->d_grid) return kKindBrickGrid;
+  return m->kind == MCL_MAP_DENSE && m->dense_tiles ? kKindDenseTiles : m->kind;
+}
 
 // Kernel mode and the value read where nothing is stored (storage units)
 // of a sensor update on map m with the caller's mode.

@@ -129,9 +129,45 @@ def run_case(torch, mcl, smap, layout=0, index=0):
 
 @pytest.mark.parametrize("origin", [(0.0, 0.0, 0.0), (-1.6, -0.8, -0.4), (3.15, -2.05, 0.6)])
 @pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16])
-def test_dense_index_edges(env, origin, dtype):
+@pytest.mark.parametrize("dims", [(48, 32, 32), (45, 30, 21)])
+def test_dense_index_edges(env, origin, dtype, dims):
+    """FP32 grids are stored in 8 x 4 tiles (45 x 30: partial tiles along
+    x and y), FP16 grids linearly."""
     torch, mcl = env
-    run_case(torch, mcl, dense_map(origin, (48, 32, 32), dtype))
+    run_case(torch, mcl, dense_map(origin, dims, dtype))
+
+
+@pytest.mark.parametrize("dims", [(48, 32, 32), (45, 30, 21), (7, 3, 5)])
+def test_dense_tiles_trilinear_and_score_map(env, dims):
+    """Tiled FP32 grids, ragged or not: the trilinear read at its edges, and
+    an FP16 score map made from the tiled grid (which keeps its tiles), against
+    the oracle."""
+    torch, mcl = env
+    origin = (-0.3, 0.25, -0.1)
+    smap = dense_map(origin, dims, scenes.F32)
+    m = mcl.map_from_scene(smap)
+    om = oracle.Map.from_scene_map(smap)
+    pos = np.concatenate([tri_positions(origin, dims), edge_positions(origin, dims)])
+    parts = np.zeros((len(pos), 6), np.float32)
+    parts[:, :3] = pos
+    scan = np.zeros((1, 3), np.float32)
+    logw = torch.empty(len(parts), device="cuda")
+    mcl.mcl_sensor_update(m, torch.from_numpy(parts).cuda(), torch.from_numpy(scan).cuda(),
+                          mcl.sensor_params(0.1, flags=mcl.MCL_TRILINEAR), logw)
+    mcl.mcl_sync()
+    Lg = logw.cpu().numpy().astype(np.float64)
+    Lo = oracle.sensor_update(om, parts, scan, 0.1, trilinear=True)
+    assert np.all(np.abs(Lg - Lo) <= 1e-5 * np.maximum(1.0, np.abs(Lo)))
+    sm = mcl.mcl_map_create_score(m, 0.1, mcl.MCL_F16)
+    mcl.mcl_sensor_update(sm, torch.from_numpy(parts).cuda(), torch.from_numpy(scan).cuda(),
+                          mcl.sensor_params(0.1, mode=mcl.MCL_SUM), logw)
+    mcl.mcl_sync()
+    Ls = logw.cpu().numpy().astype(np.float64)
+    Lo_sum = oracle.sensor_update(om, parts, scan, 0.1, oracle.SUM)
+    # one point per particle: the FP16 score of its voxel against the FP64 p_hit (r16: one FP16 rounding)
+    assert np.all(np.abs(np.exp(Ls) - np.exp(Lo_sum)) <= 2.0 ** -10 * np.exp(Lo_sum) + 1e-6)
+    sm.close()
+    m.close()
 
 
 @pytest.mark.parametrize("origin", [(0.0, 0.0, 0.0), (-1.6, -0.8, -0.4)])
