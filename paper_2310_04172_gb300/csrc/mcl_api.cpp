@@ -775,7 +775,7 @@ mcl_status enqueue_sensor(mcl_map_t m, const float* particles, int64_t P, const 
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
   set_fills(m, &a);
-  a.cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : c;
+  a.cs = sum_exponent_constant(sig, q16, scale);
   a.store_scale = (q16 && p->mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
   if (pl.dynamic) {
     a.queue = (unsigned long long*)(ws + pl.off_queue);

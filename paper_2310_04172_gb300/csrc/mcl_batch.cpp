@@ -50,7 +50,7 @@ void score_constants(const mcl_map_s* m, float sigma, int mode, SensorArgs* a) {
   const double sig = (double)sigma;
   const bool q16 = m->dtype == MCL_I16;
   const double scale = (double)m->view.scale;
-  a->cs = q16 ? (float)(-0.5 / (sig * sig) * scale * scale) : sensor_c(sigma);
+  a->cs = sum_exponent_constant(sig, q16, scale);
   a->store_scale = (q16 && mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
 }
 

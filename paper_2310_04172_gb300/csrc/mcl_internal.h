@@ -267,7 +267,7 @@ struct SensorArgs {
   // score maps, +inf for SUM: exp(-inf) = 0), so that no per-point test of
   // the flag is needed and the sums keep their bits.
   float vnear;
-  float cs;            // SUM exponent constant in storage units: -1/(2 sigma^2) (* scale^2 for I16)
+  float cs;            // SUM exponent constant, base 2, in storage units (sum_exponent_constant)
   float store_scale;   // chunk sum -> real units: scale^2 for I16 in LOGPROD (sum of q^2), else 1
   // Dynamic item order: a device counter (zero at launch) hands out the items
   // in order, one at a time per CTA; NULL: static striding over the grid.

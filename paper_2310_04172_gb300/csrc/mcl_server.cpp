@@ -317,7 +317,7 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     const double sig = (double)g.sigma, scale = (double)g.map->view.scale;
     const bool q16 = g.map->dtype == MCL_I16;
     set_fills(g.map, &a);
-    a.cs = (float)(-0.5 / (sig * sig) * (q16 ? scale * scale : 1.0));
+    a.cs = sum_exponent_constant(sig, q16, scale);
     a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
     // brick maps: items handed out in order by a counter
     if (g.map->kind == MCL_MAP_BRICK && (S->desc.shape.item_order == 0 || S->desc.shape.item_order == 3))

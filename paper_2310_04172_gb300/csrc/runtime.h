@@ -137,6 +137,14 @@ inline int kernel_kind(const mcl_map_s* m) {
   return m->kind == MCL_MAP_DENSE && m->dense_tiles ? kKindDenseTiles : m->kind;
 }
 
+// SUM mode: the kernel forms each point's p_hit without its constant as
+// 2^(v^2 cs) with the hardware base-2 exponential, v the stored value in
+// storage units: cs = -log2(e) / (2 sigma^2), times scale^2 for int16
+// values (FP64, one FP32 rounding).
+inline float sum_exponent_constant(double sigma, bool q16, double scale) {
+  return (float)(-1.4426950408889634 / (2.0 * sigma * sigma) * (q16 ? scale * scale : 1.0));
+}
+
 // Kernel mode and the value read where nothing is stored (storage units)
 // of a sensor update on map m with the caller's mode.
 inline int kernel_mode(const mcl_map_s* m, int mode) { return m->score_sigma > 0.f ? kModeScore : mode; }
