@@ -296,12 +296,12 @@ def test_brute_force_8_particles_16_points(rng, dtype, parity):
                 np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
-def near_face_scan(rng, m, pose, n):
+def near_face_scan(rng, m, pose, n, shift=0.0):
     """Sensor-frame points whose map coordinates sit on or within a few ulps
-    of voxel faces (FP64 solve, then FP32)."""
+    of voxel faces (shift 1/2: of voxel centres) (FP64 solve, then FP32)."""
     R = Rotation.from_euler("ZYX", pose[[5, 4, 3]].astype(np.float64)).as_matrix()
     dims = np.asarray(m.dims)
-    u = rng.integers(0, dims, (n, 3)).astype(np.float64)
+    u = rng.integers(0, dims, (n, 3)).astype(np.float64) + shift
     u += rng.choice([0.0, 1e-7, -1e-7, 3e-7, -3e-7, 0.5], (n, 3)) * np.maximum(u, 1.0)
     x = np.asarray(m.origin, np.float64) + u * np.float64(np.float32(m.voxel))
     return ((x - pose[:3].astype(np.float64)) @ R).astype(np.float32)

@@ -13,7 +13,8 @@ import pytest
 
 import oracle
 import scenes
-from test_oracle_pins import brute_maps, dense_map, fmaf_exact, index_frame_rows, np_stored_value
+from test_oracle_pins import (brute_maps, dense_map, fmaf_exact, index_frame_rows, near_face_scan,
+                              np_stored_value)
 
 
 @pytest.fixture
@@ -125,6 +126,28 @@ def test_brute_force_random_maps(rng, dtype, parity):
         ref = [np_trilinear(m, p, parity) for p in pts]
         np.testing.assert_allclose(d, [r[0] for r in ref], rtol=0, atol=1e-12)
         assert n == sum(r[1] for r in ref)
+
+
+def test_parity_corner_rule_per_point(rng):
+    """The parity-mode lower corner of every scan point, for rotated poses
+    and points on or next to voxel centres (where floor(f) changes):
+    floor(f) with f from the rows in the index frame with shift 1/2 and one
+    exactly rounded fma chain per axis, or -1s where no corner is inside."""
+    dense, _ = brute_maps(rng, scenes.F32)
+    om = oracle.Map.from_scene_map(dense)
+    poses = np.concatenate([rng.uniform(0.2, 1.6, (6, 3)), rng.uniform(-math.pi, math.pi, (6, 3))],
+                           1).astype(np.float32)
+    mats = oracle.pose_to_matrix(poses, parity=False)
+    for p in range(len(poses)):
+        z = near_face_scan(rng, dense, poses[p], 300, shift=0.5)
+        _, _, idx, _ = oracle.eval_points(om, poses[p], z, parity=True, trilinear=True)
+        Rp, tp = index_frame_rows(dense, mats[p], 0.5)
+        for j in range(len(z)):
+            f = [fmaf_exact(Rp[i, 0], z[j, 0], fmaf_exact(Rp[i, 1], z[j, 1], fmaf_exact(Rp[i, 2], z[j, 2], tp[i])))
+                 for i in range(3)]
+            ok = all(-1.0 <= f[k] < dense.dims[k] for k in range(3))
+            exp = [int(math.floor(f[k])) for k in range(3)] if ok else [-1, -1, -1]
+            assert list(idx[j]) == exp, (p, j)
 
 
 def test_continuous_across_faces(rng):
