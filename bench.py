@@ -761,7 +761,7 @@ def weight_report(Lg, wg, Lo) -> dict:
 
 def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, args):
     """Weight error of the headline form (int16 map) and of the same step on
-    FP32 map values against the FP64 oracle (quality mode: FP64 throughout on
+    FP16 and FP32 map values against the FP64 oracle (quality mode: FP64 throughout on
     the FP32 values) on two seeded 10,000-particle subsets: the headline's
     global-localisation cloud, and a tracking cloud Gaussian about the true
     pose (0.2 m, 2 deg), where more particles carry weight. Then the same
@@ -774,6 +774,7 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     maps = wl.info["maps"]
     P, N = len(wl.particles), len(wl.scan)
     m32 = mcl.map_from_scene(maps[scenes.F32])
+    m16 = mcl.map_from_scene(maps[scenes.F16])
     om = oracle.Map.from_scene_map(maps[scenes.F32])
     rng = np.random.default_rng(4)
     subsets = {"global_10000": wl.particles[np.sort(rng.choice(P, 10_000, replace=False))],
@@ -793,7 +794,7 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
             t0 = time.perf_counter()
             Lo = oracle.sensor_update(om, sub, wl.scan, wl.sigma_hit, mode=mode, parity=False)
             res[f"oracle_s_{key}"] = time.perf_counter() - t0
-            for label, mm in (("i16", m_head), ("f32", m32)):
+            for label, mm in (("i16", m_head), ("f16", m16), ("f32", m32)):
                 lg = torch.empty(len(sub), device=parts.device)
                 wg = torch.empty(len(sub), device=parts.device)
                 mcl.mcl_sensor_update(mm, dsub, scan, mprm, lg, wg)
@@ -817,7 +818,6 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     plain = mcl.sensor_params(wl.sigma_hit, particle_order=1, item_order=1)
     ms_f32 = timed(lambda: mcl.mcl_sensor_update(m32, parts, scan, prm, logw, w))
     ms_f32_plain = timed(lambda: mcl.mcl_sensor_update(m32, parts, scan, plain, logw, w))
-    m16 = mcl.map_from_scene(maps[scenes.F16])
     ms_f16 = timed(lambda: mcl.mcl_sensor_update(m16, parts, scan, prm, logw, w))
     m16.close()
     S = 4
