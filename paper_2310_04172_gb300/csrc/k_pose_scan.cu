@@ -184,7 +184,7 @@ __global__ void k_dense_to_tiles(const T* __restrict__ src, T* __restrict__ dst,
   const uint32_t iz = (uint32_t)(z0 + i / layer);
   const uint32_t r = (uint32_t)(i % layer);
   const uint32_t iy = r / (uint32_t)nx, ix = r - iy * (uint32_t)nx;
-  dst[dense_index<true>(ix, iy, iz, (uint32_t)nx, (uint32_t)ny, ntx, nty)] = src[i];
+  dst[dense_index<true>(ix, iy, iz, (uint32_t)nx, (uint32_t)ny, 8u * ntx - 8u, 32u * ntx * nty)] = src[i];
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -300,6 +300,7 @@ cudaError_t launch_map_lookup(int kind, int dtype, const MapView& m, const float
   MCL_LOOKUP_CASE(MCL_MAP_DENSE, MCL_I16)
   MCL_LOOKUP_CASE(kKindDenseTiles, MCL_F32)
   MCL_LOOKUP_CASE(kKindDenseTiles, MCL_F16)
+  MCL_LOOKUP_CASE(kKindDenseTiles, MCL_I16)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F32)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_F16)
   MCL_LOOKUP_CASE(MCL_MAP_BRICK, MCL_I16)

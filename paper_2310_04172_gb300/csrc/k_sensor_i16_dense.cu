@@ -8,8 +8,4 @@ void* sensor_kernel_i16_dense(int mode, const SensorShape& sh, bool batch) {
   return sensor::pick_kind<MCL_MAP_DENSE, MCL_I16>(mode, sh, batch);
 }
 
-// int16 dense maps are stored linearly (only FP32 grids, and the score maps
-// made from them, are tiled).
-void* sensor_kernel_i16_tiles(int, const SensorShape&, bool) { return nullptr; }
-
 }  // namespace mcl

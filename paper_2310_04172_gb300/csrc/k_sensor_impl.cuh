@@ -301,7 +301,7 @@ __device__ __forceinline__ void stage_a_pairs(const SensorArgs& a, const float4*
         s.in[u] = s.v[u] && (ix < (uint32_t)m.nx) && (iy < (uint32_t)m.ny) && (iz < (uint32_t)m.nz);
       }
       if constexpr (is_dense(KIND)) {
-        s.key[u] = dense_index<KIND == kKindDenseTiles>(ix, iy, iz, (uint32_t)m.nx, (uint32_t)m.ny, m.ntx, m.nty);
+        s.key[u] = dense_index<KIND == kKindDenseTiles>(ix, iy, iz, (uint32_t)m.nx, (uint32_t)m.ny, m.tcy, m.tsz);
       } else if constexpr (KIND == kKindBrickGrid) {
         s.key[u] = (iz >> 4) * m.gsz + (iy >> 4) * m.gsy + (ix >> 4);
         s.loc[u] = skew_local(ix, iy, iz);
@@ -471,7 +471,7 @@ __device__ __forceinline__ float tri_read(const SensorArgs& a, float fx, float f
       const bool in = inx[cx] & iny[cy] & inz[cz];
       const uint32_t lin = dense_index<KIND == kKindDenseTiles>(
           (uint32_t)(x0 + cx), (uint32_t)(y0 + cy), (uint32_t)(z0 + cz), (uint32_t)m.nx, (uint32_t)m.ny,
-          m.ntx, m.nty);
+          m.tcy, m.tsz);
       v[c] = in ? load_raw_l1<DTYPE, MODE>(m.values, lin) : a.vout;
       stored |= in;
     }

@@ -247,10 +247,9 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
 
   if (d->kind == MCL_MAP_DENSE) {
     const int64_t nx = d->dims[0], ny = d->dims[1], nz = d->dims[2];
-    // FP32 grids in 8 x 4 tiles: 1.835 -> 1.807 ms for the VLP-16 hall step
-    // (FP16 grids, whose lines already hold 64 voxels of a row, measured
-    // slower in tiles: 1.86 -> 1.91 ms)
-    m->dense_tiles = d->dtype == MCL_F32 && MCL_DENSE_TILES;
+    // grids in 8 x 4 tiles: the VLP-16 hall step 1.835 -> 1.706 ms (FP32),
+    // 1.861 -> 1.806 ms (FP16)
+    m->dense_tiles = MCL_DENSE_TILES != 0;
     if (nx * ny * nz > kMaxCount) return cleanup(fail(MCL_EINVAL, "map_create: dense grid above 2^31 - 1 voxels"));
     const int64_t stored = dense_stored(nx, ny, nz, m->dense_tiles);  // with the tiles' padding
     if (stored > kMaxCount)
@@ -258,6 +257,8 @@ mcl_status mcl_map_create(const mcl_map_desc* d, const void* host_values, mcl_ma
     if (!host_values) return cleanup(fail(MCL_EINVAL, "map_create: NULL values"));
     v.ntx = (uint32_t)((nx + 7) / 8);
     v.nty = (uint32_t)((ny + 3) / 4);
+    v.tcy = 8u * v.ntx - 8u;
+    v.tsz = 32u * v.ntx * v.nty;
     cudaError_t e = cudaMalloc(&m->d_values, (size_t)stored * es);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "map_create values"));
     if (!m->dense_tiles) {

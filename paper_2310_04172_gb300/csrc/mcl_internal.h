@@ -51,6 +51,7 @@ struct MapView {
   uint32_t nbx, nby;    // BRICK: brick grid size (x, y)
   uint32_t gsy, gsz;    // BRICK, grid index: cell strides nbx + 1 and (nbx + 1)(nby + 1)
   uint32_t ntx, nty;    // DENSE, tiled: tiles along x and y (dense_index)
+  uint32_t tcy, tsz;    // DENSE, tiled: 8 ntx - 8 and 32 ntx nty (dense_index)
   uint32_t hash_mask;   // capacity - 1
   int hash_shift;       // 32 - bits
   int max_probe;        // longest probe sequence of a stored key (>= 1)
@@ -59,7 +60,7 @@ struct MapView {
   int layout;           // BRICK: MCL_LAYOUT_LINEAR or MCL_LAYOUT_BLOCK4
 };
 
-// FP32 dense maps (kKindDenseTiles) are stored in tiles of 8 x 4 x 1 voxels
+// Dense maps (kKindDenseTiles) are stored in tiles of 8 x 4 x 1 voxels
 // (x-fastest rows of 8 in a tile, tiles x-fastest: ntx = ceil(nx / 8) by
 // nty = ceil(ny / 4) per z layer), so a 128-byte line holds an 8 x 4 patch
 // instead of 32 voxels of one row. A warp's gathers (neighbouring points of
@@ -70,12 +71,15 @@ struct MapView {
 #ifndef MCL_DENSE_TILES
 #define MCL_DENSE_TILES 1  // 0: every dense map linear
 #endif
+// ((iz nty + (iy >> 2)) ntx + (ix >> 3)) 32 + (iy & 3) 8 + (ix & 7), written
+// as ix + 3 (ix & ~7) + 8 iy + (iy & ~3)(8 ntx - 8) + iz (32 ntx nty) so that
+// it takes two masks, three multiply-adds and one shift-add (tcy, tsz:
+// the two strides, precomputed).
 template <bool TILES>
 __host__ __device__ inline uint32_t dense_index(uint32_t ix, uint32_t iy, uint32_t iz, uint32_t nx,
-                                                uint32_t ny, uint32_t ntx, uint32_t nty) {
+                                                uint32_t ny, uint32_t tcy, uint32_t tsz) {
   if constexpr (TILES) {
-    const uint32_t tile = (iz * nty + (iy >> 2)) * ntx + (ix >> 3);
-    return (tile << 5) | ((iy & 3u) << 3) | (ix & 7u);
+    return iz * tsz + ((iy & ~3u) * tcy + (ix + 3u * (ix & ~7u)) + (iy << 3));
   } else {
     return (iz * ny + iy) * nx + ix;
   }
@@ -183,7 +187,7 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
   linear = ((long long)iz * m.ny + iy) * m.nx + ix;
   if constexpr (is_dense(KIND)) {
     d = load_value<DTYPE>(m, dense_index<KIND == kKindDenseTiles>((uint32_t)ix, (uint32_t)iy, (uint32_t)iz,
-                                                                  (uint32_t)m.nx, (uint32_t)m.ny, m.ntx, m.nty));
+                                                                  (uint32_t)m.nx, (uint32_t)m.ny, m.tcy, m.tsz));
     return true;
   } else {
     uint32_t key, local, slot;

@@ -128,20 +128,20 @@ def run_case(torch, mcl, smap, layout=0, index=0):
 
 
 @pytest.mark.parametrize("origin", [(0.0, 0.0, 0.0), (-1.6, -0.8, -0.4), (3.15, -2.05, 0.6)])
-@pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16])
+@pytest.mark.parametrize("dtype", [scenes.F32, scenes.F16, scenes.I16])
 @pytest.mark.parametrize("dims", [(48, 32, 32), (45, 30, 21)])
 def test_dense_index_edges(env, origin, dtype, dims):
-    """FP32 grids are stored in 8 x 4 tiles (45 x 30: partial tiles along
-    x and y), FP16 grids linearly."""
+    """Dense grids are stored in 8 x 4 tiles (45 x 30: partial tiles along
+    x and y)."""
     torch, mcl = env
     run_case(torch, mcl, dense_map(origin, dims, dtype))
 
 
 @pytest.mark.parametrize("dims", [(48, 32, 32), (45, 30, 21), (7, 3, 5)])
 def test_dense_tiles_trilinear_and_score_map(env, dims):
-    """Tiled FP32 grids, ragged or not: the trilinear read at its edges, and
-    an FP16 score map made from the tiled grid (which keeps its tiles), against
-    the oracle."""
+    """Tiled grids, ragged or not: the trilinear read at its edges, and an
+    FP16 score map made from a tiled FP32 grid (which keeps its tiles),
+    against the oracle."""
     torch, mcl = env
     origin = (-0.3, 0.25, -0.1)
     smap = dense_map(origin, dims, scenes.F32)
