@@ -858,9 +858,10 @@ __global__ void __launch_bounds__(256, (MinBlocks<KIND, U, TRI>::value)) k_senso
 }
 
 // Many sessions whose maps share kind, storage type, geometry and score
-// constants: items (session, chunk, particle block) of uneven sizes, numbered
-// session by session (item_begin[s] is the first item of session s, each
-// session's items in its own sweep order). A device counter hands them out in
+// constants: items (session, chunk, particle block) of uneven sizes, listed as
+// segments of consecutive items of one session (each session's items in its
+// own sweep order; sessions on one map interleaved sweep by sweep, see
+// item_segments). A device counter hands them out in
 // order when b.base.queue is set (as in k_sensor), else they are strided over
 // the grid. Each session reads its own map (values and brick index from its
 // table entry; the rest of the view is the group's) and gets the results the
@@ -870,20 +871,21 @@ __device__ __forceinline__ bool batch_item(const BatchArgs& b, long long item, u
                                            uint32_t bar_s, float4* smat, long long& loaded,
                                            uint32_t& parity, int* pnext) {
   const SensorArgs& a = b.base;
-  int lo = 0, hi = b.n_sessions - 1;  // session whose item range holds `item`
+  int lo = 0, hi = b.n_segs - 1;  // segment that holds `item`
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(b.item_begin + mid) <= item) lo = mid; else hi = mid - 1;
+    if (__ldg(&b.segs[mid].begin) <= item) lo = mid; else hi = mid - 1;
   }
-  const BatchSession& S = b.sessions[lo];
-  const long long local = item - __ldg(b.item_begin + lo);
+  const int ses = __ldg(&b.segs[lo].session);
+  const BatchSession& S = b.sessions[ses];
+  const long long local = __ldg(&b.segs[lo].local0) + (item - __ldg(&b.segs[lo].begin));
   int c, blk;
   item_coords(local, S.nblk, S.K, S.sweep, c, blk);
   const int ppi = S.ppi, P = S.P;
   const int p0 = blk * ppi;
   const int pn = min(ppi, P - p0);
   const int cnt = min(a.chunk, S.N - c * a.chunk);
-  const long long key = ((long long)lo << 32) | (unsigned)c;
+  const long long key = ((long long)ses << 32) | (unsigned)c;
   if (key != loaded) {
     if (!stage_chunk(smem, bar_s, reinterpret_cast<const unsigned char*>(S.scan) +
                                       a.layout.chunk_offset(c),

@@ -229,13 +229,34 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     b->s.push_back(sp);
     b->total_evals += u.P * u.N;
   }
+  // per group: resident CTAs and the item order (segments of one session's
+  // items, sessions on one map interleaved sweep by sweep)
+  const size_t ng = b->g.size();
+  std::vector<std::vector<ItemSeg>> gsegs(ng);
+  std::vector<std::vector<int>> gsweeps(ng);
+  std::vector<long long> gitems(ng);
+  for (size_t k = 0; k < ng; ++k) {
+    Group& g = b->g[k];
+    int bps = 0;
+    cudaError_t e = sensor_batch_occupancy(kernel_kind(g.map), g.map->view.layout, g.map->dtype,
+                                           kernel_mode(g.map, g.mode), g.sh, &bps);
+    if (e != cudaSuccess || bps < 1) return bail(cuda_fail(e, "batch_create occupancy"));
+    const long long slots = (long long)st.sms * bps;
+    std::vector<SegSession> ss;
+    for (int i : g.sessions) {
+      const SessionPlan& sp = b->s[i];
+      ss.push_back(SegSession{sp.u.map->view.values, sp.pl.nblk, sp.pl.K, sp.pl.sweep});
+    }
+    gitems[k] = item_segments(ss, slots, g.dynamic, kBatchMaxRounds, &gsweeps[k], &gsegs[k]);
+    g.sh.grid = (int)std::min<long long>(gitems[k], slots);
+  }
   // group tables, item counters, offsets and the side tables follow the session blocks
-  std::vector<size_t> off_tab(b->g.size()), off_beg(b->g.size());
-  for (size_t k = 0; k < b->g.size(); ++k) {
+  std::vector<size_t> off_tab(ng), off_seg(ng);
+  for (size_t k = 0; k < ng; ++k) {
     off_tab[k] = off;
     off = align256(off + b->g[k].sessions.size() * sizeof(BatchSession));
-    off_beg[k] = off;
-    off = align256(off + (b->g[k].sessions.size() + 1) * sizeof(long long));
+    off_seg[k] = off;
+    off = align256(off + gsegs[k].size() * sizeof(ItemSeg));
   }
   const size_t off_queue = off;
   off = align256(off + b->g.size() * sizeof(unsigned long long));
@@ -253,7 +274,6 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
   for (size_t k = 0; k < b->g.size(); ++k) {
     Group& g = b->g[k];
     std::vector<BatchSession> tab;
-    std::vector<long long> beg{0};
     for (int i : g.sessions) {
       const SessionPlan& sp = b->s[i];
       char* ws = b->ws + sp.base;
@@ -265,21 +285,16 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       t.N = (int)sp.u.N;
       t.nblk = sp.pl.nblk;
       t.K = sp.pl.K;
-      t.sweep = sp.pl.sweep;
+      t.sweep = gsweeps[k][tab.size()];
       t.ppi = sp.pl.sh.ppi;
       session_map(sp.u.map, &t);
       tab.push_back(t);
-      beg.push_back(beg.back() + sp.pl.n_items);
     }
     e = cudaMemcpy(b->ws + off_tab[k], tab.data(), tab.size() * sizeof(BatchSession), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-      e = cudaMemcpy(b->ws + off_beg[k], beg.data(), beg.size() * sizeof(long long), cudaMemcpyHostToDevice);
+      e = cudaMemcpy(b->ws + off_seg[k], gsegs[k].data(), gsegs[k].size() * sizeof(ItemSeg),
+                     cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(cuda_fail(e, "batch_create tables"));
-    int bps = 0;
-    e = sensor_batch_occupancy(kernel_kind(g.map), g.map->view.layout, g.map->dtype, kernel_mode(g.map, g.mode),
-                               g.sh, &bps);
-    if (e != cudaSuccess || bps < 1) return bail(cuda_fail(e, "batch_create occupancy"));
-    g.sh.grid = (int)std::min<long long>(beg.back(), (long long)st.sms * bps);
     SensorArgs& a = g.args.base;
     a = SensorArgs{};
     a.map = g.map->view;
@@ -296,10 +311,10 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
       any_dynamic = true;
     }
     g.args.sessions = (const BatchSession*)(b->ws + off_tab[k]);
-    g.args.item_begin = (const long long*)(b->ws + off_beg[k]);
-    g.args.n_sessions = (int)g.sessions.size();
-    g.args.n_items = beg.back();
-    b->n_items += beg.back();
+    g.args.segs = (const ItemSeg*)(b->ws + off_seg[k]);
+    g.args.n_segs = (int)gsegs[k].size() - 1;
+    g.args.n_items = gitems[k];
+    b->n_items += gitems[k];
   }
   if (any_dynamic) b->d_queue = (unsigned long long*)(b->ws + off_queue);
   // side tables of all sessions

@@ -405,11 +405,20 @@ int side_blocks(int kind, const SideSeg& g);
 constexpr int kSideThreads = 256;  // of the per-particle side launches
 cudaError_t launch_side(int kind, const SideSeg* segs, const SegBlocks& b, cudaStream_t s);
 
+// A run of consecutive items of one session in a batched launch's item order:
+// items [begin, next segment's begin) are the session's local items local0, ...
+struct ItemSeg {
+  long long begin;
+  long long local0;
+  int session;  // index into BatchArgs::sessions (-1: the closing entry)
+  int pad;
+};
+
 struct BatchArgs {
   SensorArgs base;                 // map, score constants, chunk, ppi, status
   const BatchSession* sessions;    // device table
-  const long long* item_begin;     // device, n_sessions + 1 prefix of item counts
-  int n_sessions;
+  const ItemSeg* segs;             // device, n_segs + 1 entries (the last: begin = n_items)
+  int n_segs;
   long long n_items;
 };
 

@@ -162,7 +162,7 @@ void free_session(mcl_session_s* ss) {
 // Bytes of a slot's step tables for up to cap sessions (and as many groups).
 size_t slot_table_bytes(int cap) {
   return side_table_bytes(cap) + (size_t)cap * (align256(sizeof(BatchSession)) + 256 + 256) +
-         3 * align256((size_t)cap * 8) + 4096;
+         (size_t)cap * ((kServerMaxRounds + 1) * sizeof(ItemSeg) + 256) + 3 * align256((size_t)cap * 8) + 4096;
 }
 
 // Enqueues one batched filter step for the slot's sessions on its stream:
@@ -271,15 +271,30 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
   std::vector<SensorShape> shapes(groups.size());
   for (size_t k = 0; k < groups.size(); ++k) {
     const G& g = groups[k];
+    SensorShape sh = sl->sessions[g.idx.back()]->pl.sh;
+    int bps = 0;
+    MCL_CUDA(sensor_batch_occupancy(kernel_kind(g.map), g.map->view.layout, g.map->dtype,
+                                    kernel_mode(g.map, g.mode), sh, &bps));
+    const long long slots = (long long)S->dev.sms * std::max(bps, 1);
+    // brick maps: items handed out in order by a counter, sessions on one map interleaved
+    const bool dynamic =
+        g.map->kind == MCL_MAP_BRICK && (S->desc.shape.item_order == 0 || S->desc.shape.item_order == 3);
+    std::vector<SegSession> segin;
+    for (size_t q = 0; q < g.idx.size(); ++q) {
+      mcl_session_s* ss = sl->sessions[g.idx[q]];
+      const int K = (int)((Ns[g.idx[q]] + ss->pl.sh.chunk - 1) / ss->pl.sh.chunk);
+      segin.push_back(SegSession{ss->map->view.values, ss->pl.nblk, K, ss->pl.sweep});
+    }
+    std::vector<int> sweeps;
+    std::vector<ItemSeg> segv;
+    const long long n_items = item_segments(segin, slots, dynamic, kServerMaxRounds, &sweeps, &segv);
     BatchSession* tab = (BatchSession*)(sl->h_tab + off);
     const size_t off_tab = off;
     off = align256(off + g.idx.size() * sizeof(BatchSession));
-    long long* beg = (long long*)(sl->h_tab + off);
-    const size_t off_beg = off;
-    off = align256(off + (g.idx.size() + 1) * sizeof(long long));
+    const size_t off_seg = off;
+    off = align256(off + segv.size() * sizeof(ItemSeg));
     if (off > sl->tab_bytes) return fail(MCL_EINTERNAL, "server: step tables exceed the slot buffer");
-    beg[0] = 0;
-    SensorShape sh{};
+    std::memcpy(sl->h_tab + off_seg, segv.data(), segv.size() * sizeof(ItemSeg));
     for (size_t q = 0; q < g.idx.size(); ++q) {
       mcl_session_s* ss = sl->sessions[g.idx[q]];
       const int64_t N = Ns[g.idx[q]];
@@ -293,16 +308,12 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
       t.N = (int)N;
       t.nblk = ss->pl.nblk;
       t.K = K;
-      t.sweep = ss->pl.sweep;
+      t.sweep = sweeps[q];
       t.ppi = ss->pl.sh.ppi;
       session_map(ss->map, &t);
       tab[q] = t;
-      beg[q + 1] = beg[q] + (long long)K * ss->pl.nblk;
     }
-    int bps = 0;
-    MCL_CUDA(sensor_batch_occupancy(kernel_kind(g.map), g.map->view.layout, g.map->dtype,
-                                    kernel_mode(g.map, g.mode), sh, &bps));
-    sh.grid = (int)std::min<long long>(beg[g.idx.size()], (long long)S->dev.sms * std::max(bps, 1));
+    sh.grid = (int)std::min<long long>(n_items, slots);
     shapes[k] = sh;
     BatchArgs& b = args[k];
     b = BatchArgs{};
@@ -319,13 +330,11 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     set_fills(g.map, &a);
     a.cs = sum_exponent_constant(sig, q16, scale);
     a.store_scale = (q16 && g.mode == MCL_LOGPROD) ? (float)(scale * scale) : 1.0f;
-    // brick maps: items handed out in order by a counter
-    if (g.map->kind == MCL_MAP_BRICK && (S->desc.shape.item_order == 0 || S->desc.shape.item_order == 3))
-      a.queue = (unsigned long long*)(sl->d_tab + off_queue) + k;
+    if (dynamic) a.queue = (unsigned long long*)(sl->d_tab + off_queue) + k;
     b.sessions = (const BatchSession*)(sl->d_tab + off_tab);
-    b.item_begin = (const long long*)(sl->d_tab + off_beg);
-    b.n_sessions = (int)g.idx.size();
-    b.n_items = beg[g.idx.size()];
+    b.segs = (const ItemSeg*)(sl->d_tab + off_seg);
+    b.n_segs = (int)segv.size() - 1;
+    b.n_items = n_items;
   }
   MCL_CUDA(cudaMemcpyAsync(sl->d_tab, sl->h_tab, off, cudaMemcpyHostToDevice, st));
   for (int k : {(int)kSideMotion, (int)kSideOrderZero, (int)kSideOrderKeys, (int)kSideOrderTiles,

@@ -3,6 +3,7 @@
 // launch itself. Used by the batched sensor update and the serving loop, so
 // that a step over many sessions costs the same number of launches as a step
 // over one.
+#include <algorithm>
 #include <cstring>
 
 #include "runtime.h"
@@ -45,6 +46,56 @@ cudaError_t launch_side(int kind, const SideSeg* segs, const SegBlocks& b, cudaS
     case kSideSystematic: return launch_side_resample(kind, segs, b, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+long long item_segments(const std::vector<SegSession>& s, long long slots, bool interleave, int max_rounds,
+                        std::vector<int>* sweeps, std::vector<ItemSeg>* segs) {
+  const int n = (int)s.size();
+  segs->clear();
+  sweeps->assign(n, 0);
+  long long pos = 0;
+  if (!interleave) {
+    for (int i = 0; i < n; ++i) {
+      (*sweeps)[i] = s[i].sweep;
+      segs->push_back(ItemSeg{pos, 0, i, 0});
+      pos += (long long)s[i].nblk * s[i].K;
+    }
+  } else {
+    std::vector<char> done(n, 0);
+    for (int i = 0; i < n; ++i) {
+      if (done[i]) continue;
+      std::vector<int> on;  // the sessions on this map, in order
+      long long items = 0;
+      for (int j = i; j < n; ++j)
+        if (!done[j] && s[j].values == s[i].values) {
+          on.push_back(j);
+          done[j] = 1;
+          items += (long long)s[j].nblk * s[j].K;
+        }
+      if (on.size() == 1) {  // alone on its map: its own sweeps, one segment
+        (*sweeps)[i] = s[i].sweep;
+        segs->push_back(ItemSeg{pos, 0, i, 0});
+        pos += (long long)s[i].nblk * s[i].K;
+        continue;
+      }
+      const long long R = std::max<long long>(1, std::min<long long>(max_rounds, (items + slots - 1) / std::max<long long>(1, slots)));
+      long long rounds = 0;
+      for (int j : on) {
+        const int sw = (int)std::max<long long>(1, (s[j].nblk + R - 1) / R);
+        (*sweeps)[j] = sw;
+        rounds = std::max<long long>(rounds, (s[j].nblk + sw - 1) / sw);
+      }
+      for (long long r = 0; r < rounds; ++r)
+        for (int j : on) {
+          const long long b0 = r * (*sweeps)[j];
+          if (b0 >= s[j].nblk) continue;
+          segs->push_back(ItemSeg{pos, b0 * s[j].K, j, 0});
+          pos += std::min<long long>((*sweeps)[j], s[j].nblk - b0) * s[j].K;
+        }
+    }
+  }
+  segs->push_back(ItemSeg{pos, 0, -1, 0});
+  return pos;
 }
 
 size_t side_table_bytes(int n) {

@@ -137,6 +137,25 @@ inline int kernel_kind(const mcl_map_s* m) {
   return m->kind == MCL_MAP_DENSE && m->dense_tiles ? kKindDenseTiles : m->kind;
 }
 
+// Item order of a batched sensor launch (ItemSeg). Without interleaving,
+// session by session, each in its own sweeps. With it (dynamic item order):
+// a session alone on its map keeps its own sweeps; sessions that read the
+// same map values are interleaved sweep by sweep, in
+// R rounds with R about their items / slots (at most max_rounds), each
+// session's sweep cut to ceil(blocks / R), so that round r covers the same
+// fraction of every such session's spatial order and the items in flight read
+// one region of the map for all of them, as one session's sweep does (4
+// sessions of 250,000 particles on one building: 8.35 DRAM bytes per
+// evaluation session by session). sweeps: the sweep of each session.
+struct SegSession {
+  const void* values;
+  int nblk, K, sweep;
+};
+long long item_segments(const std::vector<SegSession>& s, long long slots, bool interleave, int max_rounds,
+                        std::vector<int>* sweeps, std::vector<ItemSeg>* segs);
+constexpr int kBatchMaxRounds = 1024;   // batches (tables built once)
+constexpr int kServerMaxRounds = 256;   // serving steps (tables in a fixed slot buffer)
+
 // SUM mode: the kernel forms each point's p_hit without its constant as
 // 2^(v^2 cs) with the hardware base-2 exponential, v the stored value in
 // storage units: cs = -log2(e) / (2 sigma^2), times scale^2 for int16
