@@ -114,7 +114,13 @@ enum { MCL_INDEX_AUTO = 0, MCL_INDEX_HASH = 1, MCL_INDEX_GRID = 2 };
  * 512 MB and the map has at most 2^20 bricks, else the hash. The grid is
  * only built with MCL_LAYOUT_LINEAR and for at most 2^20 bricks (its kernels
  * address values with 32-bit indices); MCL_INDEX_GRID beyond that is EINVAL.
- * Results do not depend on the index. */
+ * Results do not depend on the index.
+ * Device storage the library chooses (no result depends on it): with the
+ * grid index, each brick's values are rotated by its cell coordinates (voxel
+ * (ix, iy, iz) at (ix + 16 iy + 256 iz) mod 4096 of its brick) and the grid
+ * is padded by one empty cell per axis; dense grids are stored in tiles of
+ * 8 x 4 x 1 voxels, padded to whole tiles (device_bytes of mcl_map_info
+ * counts the padding). */
 typedef struct mcl_map_desc {
   uint32_t struct_size; /* sizeof(mcl_map_desc) */
   int32_t kind;         /* MCL_MAP_DENSE or MCL_MAP_BRICK */
