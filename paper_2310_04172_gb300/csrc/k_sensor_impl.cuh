@@ -649,9 +649,11 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 // the 4-deep loop of the single-session kernel (48 registers; packed pair
 // stage, dynamic sweeps: 102.6 ms against 105.9 at 4 and 108.1 at 6) and 4
 // for the batched one; 4 for the 8-deep loop (64 registers: 97.0 ms, the
-// default of the cell-grid kernel, against 103.7 at 5 and 106.9 at 3); 4 for
-// the trilinear read (crossing-bit walk, 32-bit value indices: 596 ms against
-// 602 ms at 3 and 613 ms at 5).
+// default of the cell-grid kernel, against 103.7 at 5 and 106.9 at 3); 5 for
+// the trilinear read (48 registers without spills once the guard cells took
+// the inside tests out: 363.9 against 369.1 ms at 4; with the earlier
+// crossing-bit walk 4 was best, 596 ms against 613 at 5), 4 for its batched
+// form (which would spill about 100 bytes at 48 registers).
 #ifndef MCL_SENSOR_MIN_BLOCKS
 #define MCL_SENSOR_MIN_BLOCKS 6
 #endif
@@ -662,7 +664,10 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 #define MCL_BATCH_MIN_BLOCKS_GRID 4
 #endif
 #ifndef MCL_TRI_MIN_BLOCKS
-#define MCL_TRI_MIN_BLOCKS 4
+#define MCL_TRI_MIN_BLOCKS 5
+#endif
+#ifndef MCL_TRI_BATCH_MIN_BLOCKS
+#define MCL_TRI_BATCH_MIN_BLOCKS 4
 #endif
 #ifndef MCL_U8_MIN_BLOCKS
 #define MCL_U8_MIN_BLOCKS 4
@@ -670,7 +675,8 @@ __device__ __forceinline__ void eval_tri(const SensorArgs& a, const float4* __re
 
 template <int KIND, int U, bool TRI = false, bool BATCH = false>
 struct MinBlocks {
-  static constexpr int value = TRI ? MCL_TRI_MIN_BLOCKS : U == 8 ? MCL_U8_MIN_BLOCKS
+  static constexpr int value = TRI ? (BATCH ? MCL_TRI_BATCH_MIN_BLOCKS : MCL_TRI_MIN_BLOCKS)
+                               : U == 8 ? MCL_U8_MIN_BLOCKS
                                : KIND == kKindBrickGrid
                                    ? (BATCH ? MCL_BATCH_MIN_BLOCKS_GRID : MCL_SENSOR_MIN_BLOCKS_GRID)
                                    : MCL_SENSOR_MIN_BLOCKS;
