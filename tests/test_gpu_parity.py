@@ -55,11 +55,13 @@ def dev(torch, a, dtype=None):
 
 def check_logw(Lg, Lo, tol=TOL):
     Lg = np.asarray(Lg, np.float64)
-    err = np.abs(Lg - Lo) / np.maximum(1.0, np.abs(Lo))
+    Lo = np.asarray(Lo, np.float64)
     assert np.all(np.isfinite(Lg) == np.isfinite(Lo))
     fin = np.isfinite(Lo)
-    assert err[fin].max(initial=0) <= tol, f"max rel log-weight error {err[fin].max():.3g}"
-    return err[fin].max(initial=0)
+    assert np.array_equal(Lg[~fin], Lo[~fin])  # the same infinities (SUM with nothing stored: -inf)
+    err = np.abs(Lg[fin] - Lo[fin]) / np.maximum(1.0, np.abs(Lo[fin]))
+    assert err.max(initial=0) <= tol, f"max rel log-weight error {err.max(initial=0):.3g}"
+    return err.max(initial=0)
 
 
 def check_w(wg, Lo, mode, tol=TOL):
