@@ -58,7 +58,7 @@ def check_logw(Lg, Lo, tol=TOL):
     Lo = np.asarray(Lo, np.float64)
     assert np.all(np.isfinite(Lg) == np.isfinite(Lo))
     fin = np.isfinite(Lo)
-    assert np.array_equal(Lg[~fin], Lo[~fin])  # the same infinities (SUM with nothing stored: -inf)
+    assert np.array_equal(Lg[~fin], Lo[~fin], equal_nan=True)  # the same infinities (SUM, nothing stored: -inf)
     err = np.abs(Lg[fin] - Lo[fin]) / np.maximum(1.0, np.abs(Lo[fin]))
     assert err.max(initial=0) <= tol, f"max rel log-weight error {err.max(initial=0):.3g}"
     return err.max(initial=0)
