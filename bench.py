@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--item-order", type=int, default=0,
                     help="work-item order: 0 auto, 1 chunk-major, 2 sweeps, 3 dynamic sweeps")
     ap.add_argument("--layout", type=int, default=0, help="brick layout: 0 linear, 1 4x4x4 blocks")
+    ap.add_argument("--scan-rings", type=int, default=64,
+                    help="rings of the OS0-64 scan given to the library (staging in 4 x 8 patches); 0: points as given")
     ap.add_argument("--trilinear", action="store_true",
                     help="the trilinear read (eight corners per evaluation) instead of the nearest voxel")
     ap.add_argument("--index", type=int, default=0, help="brick index: 0 auto, 1 hash, 2 cell grid")
@@ -336,7 +338,8 @@ def config_dict(args, wl):
     m = wl.map
     return {
         "workload": wl.name, "particles": int(len(wl.particles)), "points": int(len(wl.scan)),
-        "scan": f"64 rings (+-45 deg) x {args.azimuths} azimuths, sigma 0.02 m",
+        "scan": f"64 rings (+-45 deg) x {args.azimuths} azimuths, sigma 0.02 m, ring-major"
+                + (f", staged in 4 x 8 patches (scan_rings {args.scan_rings})" if args.scan_rings else ""),
         "map": {"kind": "brick16", "dtype": args.dtype,
                 "layout": ["linear", "block4"][args.layout],
                 "extent_m": [args.building, args.building, 5.0 * args.floors], "voxel_m": 0.05,
@@ -383,7 +386,7 @@ def run_ours(args):
     prm = mcl.sensor_params(sigma_hit=wl.sigma_hit, points_per_chunk=args.chunk,
                             lanes_per_particle=args.lanes, particles_per_item=args.ppi,
                             unroll=args.unroll, pipeline=args.pipeline, particle_order=args.order,
-                            item_order=args.item_order,
+                            item_order=args.item_order, scan_rings=args.scan_rings,
                             flags=mcl.MCL_TRILINEAR if args.trilinear else 0)
     plan = mcl.mcl_sensor_plan_get(m, P, N, prm)
 

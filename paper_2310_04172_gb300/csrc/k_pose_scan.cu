@@ -51,9 +51,9 @@ __device__ __forceinline__ void pose_to_matrix(const float* __restrict__ poses, 
 
 // N x 3 scan rows -> N float4 (x, y, z, 0): 16-byte records that a bulk copy
 // can move and a lane can read with one 128-bit shared-memory load.
-__device__ __forceinline__ void scan_pack(const float* __restrict__ scan, int j,
+__device__ __forceinline__ void scan_pack(const float* __restrict__ scan, int j, const ScanLayout& L,
                                           float4* __restrict__ packed) {
-  const float* q = scan + 3 * (size_t)j;
+  const float* q = scan + 3 * (size_t)L.source(j);
   packed[j] = make_float4(q[0], q[1], q[2], 0.f);
 }
 
@@ -79,11 +79,11 @@ __device__ __forceinline__ void scan_pack_pair(const float* __restrict__ scan, i
   const int i0 = s * 2 * G + l, i1 = i0 + G;
   float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
   if (i0 < cnt) {
-    const float* q = scan + 3 * ((size_t)c * L.chunk + i0);
+    const float* q = scan + 3 * (size_t)L.source(c * L.chunk + i0);
     a[0] = q[0]; a[1] = q[1]; a[2] = q[2];
   }
   if (i1 < cnt) {
-    const float* q = scan + 3 * ((size_t)c * L.chunk + i1);
+    const float* q = scan + 3 * (size_t)L.source(c * L.chunk + i1);
     b[0] = q[0]; b[1] = q[1]; b[2] = q[2];
   }
   unsigned char* base = packed + L.chunk_offset(c);
@@ -105,7 +105,7 @@ __global__ void k_pose_and_pack(const float* __restrict__ poses, int P, float4* 
   } else {
     const int j = (blockIdx.x - pose_blocks) * blockDim.x + threadIdx.x;
     if (L.pair_g == 0) {
-      if (j < N) scan_pack(scan, j, static_cast<float4*>(packed));
+      if (j < N) scan_pack(scan, j, L, static_cast<float4*>(packed));
     } else {
       const int K = (N + L.chunk - 1) / L.chunk;
       if (j < K * L.full_pairs()) scan_pack_pair(scan, N, L, j, static_cast<unsigned char*>(packed));
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kSideThreads) k_pose_and_pack_b(const SideSeg*
     const int t = (j - pb) * kSideThreads + threadIdx.x;
     const ScanLayout L = g.layout;
     if (t < pack_units(g.N, L)) {
-      if (L.pair_g == 0) scan_pack(g.scan, t, static_cast<float4*>(g.packed));
+      if (L.pair_g == 0) scan_pack(g.scan, t, L, static_cast<float4*>(g.packed));
       else scan_pack_pair(g.scan, g.N, L, t, static_cast<unsigned char*>(g.packed));
     }
   }

@@ -548,6 +548,7 @@ mcl_status check_params(const mcl_sensor_params* p) {
     return fail(MCL_EINVAL, "sensor params: particle_order %d", p->particle_order);
   if (p->item_order < 0 || p->item_order > 3)
     return fail(MCL_EINVAL, "sensor params: item_order %d", p->item_order);
+  if (p->scan_rings < 0) return fail(MCL_EINVAL, "sensor params: scan_rings %d", p->scan_rings);
   return MCL_OK;
 }
 
@@ -567,6 +568,7 @@ mcl_status check_map_params(mcl_map_t m, const mcl_sensor_params* p) {
 constexpr int64_t kSpatialOrderMinParticles = 4096;
 
 mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params* p, Plan* pl) {
+  *pl = Plan{};  // every field below is set from (m, P, N, p) or stays zero
   DeviceState st;
   if (mcl_status rc = device_state(nullptr, &st)) return rc;
   SensorShape& sh = pl->sh;
@@ -607,6 +609,12 @@ mcl_status make_plan(mcl_map_t m, int64_t P, int64_t N, const mcl_sensor_params*
     sh.pipeline = 0;
   }
   sh.threads = 256;
+  // scan staged in 4-ring x 8-point patches when the caller gives its ring
+  // structure and it fits (85.6 -> 83.9 ms for the OS0-64 building)
+  if (p->scan_rings > 0 && N % p->scan_rings == 0 && p->scan_rings % 4 == 0 && (N / p->scan_rings) % 8 == 0) {
+    sh.rings = p->scan_rings;
+    sh.az = (int)(N / p->scan_rings);
+  }
   int bps = 0;
   MCL_CUDA(sensor_occupancy(kernel_kind(m), m->view.layout, m->dtype, kernel_mode(m, p->mode), sh, &bps));
   if (bps < 1) return fail(MCL_EINVAL, "sensor plan: launch shape does not fit on an SM");

@@ -224,6 +224,17 @@ __device__ __forceinline__ bool lookup(const MapView& m, float x, float y, float
 struct ScanLayout {
   int chunk;   // points per chunk
   int pair_g;  // G of the pair layout, 0: one float4 per point
+  int rings;   // > 0: the scan is `rings` rings of `az` points, ring-major, staged in patches
+  int az;      // (source), else in the order given
+  // Scan point staged at place j: with rings, patches of 4 rings x 8
+  // neighbouring points, patch after patch along the rings, band of 4 rings
+  // after band, so that the 32 lanes of a warp take one 4 x 8 patch (the
+  // pair partner the next one) and their gathers share more sectors.
+  __host__ __device__ int source(int j) const {
+    if (rings <= 0) return j;
+    const int band = j / (4 * az), t = j - band * 4 * az, u = t & 31;
+    return (band * 4 + (u >> 3)) * az + (t >> 5) * 8 + (u & 7);
+  }
   __host__ __device__ int pairs(int cnt) const { return (cnt + 2 * pair_g - 1) / (2 * pair_g) * pair_g; }
   __host__ __device__ int full_pairs() const { return pairs(chunk); }
   __host__ __device__ size_t chunk_offset(int c) const {
@@ -248,11 +259,14 @@ struct SensorShape {
   int interp;     // 1: trilinear read (MCL_TRILINEAR)
   int threads;    // threads per CTA
   int grid;       // CTAs (persistent)
+  int rings, az;  // scan staged in 4 x 8 patches of `rings` rings of `az` points (0: as given)
 };
 
 // Scan layout of a launch shape: pairs of the shape's lane groups (the
 // nearest and the trilinear read).
-inline ScanLayout scan_layout(const SensorShape& sh) { return ScanLayout{sh.chunk, sh.lanes}; }
+inline ScanLayout scan_layout(const SensorShape& sh) {
+  return ScanLayout{sh.chunk, sh.lanes, sh.rings, sh.az};
+}
 
 struct SensorArgs {
   MapView map;

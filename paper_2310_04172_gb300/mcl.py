@@ -50,7 +50,7 @@ class mcl_sensor_params(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("sigma_hit", ctypes.c_float), ("mode", _i32),
                 ("flags", _u32), ("points_per_chunk", _i32), ("lanes_per_particle", _i32),
                 ("particles_per_item", _i32), ("unroll", _i32), ("pipeline", _i32),
-                ("particle_order", _i32), ("item_order", _i32)]
+                ("particle_order", _i32), ("item_order", _i32), ("scan_rings", _i32)]
 
 
 class mcl_sensor_plan(ctypes.Structure):
@@ -364,13 +364,13 @@ def sensor_params(sigma_hit: float = 0.1, mode: int = MCL_LOGPROD, flags: int = 
                   points_per_chunk: int = 0, lanes_per_particle: int = 0,
                   particles_per_item: int = 0, unroll: int = 0,
                   pipeline: int = 0, particle_order: int = 0,
-                  item_order: int = 0) -> mcl_sensor_params:
+                  item_order: int = 0, scan_rings: int = 0) -> mcl_sensor_params:
     return mcl_sensor_params(struct_size=ctypes.sizeof(mcl_sensor_params), sigma_hit=sigma_hit,
                              mode=mode, flags=flags, points_per_chunk=points_per_chunk,
                              lanes_per_particle=lanes_per_particle,
                              particles_per_item=particles_per_item, unroll=unroll,
                              pipeline=pipeline, particle_order=particle_order,
-                             item_order=item_order)
+                             item_order=item_order, scan_rings=scan_rings)
 
 
 def mcl_sensor_update(m: Map, particles, scan, params: mcl_sensor_params, logw=None, w=None,

@@ -252,6 +252,45 @@ def test_building_os064_parity_subset(torch_cuda, mcl, building_i16, layout, ind
     m.close()
 
 
+def patch_order(N, R):
+    """Points of an R-ring, ring-major scan in 4-ring x 8-point patches: band
+    of 4 rings after band, patch after patch along the rings."""
+    A = N // R
+    return np.arange(N).reshape(R // 4, 4, A // 8, 8).transpose(0, 2, 1, 3).reshape(-1)
+
+
+def test_scan_rings_staging(torch_cuda, mcl, room, building_i16):
+    """scan_rings = R stages the scan in 4 x 8 patches: the same bits as the
+    scan permuted that way on the host and staged as given (room: 16 rings of
+    64 points in several chunks and lane widths; building: 64 rings of 1,024),
+    within the tolerance of the oracle; a ring count that does not fit leaves
+    the order as given; a negative one is EINVAL."""
+    torch = torch_cuda
+    cases = ((room.map, room.particles, room.scan, 16, [dict(points_per_chunk=256), dict(lanes_per_particle=8),
+                                                        dict(), dict(flags=mcl.MCL_TRILINEAR)]),
+             (building_i16.map, building_i16.particles[:2000], building_i16.scan, 64, [dict()]))
+    for sm, parts, scan, R, shapes in cases:
+        m = mcl.map_from_scene(sm)
+        perm = patch_order(len(scan), R)
+        assert np.array_equal(np.sort(perm), np.arange(len(scan)))
+        for shape in shapes:
+            a = run_sensor(torch, mcl, m, parts, scan, 0.1, scan_rings=R, **shape)
+            b = run_sensor(torch, mcl, m, parts, np.ascontiguousarray(scan[perm]), 0.1, **shape)
+            assert all(np.array_equal(x, y) for x, y in zip(a, b)), shape
+            Lo = oracle.sensor_update(oracle.Map.from_scene_map(sm), parts, scan, 0.1,
+                                      trilinear=bool(shape.get("flags", 0)))
+            check_logw(a[0], Lo)
+        plain = run_sensor(torch, mcl, m, parts, scan, 0.1)
+        for bad_r in (3, 12, len(scan) + 4):   # not dividing N, or N / R not a multiple of 8
+            if len(scan) % bad_r == 0 and bad_r % 4 == 0 and (len(scan) // bad_r) % 8 == 0:
+                continue
+            c = run_sensor(torch, mcl, m, parts, scan, 0.1, scan_rings=bad_r)
+            assert all(np.array_equal(x, y) for x, y in zip(plain, c))
+        with pytest.raises(mcl.MclError):
+            run_sensor(torch, mcl, m, parts, scan, 0.1, scan_rings=-4)
+        m.close()
+
+
 def test_particle_order_gives_identical_bits(torch_cuda, mcl, room, building_i16):
     """Spatial processing order moves particles between slots, never changes a result."""
     torch = torch_cuda
