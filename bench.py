@@ -489,7 +489,7 @@ def run_ours(args):
     serving = None
     if rank == 0 and not args.no_serving:
         try:
-            serving = serving_block(mcl, args.serving_seconds)
+            serving = serving_block(mcl, args.serving_seconds, rings=args.scan_rings > 0)
         except Exception as e:
             serving = {"error": f"{type(e).__name__}: {e}"}
 
@@ -638,11 +638,11 @@ def serving_sessions(mcl, srv, maps, n, p_lo, p_hi, seed):
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
-        m, sc, scan = maps[k % len(maps)]
+        m, sc, scan, rings = maps[k % len(maps)]
         P = int(round(math.exp(rng.uniform(math.log(p_lo), math.log(p_hi)))))
         parts = scenes.particles_free(sc, P, 0.1, 10.0, seed * 1000 + k)
         sess = srv.open(m, parts, len(scan), seed=seed * 1000 + k,
-                        motion_sigma=(0.02, 0.02, 0.01, 0.002, 0.002, 0.01))
+                        motion_sigma=(0.02, 0.02, 0.01, 0.002, 0.002, 0.01), scan_rings=rings)
         out.append((sess, scan, float(rng.uniform(10.0, 20.0))))
     return out
 
@@ -699,20 +699,22 @@ def vlp16_block(torch, mcl, reps: int):
             "plain_f16_map": {"ms_per_step": ms_f16, "evals_per_s": ev / (ms_f16 / 1e3)}}
 
 
-def serving_block(mcl, seconds: float, max_batch: int = 0):
+def serving_block(mcl, seconds: float, max_batch: int = 0, rings: bool = True):
     """The 64-session serving workload: 64 robot sessions over 8 maps (4 dense
     512x512x128 FP16 halls, 4 brick int16 160x160x20 m buildings), P
-    log-uniform in [1e3, 1e6], scans of 28,800 (halls) and 65,536 (buildings)
-    points, Poisson 10-20 Hz per session: first at the nominal rates (offered
-    load far above one GPU: the latest scan of a session wins), then scaled to
-    70 % of the achieved throughput. `seconds` of arrivals per load level."""
+    log-uniform in [1e3, 1e6], scans of 28,800 (halls, 16 rings) and 65,536
+    (buildings, 64 rings) points, each session given its scan's ring count
+    when `rings` (staging in 4 x 8 patches), Poisson 10-20 Hz per session:
+    first at the nominal rates (offered load far above one GPU: the latest
+    scan of a session wins), then scaled to 70 % of the achieved throughput.
+    `seconds` of arrivals per load level."""
     import scenes
     maps = []
     for k in range(4):
         hall = scenes.vlp16_multiroom(P=16, dtype=scenes.F16, seed=11 + k)
-        maps.append((mcl.map_from_scene(hall.map), hall.scene, hall.scan))
+        maps.append((mcl.map_from_scene(hall.map), hall.scene, hall.scan, 16 if rings else 0))
         bld = scenes.os064_building(P=16, dtype=scenes.I16, seed=15 + k)
-        maps.append((mcl.map_from_scene(bld.map), bld.scene, bld.scan))
+        maps.append((mcl.map_from_scene(bld.map), bld.scene, bld.scan, 64 if rings else 0))
     max_batch = max_batch or SERVING_MAX_BATCH
     srv = mcl.Server(200 << 30, 64, max_in_flight=2, max_batch=max_batch)
     sess = serving_sessions(mcl, srv, maps, 64, 1e3, 1e6, 31)
@@ -722,12 +724,13 @@ def serving_block(mcl, seconds: float, max_batch: int = 0):
     out = {"sessions": len(sess), "maps": len(maps),
            "workload": "64 sessions over 4 dense FP16 halls + 4 int16 brick buildings",
            "policy": f"max_in_flight 2, max_batch {max_batch}, longest-waiting sessions first",
+           "scan_staging": "4 x 8 patches (scan_rings 16 / 64)" if rings else "as given",
            "particles_total": int(sum(x.P for x, _, _ in sess)),
            "nominal_load": nominal, "scaled_load_70pct": dict(scaled, rate_scale=scale)}
     for x, _, _ in sess:
         x.close()
     srv.close()
-    for mm, _, _ in maps:
+    for mm, _, _, _ in maps:
         mm.close()
     return out
 
@@ -769,8 +772,9 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     global-localisation cloud, and a tracking cloud Gaussian about the true
     pose (0.2 m, 2 deg), where more particles carry weight. Then the same
     1M x 65,536 update on the FP32 map, in the same kernel shape and in the
-    plain per-session form (particles as given, chunk-major items), and the
-    int16 map in a graph-captured batch of four 250,000-particle sessions."""
+    plain per-session form (particles as given, chunk-major items, points as
+    given), and the int16 map in a graph-captured batch of four
+    250,000-particle sessions, each given the scan's ring count."""
     import numpy as np
     import oracle
     import scenes
@@ -829,7 +833,8 @@ def precision_block(torch, mcl, wl, m_head, parts, scan, prm, head_kernel_ms, ar
     outs = [(torch.empty(per, device=parts.device), torch.empty(per, device=parts.device))
             for _ in range(S)]
     batch = mcl.Batch([{"map": m_head, "particles": sess_parts[k], "scan": scan,
-                        "logw": outs[k][0], "w": outs[k][1]} for k in range(S)], use_graph=True)
+                        "logw": outs[k][0], "w": outs[k][1], "scan_rings": args.scan_rings}
+                       for k in range(S)], use_graph=True)
     ms_batch = timed(batch.run)
     kernels = batch.info()["kernels_per_run"]
     batch.close()
@@ -874,7 +879,7 @@ def run_serving(args):
     __graft_entry__.build()
     from paper_2310_04172_gb300 import mcl
     torch.cuda.set_device(0)
-    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch)
+    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch, rings=args.scan_rings > 0)
     line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
             "value": out["scaled_load_70pct"]["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32",

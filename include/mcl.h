@@ -241,7 +241,7 @@ typedef struct mcl_sensor_params {
                                  the scan is R rings of N / R points each, ring after ring;
                                  the library stages it in patches of 4 rings x 8 neighbouring
                                  points, so that the 32 lanes of a warp take one 4 x 8 patch
-                                 and their gathers share more memory sectors (85.6 -> 83.9
+                                 and their gathers share more memory sectors (86.0 -> 84.1
                                  ms for 1M particles x 64 rings x 1,024 points). Applied when
                                  R divides N, R is a multiple of 4 and N / R of 8, else the
                                  order given. Sets the order points are summed in, like
@@ -451,11 +451,14 @@ typedef struct mcl_session_update {
   float* particles_out;    /* P x 6, NULL: indices only (must not alias particles) */
   mcl_estimate* estimate;  /* NULL, or the pose estimate of the weighted particles (before
                               resampling), as mcl_sensor_update_estimate; needs w */
+  int32_t scan_rings;      /* rings of this session's scan, as mcl_sensor_params.scan_rings
+                              (0: staged in the order given); < 0 is EINVAL */
 } mcl_session_update;
 
 /* Shape of a batched step. points_per_chunk and lanes_per_particle fix the
  * summation order as in mcl_sensor_params: every session's results equal
- * those of mcl_sensor_update with the same two values. use_graph = 1
+ * those of mcl_sensor_update with the same two values (and the session's
+ * scan_rings). use_graph = 1
  * captures the whole step into a CUDA graph at the first run and replays it
  * afterwards (the plan owns all scratch, so the graph stays valid). */
 typedef struct mcl_batch_params {
@@ -630,6 +633,8 @@ typedef struct mcl_session_desc {
   int64_t first_step;       /* step counter to start from: 0, or the step of a checkpoint
                                (particles from mcl_session_read, step from
                                mcl_session_get_info) to resume the same sequence */
+  int32_t scan_rings;       /* rings of the session's scans, as mcl_sensor_params.scan_rings,
+                               applied to each submitted scan by its own N; < 0 is EINVAL */
 } mcl_session_desc;
 
 mcl_status mcl_session_open(mcl_server_t s, const mcl_session_desc* desc, mcl_session_t* out);

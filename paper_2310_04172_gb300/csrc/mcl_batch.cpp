@@ -190,7 +190,8 @@ mcl_status mcl_batch_create(const mcl_session_update* sessions, int32_t n,
     sp.u = u;
     sp.prm = mcl_sensor_params{sizeof(mcl_sensor_params), u.sigma_hit, u.mode, u.flags,
                                bp->points_per_chunk, bp->lanes_per_particle, bp->particles_per_item,
-                               bp->unroll, bp->pipeline, bp->particle_order, bp->item_order};
+                               bp->unroll, bp->pipeline, bp->particle_order, bp->item_order,
+                               u.scan_rings};
     if (mcl_status rc = check_params(&sp.prm)) return bail(rc);
     if (mcl_status rc = make_plan(u.map, u.P, u.N, &sp.prm, &sp.pl)) return bail(rc);
     const int nt = resample_tiles((int)u.P);

@@ -72,6 +72,7 @@ struct mcl_session_s {
   float sigma = 0.1f;
   int mode = 0;
   uint32_t flags = 0;
+  int scan_rings = 0;
   float msig[6] = {0, 0, 0, 0, 0, 0};
   uint64_t seed = 0;
   int64_t step = 0;
@@ -220,7 +221,9 @@ mcl_status enqueue_step(mcl_server_s* S, Slot* sl, const std::vector<int64_t>& N
     q.mats = (float4*)(ws + pl.off_mats);
     q.frame = sensor_frame(ss->map->view, pl.sh.interp != 0);
     q.packed = ws + pl.off_scan;
-    q.layout = scan_layout(pl.sh);
+    q.layout = scan_layout(pl.sh);  // staging order by this scan's own N
+    q.layout.rings = patch_rings(Ns[i], ss->scan_rings);
+    q.layout.az = q.layout.rings ? (int)(Ns[i] / q.layout.rings) : 0;
     q.partial = (const float*)(ws + pl.off_partial);
     q.K = (int)((Ns[i] + pl.sh.chunk - 1) / pl.sh.chunk);
     q.mode = ss->mode;
@@ -492,7 +495,7 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   mcl_sensor_params prm{sizeof(mcl_sensor_params), d->sigma_hit, d->mode, d->flags,
                         S->desc.shape.points_per_chunk, S->desc.shape.lanes_per_particle,
                         S->desc.shape.particles_per_item, S->desc.shape.unroll, S->desc.shape.pipeline,
-                        S->desc.shape.particle_order, S->desc.shape.item_order};
+                        S->desc.shape.particle_order, S->desc.shape.item_order, d->scan_rings};
   if (mcl_status rc = check_params(&prm)) return rc;
   int dev = 0;
   MCL_CUDA(cudaGetDevice(&dev));
@@ -505,6 +508,7 @@ mcl_status mcl_session_open(mcl_server_t S, const mcl_session_desc* d, mcl_sessi
   ss->sigma = d->sigma_hit;
   ss->mode = d->mode;
   ss->flags = d->flags;
+  ss->scan_rings = d->scan_rings;
   std::copy(d->motion_sigma, d->motion_sigma + 6, ss->msig);
   ss->seed = d->seed;
   ss->step = d->first_step;

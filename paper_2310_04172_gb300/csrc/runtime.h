@@ -156,6 +156,16 @@ long long item_segments(const std::vector<SegSession>& s, long long slots, bool 
 constexpr int kBatchMaxRounds = 1024;   // batches (tables built once)
 constexpr int kServerMaxRounds = 256;   // serving steps (tables in a fixed slot buffer)
 
+// Ring count of the 4-ring x 8-point patch staging (SensorShape::rings)
+// for a scan of N points that the caller says holds `rings` rings, ring
+// after ring: `rings` when it divides N, is a multiple of 4 and N / rings
+// one of 8, else 0 (the points staged in the order given). The rule
+// make_plan applies to the scan size it plans for; a serving step applies it
+// to each submitted scan's own size.
+inline int patch_rings(int64_t N, int rings) {
+  return rings > 0 && N % rings == 0 && rings % 4 == 0 && (N / rings) % 8 == 0 ? rings : 0;
+}
+
 // SUM mode: the kernel forms each point's p_hit without its constant as
 // 2^(v^2 cs) with the hardware base-2 exponential, v the stored value in
 // storage units: cs = -log2(e) / (2 sigma^2), times scale^2 for int16

@@ -79,7 +79,7 @@ class mcl_session_update(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("particles", _c_void_p), ("P", _i64),
                 ("scan", _c_void_p), ("N", _i64), ("sigma_hit", ctypes.c_float), ("mode", _i32),
                 ("flags", _u32), ("logw", _c_void_p), ("w", _c_void_p), ("resample_idx", _c_void_p),
-                ("particles_out", _c_void_p), ("estimate", _c_void_p)]
+                ("particles_out", _c_void_p), ("estimate", _c_void_p), ("scan_rings", _i32)]
 
 
 class mcl_batch_params(ctypes.Structure):
@@ -103,7 +103,7 @@ class mcl_session_desc(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("map", _c_void_p), ("P", _i64), ("max_N", _i64),
                 ("particles", _c_void_p), ("sigma_hit", ctypes.c_float), ("mode", _i32),
                 ("flags", _u32), ("motion_sigma", ctypes.c_float * 6), ("seed", _u64),
-                ("first_step", _i64)]
+                ("first_step", _i64), ("scan_rings", _i32)]
 
 
 class mcl_session_info(ctypes.Structure):
@@ -520,7 +520,7 @@ class Batch:
     """Owning handle of a batched step plan (mcl_batch_t). `sessions` is a list of
     dicts with keys map, particles, scan, logw, w, and optionally sigma_hit,
     mode, flags, resample_idx, particles_out, estimate (a buffer from
-    estimate_buffer()); the CUDA tensors stay referenced."""
+    estimate_buffer()), scan_rings; the CUDA tensors stay referenced."""
 
     def __init__(self, sessions, points_per_chunk=0, lanes_per_particle=0, particles_per_item=0,
                  unroll=0, pipeline=0, particle_order=0, use_graph=False, item_order=0):
@@ -543,6 +543,7 @@ class Batch:
             u.resample_idx = _dev_ptr(s.get("resample_idx"), torch.int32, None, "resample_idx")
             u.particles_out = _dev_ptr(s.get("particles_out"), torch.float32, 6, "particles_out")
             u.estimate = _est_ptr(s.get("estimate"))
+            u.scan_rings = int(s.get("scan_rings", 0))
             self._keep.append(s)
         bp = mcl_batch_params(struct_size=ctypes.sizeof(mcl_batch_params),
                               points_per_chunk=points_per_chunk, lanes_per_particle=lanes_per_particle,
@@ -718,12 +719,12 @@ class Server:
 
     def open(self, m: Map, particles: np.ndarray, max_N: int, sigma_hit: float = 0.1,
              mode: int = MCL_LOGPROD, flags: int = 0, motion_sigma=(0,) * 6, seed: int = 0,
-             first_step: int = 0):
+             first_step: int = 0, scan_rings: int = 0):
         parts = np.ascontiguousarray(particles, np.float32).reshape(-1, 6)
         d = mcl_session_desc(struct_size=ctypes.sizeof(mcl_session_desc), map=m.handle, P=len(parts),
                              max_N=int(max_N), particles=parts.ctypes.data_as(ctypes.c_void_p),
                              sigma_hit=sigma_hit, mode=mode, flags=flags, seed=int(seed),
-                             first_step=int(first_step))
+                             first_step=int(first_step), scan_rings=int(scan_rings))
         d.motion_sigma[:] = [float(x) for x in motion_sigma]
         h = ctypes.c_void_p()
         _check(lib().mcl_session_open(self.handle, ctypes.byref(d), ctypes.byref(h)))

@@ -2,7 +2,8 @@
 share geometry, over (session, chunk, particle block) items of uneven size;
 one launch per side step for all sessions): every session's log-weights,
 weights and resampled indices (and pose estimates) are identical, bit for bit,
-to the single-session calls with the same chunk and lane split — alone or in
+to the single-session calls with the same chunk and lane split and the same
+ring count of the scan (staged in 4 x 8 patches, or as given) — alone or in
 the mix, plain or replayed from a CUDA graph — and the launches of a step do
 not grow with the number of sessions."""
 import numpy as np
@@ -38,19 +39,22 @@ def make_sessions(torch, room, hall, bld, maps, rng):
     def t(a):
         return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
+    # scan rings: 16 for the VLP-16 scans, 64 for OS0-64, 0 for points as
+    # given; 777 points of 16 rings do not fit the patches (staged as given)
     specs = [
-        ("room", room.particles, room.scan, 0, True),
-        ("room_i16", room.particles[:700], room.scan, 0, False),
-        ("hall", hall.particles, hall.scan, 0, True),
-        ("bld", bld.particles, bld.scan, 0, True),
-        ("room", room.particles[::-1].copy(), room.scan[:777], 0, False),   # same map, ragged N
-        ("room", room.particles[:333], room.scan, 1, True),                 # SUM mode: own group
+        ("room", room.particles, room.scan, 0, True, 16),
+        ("room_i16", room.particles[:700], room.scan, 0, False, 0),
+        ("hall", hall.particles, hall.scan, 0, True, 16),
+        ("bld", bld.particles, bld.scan, 0, True, 64),
+        ("room", room.particles[::-1].copy(), room.scan[:777], 0, False, 16),   # same map, ragged N
+        ("room", room.particles[:333], room.scan, 1, True, 0),                  # SUM mode: own group
     ]
     sessions = []
-    for name, parts, scan, mode, res in specs:
+    for name, parts, scan, mode, res, rings in specs:
         P = len(parts)
         s = {"map": maps[name], "particles": t(parts), "scan": t(scan), "sigma_hit": 0.1,
-             "mode": mode, "logw": torch.empty(P, device="cuda"), "w": torch.empty(P, device="cuda")}
+             "mode": mode, "logw": torch.empty(P, device="cuda"), "w": torch.empty(P, device="cuda"),
+             "scan_rings": rings}
         if res:
             s["resample_idx"] = torch.empty(P, dtype=torch.int32, device="cuda")
             s["particles_out"] = torch.empty((P, 6), device="cuda")
@@ -62,7 +66,7 @@ def single(torch, mcl, s, r, chunk, lanes):
     P = s["particles"].shape[0]
     logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
     prm = mcl.sensor_params(s["sigma_hit"], mode=s["mode"], points_per_chunk=chunk,
-                            lanes_per_particle=lanes)
+                            lanes_per_particle=lanes, scan_rings=s.get("scan_rings", 0))
     if "estimate" in s:
         est = mcl.estimate_buffer()
         mcl.mcl_sensor_update_estimate(s["map"], s["particles"], s["scan"], prm, logw, w, est)
@@ -123,7 +127,8 @@ def test_batch_shares_launches_across_maps(env):
     """Sessions on two different building maps of one geometry (different
     seeds) form one group: one sensor launch reads each session's own map.
     The step's launches are the same for 1, 2, 4 and 8 sessions, and every
-    session equals its single call bit for bit."""
+    session equals its single call bit for bit, whether its scan is staged in
+    4 x 8 patches or as given (both in one group)."""
     torch, mcl, room, hall, bld, maps = env
     b1 = scenes.os064_building(P=3000, dtype=scenes.I16, seed=21, size=80.0, floors=2)
     b2 = scenes.os064_building(P=3000, dtype=scenes.I16, seed=22, size=80.0, floors=2)
@@ -140,7 +145,8 @@ def test_batch_shares_launches_across_maps(env):
                  "sigma_hit": 0.1, "mode": 0, "logw": torch.empty(P, device="cuda"),
                  "w": torch.empty(P, device="cuda"),
                  "resample_idx": torch.empty(P, dtype=torch.int32, device="cuda"),
-                 "particles_out": torch.empty((P, 6), device="cuda")}
+                 "particles_out": torch.empty((P, 6), device="cuda"),
+                 "scan_rings": 64 if k % 4 < 2 else 0}
             if k % 3 == 0:
                 s["estimate"] = mcl.estimate_buffer()
             sessions.append(s)
@@ -188,6 +194,8 @@ def test_batch_rejects_bad_sessions(env):
         mcl.Batch([{"map": maps["room"], "particles": parts, "scan": scan}])
     with pytest.raises(mcl.MclError):
         mcl.Batch([dict(ok, sigma_hit=-1.0)])
+    with pytest.raises(mcl.MclError):
+        mcl.Batch([dict(ok, scan_rings=-4)])
     b = mcl.Batch([ok])
     with pytest.raises(mcl.MclError):
         b.set_offsets([1.0])

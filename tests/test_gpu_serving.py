@@ -245,3 +245,39 @@ def test_score_map_and_trilinear_sessions_match_single_calls(env):
         s.close()
     srv.close()
     sc.close()
+
+
+def test_scan_rings_by_each_scans_own_size(env):
+    """A session opened with the scan's ring count stages each submitted scan
+    in 4 x 8 patches by that scan's own size (1,024 points of 16 rings, 512 of
+    16 rings of 32, and 900, which does not fit and is staged as given): each
+    step's weights equal the single call's with the same ring count, bit for
+    bit, and the 1,024-point step differs from the points-as-given session."""
+    import torch
+    mcl, room, hall, bld, maps = env
+    parts = torch.from_numpy(room.particles).cuda()
+    cases = (room.scan, np.ascontiguousarray(room.scan[:512]), np.ascontiguousarray(room.scan[:900]))
+    singles = []
+    for scan in cases:
+        w = torch.empty(1000, device="cuda")
+        mcl.mcl_sensor_update(maps["room"], parts, torch.from_numpy(scan).cuda(),
+                              mcl.sensor_params(0.1, scan_rings=16), None, w)
+        singles.append(w.cpu().numpy())
+    srv = mcl.Server(8 << 30, 8)
+    srv.pause(True)
+    sessions = [srv.open(maps["room"], room.particles, 2048, seed=10 + k, scan_rings=16) for k in range(3)]
+    given = srv.open(maps["room"], room.particles, 2048, seed=20)
+    tickets = [s.submit(sc) for s, sc in zip(sessions, cases)] + [given.submit(room.scan)]
+    srv.pause(False)
+    for t in tickets:
+        assert srv.wait(t, 30_000)["status"] == mcl.MCL_RESULT_DONE
+    for s, ref in zip(sessions, singles):
+        _, w = s.read()
+        assert np.array_equal(w, ref)
+    _, w_given = given.read()
+    assert not np.array_equal(w_given, singles[0])
+    for s in sessions + [given]:
+        s.close()
+    with pytest.raises(mcl.MclError):
+        srv.open(maps["room"], room.particles, 2048, scan_rings=-16)
+    srv.close()
