@@ -489,7 +489,7 @@ def run_ours(args):
     serving = None
     if rank == 0 and not args.no_serving:
         try:
-            serving = serving_block(mcl, args.serving_seconds, rings=args.scan_rings > 0)
+            serving = serving_block(mcl, args.serving_seconds)
         except Exception as e:
             serving = {"error": f"{type(e).__name__}: {e}"}
 
@@ -699,12 +699,14 @@ def vlp16_block(torch, mcl, reps: int):
             "plain_f16_map": {"ms_per_step": ms_f16, "evals_per_s": ev / (ms_f16 / 1e3)}}
 
 
-def serving_block(mcl, seconds: float, max_batch: int = 0, rings: bool = True):
+def serving_block(mcl, seconds: float, max_batch: int = 0, rings: bool = False):
     """The 64-session serving workload: 64 robot sessions over 8 maps (4 dense
     512x512x128 FP16 halls, 4 brick int16 160x160x20 m buildings), P
     log-uniform in [1e3, 1e6], scans of 28,800 (halls, 16 rings) and 65,536
-    (buildings, 64 rings) points, each session given its scan's ring count
-    when `rings` (staging in 4 x 8 patches), Poisson 10-20 Hz per session:
+    (buildings, 64 rings) points, staged as given (`rings`: each session
+    given its scan's ring count, staging in 4 x 8 patches, which costs more
+    than it saves once a session's particles have converged), Poisson
+    10-20 Hz per session:
     first at the nominal rates (offered load far above one GPU: the latest
     scan of a session wins), then scaled to 70 % of the achieved throughput.
     `seconds` of arrivals per load level."""
@@ -879,7 +881,7 @@ def run_serving(args):
     __graft_entry__.build()
     from paper_2310_04172_gb300 import mcl
     torch.cuda.set_device(0)
-    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch, rings=args.scan_rings > 0)
+    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch)
     line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
             "value": out["scaled_load_70pct"]["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32",

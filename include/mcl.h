@@ -241,11 +241,16 @@ typedef struct mcl_sensor_params {
                                  the scan is R rings of N / R points each, ring after ring;
                                  the library stages it in patches of 4 rings x 8 neighbouring
                                  points, so that the 32 lanes of a warp take one 4 x 8 patch
-                                 and their gathers share more memory sectors (86.0 -> 84.1
-                                 ms for 1M particles x 64 rings x 1,024 points). Applied when
-                                 R divides N, R is a multiple of 4 and N / R of 8, else the
-                                 order given. Sets the order points are summed in, like
-                                 points_per_chunk; < 0 is EINVAL */
+                                 and their gathers share more DRAM sectors. It pays where
+                                 the particles are spread over the map (global
+                                 localisation, DRAM-bound: 86.0 -> 84.1 ms for 1M uniform
+                                 particles x 64 rings x 1,024 points) and costs where they
+                                 have converged (tracking, served from L1 and L2: the
+                                 patch spans more cache lines than a run along one ring;
+                                 +4 % on int16 bricks, up to 1.9x on a dense FP16 map).
+                                 Applied when R divides N, R is a multiple of 4 and N / R
+                                 of 8, else the order given. Sets the order points are
+                                 summed in, like points_per_chunk; < 0 is EINVAL */
 } mcl_sensor_params;
 
 /* Sensor update of P particles (device, P x 6 FP32) against one scan
