@@ -1108,7 +1108,8 @@ def run_variants(args):
     the read and the score: nearest-voxel LOGPROD (the headline), SUM on the
     TSDF (exp per evaluation), SUM on an FP16 score map (the exponential
     precomputed per voxel), and the trilinear read (eight corner values per
-    evaluation, one brick-index probe per distinct brick)."""
+    evaluation, one brick-index probe per distinct brick); the scan staged as
+    the headline stages it (`--scan-rings`)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -1133,7 +1134,7 @@ def run_variants(args):
                 ("nearest_sum_score_f16", sc, mcl.MCL_SUM, 0, 1),
                 ("trilinear_logprod", m, mcl.MCL_LOGPROD, mcl.MCL_TRILINEAR, 8))
     for name, mm, mode, flags, corners in variants:
-        prm = mcl.sensor_params(wl.sigma_hit, mode=mode, flags=flags)
+        prm = mcl.sensor_params(wl.sigma_hit, mode=mode, flags=flags, scan_rings=args.scan_rings)
         for _ in range(max(args.warmup, 3)):
             mcl.mcl_sensor_update(mm, parts, scan, prm, logw, w)
         torch.cuda.synchronize()
@@ -1159,6 +1160,8 @@ def run_variants(args):
             "config": {"workload": config_dict(args, wl)["workload"],
                        "bytes_per_eval": "corner values x element bytes + one brick-index entry "
                                          "(4 B cell grid, 8 B hash)",
+                       "scan": f"staged in 4 x 8 patches (scan_rings {args.scan_rings})"
+                               if args.scan_rings else "points as given",
                        "score_map_build_s": score_build_s},
             "results": out}
     print(json.dumps(line), flush=True)
