@@ -208,7 +208,7 @@ enum { MCL_LOGPROD = 0, MCL_SUM = 1 };
  * (points of one particle are split in chunks of points_per_chunk, each
  * summed by lanes_per_particle lanes and a shuffle tree, chunks added in
  * order); 0 selects the defaults 2048 and 32. Results are bit-reproducible
- * for equal (points_per_chunk, lanes_per_particle). */
+ * for equal (points_per_chunk, lanes_per_particle, scan_rings). */
 typedef struct mcl_sensor_params {
   uint32_t struct_size;       /* sizeof(mcl_sensor_params) */
   float sigma_hit;            /* sigma of Eq. 3 (m), > 0 */
@@ -335,7 +335,8 @@ mcl_status mcl_pose_to_matrix(const float* particles, int64_t P, float* out_mat,
 
 /* Launch plan the sensor update would use for these sizes on the current
  * device (no work is enqueued). workspace_bytes is the scratch the call
- * needs; points_per_chunk * lanes_per_particle fix the summation order. */
+ * needs; points_per_chunk, lanes_per_particle and scan_rings fix the
+ * summation order. */
 typedef struct mcl_sensor_plan {
   uint32_t struct_size;
   int32_t points_per_chunk, lanes_per_particle, particles_per_item, unroll, pipeline;
@@ -360,7 +361,8 @@ mcl_status mcl_sensor_plan_get(mcl_map_t map, int64_t P, int64_t N,
  * {32, 16} (those two fix the FP32 summation order: keep a tuned pair fixed
  * for a session). The winner is appended to the JSON-lines cache at
  * cache_path (NULL: $MCL_TUNE_CACHE) when use_cache = 1, keyed by GPU name,
- * map kind, layout, storage type, score mode and the power-of-two buckets of P
+ * map kind, layout, storage type, score mode (a score map's own), flags,
+ * whether base's scan_rings applies to N, and the power-of-two buckets of P
  * and N; a later call with the same key returns it without timing. Synchronous:
  * returns after timing. Allocates a scratch buffer of max_particles floats. */
 typedef struct mcl_tune_params {

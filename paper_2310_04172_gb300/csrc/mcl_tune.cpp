@@ -34,12 +34,16 @@ int log2_bucket(int64_t v) {
   return b;
 }
 
-std::string tune_key(const mcl_map_s* m, int mode, int64_t P, int64_t N, bool summation) {
+// Cache key: GPU, kernel kind, brick layout, storage type, kernel mode (the
+// score map's own), read and neglect flags, whether the scan is staged in
+// patches, and the power-of-two buckets of P and N.
+std::string tune_key(const mcl_map_s* m, const mcl_sensor_params* p, int64_t P, int64_t N, bool summation) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, m->device);
-  char buf[256];
-  snprintf(buf, sizeof buf, "%s|k%d|l%d|d%d|m%d|P%d|N%d|s%d", prop.name, kernel_kind(m), m->view.layout,
-           m->dtype, mode, log2_bucket(P), log2_bucket(N), summation ? 1 : 0);
+  char buf[320];
+  snprintf(buf, sizeof buf, "%s|k%d|l%d|d%d|m%d|f%u|r%d|P%d|N%d|s%d", prop.name, kernel_kind(m),
+           m->view.layout, m->dtype, kernel_mode(m, p->mode), (unsigned)p->flags,
+           patch_rings(N, p->scan_rings) ? 1 : 0, log2_bucket(P), log2_bucket(N), summation ? 1 : 0);
   std::string s(buf);
   for (char& c : s)
     if (c == '"' || c == ' ') c = '_';
@@ -113,7 +117,7 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
   const bool summation = tp->tune_summation != 0;
   const char* path = tp->cache_path ? tp->cache_path : getenv("MCL_TUNE_CACHE");
   if (!tp->use_cache) path = nullptr;
-  const std::string key = tune_key(m, base->mode, P, N, summation);
+  const std::string key = tune_key(m, base, P, N, summation);
 
   Knobs best{base->points_per_chunk ? base->points_per_chunk : 2048,
              base->lanes_per_particle ? base->lanes_per_particle : 32,

@@ -1,5 +1,6 @@
 """Autotuner: times launch shapes on the caller's data, caches the winner per
-(GPU, map, storage type, mode, size buckets), and its shapes keep parity."""
+(GPU, map, storage type, mode, flags, scan staging, size buckets), and its
+shapes keep parity."""
 import numpy as np
 import pytest
 
@@ -28,6 +29,11 @@ def test_autotune_picks_a_valid_faster_shape_and_caches_it(tmp_path):
     best2, info2 = mcl.mcl_autotune(m, parts, scan, base, max_particles=8192, cache_path=cache,
                                     tune_summation=True)
     assert info2["from_cache"] and info2["shape"] == info["shape"]
+    # another read (trilinear) or another scan staging is another key: timed, not served
+    for other in (mcl.sensor_params(0.1, flags=mcl.MCL_TRILINEAR), mcl.sensor_params(0.1, scan_rings=64)):
+        _, info3 = mcl.mcl_autotune(m, parts, scan, other, max_particles=4096, cache_path=cache)
+        assert not info3["from_cache"] and info3["candidates"] >= 1
+    assert open(cache).read().count('"key"') == 3
     # the tuned shape is a valid shape with parity against the oracle
     P = 2000
     logw = torch.empty(P, device="cuda")
