@@ -355,11 +355,12 @@ mcl_status mcl_sensor_plan_get(mcl_map_t map, int64_t P, int64_t N,
 
 /* Autotuner of the launch shape (the paper has none; the shape is a GB300
  * choice). Times candidates with CUDA events on the caller's particles (the
- * first max_particles of them) and scan, by coordinate descent over particles
- * per item, unroll, pipeline and particle order, and with tune_summation = 1
- * also over points_per_chunk in {1024, 2048, 4096} and lanes_per_particle in
- * {32, 16} (those two fix the FP32 summation order: keep a tuned pair fixed
- * for a session). The winner is appended to the JSON-lines cache at
+ * first max_particles of them) and scan, by coordinate descent from base's
+ * shape (0 fields: the library's defaults) over particles per item, unroll,
+ * pipeline, particle order and item order, and with tune_summation = 1 also
+ * over points_per_chunk in {1024, 2048, 4096} and lanes_per_particle in
+ * {32, 16} (32 only for MCL_TRILINEAR; those two fix the FP32 summation
+ * order: keep a tuned pair fixed for a session). The winner is appended to the JSON-lines cache at
  * cache_path (NULL: $MCL_TUNE_CACHE) when use_cache = 1, keyed by GPU name,
  * map kind, layout, storage type, score mode (a score map's own), flags,
  * whether base's scan_rings applies to N, and the power-of-two buckets of P

@@ -119,11 +119,9 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
   if (!tp->use_cache) path = nullptr;
   const std::string key = tune_key(m, base, P, N, summation);
 
-  Knobs best{base->points_per_chunk ? base->points_per_chunk : 2048,
-             base->lanes_per_particle ? base->lanes_per_particle : 32,
-             base->particles_per_item, base->unroll ? base->unroll : 4,
-             base->pipeline ? base->pipeline : 1, base->particle_order ? base->particle_order : 2,
-             base->item_order};
+  // the base shape as given (a 0 keeps the library's default for that field)
+  Knobs best{base->points_per_chunk, base->lanes_per_particle, base->particles_per_item, base->unroll,
+             base->pipeline,         base->particle_order,     base->item_order};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     double ms = 0;
@@ -174,7 +172,11 @@ mcl_status mcl_autotune(mcl_map_t m, const float* particles, int64_t P, const fl
         if (rc != MCL_OK || best.*field == v) continue;
         Knobs k = best;
         k.*field = v;
-        if (k.lanes < 32 && (k.unroll != 4 || k.pipeline == 2)) continue;  // not instantiated
+        const int g = k.lanes ? k.lanes : 32;
+        if ((base->flags & MCL_TRILINEAR) && g != 32) continue;  // the trilinear read takes 32 lanes
+        // narrower lane groups run the plain 4-deep loop: other unrolls and
+        // pipelining would time the same kernel again
+        if (g < 32 && ((k.unroll != 0 && k.unroll != 4) || k.pipeline == 2)) continue;
         if (k.unroll == 8 && k.pipeline == 2) continue;
         double t = 0;
         rc = time_knobs(k, &t);

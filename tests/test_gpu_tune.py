@@ -30,9 +30,14 @@ def test_autotune_picks_a_valid_faster_shape_and_caches_it(tmp_path):
                                     tune_summation=True)
     assert info2["from_cache"] and info2["shape"] == info["shape"]
     # another read (trilinear) or another scan staging is another key: timed, not served
+    # (the trilinear read keeps 32 lanes while the summation is tuned)
     for other in (mcl.sensor_params(0.1, flags=mcl.MCL_TRILINEAR), mcl.sensor_params(0.1, scan_rings=64)):
-        _, info3 = mcl.mcl_autotune(m, parts, scan, other, max_particles=4096, cache_path=cache)
+        b3, info3 = mcl.mcl_autotune(m, parts, scan, other, max_particles=4096, cache_path=cache,
+                                     tune_summation=True)
         assert not info3["from_cache"] and info3["candidates"] >= 1
+        assert b3.flags == other.flags and b3.scan_rings == other.scan_rings
+        if other.flags:
+            assert b3.lanes_per_particle in (0, 32)
     assert open(cache).read().count('"key"') == 3
     # the tuned shape is a valid shape with parity against the oracle
     P = 2000
