@@ -62,13 +62,17 @@ def parse_args(argv=None):
                     help="the trilinear read (eight corners per evaluation) instead of the nearest voxel")
     ap.add_argument("--index", type=int, default=0, help="brick index: 0 auto, 1 hash, 2 cell grid")
     ap.add_argument("--mode", default="headline",
-                    choices=["headline", "serving", "precision", "vlp16", "filter", "variants", "trilinear"],
+                    choices=["headline", "serving", "precision", "vlp16", "filter", "variants", "trilinear",
+                             "batch"],
                     help="headline: 1M x 65,536 int16 step (+ serving probe); serving: 64 sessions over "
                          "8 maps; precision: f32/f16/i16 sweep with oracle weight error; vlp16: plain vs "
                          "batched graph-captured form on the VLP-16 tracking workload; filter: whole "
                          "filter steps (motion, sensor, estimate, resampling) as separate calls, as one "
                          "call and replayed from a CUDA graph; variants (or trilinear): the 1M x 65,536 "
-                         "step with SUM on the TSDF, SUM on an FP16 score map and the trilinear read")
+                         "step with SUM on the TSDF, SUM on an FP16 score map and the trilinear read; "
+                         "batch: the 1M x 65,536 update as one session and as a graph-captured batch of "
+                         "--sessions sessions on the same map")
+    ap.add_argument("--sessions", type=int, default=4, help="--mode batch: sessions of P / S particles")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run of the headline")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the weight-error report and the storage/form comparison of the headline")
@@ -1170,6 +1174,71 @@ def run_variants(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched sessions on one map
+def run_batch(args):
+    """The headline update (int16 bricks, 1M uniform particles x 65,536
+    points) as one sensor update and as a graph-captured batch of `--sessions`
+    sessions of P / S particles on the same map (one persistent sensor launch,
+    the sessions' work items interleaved sweep by sweep), each given the
+    scan's ring count like the headline: milliseconds per update, evaluations
+    per second and the kernels of a batched run."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_04172_gb300 import mcl
+    torch.cuda.set_device(0)
+    wl = make_workload(args, 0)
+    m = mcl.map_from_scene(wl.map)
+    parts = torch.from_numpy(wl.particles).cuda()
+    scan = torch.from_numpy(np.ascontiguousarray(wl.scan)).cuda()
+    P, N = parts.shape[0], scan.shape[0]
+    S = max(1, args.sessions)
+    per = P // S
+    prm = mcl.sensor_params(wl.sigma_hit, scan_rings=args.scan_rings)
+    logw, w = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
+    sessions = [{"map": m, "particles": parts[k * per:(k + 1) * per].contiguous(), "scan": scan,
+                 "sigma_hit": wl.sigma_hit, "scan_rings": args.scan_rings,
+                 "logw": torch.empty(per, device="cuda"), "w": torch.empty(per, device="cuda")}
+                for k in range(S)]
+    batch = mcl.Batch(sessions, use_graph=True)
+    reps = max(1, args.steps)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        e.synchronize()
+        return a.elapsed_time(e) / reps
+
+    ms_single = timed(lambda: mcl.mcl_sensor_update(m, parts, scan, prm, logw, w))
+    ms_batch = timed(batch.run)
+    info = batch.info()
+    batch.close()
+    m.close()
+    ev_batch = float(S * per) * N
+    line = {"mode": "batch", "metric": "particle×point evals/s (1M×65,536, int16 TSDF, batched sessions)",
+            "value": ev_batch / (ms_batch / 1e3), "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32", "steps": reps,
+            "config": {"workload": config_dict(args, wl)["workload"], "sessions": S,
+                       "particles_per_session": per,
+                       "scan": f"staged in 4 x 8 patches (scan_rings {args.scan_rings})"
+                               if args.scan_rings else "points as given"},
+            "results": {"single": {"particles": P, "ms_per_update": ms_single,
+                                   "evals_per_s": float(P) * N / (ms_single / 1e3)},
+                        "batched_graph": {"sessions": S, "ms_per_update": ms_batch,
+                                          "evals_per_s": ev_batch / (ms_batch / 1e3),
+                                          "groups": info["n_groups"], "items": info["n_items"],
+                                          "kernels_per_run": info["kernels_per_run"]}}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -1184,6 +1253,8 @@ def main(argv=None):
         return run_filter(args)
     if args.mode in ("variants", "trilinear"):
         return run_variants(args)
+    if args.mode == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 
