@@ -81,6 +81,8 @@ def parse_args(argv=None):
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     ap.add_argument("--serving-batch", type=int, default=0,
                     help="sessions per batched serving step (0: the default policy)")
+    ap.add_argument("--serving-scan-rings", action="store_true",
+                    help="serving sessions given their scans' ring counts (4 x 8 patch staging)")
     ap.add_argument("--filter-workloads", default="room,hall",
                     help="--mode filter: comma list of room, hall")
     return ap.parse_args(argv)
@@ -493,7 +495,7 @@ def run_ours(args):
     serving = None
     if rank == 0 and not args.no_serving:
         try:
-            serving = serving_block(mcl, args.serving_seconds)
+            serving = serving_block(mcl, args.serving_seconds, rings=args.serving_scan_rings)
         except Exception as e:
             serving = {"error": f"{type(e).__name__}: {e}"}
 
@@ -885,7 +887,7 @@ def run_serving(args):
     __graft_entry__.build()
     from paper_2310_04172_gb300 import mcl
     torch.cuda.set_device(0)
-    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch)
+    out = serving_block(mcl, args.serving_seconds * 2, args.serving_batch, rings=args.serving_scan_rings)
     line = {"mode": "serving", "metric": "serving p50/p99 update latency (64 sessions, 8 maps)",
             "value": out["scaled_load_70pct"]["p99_ms"], "unit": "ms (p99)", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32",
