@@ -19,7 +19,7 @@
  *   weights summed for normalisation                          Sec. V-A
  *   resampling draws a new set in proportion to the weights   Sec. III
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *   - (phi, psi, theta) = (roll, pitch, yaw), R = Rz(yaw) Ry(pitch) Rx(roll).
  *   - per-point scores combine as a product of p_hit (sum of log p_hit, the
  *     normalising constant dropped: mode LOGPROD) or as a plain sum of p_hit
