@@ -63,3 +63,17 @@ def test_single_rank_helpers_are_identity():
     assert bench.max_over_ranks(None, 5.0) == 5.0 and bench.sum_over_ranks(None, 7.0) == 7.0
     args = bench.parse_args([])
     assert args.gpus == 1 and args.steps >= 1 and args.warmup >= 3
+
+
+def test_traffic_record_is_used_only_for_its_kernel_source(monkeypatch):
+    """roofline.traffic comes from the committed one-pass ncu record only while
+    the sensor kernel's sources hash to the digest stored with the counters
+    (scaled by the launch's evaluations); for any other source it is None."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "sensor_dram_traffic.json")))
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda: rec["kernel_digest"])
+    assert bench.measured_traffic(1000, 2048) == rec["dram_bytes_per_eval"] * 1000 * 2048
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda: "not-" + rec["kernel_digest"])
+    assert bench.measured_traffic(1000, 2048) is None
