@@ -240,8 +240,9 @@ def kernel_source_digest() -> str:
 
 
 def measured_traffic(P: int, N: int):
-    """DRAM bytes per sensor launch from the committed ncu summary, scaled by
-    evaluations, if it was taken on the current kernel source; else None."""
+    """DRAM bytes (read + write) per sensor launch from the committed ncu
+    summary, scaled by evaluations, if it was taken on the current kernel
+    source; else None."""
     path = os.path.join(ROOT, "profiles", "sensor_dram_traffic.json")
     try:
         rec = json.load(open(path))
@@ -249,7 +250,8 @@ def measured_traffic(P: int, N: int):
         return None
     if rec.get("kernel_digest") != kernel_source_digest():
         return None
-    return rec["dram_bytes_per_eval"] * P * N
+    per_eval = (rec["dram_bytes_read"] + rec.get("dram_bytes_write", 0.0)) / rec["evals"]
+    return per_eval * P * N
 
 
 def gather_source_digest() -> str:

@@ -67,13 +67,16 @@ def test_single_rank_helpers_are_identity():
 
 def test_traffic_record_is_used_only_for_its_kernel_source(monkeypatch):
     """roofline.traffic comes from the committed one-pass ncu record only while
-    the sensor kernel's sources hash to the digest stored with the counters
-    (scaled by the launch's evaluations); for any other source it is None."""
+    the sensor kernel's sources hash to the digest stored with the counters:
+    its DRAM bytes read and written, scaled by the launch's evaluations; for
+    any other source it is None."""
     import json
     sys.path.insert(0, ROOT)
     import bench
     rec = json.load(open(os.path.join(ROOT, "profiles", "sensor_dram_traffic.json")))
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: rec["kernel_digest"])
-    assert bench.measured_traffic(1000, 2048) == rec["dram_bytes_per_eval"] * 1000 * 2048
+    per_eval = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["evals"]
+    assert bench.measured_traffic(1000, 2048) == per_eval * 1000 * 2048
+    assert abs(bench.measured_traffic(1_000_000, 65536) - (rec["dram_bytes_read"] + rec["dram_bytes_write"])) < 1.0
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "not-" + rec["kernel_digest"])
     assert bench.measured_traffic(1000, 2048) is None
